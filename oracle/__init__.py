@@ -1,0 +1,281 @@
+"""FP64 CPU oracle for the star stencil and the acoustic leapfrog step.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's ``cpu_baseline`` / ``--impl reference`` legs may import this
+package.  The library's product path never loads it, and it never imports the
+library: the two share no code (only the seeded inputs of ``workloads``).
+
+What each function follows (arXiv 2309.04671):
+
+* :func:`fd2_weights` -- the discretisation parameters c_m of Eq. 3 for the
+  centred second derivative of order 2R, defined as the unique weights that
+  differentiate every polynomial of degree <= 2R+1 exactly (moment
+  conditions), solved in exact rational arithmetic.  The paper names the
+  c_m but leaves their values to the user; the 25-point instance uses R = 4.
+* :func:`stencil_apply` -- Eq. 3 (Sec. 2.2) at every interior point, halo read
+  as given (C, ``oracle.c``).
+* :func:`wave_step` / :func:`wave_propagate` -- Eq. 2 and Algorithm 1 with a
+  zero (Dirichlet) halo; the source enters as dt^2 V^2 f^n after the stencil
+  update (C, ``oracle.c``).
+* :func:`err_norms` -- the paper's accuracy metrics (Sec. 11.1: maximum
+  absolute error and RMSD against a reference), plus the normwise relative
+  maximum and L2 errors.
+
+Pins (tests/test_oracle_*.py): moment conditions and a published table of the
+weights, polynomial exactness, the plane-wave symbol, operator symmetry, a
+Kronecker-sum brute force, the stencil footprint against the paper's Table 4,
+discrete energy conservation, time reversal and special cases of the step.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from fractions import Fraction
+from functools import lru_cache
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_i64 = ctypes.c_longlong
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_ip = ctypes.POINTER(ctypes.c_longlong)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, OpenMP, strict IEEE double)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+               _SRC, "-o", tmp]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            lib.oracle_stencil_apply.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, ctypes.c_int, _dp, _dp, _dp]
+            lib.oracle_stencil_apply.restype = None
+            lib.oracle_stencil_points_f32.argtypes = [_fp, _i64, _i64, _i64, _i64, ctypes.c_int, _dp, _dp, _dp,
+                                                      _i64, _ip, _dp]
+            lib.oracle_stencil_points_f32.restype = None
+            lib.oracle_wave_step.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                             _i64, _i64, _i64, _i64, ctypes.c_int, _dp,
+                                             _i64, _ip, _dp, _i64, _ip, _dp]
+            lib.oracle_wave_step.restype = None
+            lib.oracle_wave_points_f32.argtypes = [_fp, _fp, _fp, ctypes.c_double, ctypes.c_double,
+                                                   _i64, _i64, _i64, _i64, ctypes.c_int, _dp, _i64, _ip, _dp]
+            lib.oracle_wave_points_f32.restype = None
+            lib.oracle_wave_propagate.argtypes = [_dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                                  _i64, _i64, _i64, _i64, ctypes.c_int, _dp, _i64, _i64,
+                                                  _i64, _ip, _dp, _i64, _i64, _ip, _dp, _i64]
+            lib.oracle_wave_propagate.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def _f(a):
+    return a.ctypes.data_as(_fp) if a is not None else None
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip) if a is not None else None
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dims(a: np.ndarray, halo: int):
+    nz, ny, nx = (s - 2 * halo for s in a.shape)
+    if min(nx, ny, nz) < 0:
+        raise ValueError("halo larger than the array")
+    return nx, ny, nz
+
+
+# ---------------------------------------------------------------------------
+# Eq. 3 parameters: centred second-derivative weights of order 2R
+# ---------------------------------------------------------------------------
+@lru_cache(maxsize=None)
+def fd2_weights(R: int) -> tuple[Fraction, ...]:
+    """Exact weights (c_0, c_1, ..., c_R) with c_{-m} = c_m.
+
+    Definition: the symmetric stencil sum_{m=-R..R} c_|m| f(m) must equal
+    f''(0) for every polynomial f of degree <= 2R+1.  Odd powers cancel by
+    symmetry; the even powers x^{2j}, j = 0..R, give R+1 linear equations
+        j = 0:  c_0 + 2 sum_m c_m = 0
+        j >= 1: 2 sum_m m^{2j} c_m = (2j)! [j == 1]
+    solved here by Gauss-Jordan elimination over the rationals.
+    """
+    if not 1 <= R <= 8:
+        raise ValueError("radius must be in 1..8")
+    n = R + 1
+    A = [[Fraction(0)] * (n + 1) for _ in range(n)]
+    for j in range(n):
+        if j == 0:
+            A[0][0] = Fraction(1)
+            for m in range(1, n):
+                A[0][m] = Fraction(2)
+        else:
+            A[j][0] = Fraction(0)
+            for m in range(1, n):
+                A[j][m] = Fraction(2 * m ** (2 * j))
+        A[j][n] = Fraction(2) if j == 1 else Fraction(0)   # (2j)! * [j == 1] = 2
+    for col in range(n):
+        piv = next(r for r in range(col, n) if A[r][col] != 0)
+        A[col], A[piv] = A[piv], A[col]
+        pv = A[col][col]
+        A[col] = [x / pv for x in A[col]]
+        for r in range(n):
+            if r != col and A[r][col] != 0:
+                fac = A[r][col]
+                A[r] = [x - fac * y for x, y in zip(A[r], A[col])]
+    return tuple(A[r][n] for r in range(n))
+
+
+def fd2_coeffs(R: int) -> np.ndarray:
+    """float64 (c_0..c_R) of :func:`fd2_weights`."""
+    return np.array([float(w) for w in fd2_weights(R)], dtype=np.float64)
+
+
+def axis_coeffs(R: int, h: float) -> np.ndarray:
+    """Per-axis weights c_m / h^2 of Eq. 3 for grid spacing h."""
+    return fd2_coeffs(R) / (h * h)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 3: stencil_apply
+# ---------------------------------------------------------------------------
+def stencil_apply(inp: np.ndarray, radius: int, cx, cy, cz, halo: int,
+                  out: np.ndarray | None = None) -> np.ndarray:
+    """out = L inp on the interior (FP64); the halo of ``out`` is left as given
+    (zeros when ``out`` is None).  ``cx/cy/cz`` hold (c_a0, c_a1, ..., c_aR)."""
+    if not 1 <= radius <= 4 or radius > halo:
+        raise ValueError("need 1 <= radius <= 4 and radius <= halo")
+    x = _f64(inp)
+    nx, ny, nz = _dims(x, halo)
+    o = np.zeros_like(x) if out is None else out
+    if o.dtype != np.float64 or not o.flags.c_contiguous or o.shape != x.shape:
+        raise ValueError("out must be a C-contiguous float64 array shaped like inp")
+    c = [_f64(np.asarray(v)[: radius + 1]) for v in (cx, cy, cz)]
+    if any(v.size != radius + 1 for v in c):
+        raise ValueError("each coefficient array needs radius+1 entries")
+    _load().oracle_stencil_apply(_d(x), _d(o), nx, ny, nz, halo, radius, _d(c[0]), _d(c[1]), _d(c[2]))
+    return o
+
+
+def stencil_points(inp_f32: np.ndarray, radius: int, cx, cy, cz, halo: int,
+                   idx: np.ndarray) -> np.ndarray:
+    """Eq. 3 at the interior linear indices ``idx`` of an FP32 field, in FP64."""
+    x = np.ascontiguousarray(inp_f32, dtype=np.float32)
+    nx, ny, nz = _dims(x, halo)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    c = [_f64(np.asarray(v)[: radius + 1]) for v in (cx, cy, cz)]
+    out = np.empty(idx.size, np.float64)
+    _load().oracle_stencil_points_f32(_f(x), nx, ny, nz, halo, radius, _d(c[0]), _d(c[1]), _d(c[2]),
+                                      idx.size, _i(idx), _d(out))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Eq. 2 / Algorithm 1: the leapfrog step and the time loop
+# ---------------------------------------------------------------------------
+def wave_step(u_prev, u, vel, dt: float, h: float, halo: int, *, radius: int = 4, coeffs=None,
+              src_idx=None, src_f=None, rec_idx=None):
+    """One step of Eq. 2; returns (u_next, rec_values)."""
+    up, uc, v = _f64(u_prev), _f64(u), _f64(vel)
+    nx, ny, nz = _dims(uc, halo)
+    c = fd2_coeffs(radius) if coeffs is None else _f64(coeffs)
+    nxt = up.copy()
+    si = np.zeros(0, np.int64) if src_idx is None else np.ascontiguousarray(src_idx, np.int64)
+    sf = np.zeros(si.size, np.float64) if src_f is None else _f64(np.asarray(src_f).reshape(-1))
+    ri = np.zeros(0, np.int64) if rec_idx is None else np.ascontiguousarray(rec_idx, np.int64)
+    ro = np.zeros(max(ri.size, 1), np.float64)
+    _load().oracle_wave_step(_d(up), _d(uc), _d(nxt), _d(v), dt, h, nx, ny, nz, halo, radius, _d(c),
+                             si.size, _i(si), _d(sf), ri.size, _i(ri), _d(ro))
+    return nxt, ro[: ri.size]
+
+
+def wave_points(u_prev_f32, u_f32, vel_f32, dt: float, h: float, halo: int, idx, *, radius: int = 4,
+                coeffs=None) -> np.ndarray:
+    """The update of Eq. 2 (no source) at interior linear indices ``idx`` of FP32 fields."""
+    up = np.ascontiguousarray(u_prev_f32, np.float32)
+    uc = np.ascontiguousarray(u_f32, np.float32)
+    v = np.ascontiguousarray(vel_f32, np.float32)
+    nx, ny, nz = _dims(uc, halo)
+    c = fd2_coeffs(radius) if coeffs is None else _f64(coeffs)
+    idx = np.ascontiguousarray(idx, np.int64)
+    out = np.empty(idx.size, np.float64)
+    _load().oracle_wave_points_f32(_f(up), _f(uc), _f(v), dt, h, nx, ny, nz, halo, radius, _d(c),
+                                   idx.size, _i(idx), _d(out))
+    return out
+
+
+def wave_propagate(u_prev, u, vel, dt: float, h: float, halo: int, nsteps: int, *, t0: int = 0,
+                   radius: int = 4, coeffs=None, src_idx=None, src_amp=None, rec_idx=None,
+                   rec_nt: int | None = None):
+    """Algorithm 1 for ``nsteps`` steps from time index ``t0``.
+
+    ``src_amp`` is (nt, nsrc): row n is f^n.  Returns (u_prev, u, trace) with
+    (u_prev, u) = (u^{t0+nsteps-1}, u^{t0+nsteps}) and trace (rec_nt, nrec),
+    row n = u^{n+1} at the receivers (rows outside [t0, t0+nsteps) are zero).
+    """
+    up, uc, v = _f64(u_prev).copy(), _f64(u).copy(), _f64(vel)
+    nx, ny, nz = _dims(uc, halo)
+    c = fd2_coeffs(radius) if coeffs is None else _f64(coeffs)
+    si = np.zeros(0, np.int64) if src_idx is None else np.ascontiguousarray(src_idx, np.int64).reshape(-1)
+    if src_amp is None:
+        sa = np.zeros((0, si.size), np.float64)
+    else:
+        sa = _f64(np.asarray(src_amp).reshape(-1, si.size))
+    ri = np.zeros(0, np.int64) if rec_idx is None else np.ascontiguousarray(rec_idx, np.int64).reshape(-1)
+    rnt = (t0 + nsteps) if rec_nt is None else rec_nt
+    tr = np.zeros((rnt, ri.size), np.float64)
+    rc = _load().oracle_wave_propagate(_d(up), _d(uc), _d(v), dt, h, nx, ny, nz, halo, radius, _d(c),
+                                       nsteps, t0, si.size, _i(si), _d(sa) if sa.size else None,
+                                       sa.shape[0], ri.size, _i(ri), _d(tr) if tr.size else None, rnt)
+    if rc != 0:
+        raise MemoryError("oracle_wave_propagate could not allocate its work buffers")
+    return up, uc, tr
+
+
+# ---------------------------------------------------------------------------
+# Sec. 11.1 accuracy metrics
+# ---------------------------------------------------------------------------
+def err_norms(x, ref) -> dict:
+    """Errors of ``x`` against ``ref`` (same shape), computed in FP64.
+
+    max_abs and rmsd are the paper's metrics; norm_max_rel = max|x-ref| / max|ref|
+    and l2_rel = ||x-ref||_2 / ||ref||_2 are scale-free versions.
+    """
+    a = np.asarray(x, dtype=np.float64)
+    b = np.asarray(ref, dtype=np.float64)
+    d = a - b
+    max_abs = float(np.max(np.abs(d))) if d.size else 0.0
+    ref_max = float(np.max(np.abs(b))) if b.size else 0.0
+    l2 = float(np.sqrt(np.sum(d * d)))
+    l2_ref = float(np.sqrt(np.sum(b * b)))
+    return {
+        "max_abs": max_abs,
+        "rmsd": float(np.sqrt(np.mean(d * d))) if d.size else 0.0,
+        "norm_max_rel": max_abs / ref_max if ref_max > 0 else (0.0 if max_abs == 0 else float("inf")),
+        "l2_rel": l2 / l2_ref if l2_ref > 0 else (0.0 if l2 == 0 else float("inf")),
+        "ref_max": ref_max,
+        "finite": bool(np.all(np.isfinite(a))),
+    }
