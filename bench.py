@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Throughput of the 25-point acoustic leapfrog on one GB300.
+
+Workload (default): wave_propagate on a 512^3 interior (halo 4), FP32,
+radius-4 8th-order star Laplacian, layered velocity 1500-4500 m/s with 16
+seeded Gaussian perturbations, h = 10 m, dt at CFL 0.4, 15 Hz Ricker source
+at depth 20.  One benchmark "step" = one wave_propagate call of 100 leapfrog
+steps (Algorithm 1) over the whole grid.  Fields (3 x 562 MB) are larger
+than L2, so no flush is needed between steps.
+
+Prints ONE JSON line (rank 0) with Gpoint-updates/s for the whole job, the
+roofline of the dominant kernel (HBM bound, 16 algorithmic bytes per point
+update), an end-to-end number through host buffers, the FP64 oracle timed on
+the host cores, SM clocks sampled during the timed region, and the number of
+kernel launches.  --impl reference times the FP64 oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Gpoint-updates/s & % HBM roofline, 25-pt 512^3; BF16/batched vs plain FP32"
+UNIT = "Gpoint-updates/s"
+BYTES_PER_POINT = 16          # read u, u_prev, vel; write u_next (FP32)
+FALLBACK_HBM_GBS = 6800.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_tma_wave_512_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2309_04671_gb300", "csrc", f) for f in ("k_tma.cu", "gbs_internal.cuh")]
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=512, help="interior side")
+    ap.add_argument("--nsteps", type=int, default=100, help="leapfrog steps per benchmark step")
+    ap.add_argument("--tile-y", type=int, default=0)
+    ap.add_argument("--zchunk", type=int, default=0)
+    ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--graph", action="store_true", help="replay the step loop as a CUDA graph")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--ref-leapfrog", type=int, default=2, help="oracle leapfrog steps per reference step")
+    return ap.parse_args()
+
+
+def workload_desc(n, nsteps):
+    return (f"wave_propagate {n}^3 interior + halo 4, FP32, 25-pt radius-4 8th-order Laplacian, "
+            f"{nsteps} leapfrog steps per step, layered 1500-4500 m/s + 16 Gaussians, h=10 m, CFL 0.4, "
+            f"15 Hz Ricker at depth 20")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        self.windows = []
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def mark(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        lo = min(w[0] for w in self.windows) - 1.0 if self.windows else -1e18
+        hi = max(w[1] for w in self.windows) + 1.0 if self.windows else 1e18
+        sel = [r for r in rows if lo <= r[0] <= hi] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in sel for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": max(r[2] for r in sel),
+                "reasons": reasons, "samples": len(sel)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(n):
+    """DRAM bytes per launch from the committed ncu summary, if it matches
+    the current kernel source and workload size."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_sha") != kernel_sha() or int(t.get("n", -1)) != n:
+        return None
+    return float(t["dram_bytes_per_launch"])
+
+
+def dist_init(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(prob, target_s):
+    """FP64 oracle (C, OpenMP over z) on the host cores: leapfrog steps of the
+    same grid, timed; returns (Gpt/s, steps, seconds, threads)."""
+    import oracle
+    oracle.build()
+    n, halo = prob.nx, prob.halo
+    z = np.zeros(W_padded(prob), np.float64)
+    vel = prob.vel.astype(np.float64)
+    t0 = time.perf_counter()
+    a, b, _ = oracle.wave_propagate(z, z, vel, prob.dt, prob.h, halo, 1,
+                                    src_idx=prob.src_idx, src_amp=prob.src_amp)
+    one = time.perf_counter() - t0
+    steps = max(1, min(50, int(target_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.wave_propagate(a, b, vel, prob.dt, prob.h, halo, steps, t0=1,
+                          src_idx=prob.src_idx, src_amp=prob.src_amp)
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return prob.npoints * steps / dt / 1e9, steps, dt, threads
+
+
+def W_padded(prob):
+    import workloads as W
+    return W.padded_shape(prob.nx, prob.ny, prob.nz, prob.halo)
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    oracle.build()
+    prob = W.layered_problem(n=args.n, nsteps=args.nsteps)
+    z = np.zeros(W_padded(prob), np.float64)
+    vel = prob.vel.astype(np.float64)
+    a, b = z, z.copy()
+    t = 0
+    per = max(1, args.ref_leapfrog)
+    for _ in range(max(0, args.warmup)):
+        a, b, _ = oracle.wave_propagate(a, b, vel, prob.dt, prob.h, prob.halo, per, t0=t,
+                                        src_idx=prob.src_idx, src_amp=prob.src_amp)
+        t += per
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        a, b, _ = oracle.wave_propagate(a, b, vel, prob.dt, prob.h, prob.halo, per, t0=t,
+                                        src_idx=prob.src_idx, src_amp=prob.src_amp)
+        t += per
+    el = time.perf_counter() - t0
+    value = prob.npoints * per * args.steps / el / 1e9
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(args.n, args.nsteps),
+                   "reference_step": f"{per} FP64 leapfrog steps of the full grid per step (bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} x {per} FP64 leapfrog steps of the {args.n}^3 grid"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    import paper_2309_04671_gb300 as gbs
+    import workloads as W
+
+    world, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gbs.load()
+
+    prob = W.layered_problem(n=args.n, nsteps=args.nsteps)
+    n, halo, ns = prob.nx, prob.halo, prob.nsteps
+    shape = W_padded(prob)
+    a = torch.zeros(shape, device=dev)
+    b = torch.zeros(shape, device=dev)
+    vel = torch.from_numpy(prob.vel).to(dev)
+    si = torch.from_numpy(prob.src_idx).to(dev)
+    sa = torch.from_numpy(prob.src_amp).to(dev)
+    kw = dict(src_idx=si, src_amp=sa, kernel=args.kernel, tile_y=args.tile_y, zchunk=args.zchunk,
+              use_graph=args.graph)
+    stream = torch.cuda.current_stream()
+
+    # warm-up (also builds the wavefield)
+    for _ in range(max(3, args.warmup)):
+        a, b = gbs.wave_propagate(a, b, vel, prob.dt, prob.h, halo, ns, **kw)
+    gbs.device_status()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    gbs.profile_enable(True)
+    gbs.profile_take()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        a, b = gbs.wave_propagate(a, b, vel, prob.dt, prob.h, halo, ns, **kw)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.time()
+    barrier(world)
+    clocks.mark(w0, w1)
+    kernel_ms, kernel_launches = gbs.profile_take()
+    gbs.profile_enable(False)
+    gbs.device_status()
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    clk = clocks.stop()
+
+    points = prob.npoints * ns * args.steps * world
+    value = points / (elapsed_ms * 1e-3) / 1e9
+    hbm, peak_kind = peaks()
+    per_launch_ms = kernel_ms / max(1, kernel_launches)
+    alg_bytes = BYTES_PER_POINT * prob.npoints
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9 if kernel_launches else None
+    traffic = traffic_per_launch(n)
+    inject_launches = args.steps * min(ns, prob.src_amp.shape[0])
+
+    # end to end through host buffers (pinned), same call a user makes
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.zeros(shape, dtype=torch.float32).pin_memory()
+        hu = torch.zeros(shape, dtype=torch.float32).pin_memory()
+        hv = torch.from_numpy(prob.vel).pin_memory()
+        hsi, hsa = torch.from_numpy(prob.src_idx), torch.from_numpy(prob.src_amp)
+        e2e_steps = max(1, min(3, args.steps))
+        gbs.wave_propagate(hp, hu, hv, prob.dt, prob.h, halo, ns, src_idx=hsi, src_amp=hsa, kernel=args.kernel,
+                           tile_y=args.tile_y, zchunk=args.zchunk, use_graph=args.graph)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            gbs.wave_propagate(hp, hu, hv, prob.dt, prob.h, halo, ns, src_idx=hsi, src_amp=hsa,
+                               kernel=args.kernel, tile_y=args.tile_y, zchunk=args.zchunk, use_graph=args.graph)
+        el = max_over_ranks(time.perf_counter() - t0, world)
+        fb = prob.vel.nbytes
+        e2e = {"value": prob.npoints * ns * e2e_steps * world / el / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * fb + prob.src_idx.nbytes + prob.src_amp.nbytes,
+               "d2h_bytes_per_step": 2 * fb, "steps": e2e_steps}
+        del hp, hu, hv
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, steps, secs, threads = cpu_oracle_rate(prob, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{steps} FP64 leapfrog steps of the full {n}^3 grid ({secs:.1f} s), after 1 untimed step"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(n, ns), "grid": [n, n, n], "halo": halo,
+                       "leapfrog_steps_per_step": ns, "dt": prob.dt, "h": prob.h,
+                       "l2": "no flush: each of the 3 fields (562 MB) exceeds the 129 MB L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "kernel": "k_tma<R=4,wave>" if args.kernel != 2 else "k_generic<R=4,wave>",
+                       "tile_y": args.tile_y or 16, "zchunk": args.zchunk or "auto", "graph": args.graph},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                         "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                         "kernel_ms_per_launch": per_launch_ms, "kernel_launches": kernel_launches},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": kernel_launches + inject_launches,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * gbstencil -- high-order star stencil and acoustic leapfrog wave step on
+ * NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * The operations follow arXiv 2309.04671 ("StencilPy"), Sec. 2:
+ *   - Eq. 3: the (6R+1)-point star Laplacian of radius R (R = 4: the 3D
+ *     25-point, 8th-order stencil of the Acoustic ISO kernel)
+ *         out(i,j,k) = (cx0+cy0+cz0) in(i,j,k)
+ *                      + sum_{m=1..R} cxm [in(i+m,j,k) + in(i-m,j,k)]
+ *                                   + cym [in(i,j+m,k) + in(i,j-m,k)]
+ *                                   + czm [in(i,j,k+m) + in(i,j,k-m)]
+ *   - Eq. 2: the leapfrog step of the constant-density acoustic wave equation
+ *         u^{n+1} = 2 u^n - u^{n-1} + dt^2 V^2 lap(u^n) + dt^2 V^2 f^n
+ *   - Algorithm 1: the time loop over n, source added after the update.
+ *
+ * Grid layout (Sec. 10, GPU code generation: a flattened array with halo
+ * padding).  A field with interior nx*ny*nz and halo width `halo` is a dense
+ * float array of (nx+2*halo)*(ny+2*halo)*(nz+2*halo) elements, x fastest,
+ * z slowest; interior point (i,j,k) is element
+ *     (i+halo) + (nx+2*halo) * ((j+halo) + (ny+2*halo) * (k+halo)).
+ * The "interior linear index" of (i,j,k) is i + nx*(j + ny*k).
+ * Interiors are the half-open boxes [0,nx)x[0,ny)x[0,nz) (Sec. 10, "map").
+ *
+ * Conventions shared by every call:
+ *   - Pointers to fields, index lists and traces are DEVICE pointers owned
+ *     by the caller; the library never frees or keeps them.  Coefficient
+ *     arrays are HOST pointers, read before the call returns.
+ *   - Calls enqueue work on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and return without synchronising.  The return value reports
+ *     argument validation and launch errors only.  Faults found on the
+ *     device (a pipeline wait that ran out) set a device status word that
+ *     gbs_device_status() reads.
+ *   - The halo of an output is never written.
+ *   - Zero-sized interiors are valid and do nothing.
+ *   - Fields whose halo is a multiple of 4, whose nx is a multiple of 4 and
+ *     whose pointers are 16-byte aligned take the TMA-staged kernel; all
+ *     other shapes take a plain-load kernel with the same arithmetic.
+ *   - gbs_last_error() returns a message for the last failing call of the
+ *     calling thread.
+ *   - Nothing here allocates device memory.
+ */
+#ifndef GBSTENCIL_H
+#define GBSTENCIL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBS_OK = 0,
+    GBS_EINVAL = 1,       /* bad argument: null pointer, size, radius, halo */
+    GBS_EALIGN = 2,       /* alignment demanded by an explicit kernel choice not met */
+    GBS_ECUDA = 3,        /* a CUDA runtime/driver call failed */
+    GBS_ETIMEOUT = 4,     /* device: a bounded pipeline wait ran out */
+    GBS_EUNSTABLE = 5,    /* reserved: CFL limit exceeded */
+    GBS_ENOMEM = 6,       /* reserved */
+    GBS_ENAN = 7,         /* reserved */
+    GBS_EUNSUPPORTED = 8  /* no kernel for this combination */
+} gbs_status;
+
+/* Point sources.  Step n (the step that produces u^{n+1}) adds
+ * dt^2 V(x_s)^2 * amp[n*n_src + s] at interior linear index idx[s] for
+ * n < nt; later steps inject nothing (Eq. 2 right-hand side, added after the
+ * stencil update as in Algorithm 1).  Two sources may share a cell. */
+typedef struct {
+    int64_t n;              /* number of sources (0 = none) */
+    const int64_t *idx;     /* DEVICE [n] interior linear indices */
+    const float *amp;       /* DEVICE [nt][n] source function f^n (unscaled) */
+    int64_t nt;             /* rows of amp */
+} gbs_src;
+
+/* Receivers.  Step n writes u^{n+1} at interior linear index idx[r] into
+ * trace[n*n_rec + r] for n < nt. */
+typedef struct {
+    int64_t n;
+    const int64_t *idx;     /* DEVICE [n] */
+    float *trace;           /* DEVICE [nt][n] */
+    int64_t nt;
+} gbs_rec;
+
+/* Tuning choices; a zero field means "library default". */
+typedef struct {
+    int kernel;     /* 0 auto, 1 TMA-staged (fails with GBS_EALIGN if not possible), 2 plain-load */
+    int tile_y;     /* rows per CTA tile of the TMA kernel: 16 or 32 (x is always 64) */
+    int zchunk;     /* planes streamed per CTA (>= 1) */
+    int use_graph;  /* wave_propagate: 1 = capture the step loop in a CUDA graph and replay it */
+} gbs_opts;
+
+/*
+ * Star stencil, Eq. 3: out = L in on the interior; the halo of `in` is read
+ * as given, the halo of `out` is left untouched.
+ *   in, out       DEVICE float, padded layout above; must not overlap.
+ *   radius        R in 1..4 (7, 13, 19 or 25 points).
+ *   coeffs_x/y/z  HOST float[radius+1]: element 0 is the axis' share of the
+ *                 centre weight (c_xyz = cx[0]+cy[0]+cz[0]), element m the
+ *                 weight of the two points at distance m on that axis.
+ *   halo          >= radius.
+ * Errors: GBS_EINVAL (null pointer, negative size, radius, halo < radius,
+ * aliasing in/out), GBS_ECUDA.
+ */
+gbs_status gbs_stencil_apply(const float *in, float *out, int64_t nx, int64_t ny, int64_t nz,
+                             int radius, const float *coeffs_x, const float *coeffs_y,
+                             const float *coeffs_z, int halo, void *stream);
+
+/*
+ * One leapfrog step, Eq. 2, with the 25-point (radius 4) 8th-order Laplacian
+ * of spacing h on every axis:
+ *   u_next = 2 u - u_prev + (vel dt)^2 lap_h(u) + (vel dt)^2 f^step
+ *   u_prev, u, u_next, vel  DEVICE float, padded layout, halo >= 4.  u_next
+ *                 may be u_prev (in-place update); it must not overlap u or vel.
+ *   dt, h         time step [s] and grid spacing [m], > 0.
+ *   src, rec      optional (NULL = none); row `step` of src->amp is injected,
+ *                 row `step` of rec->trace is written.
+ * The halo of u_next is not written: zero halos stay zero (Dirichlet).
+ * Errors: GBS_EINVAL, GBS_ECUDA.
+ */
+gbs_status gbs_wave_step(const float *u_prev, const float *u, float *u_next, const float *vel,
+                         float dt, float h, int64_t nx, int64_t ny, int64_t nz, int halo,
+                         const gbs_src *src, const gbs_rec *rec, int64_t step, void *stream);
+
+/*
+ * Algorithm 1: nsteps leapfrog steps n = t0, ..., t0+nsteps-1 (Eq. 2 each).
+ * On entry (u_prev, u) hold (u^{t0-1}, u^{t0}).  The two buffers are updated
+ * in place, alternately, with no copy: on return, for even nsteps u holds
+ * u^{t0+nsteps} and u_prev holds u^{t0+nsteps-1}; for odd nsteps u_prev holds
+ * u^{t0+nsteps} and u holds u^{t0+nsteps-1}.
+ *   opts          NULL = defaults (see gbs_opts).
+ * Other arguments as gbs_wave_step.  Errors: GBS_EINVAL, GBS_EALIGN,
+ * GBS_ECUDA.
+ */
+gbs_status gbs_wave_propagate(float *u_prev, float *u, const float *vel, float dt, float h,
+                              int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                              int64_t t0, const gbs_src *src, const gbs_rec *rec,
+                              const gbs_opts *opts, void *stream);
+
+/*
+ * The library's weights of the centred second derivative of order 2R
+ * (unit spacing), the values of c_xm, c_ym, c_zm used by gbs_wave_step:
+ * out[0] = c_0, out[m] = c_m, m = 1..R.  HOST out[radius+1].
+ * Errors: GBS_EINVAL for radius outside 1..4 or out == NULL.
+ */
+gbs_status gbs_fd2_coeffs(int radius, float *out);
+
+/*
+ * Kernel timing.  While enabled (on != 0), every launch of the stencil /
+ * wave-step kernel made outside stream capture is bracketed by two CUDA
+ * events recorded on the launch's own stream.  gbs_profile_take()
+ * synchronises on those events and returns the summed elapsed time (ms)
+ * and the number of launches since the last take, then forgets them.
+ * Events come from a pool the library keeps for the process lifetime.
+ * Errors: GBS_ECUDA (event creation or query failed), GBS_EINVAL (null out).
+ */
+gbs_status gbs_profile_enable(int on);
+gbs_status gbs_profile_take(double *total_ms, int64_t *launches);
+
+/* Synchronises `stream`, returns the device status word (GBS_OK or the first
+ * device-side error recorded since the last call) and clears it. */
+gbs_status gbs_device_status(void *stream);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *gbs_last_error(void);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int gbs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSTENCIL_H */

@@ -1,0 +1,271 @@
+"""GB300-native star stencil and acoustic leapfrog wave step (arXiv 2309.04671).
+
+Python binding of ``libgbstencil.so`` (C ABI in ``include/gbstencil.h``).
+This module only marshals arguments: tensors become device pointers and
+sizes, the current torch stream becomes the ``stream`` argument, and every
+step of the computation runs in the library's CUDA kernels.  There is no CPU
+path: if the library is missing or no GPU is present the calls raise.
+
+Fields are float32 CUDA tensors of shape (nz+2*halo, ny+2*halo, nx+2*halo),
+C-contiguous (x fastest), as in the paper's flattened grid with halo padding
+(Sec. 10).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbstencil.so")
+
+GBS_OK, GBS_EINVAL, GBS_EALIGN, GBS_ECUDA, GBS_ETIMEOUT = 0, 1, 2, 3, 4
+STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4: "GBS_ETIMEOUT",
+                5: "GBS_EUNSTABLE", 6: "GBS_ENOMEM", 7: "GBS_ENAN", 8: "GBS_EUNSUPPORTED"}
+
+# Entry points declared in include/gbstencil.h (checked by the tests).
+EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_fd2_coeffs",
+           "gbs_profile_enable", "gbs_profile_take", "gbs_device_status", "gbs_last_error", "gbs_version")
+
+
+class GbsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Src(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("idx", ctypes.c_void_p), ("amp", ctypes.c_void_p),
+                ("nt", ctypes.c_int64)]
+
+
+class _Rec(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("idx", ctypes.c_void_p), ("trace", ctypes.c_void_p),
+                ("nt", ctypes.c_int64)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("tile_y", ctypes.c_int), ("zchunk", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib: Optional[ctypes.CDLL] = None
+
+
+def build(force: bool = False) -> str:
+    """Compile libgbstencil.so for sm_103a (needs nvcc; no GPU needed)."""
+    from . import _build
+    return _build.build(force=force)
+
+
+def load() -> ctypes.CDLL:
+    """Load libgbstencil.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2309_04671_gb300.build() "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        i64, vp, c_int, c_float = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.gbs_stencil_apply.argtypes = [vp, vp, i64, i64, i64, c_int, fp, fp, fp, c_int, vp]
+        lib.gbs_wave_step.argtypes = [vp, vp, vp, vp, c_float, c_float, i64, i64, i64, c_int,
+                                      ctypes.POINTER(_Src), ctypes.POINTER(_Rec), i64, vp]
+        lib.gbs_wave_propagate.argtypes = [vp, vp, vp, c_float, c_float, i64, i64, i64, c_int, i64, i64,
+                                           ctypes.POINTER(_Src), ctypes.POINTER(_Rec), ctypes.POINTER(_Opts), vp]
+        lib.gbs_fd2_coeffs.argtypes = [c_int, fp]
+        lib.gbs_profile_enable.argtypes = [c_int]
+        lib.gbs_profile_take.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+        lib.gbs_device_status.argtypes = [vp]
+        lib.gbs_last_error.restype = ctypes.c_char_p
+        lib.gbs_last_error.argtypes = []
+        lib.gbs_version.argtypes = []
+        for f in ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_fd2_coeffs",
+                  "gbs_profile_enable", "gbs_profile_take", "gbs_device_status", "gbs_version"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int) -> None:
+    if rc != GBS_OK:
+        raise GbsError(rc, load().gbs_last_error().decode(errors="replace"))
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _field(t: torch.Tensor, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous() or t.dim() != 3:
+        raise TypeError(f"{name} must be a contiguous 3D float32 tensor")
+    return t.data_ptr()
+
+
+def _dims(t: torch.Tensor, halo: int):
+    nz, ny, nx = (int(s) - 2 * halo for s in t.shape)
+    if min(nx, ny, nz) < 0:
+        raise ValueError("halo larger than the field")
+    return nx, ny, nz
+
+
+def _same_shape(ref: torch.Tensor, *others):
+    for o in others:
+        if o.shape != ref.shape or o.device != ref.device:
+            raise ValueError("fields must share shape and device")
+
+
+def _idx(t, name):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous int64 CUDA tensor")
+    return t
+
+
+def _make_src(src_idx, src_amp):
+    if src_idx is None or src_idx.numel() == 0:
+        return None
+    _idx(src_idx, "src_idx")
+    if not (src_amp.is_cuda and src_amp.dtype == torch.float32 and src_amp.is_contiguous()):
+        raise TypeError("src_amp must be a contiguous float32 CUDA tensor (nt, nsrc)")
+    n = src_idx.numel()
+    nt = src_amp.numel() // n
+    return _Src(n, src_idx.data_ptr(), src_amp.data_ptr(), nt)
+
+
+def _make_rec(rec_idx, rec_trace):
+    if rec_idx is None or rec_idx.numel() == 0:
+        return None
+    _idx(rec_idx, "rec_idx")
+    if not (rec_trace.is_cuda and rec_trace.dtype == torch.float32 and rec_trace.is_contiguous()):
+        raise TypeError("rec_trace must be a contiguous float32 CUDA tensor (nt, nrec)")
+    n = rec_idx.numel()
+    return _Rec(n, rec_idx.data_ptr(), rec_trace.data_ptr(), rec_trace.numel() // n)
+
+
+def _ptr(s):
+    return ctypes.byref(s) if s is not None else None
+
+
+def fd2_coeffs(radius: int) -> list[float]:
+    """The library's weights (c_0..c_R) of the centred second derivative (unit spacing)."""
+    out = (ctypes.c_float * (radius + 1))()
+    _check(load().gbs_fd2_coeffs(radius, out))
+    return [float(v) for v in out]
+
+
+def stencil_apply(inp: torch.Tensor, out: Optional[torch.Tensor] = None, *, radius: int,
+                  cx: Sequence[float], cy: Sequence[float], cz: Sequence[float], halo: int,
+                  stream=None) -> torch.Tensor:
+    """Eq. 3 star stencil: out = L inp on the interior (out's halo untouched)."""
+    if out is None:
+        out = torch.zeros_like(inp)
+    pin, pout = _field(inp, "inp"), _field(out, "out")
+    _same_shape(inp, out)
+    nx, ny, nz = _dims(inp, halo)
+    arr = [(ctypes.c_float * (radius + 1))(*[float(v) for v in list(c)[: radius + 1]]) for c in (cx, cy, cz)]
+    if any(len(list(c)) < radius + 1 for c in (cx, cy, cz)):
+        raise ValueError("each coefficient list needs radius+1 entries")
+    _check(load().gbs_stencil_apply(pin, pout, nx, ny, nz, radius, arr[0], arr[1], arr[2], halo,
+                                    _stream(stream)))
+    return out
+
+
+def wave_step(u_prev: torch.Tensor, u: torch.Tensor, u_next: torch.Tensor, vel: torch.Tensor,
+              dt: float, h: float, halo: int, *, src_idx=None, src_amp=None, rec_idx=None,
+              rec_trace=None, step: int = 0, stream=None) -> torch.Tensor:
+    """One leapfrog step (Eq. 2); u_next may be u_prev (in place)."""
+    p = [_field(t, n) for t, n in ((u_prev, "u_prev"), (u, "u"), (u_next, "u_next"), (vel, "vel"))]
+    _same_shape(u, u_prev, u_next, vel)
+    nx, ny, nz = _dims(u, halo)
+    src = _make_src(src_idx, src_amp)
+    rec = _make_rec(rec_idx, rec_trace)
+    _check(load().gbs_wave_step(p[0], p[1], p[2], p[3], float(dt), float(h), nx, ny, nz, halo,
+                                _ptr(src), _ptr(rec), int(step), _stream(stream)))
+    return u_next
+
+
+def _opts(kernel, tile_y, zchunk, use_graph):
+    return _Opts(int(kernel), int(tile_y), int(zchunk), 1 if use_graph else 0)
+
+
+def wave_propagate(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, dt: float, h: float,
+                   halo: int, nsteps: int, *, t0: int = 0, src_idx=None, src_amp=None, rec_idx=None,
+                   rec_trace=None, kernel: int = 0, tile_y: int = 0, zchunk: int = 0,
+                   use_graph: bool = False, stream=None):
+    """Algorithm 1: nsteps leapfrog steps, in place in the two buffers.
+
+    Returns (prev, cur): the tensors that now hold u^{t0+nsteps-1} and
+    u^{t0+nsteps} (the two input buffers, swapped when nsteps is odd).
+
+    With CPU tensors (ideally pinned) the call copies the inputs to the
+    device, runs, and copies both fields (and the trace) back; it then
+    returns CPU tensors.
+    """
+    if not u.is_cuda:
+        return _wave_propagate_host(u_prev, u, vel, dt, h, halo, nsteps, t0=t0, src_idx=src_idx,
+                                    src_amp=src_amp, rec_idx=rec_idx, rec_trace=rec_trace, kernel=kernel,
+                                    tile_y=tile_y, zchunk=zchunk, use_graph=use_graph, stream=stream)
+    p = [_field(t, n) for t, n in ((u_prev, "u_prev"), (u, "u"), (vel, "vel"))]
+    _same_shape(u, u_prev, vel)
+    nx, ny, nz = _dims(u, halo)
+    src = _make_src(src_idx, src_amp)
+    rec = _make_rec(rec_idx, rec_trace)
+    opts = _opts(kernel, tile_y, zchunk, use_graph)
+    _check(load().gbs_wave_propagate(p[0], p[1], p[2], float(dt), float(h), nx, ny, nz, halo, int(nsteps),
+                                     int(t0), _ptr(src), _ptr(rec), ctypes.byref(opts), _stream(stream)))
+    return (u, u_prev) if nsteps % 2 else (u_prev, u)
+
+
+def _wave_propagate_host(u_prev, u, vel, dt, h, halo, nsteps, *, t0, src_idx, src_amp, rec_idx, rec_trace,
+                         kernel, tile_y, zchunk, use_graph, stream):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d_prev = u_prev.to(dev, non_blocking=True)
+    d_u = u.to(dev, non_blocking=True)
+    d_vel = vel.to(dev, non_blocking=True)
+    d_si = src_idx.to(dev, non_blocking=True) if src_idx is not None else None
+    d_sa = src_amp.to(dev, non_blocking=True) if src_amp is not None else None
+    d_ri = rec_idx.to(dev, non_blocking=True) if rec_idx is not None else None
+    d_tr = rec_trace.to(dev, non_blocking=True) if rec_trace is not None else None
+    a, b = wave_propagate(d_prev, d_u, d_vel, dt, h, halo, nsteps, t0=t0, src_idx=d_si, src_amp=d_sa,
+                          rec_idx=d_ri, rec_trace=d_tr, kernel=kernel, tile_y=tile_y, zchunk=zchunk,
+                          use_graph=use_graph, stream=stream)
+    # results land in the caller's host buffers: newest field into `u`, previous into `u_prev`
+    u.copy_(b, non_blocking=True)
+    u_prev.copy_(a, non_blocking=True)
+    if rec_trace is not None:
+        rec_trace.copy_(d_tr, non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    return u_prev, u
+
+
+def device_status(stream=None) -> None:
+    """Synchronise and raise GbsError if a kernel recorded a device-side error."""
+    _check(load().gbs_device_status(_stream(stream)))
+
+
+def profile_enable(on: bool = True) -> None:
+    """Bracket each stencil / wave-step kernel launch with CUDA events."""
+    _check(load().gbs_profile_enable(1 if on else 0))
+
+
+def profile_take() -> tuple[float, int]:
+    """(summed kernel milliseconds, launches) since the last take."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(load().gbs_profile_take(ctypes.byref(ms), ctypes.byref(n)))
+    return float(ms.value), int(n.value)
+
+
+def version() -> int:
+    return int(load().gbs_version())

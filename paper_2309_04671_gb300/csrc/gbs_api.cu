@@ -1,0 +1,497 @@
+// C ABI of the gbstencil library (include/gbstencil.h): argument checks,
+// TMA descriptor set-up, kernel choice and the time loop of Algorithm 1.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "gbs_internal.cuh"
+
+namespace gbs {
+namespace {
+
+thread_local char t_err[512] = "";
+
+gbs_status fail(gbs_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+gbs_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(GBS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Weights of the centred second derivative of order 2R, unit spacing
+// (Fornberg 1988, Table 1): the c_m of Eq. 3 for the Acoustic ISO kernel.
+const double kFd2[4][5] = {
+    {-2.0, 1.0, 0, 0, 0},
+    {-5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0, 0, 0},
+    {-49.0 / 18.0, 3.0 / 2.0, -3.0 / 20.0, 1.0 / 90.0, 0},
+    {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0},
+};
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Tensor map over a padded FP32 field (px x py x pz), box bw x bh x 1.
+gbs_status make_map(CUtensorMap *m, const float *base, const Grid &g, int bw, int bh)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc)
+        return fail(GBS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)(g.nz + 2 * g.halo)};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.px * 4, (cuuint64_t)(g.px * g.py) * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(GBS_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GBS_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int64_t field_elems(const Grid &g) { return g.px * g.py * (g.nz + 2 * g.halo); }
+
+bool overlap(const float *a, const float *b, int64_t n)
+{
+    return a < b + n && b < a + n;
+}
+
+gbs_status check_dims(int64_t nx, int64_t ny, int64_t nz, int halo)
+{
+    if (nx < 0 || ny < 0 || nz < 0)
+        return fail(GBS_EINVAL, "negative interior size (%lld, %lld, %lld)", (long long)nx, (long long)ny,
+                    (long long)nz);
+    if (halo < 0 || halo > 64)
+        return fail(GBS_EINVAL, "halo %d outside 0..64", halo);
+    const int64_t lim = (int64_t)1 << 30;
+    if (nx + 2 * halo >= lim || ny + 2 * halo >= lim || nz + 2 * halo >= lim)
+        return fail(GBS_EINVAL, "grid extent too large");
+    return GBS_OK;
+}
+
+Grid dense_grid(int64_t nx, int64_t ny, int64_t nz, int halo)
+{
+    Grid g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.halo = halo;
+    g.px = nx + 2 * halo;
+    g.py = ny + 2 * halo;
+    return g;
+}
+
+// The TMA kernel needs 16-byte aligned rows and tile starts: halo % 4 == 0,
+// nx % 4 == 0 (so the row pitch nx+2*halo is a multiple of 4 floats) and
+// 16-byte aligned base pointers.
+bool tma_shape_ok(const Grid &g) { return g.halo % 4 == 0 && g.nx % 4 == 0 && g.px % 4 == 0; }
+
+int pick_kernel(const gbs_opts *o, bool tma_ok, gbs_status *st)
+{
+    const int k = o ? o->kernel : 0;
+    *st = GBS_OK;
+    if (k == 1 && !tma_ok) {
+        *st = fail(GBS_EALIGN, "TMA kernel requested but halo%%4, nx%%4 or 16-byte alignment not met");
+        return 0;
+    }
+    if (k == 2)
+        return 2;
+    if (k != 0 && k != 1) {
+        *st = fail(GBS_EINVAL, "opts.kernel must be 0, 1 or 2");
+        return 0;
+    }
+    return tma_ok ? 1 : 2;
+}
+
+int pick_tile_y(const gbs_opts *o) { return (o && o->tile_y == 32) ? 32 : 16; }
+
+Coeffs wave_coeffs()
+{
+    Coeffs cf;
+    for (int a = 0; a < 3; ++a)
+        for (int m = 0; m < 5; ++m)
+            cf.c[a][m] = (float)kFd2[3][m];
+    return cf;
+}
+
+// Event bracketing of the main kernel launches (gbs_profile_enable).
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+
+    cudaEvent_t get()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess)
+            return nullptr;
+        return e;
+    }
+};
+Profiler g_prof;
+
+bool capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess)
+        return true;
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Records the opening event of a profiled launch; returns it (or null).
+cudaEvent_t prof_begin(cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (!g_prof.on || capturing(st))
+        return nullptr;
+    cudaEvent_t e = g_prof.get();
+    if (e && cudaEventRecord(e, st) != cudaSuccess) {
+        g_prof.pool.push_back(e);
+        return nullptr;
+    }
+    return e;
+}
+
+void prof_end(cudaEvent_t e0, cudaStream_t st)
+{
+    if (!e0)
+        return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    cudaEvent_t e1 = g_prof.get();
+    if (e1 && cudaEventRecord(e1, st) == cudaSuccess)
+        g_prof.pending.emplace_back(e0, e1);
+    else {
+        g_prof.pool.push_back(e0);
+        if (e1)
+            g_prof.pool.push_back(e1);
+    }
+}
+
+// One leapfrog step u_next = 2u - u_prev + (V dt)^2 (lap u + f): the fused
+// stencil/update kernel, then sources, then receivers.
+struct StepPlan {
+    int kernel;       // 1 TMA, 2 plain loads
+    int tile_y;
+    int zchunk;
+    TmaPlan tma;
+};
+
+gbs_status plan_step(StepPlan *sp, const Grid &g, const float *u_prev, const float *u, const float *vel,
+                     int kernel, int tile_y, int zchunk)
+{
+    sp->kernel = kernel;
+    sp->tile_y = tile_y;
+    sp->zchunk = zchunk;
+    if (kernel == 1) {
+        gbs_status s = make_map(&sp->tma.u, u, g, 64 + 8, tile_y + 8);
+        if (s == GBS_OK)
+            s = make_map(&sp->tma.prev, u_prev, g, 64, tile_y);
+        if (s == GBS_OK)
+            s = make_map(&sp->tma.vel, vel, g, 64, tile_y);
+        return s;
+    }
+    return GBS_OK;
+}
+
+gbs_status run_step(const StepPlan &sp, const Grid &g, const float *u_prev, const float *u, float *u_next,
+                    const float *vel, float dt, float h, const gbs_src *src, const gbs_rec *rec, int64_t step,
+                    cudaStream_t st)
+{
+    const Coeffs cf = wave_coeffs();
+    const float s = (float)((double)dt / (double)h);
+    cudaError_t e;
+    cudaEvent_t e0 = prof_begin(st);
+    if (sp.kernel == 1) {
+        e = launch_tma(4, kWave, sp.tile_y, g, sp.tma, u_next, cf, s, sp.zchunk, st);
+    } else {
+        WaveArgs w{u_prev, vel, s};
+        e = launch_generic(4, kWave, g, u, u_next, cf, w, sp.zchunk, st);
+    }
+    prof_end(e0, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "wave step launch");
+    if ((e = launch_inject(g, u_next, vel, dt, src, step, st)) != cudaSuccess)
+        return cuda_fail(e, "source injection launch");
+    if ((e = launch_record(g, u_next, rec, step, st)) != cudaSuccess)
+        return cuda_fail(e, "receiver launch");
+    return GBS_OK;
+}
+
+gbs_status check_src_rec(const gbs_src *src, const gbs_rec *rec)
+{
+    if (src && src->n > 0 && (!src->idx || (!src->amp && src->nt > 0) || src->nt < 0))
+        return fail(GBS_EINVAL, "gbs_src with n > 0 needs idx and amp");
+    if (rec && rec->n > 0 && (!rec->idx || (!rec->trace && rec->nt > 0) || rec->nt < 0))
+        return fail(GBS_EINVAL, "gbs_rec with n > 0 needs idx and trace");
+    return GBS_OK;
+}
+
+gbs_status check_wave_fields(const Grid &g, const float *u_prev, const float *u, const float *u_next,
+                             const float *vel, float dt, float h)
+{
+    if (!u_prev || !u || !u_next || !vel)
+        return fail(GBS_EINVAL, "null field pointer");
+    if (g.halo < 4)
+        return fail(GBS_EINVAL, "the 25-point step needs halo >= 4 (got %d)", g.halo);
+    if (!(dt > 0.f) || !(h > 0.f))
+        return fail(GBS_EINVAL, "dt and h must be positive");
+    const int64_t n = field_elems(g);
+    if (overlap(u_next, u, n) || overlap(u_next, vel, n))
+        return fail(GBS_EINVAL, "u_next overlaps u or vel");
+    if (u_next != u_prev && overlap(u_next, u_prev, n))
+        return fail(GBS_EINVAL, "u_next partially overlaps u_prev");
+    return GBS_OK;
+}
+
+}  // namespace
+}  // namespace gbs
+
+using namespace gbs;
+
+extern "C" gbs_status gbs_stencil_apply(const float *in, float *out, int64_t nx, int64_t ny, int64_t nz,
+                                        int radius, const float *coeffs_x, const float *coeffs_y,
+                                        const float *coeffs_z, int halo, void *stream)
+{
+    t_err[0] = 0;
+    gbs_status s = check_dims(nx, ny, nz, halo);
+    if (s != GBS_OK)
+        return s;
+    if (radius < 1 || radius > 4)
+        return fail(GBS_EINVAL, "radius %d outside 1..4", radius);
+    if (halo < radius)
+        return fail(GBS_EINVAL, "halo %d < radius %d", halo, radius);
+    if (!coeffs_x || !coeffs_y || !coeffs_z)
+        return fail(GBS_EINVAL, "null coefficient array");
+    if (nx == 0 || ny == 0 || nz == 0)
+        return GBS_OK;
+    if (!in || !out)
+        return fail(GBS_EINVAL, "null field pointer");
+    const Grid g = dense_grid(nx, ny, nz, halo);
+    if (overlap(in, out, field_elems(g)))
+        return fail(GBS_EINVAL, "in and out overlap");
+    Coeffs cf;
+    memset(&cf, 0, sizeof(cf));
+    for (int m = 0; m <= radius; ++m) {
+        cf.c[0][m] = coeffs_x[m];
+        cf.c[1][m] = coeffs_y[m];
+        cf.c[2][m] = coeffs_z[m];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool tma_ok = tma_shape_ok(g) && aligned16(in) && aligned16(out);
+    cudaError_t e;
+    cudaEvent_t e0 = prof_begin(st);
+    if (tma_ok) {
+        TmaPlan plan;
+        memset(&plan, 0, sizeof(plan));
+        if ((s = make_map(&plan.u, in, g, 64 + 8, 16 + 2 * radius)) != GBS_OK)
+            return s;
+        plan.prev = plan.u;
+        plan.vel = plan.u;
+        e = launch_tma(radius, kStencil, 16, g, plan, out, cf, 0.f, 0, st);
+    } else {
+        WaveArgs w{nullptr, nullptr, 0.f};
+        e = launch_generic(radius, kStencil, g, in, out, cf, w, 0, st);
+    }
+    prof_end(e0, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "stencil launch");
+    return GBS_OK;
+}
+
+extern "C" gbs_status gbs_wave_step(const float *u_prev, const float *u, float *u_next, const float *vel,
+                                    float dt, float h, int64_t nx, int64_t ny, int64_t nz, int halo,
+                                    const gbs_src *src, const gbs_rec *rec, int64_t step, void *stream)
+{
+    t_err[0] = 0;
+    gbs_status s = check_dims(nx, ny, nz, halo);
+    if (s != GBS_OK)
+        return s;
+    if ((s = check_src_rec(src, rec)) != GBS_OK)
+        return s;
+    if (nx == 0 || ny == 0 || nz == 0)
+        return GBS_OK;
+    const Grid g = dense_grid(nx, ny, nz, halo);
+    if ((s = check_wave_fields(g, u_prev, u, u_next, vel, dt, h)) != GBS_OK)
+        return s;
+    const bool tma_ok = tma_shape_ok(g) && aligned16(u_prev) && aligned16(u) && aligned16(u_next) && aligned16(vel);
+    StepPlan sp;
+    if ((s = plan_step(&sp, g, u_prev, u, vel, tma_ok ? 1 : 2, 16, 0)) != GBS_OK)
+        return s;
+    return run_step(sp, g, u_prev, u, u_next, vel, dt, h, src, rec, step, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" gbs_status gbs_wave_propagate(float *u_prev, float *u, const float *vel, float dt, float h,
+                                         int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                                         int64_t t0, const gbs_src *src, const gbs_rec *rec,
+                                         const gbs_opts *opts, void *stream)
+{
+    t_err[0] = 0;
+    gbs_status s = check_dims(nx, ny, nz, halo);
+    if (s != GBS_OK)
+        return s;
+    if (nsteps < 0 || t0 < 0)
+        return fail(GBS_EINVAL, "nsteps and t0 must be >= 0");
+    if ((s = check_src_rec(src, rec)) != GBS_OK)
+        return s;
+    if (opts && opts->zchunk < 0)
+        return fail(GBS_EINVAL, "opts.zchunk must be >= 0");
+    if (nx == 0 || ny == 0 || nz == 0 || nsteps == 0)
+        return GBS_OK;
+    const Grid g = dense_grid(nx, ny, nz, halo);
+    if (u_prev == u)
+        return fail(GBS_EINVAL, "u_prev and u are the same buffer");
+    if ((s = check_wave_fields(g, u_prev, u, u_prev, vel, dt, h)) != GBS_OK)
+        return s;
+    if (overlap(u_prev, u, field_elems(g)))
+        return fail(GBS_EINVAL, "u_prev and u overlap");
+    const bool tma_ok = tma_shape_ok(g) && aligned16(u_prev) && aligned16(u) && aligned16(vel);
+    const int kernel = pick_kernel(opts, tma_ok, &s);
+    if (s != GBS_OK)
+        return s;
+    const int tile_y = pick_tile_y(opts);
+    const int zchunk = (opts && opts->zchunk > 0) ? opts->zchunk
+                       : kernel == 1                ? tma_default_zchunk(4, kWave, tile_y, g)
+                                                    : 64;
+    // the two parities of the ping-pong: plan[0] reads u (B) and writes u_prev (A), plan[1] the reverse
+    float *buf[2] = {u_prev, u};
+    StepPlan plan[2];
+    if ((s = plan_step(&plan[0], g, buf[0], buf[1], vel, kernel, tile_y, zchunk)) != GBS_OK)
+        return s;
+    if ((s = plan_step(&plan[1], g, buf[1], buf[0], vel, kernel, tile_y, zchunk)) != GBS_OK)
+        return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool graph = opts && opts->use_graph && st != nullptr;
+
+    auto enqueue = [&]() -> gbs_status {
+        for (int64_t q = 0; q < nsteps; ++q) {
+            const int par = (int)(q & 1);
+            float *prev = buf[par], *cur = buf[par ^ 1];
+            gbs_status r = run_step(plan[par], g, prev, cur, prev, vel, dt, h, src, rec, t0 + q, st);
+            if (r != GBS_OK)
+                return r;
+        }
+        return GBS_OK;
+    };
+    if (!graph)
+        return enqueue();
+
+    // Capture the step loop once and replay it as one graph launch.  A first
+    // uncaptured launch of zero steps is not needed: kernel attributes are
+    // set outside the capture by the launchers on first use.
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    gbs_status r = enqueue();
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(st, &gr);
+    if (r != GBS_OK) {
+        if (gr)
+            cudaGraphDestroy(gr);
+        return r;
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGraphInstantiate");
+    e = cudaGraphLaunch(ex, st);
+    cudaGraphExecDestroy(ex);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGraphLaunch");
+    return GBS_OK;
+}
+
+extern "C" gbs_status gbs_fd2_coeffs(int radius, float *out)
+{
+    t_err[0] = 0;
+    if (radius < 1 || radius > 4 || !out)
+        return fail(GBS_EINVAL, "radius must be 1..4 and out non-null");
+    for (int m = 0; m <= radius; ++m)
+        out[m] = (float)kFd2[radius - 1][m];
+    return GBS_OK;
+}
+
+extern "C" gbs_status gbs_device_status(void *stream)
+{
+    t_err[0] = 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned a = tma_status_take(st);
+    const unsigned b = misc_status_take(st);
+    const unsigned v = a ? a : b;
+    if (v != 0)
+        return fail((gbs_status)v, "device status %u", v);
+    return GBS_OK;
+}
+
+extern "C" gbs_status gbs_profile_enable(int on)
+{
+    t_err[0] = 0;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.on = on != 0;
+    return GBS_OK;
+}
+
+extern "C" gbs_status gbs_profile_take(double *total_ms, int64_t *launches)
+{
+    t_err[0] = 0;
+    if (!total_ms || !launches)
+        return fail(GBS_EINVAL, "null output");
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    double sum = 0.0;
+    gbs_status st = GBS_OK;
+    for (auto &pr : g_prof.pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(pr.second);
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+        if (e != cudaSuccess && st == GBS_OK)
+            st = cuda_fail(e, "profiling event");
+        sum += ms;
+        g_prof.pool.push_back(pr.first);
+        g_prof.pool.push_back(pr.second);
+    }
+    *launches = (int64_t)g_prof.pending.size();
+    *total_ms = sum;
+    g_prof.pending.clear();
+    return st;
+}
+
+extern "C" const char *gbs_last_error(void) { return t_err; }
+
+extern "C" int gbs_version(void) { return 100; }

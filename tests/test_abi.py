@@ -1,0 +1,117 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The library must load, export every entry point that include/gbstencil.h
+declares, reject bad arguments before touching the device, and carry the
+same Eq. 3 weights as the oracle (which derives them independently).
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2309_04671_gb300 as gbs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbs.build()
+    return gbs.load()
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(gbs_\w+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert declared >= set(gbs.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_header_declares_extern_c():
+    src = open(os.path.join(ROOT, "include", "gbstencil.h")).read()
+    assert 'extern "C"' in src
+
+
+def test_version(lib):
+    assert gbs.version() >= 100
+
+
+@pytest.mark.parametrize("R", [1, 2, 3, 4])
+def test_library_weights_match_oracle(lib, R):
+    # the library's table (a literal) against the oracle's solved moment system
+    got = np.array(gbs.fd2_coeffs(R), np.float64)
+    want = oracle.fd2_coeffs(R)
+    np.testing.assert_array_equal(got, want.astype(np.float32).astype(np.float64))
+
+
+def test_fd2_coeffs_rejects_bad_radius(lib):
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.fd2_coeffs(5)
+    assert e.value.status == gbs.GBS_EINVAL
+
+
+def _c(vals):
+    return (ctypes.c_float * len(vals))(*vals)
+
+
+def test_stencil_validation_before_device(lib):
+    c = _c([1.0] * 5)
+    # radius out of range, halo < radius, negative size: all host-side errors
+    assert lib.gbs_stencil_apply(None, None, 8, 8, 8, 5, c, c, c, 4, None) == gbs.GBS_EINVAL
+    assert b"radius" in lib.gbs_last_error()
+    assert lib.gbs_stencil_apply(None, None, 8, 8, 8, 4, c, c, c, 3, None) == gbs.GBS_EINVAL
+    assert lib.gbs_stencil_apply(None, None, -1, 8, 8, 4, c, c, c, 4, None) == gbs.GBS_EINVAL
+    assert lib.gbs_stencil_apply(None, None, 8, 8, 8, 4, None, c, c, 4, None) == gbs.GBS_EINVAL
+    # null fields with a non-empty interior
+    assert lib.gbs_stencil_apply(None, None, 8, 8, 8, 4, c, c, c, 4, None) == gbs.GBS_EINVAL
+    # an empty interior is a valid no-op
+    assert lib.gbs_stencil_apply(None, None, 0, 8, 8, 4, c, c, c, 4, None) == gbs.GBS_OK
+    # in/out overlap is rejected (fake addresses are never dereferenced)
+    assert lib.gbs_stencil_apply(ctypes.c_void_p(4096), ctypes.c_void_p(4096 + 64), 4, 4, 4, 1, c, c, c, 1,
+                                 None) == gbs.GBS_EINVAL
+
+
+def test_wave_validation_before_device(lib):
+    fake = [ctypes.c_void_p(1 << 20), ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20), ctypes.c_void_p(4 << 20)]
+    # halo < 4 for the 25-point step
+    assert lib.gbs_wave_step(fake[0], fake[1], fake[2], fake[3], 1e-3, 10.0, 4, 4, 4, 2, None, None, 0,
+                             None) == gbs.GBS_EINVAL
+    # non-positive dt
+    assert lib.gbs_wave_step(fake[0], fake[1], fake[2], fake[3], 0.0, 10.0, 4, 4, 4, 4, None, None, 0,
+                             None) == gbs.GBS_EINVAL
+    # u_next overlapping u
+    assert lib.gbs_wave_step(fake[0], fake[1], fake[1], fake[3], 1e-3, 10.0, 4, 4, 4, 4, None, None, 0,
+                             None) == gbs.GBS_EINVAL
+    # propagate: same buffer twice, negative steps, zero steps no-op
+    assert lib.gbs_wave_propagate(fake[0], fake[0], fake[3], ctypes.c_float(1e-3), ctypes.c_float(10.0), 4, 4, 4,
+                                  4, 5, 0, None, None, None, None) == gbs.GBS_EINVAL
+    assert lib.gbs_wave_propagate(fake[0], fake[1], fake[3], ctypes.c_float(1e-3), ctypes.c_float(10.0), 4, 4, 4,
+                                  4, -1, 0, None, None, None, None) == gbs.GBS_EINVAL
+    assert lib.gbs_wave_propagate(fake[0], fake[1], fake[3], ctypes.c_float(1e-3), ctypes.c_float(10.0), 4, 4, 4,
+                                  4, 0, 0, None, None, None, None) == gbs.GBS_OK
+    # a source list with n > 0 but no index array
+    src = gbs._Src(3, None, None, 10)
+    assert lib.gbs_wave_step(fake[0], fake[1], fake[2], fake[3], 1e-3, 10.0, 4, 4, 4, 4, ctypes.byref(src), None,
+                             0, None) == gbs.GBS_EINVAL
+
+
+def test_explicit_tma_choice_checks_alignment(lib):
+    fake = [ctypes.c_void_p(1 << 20), ctypes.c_void_p(2 << 20), ctypes.c_void_p(4 << 20)]
+    opts = gbs._Opts(1, 0, 0, 0)
+    # nx = 6 is not a multiple of 4: the TMA kernel cannot take it
+    rc = lib.gbs_wave_propagate(fake[0], fake[1], fake[2], ctypes.c_float(1e-3), ctypes.c_float(10.0), 6, 4, 4,
+                                4, 3, 0, None, None, ctypes.byref(opts), None)
+    assert rc == gbs.GBS_EALIGN
