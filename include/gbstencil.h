@@ -42,6 +42,7 @@
 #ifndef GBSTENCIL_H
 #define GBSTENCIL_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -59,6 +60,13 @@ typedef enum {
     GBS_ENAN = 7,         /* reserved */
     GBS_EUNSUPPORTED = 8  /* no kernel for this combination */
 } gbs_status;
+
+/* Storage type of wave fields. */
+typedef enum {
+    GBS_F32 = 0,
+    GBS_BF16 = 1,
+    GBS_F16 = 2
+} gbs_dtype;
 
 /* Point sources.  Step n (the step that produces u^{n+1}) adds
  * dt^2 V(x_s)^2 * amp[n*n_src + s] at interior linear index idx[s] for
@@ -134,6 +142,36 @@ gbs_status gbs_wave_propagate(float *u_prev, float *u, const float *vel, float d
                               int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
                               int64_t t0, const gbs_src *src, const gbs_rec *rec,
                               const gbs_opts *opts, void *stream);
+
+/*
+ * Algorithm 1 with the wave fields stored in 16 bits (BF16 or FP16) and all
+ * arithmetic in FP32.  A stored field is code * 2^s with a power-of-two scale
+ * s per field and time level: the step that writes u^{n+1} takes s from
+ * max|u^n| so that the largest |value| sits in [2^7, 2^8) in code units (a
+ * lagged scale; powers of two scale exactly), and records max|u^{n+1}| for
+ * the next step.  Codes are rounded to nearest even.  Sources are added
+ * before rounding.
+ *   u_prev, u     DEVICE FP32 fields (layout as gbs_wave_propagate).  On entry
+ *                 (u^{t0-1}, u^{t0}); they are encoded into the workspace, the
+ *                 steps run on the 16-bit copies, and on return the two newest
+ *                 fields are decoded back with the same parity rule as
+ *                 gbs_wave_propagate (even nsteps: u newest; odd: u_prev newest).
+ *   vel           DEVICE FP32, copied into the workspace at the start.
+ *   storage       GBS_BF16 or GBS_F16.
+ *   work          DEVICE scratch of at least gbs_lp_workspace_bytes(nx, ny, nz)
+ *                 bytes, 256-byte aligned, owned by the caller; its contents on
+ *                 entry do not matter and on return are unspecified.
+ *   src           at most 16 sources (they are fused into the step kernel).
+ * Per step the kernel moves 10 bytes per point (2+2 read, 4 velocity, 2 write)
+ * against 16 for FP32.  Errors: GBS_EINVAL (including a workspace that is too
+ * small or misaligned, or more than 16 sources), GBS_ECUDA.
+ */
+size_t gbs_lp_workspace_bytes(int64_t nx, int64_t ny, int64_t nz);
+gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float *vel, float dt, float h,
+                                 int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                                 int64_t t0, const gbs_src *src, const gbs_rec *rec,
+                                 gbs_dtype storage, void *work, size_t work_bytes,
+                                 const gbs_opts *opts, void *stream);
 
 /*
  * The library's weights of the centred second derivative of order 2R

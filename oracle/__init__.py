@@ -17,6 +17,12 @@ What each function follows (arXiv 2309.04671):
 * :func:`wave_step` / :func:`wave_propagate` -- Eq. 2 and Algorithm 1 with a
   zero (Dirichlet) halo; the source enters as dt^2 V^2 f^n after the stencil
   update (C, ``oracle.c``).
+* :func:`round_to_format`, :func:`lp_scale_exponent`, :func:`lp_encode`,
+  :func:`lp_wave_step` -- wave fields stored in BF16/FP16 with a per-field
+  power-of-two scale (IEEE round-to-nearest-even from the format's
+  definition; the scale rule; one step of Eq. 2 on stored fields).  The
+  paper computes in FP32 (``st.f32``); the 16-bit storage is this library's
+  addition, pinned here against numpy/torch conversions.
 * :func:`err_norms` -- the paper's accuracy metrics (Sec. 11.1: maximum
   absolute error and RMSD against a reference), plus the normwise relative
   maximum and L2 errors.
@@ -253,6 +259,72 @@ def wave_propagate(u_prev, u, vel, dt: float, h: float, halo: int, nsteps: int, 
     if rc != 0:
         raise MemoryError("oracle_wave_propagate could not allocate its work buffers")
     return up, uc, tr
+
+
+# ---------------------------------------------------------------------------
+# 16-bit storage of wave fields: rounding, scale rule, one emulated step
+# ---------------------------------------------------------------------------
+# IEEE 754 binary formats by (significand bits p incl. the hidden bit,
+# minimum normal exponent emin, maximum exponent emax).
+FORMATS = {"bf16": (8, -126, 127), "f16": (11, -14, 15)}
+LP_TARGET = 8   # scaled fields keep max|code| in [2^7, 2^8)
+
+
+def round_to_format(x, fmt: str) -> np.ndarray:
+    """Round float64 values to the nearest value of an IEEE binary format,
+    ties to even, overflow to +-inf (the definition of round-to-nearest-even:
+    the spacing at |x| is 2^(max(floor(log2|x|), emin) - p + 1))."""
+    p, emin, emax = FORMATS[fmt]
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    nz = x != 0
+    _, E = np.frexp(np.abs(x[nz]))          # |x| = f 2^E, f in [0.5, 1): floor(log2|x|) = E - 1
+    e = np.maximum(E - 1, emin)
+    ulp = np.ldexp(1.0, e - p + 1)
+    q = np.rint(x[nz] / ulp) * ulp           # np.rint: round half to even
+    top = np.ldexp(2.0 - 2.0 ** (1 - p), emax)
+    q[np.abs(q) > top] = np.copysign(np.inf, q[np.abs(q) > top])
+    out[nz] = q
+    return out
+
+
+def lp_scale_exponent(m: float) -> int:
+    """Scale exponent s for a field of max |value| m (m an FP32 value):
+    s = E - 8 with 2^(E-1) <= m < 2^E (E = -126 below the FP32 normal range),
+    s = 0 for m = 0 or non-finite, clamped to [-100, 100]."""
+    m = float(m)
+    if not (m > 0.0) or not np.isfinite(m):
+        return 0
+    if m < 2.0 ** -126:
+        E = -126
+    else:
+        E = int(np.frexp(m)[1])
+    return int(min(100, max(-100, E - LP_TARGET)))
+
+
+def lp_encode(x, halo: int, fmt: str):
+    """Store a field in 16 bits: s from max|interior|, codes RN(x 2^-s).
+    Returns (the stored field as float64 = code * 2^s, s); the halo stays zero."""
+    x = _f64(x)
+    h = halo
+    inner = x[h:x.shape[0] - h, h:x.shape[1] - h, h:x.shape[2] - h]
+    s = lp_scale_exponent(np.float32(np.max(np.abs(inner))) if inner.size else 0.0)
+    out = np.zeros_like(x)
+    out[h:x.shape[0] - h, h:x.shape[1] - h, h:x.shape[2] - h] = round_to_format(np.ldexp(inner, -s), fmt) * 2.0 ** s
+    return out, s
+
+
+def lp_wave_step(u_prev_st, u_st, vel, dt: float, h: float, halo: int, fmt: str, **kw):
+    """One step of Eq. 2 on stored (16-bit, scaled) fields: FP64 arithmetic on
+    the stored values, then the result is stored with the scale chosen from
+    max|u^n| (the lagged rule).  Returns (stored u^{n+1} as float64, s)."""
+    nxt, _ = wave_step(u_prev_st, u_st, vel, dt, h, halo, **kw)
+    hh = halo
+    inner_u = _f64(u_st)[hh:-hh, hh:-hh, hh:-hh]
+    s = lp_scale_exponent(np.max(np.abs(inner_u)) if inner_u.size else 0.0)
+    out = np.zeros_like(nxt)
+    out[hh:-hh, hh:-hh, hh:-hh] = round_to_format(np.ldexp(nxt[hh:-hh, hh:-hh, hh:-hh], -s), fmt) * 2.0 ** s
+    return out, s
 
 
 # ---------------------------------------------------------------------------

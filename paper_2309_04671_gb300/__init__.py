@@ -27,8 +27,13 @@ STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4
                 5: "GBS_EUNSTABLE", 6: "GBS_ENOMEM", 7: "GBS_ENAN", 8: "GBS_EUNSUPPORTED"}
 
 # Entry points declared in include/gbstencil.h (checked by the tests).
-EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_fd2_coeffs",
-           "gbs_profile_enable", "gbs_profile_take", "gbs_device_status", "gbs_last_error", "gbs_version")
+EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
+           "gbs_wave_propagate_lp", "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take",
+           "gbs_device_status", "gbs_last_error", "gbs_version")
+
+GBS_F32, GBS_BF16, GBS_F16 = 0, 1, 2
+_STORAGE = {"f32": GBS_F32, "bf16": GBS_BF16, "f16": GBS_F16, torch.float32: GBS_F32,
+            torch.bfloat16: GBS_BF16, torch.float16: GBS_F16}
 
 
 class GbsError(RuntimeError):
@@ -79,6 +84,11 @@ def load() -> ctypes.CDLL:
                                       ctypes.POINTER(_Src), ctypes.POINTER(_Rec), i64, vp]
         lib.gbs_wave_propagate.argtypes = [vp, vp, vp, c_float, c_float, i64, i64, i64, c_int, i64, i64,
                                            ctypes.POINTER(_Src), ctypes.POINTER(_Rec), ctypes.POINTER(_Opts), vp]
+        lib.gbs_lp_workspace_bytes.argtypes = [i64, i64, i64]
+        lib.gbs_lp_workspace_bytes.restype = ctypes.c_size_t
+        lib.gbs_wave_propagate_lp.argtypes = [vp, vp, vp, c_float, c_float, i64, i64, i64, c_int, i64, i64,
+                                              ctypes.POINTER(_Src), ctypes.POINTER(_Rec), c_int, vp, ctypes.c_size_t,
+                                              ctypes.POINTER(_Opts), vp]
         lib.gbs_fd2_coeffs.argtypes = [c_int, fp]
         lib.gbs_profile_enable.argtypes = [c_int]
         lib.gbs_profile_take.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -86,8 +96,8 @@ def load() -> ctypes.CDLL:
         lib.gbs_last_error.restype = ctypes.c_char_p
         lib.gbs_last_error.argtypes = []
         lib.gbs_version.argtypes = []
-        for f in ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_fd2_coeffs",
-                  "gbs_profile_enable", "gbs_profile_take", "gbs_device_status", "gbs_version"):
+        for f in ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_wave_propagate_lp",
+                  "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take", "gbs_device_status", "gbs_version"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -248,6 +258,40 @@ def _wave_propagate_host(u_prev, u, vel, dt, h, halo, nsteps, *, t0, src_idx, sr
         rec_trace.copy_(d_tr, non_blocking=True)
     torch.cuda.current_stream().synchronize()
     return u_prev, u
+
+
+def lp_workspace_bytes(nx: int, ny: int, nz: int) -> int:
+    """Bytes of device scratch gbs_wave_propagate_lp needs for an nx*ny*nz interior."""
+    return int(load().gbs_lp_workspace_bytes(int(nx), int(ny), int(nz)))
+
+
+def lp_workspace(u: torch.Tensor, halo: int) -> torch.Tensor:
+    """A device workspace (uint8, 256-byte aligned) for fields shaped like ``u``."""
+    nx, ny, nz = _dims(u, halo)
+    return torch.empty(lp_workspace_bytes(nx, ny, nz) + 256, dtype=torch.uint8, device=u.device)
+
+
+def wave_propagate_lp(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, dt: float, h: float,
+                      halo: int, nsteps: int, *, storage="bf16", work: Optional[torch.Tensor] = None,
+                      t0: int = 0, src_idx=None, src_amp=None, rec_idx=None, rec_trace=None, tile_y: int = 0,
+                      zchunk: int = 0, use_graph: bool = False, stream=None):
+    """Algorithm 1 with the wave fields stored in BF16 or FP16 (per-field
+    power-of-two scale) and FP32 arithmetic.  FP32 fields in and out; returns
+    (prev, cur) with the same parity rule as :func:`wave_propagate`."""
+    p = [_field(t, n) for t, n in ((u_prev, "u_prev"), (u, "u"), (vel, "vel"))]
+    _same_shape(u, u_prev, vel)
+    nx, ny, nz = _dims(u, halo)
+    if work is None:
+        work = lp_workspace(u, halo)
+    base = work.data_ptr()
+    off = (-base) % 256
+    src = _make_src(src_idx, src_amp)
+    rec = _make_rec(rec_idx, rec_trace)
+    opts = _opts(0, tile_y, zchunk, use_graph)
+    _check(load().gbs_wave_propagate_lp(p[0], p[1], p[2], float(dt), float(h), nx, ny, nz, halo, int(nsteps),
+                                        int(t0), _ptr(src), _ptr(rec), _STORAGE[storage], base + off,
+                                        work.numel() - off, ctypes.byref(opts), _stream(stream)))
+    return (u, u_prev) if nsteps % 2 else (u_prev, u)
 
 
 def device_status(stream=None) -> None:

@@ -57,17 +57,21 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// Tensor map over a padded FP32 field (px x py x pz), box bw x bh x 1.
-gbs_status make_map(CUtensorMap *m, const float *base, const Grid &g, int bw, int bh)
+// Tensor map over a padded field (px x py x pz) of the given storage type, box bw x bh x 1.
+gbs_status make_map(CUtensorMap *m, const void *base, const Grid &g, int bw, int bh, gbs_dtype dt = GBS_F32)
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc)
         return fail(GBS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const int es = dt == GBS_F32 ? 4 : 2;
+    const CUtensorMapDataType ty = dt == GBS_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dt == GBS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)(g.nz + 2 * g.halo)};
-    const cuuint64_t strides[2] = {(cuuint64_t)g.px * 4, (cuuint64_t)(g.px * g.py) * 4};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.px * es, (cuuint64_t)(g.px * g.py) * es};
     const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+    CUresult r = enc(m, ty, 3, const_cast<void *>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
@@ -202,53 +206,144 @@ void prof_end(cudaEvent_t e0, cudaStream_t st)
 }
 
 // One leapfrog step u_next = 2u - u_prev + (V dt)^2 (lap u + f): the fused
-// stencil/update kernel, then sources, then receivers.
+// stencil/update kernel (with up to kMaxFusedSrc sources added in its
+// epilogue), else a separate injection kernel, then receivers.
 struct StepPlan {
-    int kernel;       // 1 TMA, 2 plain loads
+    int kernel;           // 1 TMA, 2 plain loads
     int tile_y;
     int zchunk;
+    gbs_dtype storage;    // of u, u_prev, u_next (vel is FP32)
     TmaPlan tma;
 };
 
-gbs_status plan_step(StepPlan *sp, const Grid &g, const float *u_prev, const float *u, const float *vel,
-                     int kernel, int tile_y, int zchunk)
+gbs_status plan_step(StepPlan *sp, const Grid &g, const void *u_prev, const void *u, const float *vel,
+                     int kernel, int tile_y, int zchunk, gbs_dtype storage = GBS_F32)
 {
     sp->kernel = kernel;
     sp->tile_y = tile_y;
     sp->zchunk = zchunk;
+    sp->storage = storage;
     if (kernel == 1) {
-        gbs_status s = make_map(&sp->tma.u, u, g, 64 + 8, tile_y + 8);
+        gbs_status s = make_map(&sp->tma.u, u, g, 64 + 8, tile_y + 8, storage);
+        if (s == GBS_OK)   // 16-bit u_prev boxes carry 4 extra columns each side (16-byte aligned start)
+            s = make_map(&sp->tma.prev, u_prev, g, storage == GBS_F32 ? 64 : 72, tile_y, storage);
         if (s == GBS_OK)
-            s = make_map(&sp->tma.prev, u_prev, g, 64, tile_y);
-        if (s == GBS_OK)
-            s = make_map(&sp->tma.vel, vel, g, 64, tile_y);
+            s = make_map(&sp->tma.vel, vel, g, 64, tile_y, GBS_F32);
         return s;
     }
     return GBS_OK;
 }
 
-gbs_status run_step(const StepPlan &sp, const Grid &g, const float *u_prev, const float *u, float *u_next,
-                    const float *vel, float dt, float h, const gbs_src *src, const gbs_rec *rec, int64_t step,
-                    cudaStream_t st)
+// t = the time level of u (the step writes u^{t+1}); meta = 16-bit state or null;
+// gidx = the grid interior linear indices refer to (the caller's)
+gbs_status run_step(const StepPlan &sp, const Grid &g, const void *u_prev, const void *u, void *u_next,
+                    const float *vel, float dt, float h, const gbs_src *src, const gbs_rec *rec, int64_t t,
+                    int *meta, cudaStream_t st, const Grid *gidx = nullptr)
 {
-    const Coeffs cf = wave_coeffs();
+    const Grid &gx = gidx ? *gidx : g;
     const float s = (float)((double)dt / (double)h);
+    const bool has_src = src && src->n > 0 && t < src->nt;
+    const bool fused = sp.kernel == 1 && (!src || src->n <= kMaxFusedSrc);
     cudaError_t e;
     cudaEvent_t e0 = prof_begin(st);
     if (sp.kernel == 1) {
-        e = launch_tma(4, kWave, sp.tile_y, g, sp.tma, u_next, cf, s, sp.zchunk, st);
+        StepParams p;
+        memset(&p, 0, sizeof(p));
+        p.g = g;
+        p.out = u_next;
+        p.cf = wave_coeffs();
+        p.s = s;
+        p.dt = dt;
+        p.zchunk = sp.zchunk;
+        p.inx = gx.nx;
+        p.iny = gx.ny;
+        if (fused && has_src) {
+            p.src_idx = src->idx;
+            p.src_amp = src->amp + t * src->n;
+            p.nsrc = (int)src->n;
+        }
+        if (meta) {
+            p.meta = meta;
+            p.slot_u = (int)(t % kMetaSlots);
+            p.slot_next = (int)((t + 1) % kMetaSlots);
+            p.slot_prev = (int)((t + 2) % kMetaSlots);
+        }
+        e = launch_tma(4, kWave, sp.tile_y, sp.storage, sp.tma, p, st);
     } else {
-        WaveArgs w{u_prev, vel, s};
-        e = launch_generic(4, kWave, g, u, u_next, cf, w, sp.zchunk, st);
+        WaveArgs w{static_cast<const float *>(u_prev), vel, s};
+        e = launch_generic(4, kWave, g, static_cast<const float *>(u), static_cast<float *>(u_next), wave_coeffs(), w,
+                           sp.zchunk, st);
     }
     prof_end(e0, st);
     if (e != cudaSuccess)
         return cuda_fail(e, "wave step launch");
-    if ((e = launch_inject(g, u_next, vel, dt, src, step, st)) != cudaSuccess)
+    if (!fused && (e = launch_inject(g, static_cast<float *>(u_next), vel, dt, src, t, st)) != cudaSuccess)
         return cuda_fail(e, "source injection launch");
-    if ((e = launch_record(g, u_next, rec, step, st)) != cudaSuccess)
+    if (meta)
+        e = launch_lp_record(sp.storage, gx, g, u_next, meta + ((t + 1) % kMetaSlots) * kMetaInts, rec, t, st);
+    else
+        e = launch_record(g, static_cast<const float *>(u_next), rec, t, st);
+    if (e != cudaSuccess)
         return cuda_fail(e, "receiver launch");
     return GBS_OK;
+}
+
+// Capture the work `enqueue` puts on `st` into a graph and launch it once.
+template <typename F>
+gbs_status run_captured(cudaStream_t st, F &&enqueue)
+{
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    gbs_status r = enqueue();
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(st, &gr);
+    if (r != GBS_OK) {
+        if (gr)
+            cudaGraphDestroy(gr);
+        return r;
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGraphInstantiate");
+    e = cudaGraphLaunch(ex, st);
+    cudaGraphExecDestroy(ex);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGraphLaunch");
+    return GBS_OK;
+}
+
+// Workspace of the 16-bit path: two 16-bit fields and an FP32 copy of the
+// velocity in the internal layout (halo 4, row pitch a multiple of 8
+// elements so every TMA box row starts on 16 bytes), then the scale state.
+struct LpLayout {
+    Grid g;
+    size_t off_a, off_b, off_vel, off_meta, meta_bytes, total;
+};
+
+size_t round256(size_t v) { return (v + 255) / 256 * 256; }
+
+LpLayout lp_layout(int64_t nx, int64_t ny, int64_t nz)
+{
+    LpLayout L;
+    L.g.nx = (nx + 3) / 4 * 4;   // dead columns up to a multiple of 4 (zero field, zero velocity)
+    L.g.ny = ny;
+    L.g.nz = nz;
+    L.g.halo = 4;
+    L.g.px = (L.g.nx + 8 + 7) / 8 * 8;
+    L.g.py = ny + 8;
+    const size_t n = (size_t)L.g.px * (size_t)L.g.py * (size_t)(nz + 8);
+    L.off_a = 0;
+    L.off_b = round256(n * 2);
+    L.off_vel = L.off_b + round256(n * 2);
+    L.off_meta = L.off_vel + round256(n * 4);
+    L.meta_bytes = round256(kMetaSlots * kMetaInts * sizeof(int));
+    L.total = L.off_meta + L.meta_bytes;
+    return L;
 }
 
 gbs_status check_src_rec(const gbs_src *src, const gbs_rec *rec)
@@ -321,7 +416,12 @@ extern "C" gbs_status gbs_stencil_apply(const float *in, float *out, int64_t nx,
             return s;
         plan.prev = plan.u;
         plan.vel = plan.u;
-        e = launch_tma(radius, kStencil, 16, g, plan, out, cf, 0.f, 0, st);
+        StepParams p;
+        memset(&p, 0, sizeof(p));
+        p.g = g;
+        p.out = out;
+        p.cf = cf;
+        e = launch_tma(radius, kStencil, 16, GBS_F32, plan, p, st);
     } else {
         WaveArgs w{nullptr, nullptr, 0.f};
         e = launch_generic(radius, kStencil, g, in, out, cf, w, 0, st);
@@ -351,7 +451,7 @@ extern "C" gbs_status gbs_wave_step(const float *u_prev, const float *u, float *
     StepPlan sp;
     if ((s = plan_step(&sp, g, u_prev, u, vel, tma_ok ? 1 : 2, 16, 0)) != GBS_OK)
         return s;
-    return run_step(sp, g, u_prev, u, u_next, vel, dt, h, src, rec, step, static_cast<cudaStream_t>(stream));
+    return run_step(sp, g, u_prev, u, u_next, vel, dt, h, src, rec, step, nullptr, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" gbs_status gbs_wave_propagate(float *u_prev, float *u, const float *vel, float dt, float h,
@@ -384,7 +484,7 @@ extern "C" gbs_status gbs_wave_propagate(float *u_prev, float *u, const float *v
         return s;
     const int tile_y = pick_tile_y(opts);
     const int zchunk = (opts && opts->zchunk > 0) ? opts->zchunk
-                       : kernel == 1                ? tma_default_zchunk(4, kWave, tile_y, g)
+                       : kernel == 1                ? tma_default_zchunk(4, kWave, tile_y, GBS_F32, g)
                                                     : 64;
     // the two parities of the ping-pong: plan[0] reads u (B) and writes u_prev (A), plan[1] the reverse
     float *buf[2] = {u_prev, u};
@@ -400,41 +500,112 @@ extern "C" gbs_status gbs_wave_propagate(float *u_prev, float *u, const float *v
         for (int64_t q = 0; q < nsteps; ++q) {
             const int par = (int)(q & 1);
             float *prev = buf[par], *cur = buf[par ^ 1];
-            gbs_status r = run_step(plan[par], g, prev, cur, prev, vel, dt, h, src, rec, t0 + q, st);
+            gbs_status r = run_step(plan[par], g, prev, cur, prev, vel, dt, h, src, rec, t0 + q, nullptr, st);
             if (r != GBS_OK)
                 return r;
         }
         return GBS_OK;
     };
-    if (!graph)
-        return enqueue();
-
-    // Capture the step loop once and replay it as one graph launch.  A first
-    // uncaptured launch of zero steps is not needed: kernel attributes are
-    // set outside the capture by the launchers on first use.
-    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "cudaStreamBeginCapture");
-    gbs_status r = enqueue();
-    cudaGraph_t gr = nullptr;
-    e = cudaStreamEndCapture(st, &gr);
-    if (r != GBS_OK) {
-        if (gr)
-            cudaGraphDestroy(gr);
-        return r;
+    if (kernel == 1 && graph) {
+        cudaError_t e = tma_prepare_wave(GBS_F32, tile_y);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "kernel attributes");
     }
-    if (e != cudaSuccess)
-        return cuda_fail(e, "cudaStreamEndCapture");
-    cudaGraphExec_t ex = nullptr;
-    e = cudaGraphInstantiate(&ex, gr, 0);
-    cudaGraphDestroy(gr);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "cudaGraphInstantiate");
-    e = cudaGraphLaunch(ex, st);
-    cudaGraphExecDestroy(ex);
-    if (e != cudaSuccess)
-        return cuda_fail(e, "cudaGraphLaunch");
-    return GBS_OK;
+    return graph ? run_captured(st, enqueue) : enqueue();
+}
+
+extern "C" size_t gbs_lp_workspace_bytes(int64_t nx, int64_t ny, int64_t nz)
+{
+    if (nx < 0 || ny < 0 || nz < 0)
+        return 0;
+    const LpLayout L = lp_layout(nx, ny, nz);
+    return L.total;
+}
+
+extern "C" gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float *vel, float dt, float h,
+                                            int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                                            int64_t t0, const gbs_src *src, const gbs_rec *rec,
+                                            gbs_dtype storage, void *work, size_t work_bytes,
+                                            const gbs_opts *opts, void *stream)
+{
+    t_err[0] = 0;
+    gbs_status s = check_dims(nx, ny, nz, halo);
+    if (s != GBS_OK)
+        return s;
+    if (storage != GBS_BF16 && storage != GBS_F16)
+        return fail(GBS_EINVAL, "storage must be GBS_BF16 or GBS_F16");
+    if (nsteps < 0 || t0 < 0)
+        return fail(GBS_EINVAL, "nsteps and t0 must be >= 0");
+    if ((s = check_src_rec(src, rec)) != GBS_OK)
+        return s;
+    if (src && src->n > kMaxFusedSrc)
+        return fail(GBS_EINVAL, "16-bit storage takes at most %d sources (got %lld)", kMaxFusedSrc,
+                    (long long)src->n);
+    if (opts && (opts->zchunk < 0 || opts->kernel == 2))
+        return fail(GBS_EINVAL, "16-bit storage runs the TMA kernel only; zchunk must be >= 0");
+    if (nx == 0 || ny == 0 || nz == 0 || nsteps == 0)
+        return GBS_OK;
+    const Grid gc = dense_grid(nx, ny, nz, halo);
+    if (u_prev == u)
+        return fail(GBS_EINVAL, "u_prev and u are the same buffer");
+    if ((s = check_wave_fields(gc, u_prev, u, u_prev, vel, dt, h)) != GBS_OK)
+        return s;
+    if (overlap(u_prev, u, field_elems(gc)))
+        return fail(GBS_EINVAL, "u_prev and u overlap");
+    const LpLayout L = lp_layout(nx, ny, nz);
+    if (!work || work_bytes < L.total)
+        return fail(GBS_EINVAL, "workspace of %zu bytes needed (got %zu)", L.total, work_bytes);
+    if ((reinterpret_cast<uintptr_t>(work) & 255u) != 0)
+        return fail(GBS_EINVAL, "workspace must be 256-byte aligned");
+    unsigned char *w = static_cast<unsigned char *>(work);
+    void *buf[2] = {w + L.off_a, w + L.off_b};   // 16-bit copies of u_prev (A) and u (B)
+    float *vel_i = reinterpret_cast<float *>(w + L.off_vel);
+    int *meta = reinterpret_cast<int *>(w + L.off_meta);
+    const Grid &gi = L.g;
+    const int tile_y = pick_tile_y(opts);
+    const int zchunk = (opts && opts->zchunk > 0) ? opts->zchunk : tma_default_zchunk(4, kWave, tile_y, storage, gi);
+    StepPlan plan[2];
+    if ((s = plan_step(&plan[0], gi, buf[0], buf[1], vel_i, 1, tile_y, zchunk, storage)) != GBS_OK)
+        return s;
+    if ((s = plan_step(&plan[1], gi, buf[1], buf[0], vel_i, 1, tile_y, zchunk, storage)) != GBS_OK)
+        return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool graph = opts && opts->use_graph && st != nullptr;
+    const int slot_prev0 = (int)((t0 + 2) % kMetaSlots), slot_u0 = (int)(t0 % kMetaSlots);
+
+    auto enqueue = [&]() -> gbs_status {
+        cudaError_t e = cudaMemsetAsync(w, 0, L.off_meta + L.meta_bytes, st);
+        if (e == cudaSuccess)
+            e = launch_copy_f32(gc, vel, gi, vel_i, st);
+        if (e == cudaSuccess)
+            e = launch_lp_encode(storage, gc, u_prev, gi, buf[0], meta + slot_prev0 * kMetaInts, st);
+        if (e == cudaSuccess)
+            e = launch_lp_encode(storage, gc, u, gi, buf[1], meta + slot_u0 * kMetaInts, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "16-bit encode");
+        for (int64_t q = 0; q < nsteps; ++q) {
+            const int par = (int)(q & 1);
+            void *prev = buf[par], *cur = buf[par ^ 1];
+            gbs_status r = run_step(plan[par], gi, prev, cur, prev, vel_i, dt, h, src, rec, t0 + q, meta, st, &gc);
+            if (r != GBS_OK)
+                return r;
+        }
+        // A holds time t0+nsteps when nsteps is odd, else t0+nsteps-1; B the other
+        const int64_t tn = t0 + nsteps;
+        const int64_t ta = (nsteps & 1) ? tn : tn - 1, tb = (nsteps & 1) ? tn - 1 : tn;
+        e = launch_lp_decode(storage, gi, buf[0], meta + (ta % kMetaSlots) * kMetaInts, gc, u_prev, st);
+        if (e == cudaSuccess)
+            e = launch_lp_decode(storage, gi, buf[1], meta + (tb % kMetaSlots) * kMetaInts, gc, u, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "16-bit decode");
+        return GBS_OK;
+    };
+    if (graph) {
+        cudaError_t e = tma_prepare_wave(storage, tile_y);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "kernel attributes");
+    }
+    return graph ? run_captured(st, enqueue) : enqueue();
 }
 
 extern "C" gbs_status gbs_fd2_coeffs(int radius, float *out)

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/gbstencil.h"
 
 namespace gbs {
@@ -42,6 +44,60 @@ struct WaveArgs {
     float s;               // dt / h
 };
 
+// Point sources added inside the step kernel (at most this many per call;
+// longer lists go through the separate injection kernel).
+constexpr int kMaxFusedSrc = 16;
+
+// State of fields stored in 16 bits (one slot per time level, three slots
+// in rotation, kMetaInts ints each): the scale exponent s (field = code *
+// 2^s), the FP32 bits of max |stored value|, and a scratch word used while
+// encoding.
+constexpr int kMetaInts = 4;
+constexpr int kMetaScale = 0;
+constexpr int kMetaMax = 1;
+constexpr int kMetaTmp = 2;
+constexpr int kMetaSlots = 3;
+// Codes are scaled so that the largest |value| of the field lands in
+// [2^(kLpTarget-1), 2^kLpTarget): 2^8 below the FP16 maximum, far above its
+// subnormals.
+constexpr int kLpTarget = 8;
+
+// 2^k for integer k in [-126, 127], built from the exponent field.
+__device__ __forceinline__ float pow2f(int k)
+{
+    return __uint_as_float((unsigned)(k + 127) << 23);
+}
+
+// Scale exponent for a field whose largest |value| is m: s = E - kLpTarget
+// with 2^(E-1) <= m < 2^E (E = -126 for m below the FP32 normal range), s = 0
+// for m = 0 or a non-finite m, clamped to [-100, 100].
+__device__ __forceinline__ int lp_scale_exponent(float m)
+{
+    if (!(m > 0.f) || !(m <= 3.4028234663852886e38f))
+        return 0;
+    const int ex = (int)((__float_as_uint(m) >> 23) & 0xffu);
+    const int E = ex == 0 ? -126 : ex - 126;
+    const int s = E - kLpTarget;
+    return s < -100 ? -100 : (s > 100 ? 100 : s);
+}
+
+// Arguments of one launch of the TMA kernel.
+struct StepParams {
+    Grid g;                    // geometry of u, u_prev, vel and out
+    void *out;                 // storage type of the launch
+    Coeffs cf;
+    float s;                   // dt / h
+    float dt;
+    int zchunk;                // planes per CTA (0 = default)
+    int tiles_x;               // set by the launcher
+    const int64_t *src_idx;    // fused sources: interior linear indices
+    const float *src_amp;      // this step's row f^n (nullptr: no injection this step)
+    int nsrc;                  // <= kMaxFusedSrc
+    int *meta;                 // 16-bit storage state (kMetaSlots x kMetaInts), else nullptr
+    int slot_prev, slot_u, slot_next;
+    int64_t inx, iny;          // interior sizes that interior linear indices refer to
+};
+
 // Launchers (return a cudaError_t of the launch).
 cudaError_t launch_generic(int radius, Mode mode, const Grid &g, const float *in, float *out,
                            const Coeffs &cf, const WaveArgs &w, int zchunk, cudaStream_t st);
@@ -49,11 +105,25 @@ cudaError_t launch_generic(int radius, Mode mode, const Grid &g, const float *in
 struct TmaPlan {
     CUtensorMap u;       // box (64+8) x (TY+2R) x 1 over the padded field
     CUtensorMap prev;    // box 64 x TY x 1 (wave mode)
-    CUtensorMap vel;     // box 64 x TY x 1 (wave mode)
+    CUtensorMap vel;     // box 64 x TY x 1 (wave mode), FP32
 };
-cudaError_t launch_tma(int radius, Mode mode, int tile_y, const Grid &g, const TmaPlan &plan,
-                       float *out, const Coeffs &cf, float s, int zchunk, cudaStream_t st);
-int tma_default_zchunk(int radius, Mode mode, int tile_y, const Grid &g);
+cudaError_t launch_tma(int radius, Mode mode, int tile_y, gbs_dtype storage, const TmaPlan &plan,
+                       const StepParams &p, cudaStream_t st);
+int tma_default_zchunk(int radius, Mode mode, int tile_y, gbs_dtype storage, const Grid &g);
+// Sets the wave kernel's shared-memory attribute (call before stream capture).
+cudaError_t tma_prepare_wave(gbs_dtype storage, int tile_y);
+
+// 16-bit storage helpers (k_lp.cu).  Grids: `gc` the caller's FP32 layout,
+// `gi` the internal 16-bit layout (gi.nx = nx rounded up to 4: the extra
+// "dead" columns hold zero fields and zero velocity).  Loops run over the
+// caller's interior; interior linear indices refer to the caller's sizes.
+cudaError_t launch_lp_encode(gbs_dtype storage, const Grid &gc, const float *x, const Grid &gi, void *q,
+                             int *meta_slot, cudaStream_t st);
+cudaError_t launch_lp_decode(gbs_dtype storage, const Grid &gi, const void *q, const int *meta_slot,
+                             const Grid &gc, float *x, cudaStream_t st);
+cudaError_t launch_copy_f32(const Grid &gc, const float *x, const Grid &gi, float *y, cudaStream_t st);
+cudaError_t launch_lp_record(gbs_dtype storage, const Grid &gc, const Grid &gi, const void *q,
+                             const int *meta_slot, const gbs_rec *rec, int64_t step, cudaStream_t st);
 
 // Each kernel translation unit keeps its own device status word; these read
 // it (after synchronising `st`) and reset it to GBS_OK.
@@ -89,6 +159,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
+}
+
+// Plain arrive (count 1) with release semantics for the CTA.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)

@@ -1,5 +1,6 @@
 // TMA-staged 2.5D streaming kernel for the star stencil (Eq. 3) and the
-// fused leapfrog step (Eq. 2) on sm_103a.
+// fused leapfrog step (Eq. 2) on sm_103a, for FP32 fields and for fields
+// stored in BF16 / FP16 with a per-field power-of-two scale.
 //
 // Work decomposition.  A CTA owns a 64 x TY tile of the interior xy plane
 // and streams a chunk of z planes (the paper's 2.5D streaming templates,
@@ -9,18 +10,36 @@
 // shares with its neighbours are served from L2.
 //
 // Data movement.  One thread issues 3D tiled TMA loads
-// (cp.async.bulk.tensor): for each plane q the (64+8) x (TY+2R) box of u
-// around the tile into a ring of S shared-memory stages, and, in wave mode,
-// the 64 x TY interior tiles of u_prev and vel into a second ring.  Each
-// stage completes on its own mbarrier (expect_tx), so the loads of the next
+// (cp.async.bulk.tensor): for each plane the (64+8) x (TY+2R) box of u
+// around the tile into a ring of shared-memory stages, and, in wave mode,
+// the interior tiles of u_prev and vel into a second ring.  Each stage
+// completes on its own mbarrier (expect_tx), so the loads of the next
 // planes run while the current plane is computed.  TMA zero-fills outside
 // the array; those values only reach outputs that are not stored.
 //
-// Arithmetic.  A thread owns 4 consecutive x points (one float4) in VY = 2
-// rows.  The 2R+1 values of its points along z live in a register queue
-// (the paper's "--mem-type reg" choice for star shapes); x and y neighbours
-// come from the staged plane with 16-byte shared loads.  The epilogue writes
-// float4s straight to global memory (the `f4` template's vector stores).
+// Arithmetic.  A thread owns 4 consecutive x points in VY = 2 rows.  The
+// 2R+1 values of its points along z live in a register queue (the paper's
+// "--mem-type reg" choice for star shapes); x and y neighbours come from the
+// staged plane with vector shared loads.  All arithmetic is FP32, issued as
+// packed f32x2 operations (two points per instruction).  The epilogue writes
+// 4 points per vector store (the `f4` template's vector stores).
+//
+// Sources.  Up to kMaxFusedSrc point sources are added in the epilogue by
+// the thread that owns the cell, after the stencil update (Algorithm 1) and
+// before the value is stored (and, for 16-bit fields, rounded).
+//
+// 16-bit storage.  A stored field is q * 2^s with q a BF16/FP16 code and s
+// an integer kept in a small device state array (one slot per time level,
+// three slots in rotation).  Each plane is converted once to FP32 in shared
+// memory (owners convert their own points, all threads share the halo), the
+// stencil runs on codes, and the update in code units of the output is
+//   q^{n+1} = (V s)^2 k_u lap(q_u) + 2 k_u q_u - k_p q_p + k_o (V dt)^2 f
+// with k_u = 2^(s_u - s_next), k_p = 2^(s_p - s_next), k_o = 2^-s_next; it
+// is rounded to nearest even.  s_next comes from max |u^n| recorded when
+// u^n was written (a lagged scale); the kernel records max|u^{n+1}|.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "gbs_internal.cuh"
 
 namespace gbs {
@@ -28,56 +47,218 @@ namespace {
 
 __device__ unsigned g_status_tma = 0;
 
-constexpr int kTX = 64;   // tile width (points); 16 threads x float4
-constexpr int kVY = 2;    // rows per thread
+constexpr int kTX = 64;     // tile width (points); 16 threads x 4 points
+constexpr int kVY = 2;      // rows per thread
+constexpr int kUnroll = 2;  // planes per iteration of the z loop (queue shifted once per iteration)
 
-template <int R, int MODE, int TY>
+template <typename T>
+struct Storage {
+    static constexpr bool kLow = !std::is_same<T, float>::value;
+};
+
+template <int R, int MODE, int TY, typename T>
 struct Cfg {
+    static constexpr bool LOW = Storage<T>::kLow;
+    static constexpr int ES = (int)sizeof(T);
     static constexpr int NTX = kTX / 4;
     static constexpr int NTY = TY / kVY;
     static constexpr int NT = NTX * NTY;
-    static constexpr int BW = kTX + 8;                 // x: 4-wide halo each side (16 B aligned)
+    // warps synchronise (one CTA barrier) after every BAR_EVERY planes; the
+    // barrier releases the stages of those planes and thread 0 refills them
+    static constexpr int BAR_EVERY = LOW ? 1 : kUnroll;
+    static constexpr int BW = kTX + 8;                 // x: 4-wide halo each side
     static constexpr int BH = TY + 2 * R;
-    static constexpr int S = R + 4;                    // u ring: planes k..k+R resident + 3 ahead
-    static constexpr int SP = 4;                       // u_prev/vel ring
-    static constexpr int U_FLOATS = BW * BH;
-    static constexpr int U_STRIDE = (U_FLOATS * 4 + 127) / 128 * 32;   // floats, 128 B multiple
-    static constexpr int PV_FLOATS = kTX * TY;
-    static constexpr size_t SMEM_U = (size_t)S * U_STRIDE * 4;
-    static constexpr size_t SMEM_PV = MODE == kWave ? (size_t)SP * 2 * PV_FLOATS * 4 : 0;
-    static constexpr size_t SMEM = SMEM_U + SMEM_PV + (S + SP) * 8;
-    static constexpr int MIN_BLOCKS = NT <= 128 ? 2 : 1;
+    // TMA landing ring of u boxes (storage type).  FP32: computed on in place,
+    // planes k..k+R resident + 4 ahead.  16-bit: converted on arrival, 3 ahead.
+    // Each stage completes on its own mbarrier (expect_tx).
+    static constexpr int SL = LOW ? 4 : R + 5;
+    static constexpr int L_BYTES = BW * BH * ES;
+    static constexpr int L_STRIDE = (L_BYTES + 127) / 128 * 128;
+    // 16-bit: FP32 copies of the last R+1 stencil-centre planes
+    static constexpr int SF = LOW ? R + 1 : 0;
+    static constexpr int F_STRIDE = (BW * BH * 4 + 127) / 128 * 128;
+    // u_prev tile (storage type).  Its box must start on 16 bytes: FP32 at
+    // the tile's first interior column (halo % 4 == 0), 16-bit 4 columns
+    // earlier (the internal layout has halo 4 and rows padded to 8 elements),
+    // so 16-bit boxes are 72 wide and read at column offset 4.
+    static constexpr int PVU_X0 = LOW ? 4 : 0;
+    static constexpr int PVU_W = kTX + 2 * PVU_X0;
+    static constexpr int PVU_BYTES = PVU_W * TY * ES;
+    static constexpr int PVV_BYTES = kTX * TY * 4;     // vel tile (FP32)
+    static constexpr int PV_STRIDE = PVU_BYTES + PVV_BYTES;
+    static constexpr int SP = LOW ? 4 : 5;
+    static constexpr size_t SMEM_L = (size_t)SL * L_STRIDE;
+    static constexpr size_t SMEM_F = (size_t)SF * F_STRIDE;
+    static constexpr size_t SMEM_PV = MODE == kWave ? (size_t)SP * PV_STRIDE : 0;
+    static constexpr size_t SMEM = SMEM_L + SMEM_F + SMEM_PV + (SL + SP) * 8;
+    static constexpr int MIN_BLOCKS = NT > 128 ? 1 : (LOW ? 3 : 2);
+    // halo groups of 4 elements converted by all threads (16-bit): 2 side
+    // groups per row and 16 groups per top/bottom halo row
+    static constexpr int HALO_GROUPS = 2 * BH + 16 * 2 * R;
 };
 
-__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+// ---- packed FP32 pairs (f32x2) ----
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2 lo(const float4 &v) { return pk(v.x, v.y); }
+// global store of 4 FP32 values held as two packed pairs (no repacking moves)
+__device__ __forceinline__ void st_pairs(float *p, f2 a, f2 b)
+{
+    asm volatile("st.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ f2 hi(const float4 &v) { return pk(v.z, v.w); }
+
+// ---- 4 consecutive values of a staged tile as floats ----
+__device__ __forceinline__ float2 cvt2(unsigned u, const __nv_bfloat16 *)
+{
+    // a BF16 is the upper half of the FP32 with the same value
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+__device__ __forceinline__ float2 cvt2(unsigned u, const __half *)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(&u));
+}
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+template <typename T>
+__device__ __forceinline__ float4 ld4(const T *p)
+{
+    const uint2 raw = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = cvt2(raw.x, (const T *)nullptr), b = cvt2(raw.y, (const T *)nullptr);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Store 4 values, rounded to nearest-even for the 16-bit types.
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ void st4(__nv_bfloat16 *p, float4 v)
+{
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 raw;
+    raw.x = *reinterpret_cast<const unsigned *>(&a);
+    raw.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = raw;
+}
+__device__ __forceinline__ void st4(__half *p, float4 v)
+{
+    const __half2 a = __floats2half2_rn(v.x, v.y);
+    const __half2 b = __floats2half2_rn(v.z, v.w);
+    uint2 raw;
+    raw.x = *reinterpret_cast<const unsigned *>(&a);
+    raw.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = raw;
+}
+
+// The value a float takes once rounded to the storage type.
+__device__ __forceinline__ float rounded(float v, float *) { return v; }
+__device__ __forceinline__ float rounded(float v, __nv_bfloat16 *) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float rounded(float v, __half *) { return __half2float(__float2half_rn(v)); }
+
 __device__ __forceinline__ float at(const float4 &v, int e)
 {
     return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
 }
-
-template <int R, int MODE, int TY>
-__global__ void __launch_bounds__(Cfg<R, MODE, TY>::NT, Cfg<R, MODE, TY>::MIN_BLOCKS)
-    k_tma(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_prev,
-          const __grid_constant__ CUtensorMap tm_vel, const Grid g, float *out, const Coeffs cf,
-          const float s, const int zchunk, const int tiles_x)
+__device__ __forceinline__ void add_at(float4 &v, int e, float a)
 {
-    using C = Cfg<R, MODE, TY>;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    float *ring = reinterpret_cast<float *>(smem);
-    float *pv = reinterpret_cast<float *>(smem + C::SMEM_U);
-    uint64_t *bar_u = reinterpret_cast<uint64_t *>(smem + C::SMEM_U + C::SMEM_PV);
-    uint64_t *bar_pv = bar_u + C::S;
+    if (e == 0) v.x += a;
+    else if (e == 1) v.y += a;
+    else if (e == 2) v.z += a;
+    else v.w += a;
+}
 
+// Calls f(integral_constant<I>) for I = B..E-1 in order while it returns true.
+template <int B, int E, typename F>
+__device__ __forceinline__ bool static_for(F &&f)
+{
+    if constexpr (B < E) {
+        if (!f(std::integral_constant<int, B>{}))
+            return false;
+        return static_for<B + 1, E>(f);
+    }
+    return true;
+}
+
+// Packed x-neighbour pair starting at window index i (w = [lf | cen | rt]).
+__device__ __forceinline__ f2 xpair(const float4 &lf, const float4 &cen, const float4 &rt, int i)
+{
+    const float w[12] = {lf.x, lf.y, lf.z, lf.w, cen.x, cen.y, cen.z, cen.w, rt.x, rt.y, rt.z, rt.w};
+    return pk(w[i], w[i + 1]);
+}
+
+template <int R, int MODE, int TY, typename T>
+__global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::MIN_BLOCKS)
+    k_tma(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_prev,
+          const __grid_constant__ CUtensorMap tm_vel, const StepParams p)
+{
+    using C = Cfg<R, MODE, TY, T>;
+    constexpr bool kLow = C::LOW;
+    constexpr int Q = 2 * R + 1;               // z-queue length
+    constexpr int U = kUnroll;
+    constexpr int NCW = C::NT / 32;            // warps per CTA
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *land = smem;
+    float *f32ring = reinterpret_cast<float *>(smem + C::SMEM_L);
+    unsigned char *pv = smem + C::SMEM_L + C::SMEM_F;
+    uint64_t *full_u = reinterpret_cast<uint64_t *>(smem + C::SMEM_L + C::SMEM_F + C::SMEM_PV);
+    uint64_t *full_pv = full_u + C::SL;
+    __shared__ int s_nsrc;
+    __shared__ int s_src_x[kMaxFusedSrc], s_src_y[kMaxFusedSrc], s_src_z[kMaxFusedSrc];
+    __shared__ float s_src_f[kMaxFusedSrc];
+    __shared__ float s_red[C::NT / 32];
+
+    const Grid &g = p.g;
     const int tid = threadIdx.x;
     const int tx = tid % C::NTX, ty = tid / C::NTX;
-    const int64_t tx0 = (int64_t)(blockIdx.x % tiles_x) * kTX;
-    const int64_t ty0 = (int64_t)(blockIdx.x / tiles_x) * TY;
-    const int64_t z0 = (int64_t)blockIdx.y * zchunk;
-    const int64_t z1 = min(z0 + (int64_t)zchunk, g.nz);
+    const int64_t tx0 = (int64_t)(blockIdx.x % p.tiles_x) * kTX;
+    const int64_t ty0 = (int64_t)(blockIdx.x / p.tiles_x) * TY;
+    const int z0 = blockIdx.y * p.zchunk;
+    const int z1 = (int)min((int64_t)z0 + p.zchunk, g.nz);
+    const int nzc = z1 - z0;                   // output planes of this CTA
     const int H = g.halo;
-    const int64_t pfirst = z0 - R;            // first u plane streamed
-    const int64_t pend = z1 + R;              // one past the last
-    const int64_t nplanes = pend - pfirst;
+    const int pfirst = z0 - R;                 // first u plane streamed
+    const int nplanes = nzc + 2 * R;
+
+    // Every TMA box must start on a 16-byte boundary in x (a misaligned
+    // tiled copy is an illegal instruction).  The host only launches shapes
+    // that satisfy this; a CTA that would break it records GBS_EALIGN and
+    // returns before issuing any copy.
+    {
+        const int64_t xu = (H + tx0 - 4) * C::ES, xp = (H + tx0 - C::PVU_X0) * C::ES, xv = (H + tx0) * 4;
+        if ((xu & 15) != 0 || (MODE == kWave && ((xp & 15) != 0 || (xv & 15) != 0))) {
+            if (tid == 0)
+                atomicCAS(&g_status_tma, 0u, (unsigned)GBS_EALIGN);
+            return;
+        }
+    }
 
     if (tid == 0) {
         prefetch_tmap(&tm_u);
@@ -85,217 +266,452 @@ __global__ void __launch_bounds__(Cfg<R, MODE, TY>::NT, Cfg<R, MODE, TY>::MIN_BL
             prefetch_tmap(&tm_prev);
             prefetch_tmap(&tm_vel);
         }
-        for (int i = 0; i < C::S; ++i)
-            mbar_init(&bar_u[i], 1);
+        for (int i = 0; i < C::SL; ++i)
+            mbar_init(&full_u[i], 1);
         for (int i = 0; i < C::SP; ++i)
-            mbar_init(&bar_pv[i], 1);
+            mbar_init(&full_pv[i], 1);
         fence_mbar_init();
+        s_nsrc = 0;
     }
     __syncthreads();
 
-    // loads issued so far (thread 0 only): u planes [pfirst, pfirst+n_u), pv planes [z0, z0+n_pv)
-    int64_t n_u = 0, n_pv = 0;
-    auto issue_u = [&](int64_t q) {
-        const int st = (int)((q - pfirst) % C::S);
-        mbar_arrive_expect_tx(&bar_u[st], C::U_FLOATS * 4);
-        tma_load_3d(ring + st * C::U_STRIDE, &tm_u, (int)(H + tx0 - 4), (int)(H + ty0 - R),
-                    (int)(H + q), &bar_u[st]);
+    // point sources inside this CTA's box (fused injection)
+    if (MODE == kWave && p.src_amp != nullptr && tid < p.nsrc) {
+        const int64_t lin = p.src_idx[tid];
+        if (lin < 0 || lin >= p.inx * p.iny * g.nz) {
+            atomicCAS(&g_status_tma, 0u, (unsigned)GBS_EINVAL);
+        } else {
+            const int64_t i = lin % p.inx, j = (lin / p.inx) % p.iny, k = lin / (p.inx * p.iny);
+            if (i >= tx0 && i < tx0 + kTX && j >= ty0 && j < ty0 + TY && k >= z0 && k < z1) {
+                const int slot = atomicAdd(&s_nsrc, 1);
+                s_src_x[slot] = (int)(i - tx0);
+                s_src_y[slot] = (int)(j - ty0);
+                s_src_z[slot] = (int)k;
+                s_src_f[slot] = p.src_amp[tid];
+            }
+        }
+    }
+
+    // epilogue constants (identity scales for FP32)
+    float k_u = 1.f, k_p = 1.f, k_o = 1.f, sc_out = 1.f;
+    if constexpr (kLow) {
+        const int *m = p.meta;
+        const int s_u = m[p.slot_u * kMetaInts + kMetaScale];
+        const int s_p = m[p.slot_prev * kMetaInts + kMetaScale];
+        const int s_n = lp_scale_exponent(__int_as_float(m[p.slot_u * kMetaInts + kMetaMax]));
+        k_u = pow2f(s_u - s_n);
+        k_p = pow2f(s_p - s_n);
+        k_o = pow2f(-s_n);
+        sc_out = pow2f(s_n);
+        if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+            p.meta[p.slot_next * kMetaInts + kMetaScale] = s_n;
+            p.meta[p.slot_prev * kMetaInts + kMetaMax] = 0;   // the slot the next step accumulates into
+        }
+    }
+    __syncthreads();
+    float lmax = 0.f;
+
+    // Loads issued so far (thread 0 only): u planes pfirst + [0, n_u) into
+    // landing stage j % SL (use j / SL), pv planes z0 + [0, n_pv) into j % SP.
+    int n_u = 0, n_pv = 0;
+    auto issue_u = [&]() {
+        const int st = n_u % C::SL;
+        mbar_arrive_expect_tx(&full_u[st], C::L_BYTES);
+        tma_load_3d(land + st * C::L_STRIDE, &tm_u, (int)(H + tx0 - 4), (int)(H + ty0 - R), H + pfirst + n_u,
+                    &full_u[st]);
         ++n_u;
     };
-    auto issue_pv = [&](int64_t k) {
-        const int st = (int)((k - z0) % C::SP);
-        float *dst = pv + st * 2 * C::PV_FLOATS;
-        mbar_arrive_expect_tx(&bar_pv[st], 2 * C::PV_FLOATS * 4);
-        tma_load_3d(dst, &tm_prev, (int)(H + tx0), (int)(H + ty0), (int)(H + k), &bar_pv[st]);
-        tma_load_3d(dst + C::PV_FLOATS, &tm_vel, (int)(H + tx0), (int)(H + ty0), (int)(H + k),
-                    &bar_pv[st]);
+    auto issue_pv = [&]() {
+        const int st = n_pv % C::SP;
+        unsigned char *dst = pv + st * C::PV_STRIDE;
+        mbar_arrive_expect_tx(&full_pv[st], C::PV_STRIDE);
+        tma_load_3d(dst, &tm_prev, (int)(H + tx0 - C::PVU_X0), (int)(H + ty0), H + z0 + n_pv, &full_pv[st]);
+        tma_load_3d(dst + C::PVU_BYTES, &tm_vel, (int)(H + tx0), (int)(H + ty0), H + z0 + n_pv, &full_pv[st]);
         ++n_pv;
     };
     if (tid == 0) {
-        for (int64_t j = 0; j < min((int64_t)C::S, nplanes); ++j)
-            issue_u(pfirst + j);
+        while (n_u < min(C::SL, nplanes))
+            issue_u();
         if (MODE == kWave)
-            for (int64_t j = 0; j < min((int64_t)C::SP, z1 - z0); ++j)
-                issue_pv(z0 + j);
+            while (n_pv < min(C::SP, nzc))
+                issue_pv();
     }
-
-    const float c0 = cf.c[0][0] + cf.c[1][0] + cf.c[2][0];
-    const int lx = 4 + 4 * tx;     // stage column of the thread's first point
-    const int ly = R + kVY * ty;   // stage row of the thread's first row
-    const int64_t gx = tx0 + 4 * tx;
-    const int64_t gy = ty0 + kVY * ty;
-    const bool xin = gx < g.nx;    // nx % 4 == 0: a float4 is all in or all out
-
-    float4 q[2 * R + 1][kVY];
-#pragma unroll
-    for (int a = 0; a <= 2 * R; ++a)
-#pragma unroll
-        for (int r = 0; r < kVY; ++r)
-            q[a][r] = make_float4(0.f, 0.f, 0.f, 0.f);
-
-    // waits that ran out: the CTA stops at the next slot boundary
+    // waits that ran out: the CTA stops at the next barrier
     bool fail = false, aborted = false;
-    int64_t consumed_u = 0, consumed_pv = 0;
-    for (int64_t p = pfirst; p < pend; ++p) {
-        const int64_t j = p - pfirst;
-        const int st = (int)(j % C::S);
-        if (mbar_wait_bounded(&bar_u[st], (uint32_t)((j / C::S) & 1), &g_status_tma))
-            consumed_u = j + 1;
-        else
-            fail = true;
+    int consumed_u = 0, consumed_pv = 0;
+
+    {
+        const float c0 = p.cf.c[0][0] + p.cf.c[1][0] + p.cf.c[2][0];
+        const f2 C0 = pk(c0, c0);
+        f2 CX[R + 1], CY[R + 1], CZ[R + 1];
 #pragma unroll
-        for (int a = 0; a < 2 * R; ++a)
+        for (int m = 1; m <= R; ++m) {
+            CX[m] = pk(p.cf.c[0][m], p.cf.c[0][m]);
+            CY[m] = MODE == kWave ? CX[m] : pk(p.cf.c[1][m], p.cf.c[1][m]);
+            CZ[m] = MODE == kWave ? CX[m] : pk(p.cf.c[2][m], p.cf.c[2][m]);
+        }
+        const f2 S2 = pk(p.s, p.s);
+        const f2 KU = pk(k_u, k_u);
+        const f2 TWO_KU = pk(2.f * k_u, 2.f * k_u);
+        const f2 KP = pk(k_p, k_p);
+        const int nsrc_cta = s_nsrc;               // uniform over the CTA
+        const int lx = 4 + 4 * tx;                 // stage column of the thread's first point
+        const int ly = R + kVY * ty;               // stage row of the thread's first row
+        const int64_t gx = tx0 + 4 * tx;
+        const int64_t gy = ty0 + kVY * ty;
+        const bool xin = gx < g.nx;
+        T *out_base = static_cast<T *>(p.out) + (H + gx) + g.px * (H + gy);
+        const int64_t plane_stride = g.px * g.py;
+
+        // 16-bit: halo groups of 4 elements this thread converts each plane
+        // (element offsets in the box); slots past the last group repeat earlier
+        // groups (same values written twice) so every thread does the same work.
+        constexpr int kHaloPer = (C::HALO_GROUPS + C::NT - 1) / C::NT;
+        int hoff[kHaloPer];
+#pragma unroll
+        for (int h = 0; h < kHaloPer; ++h) {
+            const int gi = (C::NT * h + tid) % C::HALO_GROUPS;
+            int off = 0;
+            if (kLow) {
+                int row, col;
+                if (gi < 2 * C::BH) {
+                    row = gi >> 1;
+                    col = (gi & 1) ? C::BW - 4 : 0;
+                } else {
+                    const int t = gi - 2 * C::BH;
+                    const int hr = t >> 4;
+                    row = hr < R ? hr : hr + TY;
+                    col = 4 + 4 * (t & 15);
+                }
+                off = row * C::BW + col;
+            }
+            hoff[h] = off;
+        }
+
+        // z-queue: P[i] holds plane pfirst + base - (Q - 1) + i of the thread's
+        // points at the start of an iteration of U planes; plane pfirst + j
+        // (j = base + rho) lands in P[Q - 1 + rho], logical entry a (plane
+        // j - 2R + a) is P[rho + a].  The queue shifts down by U per iteration.
+        float4 P[Q + U - 1][kVY];
+#pragma unroll
+        for (int a = 0; a < Q + U - 1; ++a)
 #pragma unroll
             for (int r = 0; r < kVY; ++r)
-                q[a][r] = q[a + 1][r];
-        const float *su = ring + st * C::U_STRIDE;
-#pragma unroll
-        for (int r = 0; r < kVY; ++r)
-            q[2 * R][r] = lds4(su + (ly + r) * C::BW + lx);
+                P[a][r] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-        if (p >= z0 + R) {
-            const int64_t k = p - R;                       // output plane
-            const float *sc = ring + (int)((k - pfirst) % C::S) * C::U_STRIDE;
-            const float *pvp = nullptr;
-            if (MODE == kWave) {
-                const int64_t jk = k - z0;
-                const int sp = (int)(jk % C::SP);
-                if (mbar_wait_bounded(&bar_pv[sp], (uint32_t)((jk / C::SP) & 1), &g_status_tma))
-                    consumed_pv = jk + 1;
+        for (int base = 0; base < nplanes; base += U) {
+            const bool more = static_for<0, U>([&](auto rc) -> bool {
+                constexpr int rho = decltype(rc)::value;
+                const int j = base + rho;                      // plane pfirst + j arrives
+                if (j >= nplanes)
+                    return false;
+                const int st = j % C::SL;
+                if (mbar_wait_bounded(&full_u[st], (uint32_t)((j / C::SL) & 1), &g_status_tma))
+                    consumed_u = j + 1;
                 else
                     fail = true;
-                pvp = pv + sp * 2 * C::PV_FLOATS;
-            }
+                const T *su = reinterpret_cast<const T *>(land + st * C::L_STRIDE);
 #pragma unroll
-            for (int r = 0; r < kVY; ++r) {
-                const float4 cen = q[R][r];
-                const float4 lf = lds4(sc + (ly + r) * C::BW + lx - 4);
-                const float4 rt = lds4(sc + (ly + r) * C::BW + lx + 4);
-                const float wx[12] = {lf.x, lf.y, lf.z, lf.w, cen.x, cen.y, cen.z, cen.w,
-                                      rt.x, rt.y, rt.z, rt.w};
-                float acc[4];
+                for (int r = 0; r < kVY; ++r)
+                    P[Q - 1 + rho][r] = ld4(su + (ly + r) * C::BW + lx);
+                if constexpr (kLow) {
+                    // FP32 copy of the planes that are stencil centres (j in [R, nplanes-R)):
+                    // own points from the queue, halo groups shared by all threads
+                    if (j >= R && j < nplanes - R) {
+                        const int s = (j - R) % C::SF;
+                        float *fs = f32ring + s * (C::F_STRIDE / 4);
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    acc[e] = c0 * wx[4 + e];
+                        for (int r = 0; r < kVY; ++r)
+                            *reinterpret_cast<float4 *>(fs + (ly + r) * C::BW + lx) = P[Q - 1 + rho][r];
 #pragma unroll
-                for (int m = 1; m <= R; ++m) {
-                    const float4 yp = (r + m < kVY) ? q[R][r + m] : lds4(sc + (ly + r + m) * C::BW + lx);
-                    const float4 ym = (r - m >= 0) ? q[R][r - m] : lds4(sc + (ly + r - m) * C::BW + lx);
-                    const float4 zp = q[R + m][r];
-                    const float4 zm = q[R - m][r];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        acc[e] = fmaf(cf.c[0][m], wx[4 + e + m] + wx[4 + e - m], acc[e]);
-                        acc[e] = fmaf(cf.c[1][m], at(yp, e) + at(ym, e), acc[e]);
-                        acc[e] = fmaf(cf.c[2][m], at(zp, e) + at(zm, e), acc[e]);
+                        for (int h = 0; h < kHaloPer; ++h)
+                            *reinterpret_cast<float4 *>(fs + hoff[h]) = ld4(su + hoff[h]);
                     }
                 }
-                float4 res;
-                if (MODE == kWave) {
-                    const int o = (kVY * ty + r) * kTX + 4 * tx;
-                    const float4 up = lds4(pvp + o);
-                    const float4 vv = lds4(pvp + C::PV_FLOATS + o);
-                    float rr[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float vs = at(vv, e) * s;
-                        rr[e] = fmaf(vs * vs, acc[e], fmaf(2.f, at(cen, e), -at(up, e)));
+
+                if (j >= 2 * R) {
+                    // output plane k = z0 + cj; centre plane pfirst + j - R
+                    const int cj = j - 2 * R;
+                    const int k = z0 + cj;
+                    const float *sc;
+                    if constexpr (kLow) {
+                        sc = f32ring + (cj % C::SF) * (C::F_STRIDE / 4);
+                    } else {
+                        sc = reinterpret_cast<const float *>(land + ((j - R) % C::SL) * C::L_STRIDE);
                     }
-                    res = make_float4(rr[0], rr[1], rr[2], rr[3]);
-                } else {
-                    res = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                    const T *pvu = nullptr;
+                    const float *pvv = nullptr;
+                    const int sp = cj % C::SP;
+                    if (MODE == kWave) {
+                        if (mbar_wait_bounded(&full_pv[sp], (uint32_t)((cj / C::SP) & 1), &g_status_tma))
+                            consumed_pv = cj + 1;
+                        else
+                            fail = true;
+                        pvu = reinterpret_cast<const T *>(pv + sp * C::PV_STRIDE);
+                        pvv = reinterpret_cast<const float *>(pv + sp * C::PV_STRIDE + C::PVU_BYTES);
+                    }
+                    f2 res_l[kVY], res_h[kVY];
+                    float4 vel4[kVY];
+#pragma unroll
+                    for (int r = 0; r < kVY; ++r) {
+                        const float4 cen = P[rho + R][r];
+                        const float4 lf = ld4(sc + (ly + r) * C::BW + lx - 4);
+                        const float4 rt = ld4(sc + (ly + r) * C::BW + lx + 4);
+                        // two independent accumulation chains (odd and even distances)
+                        f2 acc_l = mul2(C0, lo(cen)), acc_h = mul2(C0, hi(cen));
+                        f2 acc2_l = 0ull, acc2_h = 0ull;   // +0.0f pairs
+#pragma unroll
+                        for (int m = 1; m <= R; ++m) {
+                            const float4 yp = (r + m < kVY) ? P[rho + R][r + m] : ld4(sc + (ly + r + m) * C::BW + lx);
+                            const float4 ym = (r - m >= 0) ? P[rho + R][r - m] : ld4(sc + (ly + r - m) * C::BW + lx);
+                            const float4 zp = P[rho + R + m][r];
+                            const float4 zm = P[rho + R - m][r];
+                            f2 xs_l, xs_h;
+                            if (m & 1) {
+                                // odd distance: the neighbour pairs straddle register pairs, add per point
+                                const float w[12] = {lf.x, lf.y, lf.z, lf.w, cen.x, cen.y, cen.z, cen.w,
+                                                     rt.x, rt.y, rt.z, rt.w};
+                                xs_l = pk(w[4 + m] + w[4 - m], w[5 + m] + w[5 - m]);
+                                xs_h = pk(w[6 + m] + w[6 - m], w[7 + m] + w[7 - m]);
+                            } else {
+                                xs_l = add2(xpair(lf, cen, rt, 4 + m), xpair(lf, cen, rt, 4 - m));
+                                xs_h = add2(xpair(lf, cen, rt, 6 + m), xpair(lf, cen, rt, 6 - m));
+                            }
+                            const f2 ys_l = add2(lo(yp), lo(ym)), ys_h = add2(hi(yp), hi(ym));
+                            const f2 zs_l = add2(lo(zp), lo(zm)), zs_h = add2(hi(zp), hi(zm));
+                            f2 &al = (m & 1) ? acc_l : acc2_l;
+                            f2 &ah = (m & 1) ? acc_h : acc2_h;
+                            if (MODE == kWave) {
+                                // one weight per distance on every axis (the wave operator)
+                                al = fma2(CX[m], add2(add2(xs_l, ys_l), zs_l), al);
+                                ah = fma2(CX[m], add2(add2(xs_h, ys_h), zs_h), ah);
+                            } else {
+                                al = fma2(CZ[m], zs_l, fma2(CY[m], ys_l, fma2(CX[m], xs_l, al)));
+                                ah = fma2(CZ[m], zs_h, fma2(CY[m], ys_h, fma2(CX[m], xs_h, ah)));
+                            }
+                        }
+                        acc_l = add2(acc_l, acc2_l);
+                        acc_h = add2(acc_h, acc2_h);
+                        if (MODE == kWave) {
+                            const float4 up = ld4(pvu + (kVY * ty + r) * C::PVU_W + C::PVU_X0 + 4 * tx);
+                            vel4[r] = ld4(pvv + (kVY * ty + r) * kTX + 4 * tx);
+                            const f2 vs_l = mul2(lo(vel4[r]), S2), vs_h = mul2(hi(vel4[r]), S2);
+                            f2 c_l, c_h, t_l, t_h;
+                            if (kLow) {
+                                c_l = mul2(mul2(vs_l, KU), vs_l);
+                                c_h = mul2(mul2(vs_h, KU), vs_h);
+                                t_l = sub2(mul2(TWO_KU, lo(cen)), mul2(KP, lo(up)));
+                                t_h = sub2(mul2(TWO_KU, hi(cen)), mul2(KP, hi(up)));
+                            } else {
+                                c_l = mul2(vs_l, vs_l);
+                                c_h = mul2(vs_h, vs_h);
+                                t_l = sub2(add2(lo(cen), lo(cen)), lo(up));
+                                t_h = sub2(add2(hi(cen), hi(cen)), hi(up));
+                            }
+                            acc_l = fma2(c_l, acc_l, t_l);
+                            acc_h = fma2(c_h, acc_h, t_h);
+                        }
+                        res_l[r] = acc_l;
+                        res_h[r] = acc_h;
+                    }
+                    if (MODE == kWave && nsrc_cta > 0) {
+                        // rare: this CTA holds a source cell
+                        for (int i = 0; i < nsrc_cta; ++i) {
+                            if (s_src_z[i] != k || (s_src_x[i] >> 2) != tx)
+                                continue;
+                            const int e = s_src_x[i] & 3;
+#pragma unroll
+                            for (int r = 0; r < kVY; ++r) {
+                                if (s_src_y[i] == kVY * ty + r) {
+                                    const float vdt = at(vel4[r], e) * p.dt;
+                                    float4 v;
+                                    upk(res_l[r], v.x, v.y);
+                                    upk(res_h[r], v.z, v.w);
+                                    add_at(v, e, vdt * vdt * s_src_f[i] * k_o);
+                                    res_l[r] = lo(v);
+                                    res_h[r] = hi(v);
+                                }
+                            }
+                        }
+                    }
+                    T *dst = out_base + plane_stride * (int64_t)(H + k);
+#pragma unroll
+                    for (int r = 0; r < kVY; ++r) {
+                        if (!(xin && gy + r < g.ny))
+                            continue;
+                        if constexpr (kLow) {
+                            float4 v;
+                            upk(res_l[r], v.x, v.y);
+                            upk(res_h[r], v.z, v.w);
+                            lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+                            st4(dst + r * g.px, v);
+                        } else {
+                            st_pairs(dst + r * g.px, res_l[r], res_h[r]);
+                        }
+                    }
                 }
-                if (xin && gy + r < g.ny)
-                    *reinterpret_cast<float4 *>(out + (H + gx) + g.px * ((H + gy + r) + g.py * (H + k))) = res;
-            }
-        }
-        // every thread is done with stage(p-R) and pv(k); all see the same verdict
-        if (__syncthreads_or(fail)) {
-            aborted = true;
-            break;
-        }
-        if (tid == 0) {
-            if (p >= z0 && p - R + C::S < pend)
-                issue_u(p - R + C::S);
-            if (MODE == kWave && p >= z0 + R && (p - R) - z0 + C::SP < z1 - z0)
-                issue_pv(p - R + C::SP);
+                if ((rho + 1) % C::BAR_EVERY == 0) {
+                    // every thread is done with the stages of planes up to j; all see the same verdict
+                    if (__syncthreads_or(fail)) {
+                        aborted = true;
+                        return false;
+                    }
+                    if (tid == 0) {
+                        // released: 16-bit landing stages of planes <= j (converted), FP32 stages
+                        // of planes that were centres or are never centres, pv stages of outputs <= j-2R
+                        const int rel_u = kLow ? j + 1 : max(0, j - R + 1);
+                        while (n_u < nplanes && n_u < rel_u + C::SL)
+                            issue_u();
+                        if (MODE == kWave) {
+                            const int rel_pv = max(0, j - 2 * R + 1);
+                            while (n_pv < nzc && n_pv < rel_pv + C::SP)
+                                issue_pv();
+                        }
+                    }
+                }
+                return true;
+            });
+            if (!more)
+                break;
+#pragma unroll
+            for (int a = 0; a < Q - 1; ++a)
+#pragma unroll
+                for (int r = 0; r < kVY; ++r)
+                    P[a][r] = P[a + U][r];
         }
     }
 
     // On an aborted wait, let the copies still in flight land (bounded)
     // before the CTA's shared memory is released.
     if (aborted && tid == 0) {
-        for (int64_t jj = consumed_u; jj < n_u; ++jj)
-            mbar_wait_bounded(&bar_u[jj % C::S], (uint32_t)((jj / C::S) & 1), &g_status_tma);
-        for (int64_t jj = consumed_pv; jj < n_pv; ++jj)
-            mbar_wait_bounded(&bar_pv[jj % C::SP], (uint32_t)((jj / C::SP) & 1), &g_status_tma);
+        for (int jj = consumed_u; jj < n_u; ++jj)
+            mbar_wait_bounded(&full_u[jj % C::SL], (uint32_t)((jj / C::SL) & 1), &g_status_tma);
+        for (int jj = consumed_pv; jj < n_pv; ++jj)
+            mbar_wait_bounded(&full_pv[jj % C::SP], (uint32_t)((jj / C::SP) & 1), &g_status_tma);
+    }
+
+    if constexpr (kLow) {
+        // max |value| of this CTA before rounding; rounding is monotone, so the
+        // rounded maximum is the largest stored code -> state slot of u^{n+1}
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        if ((tid & 31) == 0)
+            s_red[tid >> 5] = lmax;
+        __syncthreads();
+        if (tid == 0) {
+            float mx = 0.f;
+            for (int w = 0; w < NCW; ++w)
+                mx = fmaxf(mx, s_red[w]);
+            atomicMax(reinterpret_cast<unsigned *>(p.meta + p.slot_next * kMetaInts + kMetaMax),
+                      __float_as_uint(rounded(mx, (T *)nullptr) * sc_out));
+        }
     }
 }
 
-template <int R, int MODE, int TY>
-cudaError_t launch_cfg(const Grid &g, const TmaPlan &plan, float *out, const Coeffs &cf, float s,
-                       int zchunk, cudaStream_t st)
+// The dynamic shared-memory opt-in, set once per instantiation and device
+// (outside any stream capture on the first launch, or by tma_prepare_wave).
+template <int R, int MODE, int TY, typename T>
+cudaError_t prepare_cfg()
 {
-    using C = Cfg<R, MODE, TY>;
-    static bool attr_set = false;   // per instantiation; setting twice is harmless
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tma<R, MODE, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)C::SMEM);
-        if (e != cudaSuccess)
-            return e;
-        attr_set = true;
-    }
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev >= 0 && dev < 64 && done[dev])
+        return cudaSuccess;
+    e = cudaFuncSetAttribute(k_tma<R, MODE, TY, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg<R, MODE, TY, T>::SMEM);
+    if (e == cudaSuccess && dev >= 0 && dev < 64)
+        done[dev] = true;
+    return e;
+}
+
+template <int R, int MODE, int TY, typename T>
+cudaError_t launch_cfg(const TmaPlan &plan, const StepParams &p0, cudaStream_t st)
+{
+    using C = Cfg<R, MODE, TY, T>;
+    cudaError_t e = prepare_cfg<R, MODE, TY, T>();
+    if (e != cudaSuccess)
+        return e;
+    StepParams p = p0;
+    const Grid &g = p.g;
     const int64_t tiles_x = (g.nx + kTX - 1) / kTX;
     const int64_t tiles_y = (g.ny + TY - 1) / TY;
-    const int64_t nchunks = (g.nz + zchunk - 1) / zchunk;
+    const int64_t nchunks = (g.nz + p.zchunk - 1) / p.zchunk;
     if (tiles_x * tiles_y > 0x7fffffff || nchunks > 65535)
         return cudaErrorInvalidConfiguration;
+    p.tiles_x = (int)tiles_x;
     dim3 grid((unsigned)(tiles_x * tiles_y), (unsigned)nchunks);
-    k_tma<R, MODE, TY><<<grid, C::NT, C::SMEM, st>>>(plan.u, plan.prev, plan.vel, g, out, cf, s, zchunk,
-                                                    (int)tiles_x);
+    k_tma<R, MODE, TY, T><<<grid, C::NT, C::SMEM, st>>>(plan.u, plan.prev, plan.vel, p);
     return cudaGetLastError();
 }
 
 template <int MODE, int TY>
-cudaError_t launch_mode(int radius, const Grid &g, const TmaPlan &plan, float *out, const Coeffs &cf,
-                        float s, int zchunk, cudaStream_t st)
+cudaError_t launch_stencil_r(int radius, const TmaPlan &plan, const StepParams &p, cudaStream_t st)
 {
     switch (radius) {
-    case 1: return launch_cfg<1, MODE, TY>(g, plan, out, cf, s, zchunk, st);
-    case 2: return launch_cfg<2, MODE, TY>(g, plan, out, cf, s, zchunk, st);
-    case 3: return launch_cfg<3, MODE, TY>(g, plan, out, cf, s, zchunk, st);
-    case 4: return launch_cfg<4, MODE, TY>(g, plan, out, cf, s, zchunk, st);
+    case 1: return launch_cfg<1, MODE, TY, float>(plan, p, st);
+    case 2: return launch_cfg<2, MODE, TY, float>(plan, p, st);
+    case 3: return launch_cfg<3, MODE, TY, float>(plan, p, st);
+    case 4: return launch_cfg<4, MODE, TY, float>(plan, p, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
+template <typename T>
+cudaError_t launch_wave_t(int tile_y, const TmaPlan &plan, const StepParams &p, cudaStream_t st)
+{
+    return tile_y == 32 ? launch_cfg<4, kWave, 32, T>(plan, p, st) : launch_cfg<4, kWave, 16, T>(plan, p, st);
+}
+
 }  // namespace
 
-cudaError_t launch_tma(int radius, Mode mode, int tile_y, const Grid &g, const TmaPlan &plan, float *out,
-                       const Coeffs &cf, float s, int zchunk, cudaStream_t st)
+cudaError_t launch_tma(int radius, Mode mode, int tile_y, gbs_dtype storage, const TmaPlan &plan,
+                       const StepParams &p0, cudaStream_t st)
 {
-    if (zchunk <= 0)
-        zchunk = tma_default_zchunk(radius, mode, tile_y, g);
+    StepParams p = p0;
+    if (p.zchunk <= 0)
+        p.zchunk = tma_default_zchunk(radius, mode, tile_y, storage, p.g);
     if (mode == kWave) {
         if (radius != 4)
             return cudaErrorInvalidValue;
-        return tile_y == 32 ? launch_cfg<4, kWave, 32>(g, plan, out, cf, s, zchunk, st)
-                            : launch_cfg<4, kWave, 16>(g, plan, out, cf, s, zchunk, st);
+        switch (storage) {
+        case GBS_F32: return launch_wave_t<float>(tile_y, plan, p, st);
+        case GBS_BF16: return launch_wave_t<__nv_bfloat16>(tile_y, plan, p, st);
+        case GBS_F16: return launch_wave_t<__half>(tile_y, plan, p, st);
+        default: return cudaErrorInvalidValue;
+        }
     }
-    return tile_y == 32 ? launch_mode<kStencil, 32>(radius, g, plan, out, cf, s, zchunk, st)
-                        : launch_mode<kStencil, 16>(radius, g, plan, out, cf, s, zchunk, st);
+    if (storage != GBS_F32)
+        return cudaErrorInvalidValue;
+    return tile_y == 32 ? launch_stencil_r<kStencil, 32>(radius, plan, p, st)
+                        : launch_stencil_r<kStencil, 16>(radius, plan, p, st);
+}
+
+cudaError_t tma_prepare_wave(gbs_dtype storage, int tile_y)
+{
+    const bool t32 = tile_y == 32;
+    switch (storage) {
+    case GBS_F32: return t32 ? prepare_cfg<4, kWave, 32, float>() : prepare_cfg<4, kWave, 16, float>();
+    case GBS_BF16:
+        return t32 ? prepare_cfg<4, kWave, 32, __nv_bfloat16>() : prepare_cfg<4, kWave, 16, __nv_bfloat16>();
+    case GBS_F16: return t32 ? prepare_cfg<4, kWave, 32, __half>() : prepare_cfg<4, kWave, 16, __half>();
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // z-chunk choice: CTAs of a launch have equal work, so the launch takes
 // ceil(CTAs / resident slots) "waves", each as long as one CTA's chunk plus
 // its 2R extra u planes (a quarter of a full plane's bytes in wave mode).
 // Pick the chunk count that minimises waves x per-CTA planes.
-int tma_default_zchunk(int radius, Mode mode, int tile_y, const Grid &g)
+int tma_default_zchunk(int radius, Mode mode, int tile_y, gbs_dtype storage, const Grid &g)
 {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = (tile_y == 32) ? 1 : 2;
+    const int per_sm = (tile_y == 32) ? 1 : (storage == GBS_F32 ? 2 : 3);
     const int64_t slots = (int64_t)sms * per_sm;
     const int64_t tiles = ((g.nx + kTX - 1) / kTX) * ((g.ny + tile_y - 1) / tile_y);
     const double halo_cost = (mode == kWave ? 0.25 : 0.5) * 2 * radius;
