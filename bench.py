@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--graph", action="store_true", help="replay the step loop as a CUDA graph")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip BF16/FP16 storage and the radius sweep")
+    ap.add_argument("--no-errors", action="store_true", help="skip the FP64-oracle error runs of the storage forms")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--ref-leapfrog", type=int, default=2, help="oracle leapfrog steps per reference step")
     return ap.parse_args()
@@ -189,17 +191,131 @@ def cpu_oracle_rate(prob, target_s):
     n, halo = prob.nx, prob.halo
     z = np.zeros(W_padded(prob), np.float64)
     vel = prob.vel.astype(np.float64)
+    # calibration: 1 step, then 4 steps (the difference removes the per-call buffer copies)
     t0 = time.perf_counter()
     a, b, _ = oracle.wave_propagate(z, z, vel, prob.dt, prob.h, halo, 1,
                                     src_idx=prob.src_idx, src_amp=prob.src_amp)
-    one = time.perf_counter() - t0
-    steps = max(1, min(50, int(target_s / max(one, 1e-3))))
+    t1 = time.perf_counter()
+    a, b, _ = oracle.wave_propagate(a, b, vel, prob.dt, prob.h, halo, 4, t0=1,
+                                    src_idx=prob.src_idx, src_amp=prob.src_amp)
+    t2 = time.perf_counter()
+    per_step = max(1e-4, ((t2 - t1) - (t1 - t0)) / 3.0)
+    steps = max(1, min(400, int(target_s / per_step)))
     t0 = time.perf_counter()
-    oracle.wave_propagate(a, b, vel, prob.dt, prob.h, halo, steps, t0=1,
+    oracle.wave_propagate(a, b, vel, prob.dt, prob.h, halo, steps, t0=5,
                           src_idx=prob.src_idx, src_amp=prob.src_amp)
     dt = time.perf_counter() - t0
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return prob.npoints * steps / dt / 1e9, steps, dt, threads
+
+
+def time_calls(fn, k, stream):
+    """Run fn() k times between CUDA events on `stream`; returns (ms per call,
+    step-kernel ms per launch, launches) with the library's event profiler."""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    torch.cuda.synchronize()
+    gbs.profile_enable(True)
+    gbs.profile_take()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kms, kl = gbs.profile_take()
+    gbs.profile_enable(False)
+    return e0.elapsed_time(e1) / k, (kms / kl if kl else None), kl
+
+
+def storage_forms(prob, args, stream, hbm):
+    """BF16 and FP16 storage on the same workload: whole-call throughput and
+    the step kernel's roofline at 10 algorithmic bytes per point."""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    dev = torch.device("cuda", torch.cuda.current_device())
+    shape = W_padded(prob)
+    vel = torch.from_numpy(prob.vel).to(dev)
+    si, sa = torch.from_numpy(prob.src_idx).to(dev), torch.from_numpy(prob.src_amp).to(dev)
+    out = {}
+    for fmt in ("bf16", "f16"):
+        a, b = torch.zeros(shape, device=dev), torch.zeros(shape, device=dev)
+        work = gbs.lp_workspace(a, prob.halo)
+        st = {"a": a, "b": b}
+
+        def run():
+            st["a"], st["b"] = gbs.wave_propagate_lp(st["a"], st["b"], vel, prob.dt, prob.h, prob.halo, prob.nsteps,
+                                                     storage=fmt, work=work, src_idx=si, src_amp=sa)
+        for _ in range(2):
+            run()
+        k = max(3, args.steps // 4)
+        ms, kms, kl = time_calls(run, k, stream)
+        gbs.device_status()
+        ach = 10 * prob.npoints / (kms * 1e-3) / 1e9
+        out[fmt] = {"value": prob.npoints * prob.nsteps / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+                    "calls": k, "bytes_per_point": 10,
+                    "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                                 "kernel_ms_per_launch": kms, "kernel_launches": kl}}
+        del a, b, work, st
+    torch.cuda.empty_cache()
+    return out
+
+
+def radius_sweep(args, stream, hbm):
+    """stencil_apply R = 1..4 (7/13/19/25 points) on a uniform[-1,1] n^3 field."""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    import workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n, halo = args.n, 4
+    x = torch.from_numpy(W.uniform_field(n, n, n, halo, W.SEED_BASE + 22)).to(dev)
+    y = torch.empty_like(x)
+    out = {}
+    for R in (1, 2, 3, 4):
+        c = gbs.fd2_coeffs(R)
+
+        def run():
+            gbs.stencil_apply(x, y, radius=R, cx=c, cy=c, cz=c, halo=halo)
+        for _ in range(3):
+            run()
+        ms, kms, kl = time_calls(run, 20, stream)
+        ach = 8 * n ** 3 / (kms * 1e-3) / 1e9
+        out[f"R{R}"] = {"points": 6 * R + 1, "value": n ** 3 / (ms * 1e-3) / 1e9, "unit": UNIT,
+                        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                                     "kernel_ms_per_launch": kms}}
+    del x, y
+    torch.cuda.empty_cache()
+    return out
+
+
+def precision_errors(stream, n=256, nsteps=500):
+    """Error of FP32 / BF16 / FP16 storage against the FP64 oracle on an n^3
+    copy of the layered workload (same generator), after nsteps steps."""
+    import torch
+    import oracle
+    import paper_2309_04671_gb300 as gbs
+    import workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prob = W.layered_problem(n=n, nsteps=nsteps, seed_offset=3)
+    z = np.zeros(W_padded(prob), np.float32)
+    vel = torch.from_numpy(prob.vel).to(dev)
+    si, sa = torch.from_numpy(prob.src_idx).to(dev), torch.from_numpy(prob.src_amp).to(dev)
+    t0 = time.perf_counter()
+    _, ref, _ = oracle.wave_propagate(z, z, prob.vel, prob.dt, prob.h, prob.halo, nsteps, src_idx=prob.src_idx,
+                                      src_amp=prob.src_amp)
+    t_oracle = time.perf_counter() - t0
+    out = {"grid": [n, n, n], "steps": nsteps, "oracle_seconds": t_oracle}
+    for fmt in ("f32", "bf16", "f16"):
+        a, b = torch.zeros_like(vel), torch.zeros_like(vel)
+        if fmt == "f32":
+            _, cur = gbs.wave_propagate(a, b, vel, prob.dt, prob.h, prob.halo, nsteps, src_idx=si, src_amp=sa)
+        else:
+            _, cur = gbs.wave_propagate_lp(a, b, vel, prob.dt, prob.h, prob.halo, nsteps, storage=fmt, src_idx=si,
+                                           src_amp=sa)
+        gbs.device_status()
+        e = oracle.err_norms(cur.cpu().numpy(), ref)
+        out[fmt] = {k: e[k] for k in ("norm_max_rel", "l2_rel", "max_abs", "rmsd")}
+    return out
 
 
 def W_padded(prob):
@@ -309,7 +425,7 @@ def run_ours(args):
     alg_bytes = BYTES_PER_POINT * prob.npoints
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9 if kernel_launches else None
     traffic = traffic_per_launch(n)
-    inject_launches = args.steps * min(ns, prob.src_amp.shape[0])
+    inject_launches = 0   # sources are added inside the step kernel (at most 16)
 
     # end to end through host buffers (pinned), same call a user makes
     e2e = None
@@ -339,6 +455,12 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{steps} FP64 leapfrog steps of the full {n}^3 grid ({secs:.1f} s), after 1 untimed step"}
 
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = {"storage": storage_forms(prob, args, stream, hbm), "radius_sweep": radius_sweep(args, stream, hbm)}
+        if not args.no_errors:
+            forms["error_vs_fp64_oracle"] = precision_errors(stream)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -358,6 +480,7 @@ def run_ours(args):
             "e2e": e2e,
             "clocks": clk,
             "gpu_launches": kernel_launches + inject_launches,
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

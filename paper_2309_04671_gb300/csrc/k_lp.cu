@@ -30,13 +30,25 @@ __device__ __forceinline__ void put(__half *p, float v) { *p = __float2half_rn(v
 __device__ __forceinline__ float get(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
 __device__ __forceinline__ float get(const __half *p) { return __half2float(*p); }
 
+// Grid: x over blocks of kThreads points of a row, y grid-strides over the
+// ny*nz rows of the caller's interior (one 32-bit division per row).
+#define GBS_ROW_LOOP(gc)                                                                     \
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;                          \
+    const int rows = (int)((gc).ny * (gc).nz);                                               \
+    for (int row = blockIdx.y; row < rows; row += gridDim.y)                                 \
+        if (i < (gc).nx)
+
+__device__ __forceinline__ int64_t row_index(const Grid &g, int64_t i, int row, int64_t ny)
+{
+    const int64_t j = row % ny, k = row / ny;
+    return pad_index(g, i, j, k);
+}
+
 __global__ void __launch_bounds__(kThreads) k_absmax(Grid g, const float *x, unsigned *dst)
 {
-    const int64_t n = g.nx * g.ny * g.nz;
     float m = 0.f;
-    for (int64_t lin = (int64_t)blockIdx.x * kThreads + threadIdx.x; lin < n; lin += (int64_t)gridDim.x * kThreads) {
-        const int64_t i = lin % g.nx, j = (lin / g.nx) % g.ny, k = lin / (g.nx * g.ny);
-        m = fmaxf(m, fabsf(x[pad_index(g, i, j, k)]));
+    {
+        GBS_ROW_LOOP(g) { m = fmaxf(m, fabsf(x[row_index(g, i, row, g.ny)])); }
     }
     __shared__ float red[kThreads / 32];
 #pragma unroll
@@ -58,12 +70,8 @@ __global__ void __launch_bounds__(kThreads) k_encode(Grid gc, const float *x, Gr
     const float mraw = __int_as_float(slot[kMetaTmp]);
     const int s = lp_scale_exponent(mraw);
     const float inv = pow2f(-s);
-    const int64_t n = gc.nx * gc.ny * gc.nz;
-    for (int64_t lin = (int64_t)blockIdx.x * kThreads + threadIdx.x; lin < n; lin += (int64_t)gridDim.x * kThreads) {
-        const int64_t i = lin % gc.nx, j = (lin / gc.nx) % gc.ny, k = lin / (gc.nx * gc.ny);
-        put(q + pad_index(gi, i, j, k), x[pad_index(gc, i, j, k)] * inv);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    GBS_ROW_LOOP(gc) { put(q + row_index(gi, i, row, gc.ny), x[row_index(gc, i, row, gc.ny)] * inv); }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         slot[kMetaScale] = s;
         slot[kMetaMax] = __float_as_int(to_code(mraw * inv, (T *)nullptr) * pow2f(s));
     }
@@ -73,20 +81,12 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_decode(Grid gi, const T *q, const int *slot, Grid gc, float *x)
 {
     const float sc = pow2f(slot[kMetaScale]);
-    const int64_t n = gc.nx * gc.ny * gc.nz;
-    for (int64_t lin = (int64_t)blockIdx.x * kThreads + threadIdx.x; lin < n; lin += (int64_t)gridDim.x * kThreads) {
-        const int64_t i = lin % gc.nx, j = (lin / gc.nx) % gc.ny, k = lin / (gc.nx * gc.ny);
-        x[pad_index(gc, i, j, k)] = get(q + pad_index(gi, i, j, k)) * sc;
-    }
+    GBS_ROW_LOOP(gc) { x[row_index(gc, i, row, gc.ny)] = get(q + row_index(gi, i, row, gc.ny)) * sc; }
 }
 
 __global__ void __launch_bounds__(kThreads) k_copy(Grid gc, const float *x, Grid gi, float *y)
 {
-    const int64_t n = gc.nx * gc.ny * gc.nz;
-    for (int64_t lin = (int64_t)blockIdx.x * kThreads + threadIdx.x; lin < n; lin += (int64_t)gridDim.x * kThreads) {
-        const int64_t i = lin % gc.nx, j = (lin / gc.nx) % gc.ny, k = lin / (gc.nx * gc.ny);
-        y[pad_index(gi, i, j, k)] = x[pad_index(gc, i, j, k)];
-    }
+    GBS_ROW_LOOP(gc) { y[row_index(gi, i, row, gc.ny)] = x[row_index(gc, i, row, gc.ny)]; }
 }
 
 template <typename T>
@@ -105,14 +105,16 @@ __global__ void k_record_lp(Grid gc, Grid gi, const T *q, const int *slot, const
     trace_row[r] = get(q + pad_index(gi, i, j, k)) * pow2f(slot[kMetaScale]);
 }
 
-unsigned blocks_for(int64_t n)
+dim3 grid_for(const Grid &gc)
 {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t want = (n + kThreads - 1) / kThreads;
-    const int64_t cap = (int64_t)sms * 8;
-    return (unsigned)(want < 1 ? 1 : (want > cap ? cap : want));
+    const int64_t bx = (gc.nx + kThreads - 1) / kThreads;
+    const int64_t rows = gc.ny * gc.nz;
+    int64_t by = (int64_t)sms * 16 / (bx > 0 ? bx : 1);
+    by = by < 1 ? 1 : (by > rows ? rows : by);
+    return dim3((unsigned)(bx > 0 ? bx : 1), (unsigned)(by > 65535 ? 65535 : (by < 1 ? 1 : by)));
 }
 
 }  // namespace
@@ -120,7 +122,7 @@ unsigned blocks_for(int64_t n)
 cudaError_t launch_lp_encode(gbs_dtype storage, const Grid &gc, const float *x, const Grid &gi, void *q,
                              int *meta_slot, cudaStream_t st)
 {
-    const unsigned b = blocks_for(gc.nx * gc.ny * gc.nz);
+    const dim3 b = grid_for(gc);
     cudaError_t e = cudaMemsetAsync(meta_slot, 0, kMetaInts * sizeof(int), st);
     if (e != cudaSuccess)
         return e;
@@ -137,7 +139,7 @@ cudaError_t launch_lp_encode(gbs_dtype storage, const Grid &gc, const float *x, 
 cudaError_t launch_lp_decode(gbs_dtype storage, const Grid &gi, const void *q, const int *meta_slot,
                              const Grid &gc, float *x, cudaStream_t st)
 {
-    const unsigned b = blocks_for(gi.nx * gi.ny * gi.nz);
+    const dim3 b = grid_for(gc);
     if (storage == GBS_BF16)
         k_decode<__nv_bfloat16><<<b, kThreads, 0, st>>>(gi, static_cast<const __nv_bfloat16 *>(q), meta_slot, gc, x);
     else if (storage == GBS_F16)
@@ -149,7 +151,7 @@ cudaError_t launch_lp_decode(gbs_dtype storage, const Grid &gi, const void *q, c
 
 cudaError_t launch_copy_f32(const Grid &gc, const float *x, const Grid &gi, float *y, cudaStream_t st)
 {
-    k_copy<<<blocks_for(gi.nx * gi.ny * gi.nz), kThreads, 0, st>>>(gc, x, gi, y);
+    k_copy<<<grid_for(gc), kThreads, 0, st>>>(gc, x, gi, y);
     return cudaGetLastError();
 }
 

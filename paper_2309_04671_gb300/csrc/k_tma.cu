@@ -65,17 +65,19 @@ struct Cfg {
     static constexpr int NT = NTX * NTY;
     // warps synchronise (one CTA barrier) after every BAR_EVERY planes; the
     // barrier releases the stages of those planes and thread 0 refills them
-    static constexpr int BAR_EVERY = LOW ? 1 : kUnroll;
+    static constexpr int BAR_EVERY = kUnroll;
     static constexpr int BW = kTX + 8;                 // x: 4-wide halo each side
     static constexpr int BH = TY + 2 * R;
     // TMA landing ring of u boxes (storage type).  FP32: computed on in place,
-    // planes k..k+R resident + 4 ahead.  16-bit: converted on arrival, 3 ahead.
+    // planes k..k+R resident + 4 ahead.  16-bit: converted on arrival, 2 ahead
+    // (small rings keep three CTAs per SM).
     // Each stage completes on its own mbarrier (expect_tx).
-    static constexpr int SL = LOW ? 4 : R + 5;
+    static constexpr int SL = LOW ? 3 : R + 5;
     static constexpr int L_BYTES = BW * BH * ES;
     static constexpr int L_STRIDE = (L_BYTES + 127) / 128 * 128;
-    // 16-bit: FP32 copies of the last R+1 stencil-centre planes
-    static constexpr int SF = LOW ? R + 1 : 0;
+    // 16-bit: FP32 copies of the last R+2 stencil-centre planes (one more than
+    // R+1 because warps synchronise only every kUnroll planes)
+    static constexpr int SF = LOW ? R + 2 : 0;
     static constexpr int F_STRIDE = (BW * BH * 4 + 127) / 128 * 128;
     // u_prev tile (storage type).  Its box must start on 16 bytes: FP32 at
     // the tile's first interior column (halo % 4 == 0), 16-bit 4 columns
@@ -86,7 +88,7 @@ struct Cfg {
     static constexpr int PVU_BYTES = PVU_W * TY * ES;
     static constexpr int PVV_BYTES = kTX * TY * 4;     // vel tile (FP32)
     static constexpr int PV_STRIDE = PVU_BYTES + PVV_BYTES;
-    static constexpr int SP = LOW ? 4 : 5;
+    static constexpr int SP = LOW ? 3 : 5;
     static constexpr size_t SMEM_L = (size_t)SL * L_STRIDE;
     static constexpr size_t SMEM_F = (size_t)SF * F_STRIDE;
     static constexpr size_t SMEM_PV = MODE == kWave ? (size_t)SP * PV_STRIDE : 0;
