@@ -174,6 +174,26 @@ gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float *vel, floa
                                  const gbs_opts *opts, void *stream);
 
 /*
+ * Error norms of a field against a reference over the interior, accumulated
+ * in FP64 (the accuracy metrics of Sec. 11.1: maximum absolute error and RMSD
+ * against a reference implementation, plus scale-free versions).
+ *   x, ref        DEVICE float fields, padded layout; ref may be NULL (norms
+ *                 of x itself, as if ref were zero).
+ *   out           DEVICE double[8]: max|x-ref|, max|ref|, sum (x-ref)^2,
+ *                 sum ref^2, number of points, max|x-ref|/max|ref|,
+ *                 sqrt(sum (x-ref)^2 / sum ref^2), sqrt(sum (x-ref)^2 / n).
+ *   work          DEVICE scratch of at least gbs_norms_workspace_bytes(ny, nz)
+ *                 bytes (one record of 4 doubles per 64 rows), 8-byte aligned,
+ *                 owned by the caller; its contents do not matter.
+ * The result does not depend on the order of launch or the stream: the
+ * partial records are reduced in a fixed order.
+ * Errors: GBS_EINVAL (null pointer, small workspace), GBS_ECUDA.
+ */
+size_t gbs_norms_workspace_bytes(int64_t ny, int64_t nz);
+gbs_status gbs_field_norms(const float *x, const float *ref, int64_t nx, int64_t ny, int64_t nz, int halo,
+                           double *out, void *work, size_t work_bytes, void *stream);
+
+/*
  * The library's weights of the centred second derivative of order 2R
  * (unit spacing), the values of c_xm, c_ym, c_zm used by gbs_wave_step:
  * out[0] = c_0, out[m] = c_m, m = 1..R.  HOST out[radius+1].

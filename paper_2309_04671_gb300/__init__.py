@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4
 
 # Entry points declared in include/gbstencil.h (checked by the tests).
 EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
-           "gbs_wave_propagate_lp", "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take",
+           "gbs_wave_propagate_lp", "gbs_norms_workspace_bytes", "gbs_field_norms", "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take",
            "gbs_device_status", "gbs_last_error", "gbs_version")
 
 GBS_F32, GBS_BF16, GBS_F16 = 0, 1, 2
@@ -89,6 +89,10 @@ def load() -> ctypes.CDLL:
         lib.gbs_wave_propagate_lp.argtypes = [vp, vp, vp, c_float, c_float, i64, i64, i64, c_int, i64, i64,
                                               ctypes.POINTER(_Src), ctypes.POINTER(_Rec), c_int, vp, ctypes.c_size_t,
                                               ctypes.POINTER(_Opts), vp]
+        lib.gbs_norms_workspace_bytes.argtypes = [i64, i64]
+        lib.gbs_norms_workspace_bytes.restype = ctypes.c_size_t
+        lib.gbs_field_norms.argtypes = [vp, vp, i64, i64, i64, c_int, vp, vp, ctypes.c_size_t, vp]
+        lib.gbs_field_norms.restype = ctypes.c_int
         lib.gbs_fd2_coeffs.argtypes = [c_int, fp]
         lib.gbs_profile_enable.argtypes = [c_int]
         lib.gbs_profile_take.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -292,6 +296,33 @@ def wave_propagate_lp(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, 
                                         int(t0), _ptr(src), _ptr(rec), _STORAGE[storage], base + off,
                                         work.numel() - off, ctypes.byref(opts), _stream(stream)))
     return (u, u_prev) if nsteps % 2 else (u_prev, u)
+
+
+NORM_KEYS = ("max_abs", "ref_max", "sum_sq_diff", "sum_sq_ref", "npoints", "norm_max_rel", "l2_rel", "rmsd")
+
+
+def field_norms(x: torch.Tensor, ref: Optional[torch.Tensor] = None, *, halo: int, out: Optional[torch.Tensor] = None,
+                work: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """FP64 error norms of ``x`` against ``ref`` over the interior; returns a
+    device float64 tensor of 8 values (see NORM_KEYS)."""
+    px = _field(x, "x")
+    pr = None
+    if ref is not None:
+        pr = _field(ref, "ref")
+        _same_shape(x, ref)
+    nx, ny, nz = _dims(x, halo)
+    if out is None:
+        out = torch.empty(8, dtype=torch.float64, device=x.device)
+    need = int(load().gbs_norms_workspace_bytes(ny, nz))
+    if work is None:
+        work = torch.empty(max(need, 8), dtype=torch.uint8, device=x.device)
+    _check(load().gbs_field_norms(px, pr, nx, ny, nz, halo, out.data_ptr(), work.data_ptr(), work.numel(),
+                                  _stream(stream)))
+    return out
+
+
+def norms_dict(t: torch.Tensor) -> dict:
+    return dict(zip(NORM_KEYS, (float(v) for v in t.cpu())))
 
 
 def device_status(stream=None) -> None:

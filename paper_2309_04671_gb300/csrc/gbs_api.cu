@@ -608,6 +608,40 @@ extern "C" gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float
     return graph ? run_captured(st, enqueue) : enqueue();
 }
 
+extern "C" size_t gbs_norms_workspace_bytes(int64_t ny, int64_t nz)
+{
+    if (ny < 0 || nz < 0)
+        return 0;
+    Grid g = dense_grid(0, ny, nz, 0);
+    return (size_t)norms_partials(g) * 4 * sizeof(double);
+}
+
+extern "C" gbs_status gbs_field_norms(const float *x, const float *ref, int64_t nx, int64_t ny, int64_t nz,
+                                      int halo, double *out, void *work, size_t work_bytes, void *stream)
+{
+    t_err[0] = 0;
+    gbs_status s = check_dims(nx, ny, nz, halo);
+    if (s != GBS_OK)
+        return s;
+    if (!out)
+        return fail(GBS_EINVAL, "null output");
+    const Grid g = dense_grid(nx, ny, nz, halo);
+    const size_t need = (size_t)norms_partials(g) * 4 * sizeof(double);
+    if ((nx > 0 && ny > 0 && nz > 0) && !x)
+        return fail(GBS_EINVAL, "null field pointer");
+    if (need > 0 && (!work || work_bytes < need))
+        return fail(GBS_EINVAL, "workspace of %zu bytes needed (got %zu)", need, work_bytes);
+    if ((reinterpret_cast<uintptr_t>(work) & 7u) != 0)
+        return fail(GBS_EINVAL, "workspace must be 8-byte aligned");
+    Grid ge = g;
+    if (nx == 0 || ny == 0 || nz == 0)
+        ge.ny = ge.nz = 0;   // no rows: only the final pass runs (zeros)
+    cudaError_t e = launch_norms(ge, x, ref, out, static_cast<double *>(work), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return cuda_fail(e, "norms launch");
+    return GBS_OK;
+}
+
 extern "C" gbs_status gbs_fd2_coeffs(int radius, float *out)
 {
     t_err[0] = 0;

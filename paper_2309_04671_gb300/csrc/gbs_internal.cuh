@@ -135,6 +135,14 @@ cudaError_t launch_inject(const Grid &g, float *u_next, const float *vel, float 
 cudaError_t launch_record(const Grid &g, const float *u_next, const gbs_rec *rec, int64_t step,
                           cudaStream_t st);
 
+// Error norms (k_norms.cu): one FP64 partial record of 4 doubles per block
+// of kNormRowsPerBlock rows; `out` receives kNormOut doubles.
+constexpr int kNormRowsPerBlock = 64;
+constexpr int kNormOut = 8;
+int64_t norms_partials(const Grid &g);
+cudaError_t launch_norms(const Grid &g, const float *x, const float *ref, double *out, double *part,
+                         cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // PTX helpers (sm_90+ mbarrier / TMA; valid on sm_103a)
 // ---------------------------------------------------------------------------

@@ -115,3 +115,15 @@ def test_explicit_tma_choice_checks_alignment(lib):
     rc = lib.gbs_wave_propagate(fake[0], fake[1], fake[2], ctypes.c_float(1e-3), ctypes.c_float(10.0), 6, 4, 4,
                                 4, 3, 0, None, None, ctypes.byref(opts), None)
     assert rc == gbs.GBS_EALIGN
+
+
+def test_norms_workspace_and_validation(lib):
+    # one record of 4 doubles per 64 rows of the interior
+    assert lib.gbs_norms_workspace_bytes(10, 13) == ((10 * 13 + 63) // 64) * 32
+    assert lib.gbs_norms_workspace_bytes(512, 512) == 4096 * 32
+    out = ctypes.c_void_p(1 << 20)
+    small = ctypes.c_void_p(2 << 20)
+    x = ctypes.c_void_p(3 << 20)
+    assert lib.gbs_field_norms(x, None, 8, 8, 8, 4, out, small, 8, None) == gbs.GBS_EINVAL
+    assert b"workspace" in lib.gbs_last_error()
+    assert lib.gbs_field_norms(x, None, 8, 8, 8, 4, None, small, 64, None) == gbs.GBS_EINVAL
