@@ -194,6 +194,32 @@ gbs_status gbs_field_norms(const float *x, const float *ref, int64_t nx, int64_t
                            double *out, void *work, size_t work_bytes, void *stream);
 
 /*
+ * gbs_field_norms without a workspace: the same norms, with the partial
+ * records kept in a scratch array built into the library instead of caller
+ * memory.  The paper has no counterpart; this entry point exists for callers
+ * that cannot allocate device memory at the point where they need the
+ * norms -- code running while a stream is being captured into a CUDA graph
+ * (cudaMalloc is not permitted there), host code inside a latency-critical
+ * loop where cudaMalloc/cudaFree could synchronise the device, or a host
+ * application whose own allocator owns all device memory and cannot be
+ * reached through this C interface.
+ *   x, ref, out   as gbs_field_norms (out: DEVICE double[8]).
+ * Limit: the built-in scratch holds 16384 records of 64 rows, i.e. interiors
+ * with ny*nz <= 1,048,576 (for example 1024 x 1024 in y and z, any nx);
+ * larger interiors are rejected with GBS_EINVAL and a message naming the
+ * limit.  The array (512 KiB) is held by every GPU that loads the library
+ * until the process exits, and every call shares it: calls that overlap on
+ * the GPU (on different streams, or from different threads) race and must
+ * be serialised by the caller.  Nothing in it needs clearing between calls.
+ * The first call on a device looks up the array's device address (and may
+ * load the library's GPU code on that device); make that first call outside
+ * any stream capture.  No device memory is allocated or freed.
+ * Errors: GBS_EINVAL, GBS_ECUDA.
+ */
+gbs_status gbs_field_norms_noalloc(const float *x, const float *ref, int64_t nx, int64_t ny, int64_t nz,
+                                   int halo, double *out, void *stream);
+
+/*
  * The library's weights of the centred second derivative of order 2R
  * (unit spacing), the values of c_xm, c_ym, c_zm used by gbs_wave_step:
  * out[0] = c_0, out[m] = c_m, m = 1..R.  HOST out[radius+1].

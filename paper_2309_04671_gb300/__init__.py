@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4
 
 # Entry points declared in include/gbstencil.h (checked by the tests).
 EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
-           "gbs_wave_propagate_lp", "gbs_norms_workspace_bytes", "gbs_field_norms", "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take",
+           "gbs_wave_propagate_lp", "gbs_norms_workspace_bytes", "gbs_field_norms", "gbs_field_norms_noalloc",
+           "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take",
            "gbs_device_status", "gbs_last_error", "gbs_version")
 
 GBS_F32, GBS_BF16, GBS_F16 = 0, 1, 2
@@ -93,6 +94,8 @@ def load() -> ctypes.CDLL:
         lib.gbs_norms_workspace_bytes.restype = ctypes.c_size_t
         lib.gbs_field_norms.argtypes = [vp, vp, i64, i64, i64, c_int, vp, vp, ctypes.c_size_t, vp]
         lib.gbs_field_norms.restype = ctypes.c_int
+        lib.gbs_field_norms_noalloc.argtypes = [vp, vp, i64, i64, i64, c_int, vp, vp]
+        lib.gbs_field_norms_noalloc.restype = ctypes.c_int
         lib.gbs_fd2_coeffs.argtypes = [c_int, fp]
         lib.gbs_profile_enable.argtypes = [c_int]
         lib.gbs_profile_take.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -318,6 +321,24 @@ def field_norms(x: torch.Tensor, ref: Optional[torch.Tensor] = None, *, halo: in
         work = torch.empty(max(need, 8), dtype=torch.uint8, device=x.device)
     _check(load().gbs_field_norms(px, pr, nx, ny, nz, halo, out.data_ptr(), work.data_ptr(), work.numel(),
                                   _stream(stream)))
+    return out
+
+
+def field_norms_noalloc(x: torch.Tensor, ref: Optional[torch.Tensor], out: torch.Tensor, *, halo: int,
+                        stream=None) -> torch.Tensor:
+    """field_norms without a workspace: for callers that cannot allocate device
+    memory where they need the norms (the library keeps the scratch; ``out``
+    is the caller's device float64 tensor of 8 values).  See the header for
+    the size limit and the rule that overlapping calls race."""
+    px = _field(x, "x")
+    pr = None
+    if ref is not None:
+        pr = _field(ref, "ref")
+        _same_shape(x, ref)
+    if not (out.is_cuda and out.dtype == torch.float64 and out.numel() >= 8 and out.is_contiguous()):
+        raise TypeError("out must be a contiguous CUDA float64 tensor of at least 8 values")
+    nx, ny, nz = _dims(x, halo)
+    _check(load().gbs_field_norms_noalloc(px, pr, nx, ny, nz, halo, out.data_ptr(), _stream(stream)))
     return out
 
 

@@ -642,6 +642,38 @@ extern "C" gbs_status gbs_field_norms(const float *x, const float *ref, int64_t 
     return GBS_OK;
 }
 
+extern "C" gbs_status gbs_field_norms_noalloc(const float *x, const float *ref, int64_t nx, int64_t ny,
+                                              int64_t nz, int halo, double *out, void *stream)
+{
+    t_err[0] = 0;
+    gbs_status s = check_dims(nx, ny, nz, halo);
+    if (s != GBS_OK)
+        return s;
+    if (!out)
+        return fail(GBS_EINVAL, "null output");
+    Grid g = dense_grid(nx, ny, nz, halo);
+    if (nx == 0 || ny == 0 || nz == 0)
+        g.ny = g.nz = 0;   // no rows: only the final pass runs (zeros)
+    else if (!x)
+        return fail(GBS_EINVAL, "null field pointer");
+    const int64_t records = norms_partials(g);
+    if (records > kNormStaticRecords)
+        return fail(GBS_EINVAL,
+                    "gbs_field_norms_noalloc: the interior has %lld rows (ny*nz) but its built-in scratch holds "
+                    "at most %lld (%lld records of %d rows); use gbs_field_norms with a workspace",
+                    (long long)(g.ny * g.nz), (long long)(kNormStaticRecords * kNormRowsPerBlock),
+                    (long long)kNormStaticRecords, kNormRowsPerBlock);
+    double *scratch = nullptr;
+    cudaError_t e = norms_static_scratch(&scratch);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "cudaGetSymbolAddress of the built-in norms scratch");
+    // pass 1 writes every record pass 2 reads: nothing in the array needs clearing
+    e = launch_norms(g, x, ref, out, scratch, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess)
+        return cuda_fail(e, "norms launch");
+    return GBS_OK;
+}
+
 extern "C" gbs_status gbs_fd2_coeffs(int radius, float *out)
 {
     t_err[0] = 0;

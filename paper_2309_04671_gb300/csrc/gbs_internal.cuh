@@ -140,6 +140,9 @@ cudaError_t launch_record(const Grid &g, const float *u_next, const gbs_rec *rec
 constexpr int kNormRowsPerBlock = 64;
 constexpr int kNormOut = 8;
 int64_t norms_partials(const Grid &g);
+// Records the allocation-free norms entry point can hold (its static scratch).
+constexpr int64_t kNormStaticRecords = 16384;
+cudaError_t norms_static_scratch(double **ptr);
 cudaError_t launch_norms(const Grid &g, const float *x, const float *ref, double *out, double *part,
                          cudaStream_t st);
 

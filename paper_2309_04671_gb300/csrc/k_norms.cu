@@ -7,9 +7,17 @@
 // rows (a row = nx points along x) one partial record (max|x-ref|, max|ref|,
 // sum (x-ref)^2, sum ref^2) in a scratch array; pass 2 reduces the records in
 // a fixed order with one CTA and writes the results.
+#include <mutex>
+
 #include "gbs_internal.cuh"
 
 namespace gbs {
+
+// Scratch of the allocation-free entry point (gbs_field_norms_noalloc): the
+// partial records live in this file-scope array instead of caller memory.
+// Every GPU that loads the library holds it (512 KiB) until the process
+// exits.  All calls share it: calls that overlap on the GPU race.
+static __device__ __align__(256) double g_norm_scratch[kNormStaticRecords * 4];
 
 namespace {
 
@@ -91,6 +99,33 @@ __global__ void __launch_bounds__(kThreads) k_norms_final(const double *part, in
 }
 
 }  // namespace
+
+// Device address of g_norm_scratch on the current device.  Host code cannot
+// use the array's name as a device pointer, so the address is looked up once
+// per device (with that device current) and cached.  The first lookup on a
+// device may load the module there, so it must not happen inside a stream
+// capture.
+cudaError_t norms_static_scratch(double **ptr)
+{
+    static std::mutex mu;
+    static double *cache[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= 64)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cache[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_norm_scratch);
+        if (e != cudaSuccess)
+            return e;
+        cache[dev] = static_cast<double *>(p);
+    }
+    *ptr = cache[dev];
+    return cudaSuccess;
+}
 
 int64_t norms_partials(const Grid &g)
 {
