@@ -37,7 +37,8 @@
  *     other shapes take a plain-load kernel with the same arithmetic.
  *   - gbs_last_error() returns a message for the last failing call of the
  *     calling thread.
- *   - Nothing here allocates device memory.
+ *   - Nothing here allocates device memory, except batch plans
+ *     (gbs_batch_plan_create), which own their buffers until destroyed.
  */
 #ifndef GBSTENCIL_H
 #define GBSTENCIL_H
@@ -172,6 +173,51 @@ gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float *vel, floa
                                  int64_t t0, const gbs_src *src, const gbs_rec *rec,
                                  gbs_dtype storage, void *work, size_t work_bytes,
                                  const gbs_opts *opts, void *stream);
+
+/*
+ * Batched propagation: many independent shots -- each its own grid sizes,
+ * velocity model, dt, h and up to 16 point sources -- advanced together, one
+ * kernel launch per time step covering every shot (Algorithm 1 per shot).
+ * The plan copies each shot into device buffers it owns, laid out so that any
+ * grid size meets the TMA kernel's alignment rules, with fields stored in
+ * `storage` (GBS_F32, or GBS_BF16/GBS_F16 with per-field power-of-two scales
+ * as gbs_wave_propagate_lp).  A run copies the shots' current fields in,
+ * advances them nsteps steps from time level t0 (u holds level t0, u_prev
+ * t0-1), and copies the two newest levels back: u receives t0+nsteps and
+ * u_prev t0+nsteps-1 whatever the parity of nsteps, so a run continues the
+ * previous one with t0 advanced by its nsteps.  Only the interior is copied:
+ * the halo is taken as zero (Dirichlet), as in gbs_wave_propagate_lp.  The
+ * caller's pointers in `shots` (fields, velocity, source arrays) are kept
+ * and must stay valid for the plan's life.  Receivers are not recorded by
+ * batch plans.
+ *   opts          tile_y (16/32) and zchunk fix the kernel's tiling; if both
+ *                 are 0 (or opts is NULL) plan creation times the candidates
+ *                 on the plan's own buffers and keeps the fastest (autotuner).
+ *   use_graph     run: 1 = capture the run into a CUDA graph, cached in the
+ *                 plan for the same (nsteps, t0), and launch it (ignored on
+ *                 the legacy default stream, NULL).
+ * Plan creation allocates device memory (fields: 2 x storage + 4 bytes per
+ * point of every shot, plus small tables) and synchronises `stream`.
+ * Errors: GBS_EINVAL, GBS_ECUDA.
+ */
+typedef struct {
+    int64_t nx, ny, nz;     /* interior of this shot */
+    int halo;               /* >= 4 */
+    float *u_prev, *u;      /* DEVICE FP32 fields in the padded layout, updated by each run */
+    const float *vel;       /* DEVICE FP32 velocity, read at each run */
+    float dt, h;
+    gbs_src src;            /* at most 16 sources (n = 0: none) */
+} gbs_shot;
+
+typedef struct gbs_batch_plan gbs_batch_plan;
+
+gbs_status gbs_batch_plan_create(gbs_batch_plan **plan, const gbs_shot *shots, int nshots, gbs_dtype storage,
+                                 const gbs_opts *opts, void *stream);
+gbs_status gbs_batch_run(gbs_batch_plan *plan, int64_t nsteps, int64_t t0, int use_graph, void *stream);
+/* The tiling the plan uses, its number of work items and interior points. */
+gbs_status gbs_batch_plan_info(const gbs_batch_plan *plan, int *tile_y, int *zchunk, int64_t *items,
+                               int64_t *points);
+void gbs_batch_plan_destroy(gbs_batch_plan *plan);
 
 /*
  * Error norms of a field against a reference over the interior, accumulated

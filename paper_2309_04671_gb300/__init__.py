@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4
 # Entry points declared in include/gbstencil.h (checked by the tests).
 EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
            "gbs_wave_propagate_lp", "gbs_norms_workspace_bytes", "gbs_field_norms", "gbs_field_norms_noalloc",
+           "gbs_batch_plan_create", "gbs_batch_run", "gbs_batch_plan_info", "gbs_batch_plan_destroy",
            "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take",
            "gbs_device_status", "gbs_last_error", "gbs_version")
 
@@ -56,6 +57,12 @@ class _Rec(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("tile_y", ctypes.c_int), ("zchunk", ctypes.c_int),
                 ("use_graph", ctypes.c_int)]
+
+
+class _Shot(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("halo", ctypes.c_int),
+                ("u_prev", ctypes.c_void_p), ("u", ctypes.c_void_p), ("vel", ctypes.c_void_p),
+                ("dt", ctypes.c_float), ("h", ctypes.c_float), ("src", _Src)]
 
 
 _lock = threading.Lock()
@@ -96,6 +103,16 @@ def load() -> ctypes.CDLL:
         lib.gbs_field_norms.restype = ctypes.c_int
         lib.gbs_field_norms_noalloc.argtypes = [vp, vp, i64, i64, i64, c_int, vp, vp]
         lib.gbs_field_norms_noalloc.restype = ctypes.c_int
+        lib.gbs_batch_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Shot), c_int, c_int,
+                                              ctypes.POINTER(_Opts), vp]
+        lib.gbs_batch_plan_create.restype = c_int
+        lib.gbs_batch_run.argtypes = [vp, i64, i64, c_int, vp]
+        lib.gbs_batch_run.restype = c_int
+        lib.gbs_batch_plan_info.argtypes = [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                            ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.gbs_batch_plan_info.restype = c_int
+        lib.gbs_batch_plan_destroy.argtypes = [vp]
+        lib.gbs_batch_plan_destroy.restype = None
         lib.gbs_fd2_coeffs.argtypes = [c_int, fp]
         lib.gbs_profile_enable.argtypes = [c_int]
         lib.gbs_profile_take.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -104,7 +121,8 @@ def load() -> ctypes.CDLL:
         lib.gbs_last_error.argtypes = []
         lib.gbs_version.argtypes = []
         for f in ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_wave_propagate_lp",
-                  "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take", "gbs_device_status", "gbs_version"):
+                  "gbs_batch_plan_create", "gbs_batch_run", "gbs_batch_plan_info", "gbs_batch_plan_destroy",
+           "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take", "gbs_device_status", "gbs_version"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -299,6 +317,62 @@ def wave_propagate_lp(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, 
                                         int(t0), _ptr(src), _ptr(rec), _STORAGE[storage], base + off,
                                         work.numel() - off, ctypes.byref(opts), _stream(stream)))
     return (u, u_prev) if nsteps % 2 else (u_prev, u)
+
+
+class Shot:
+    """One independent problem of a batch: its two FP32 wave fields (updated
+    in place by every run), velocity, dt, h, halo and up to 16 sources."""
+
+    def __init__(self, u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, dt: float, h: float, halo: int,
+                 src_idx=None, src_amp=None):
+        self.u_prev, self.u, self.vel = u_prev, u, vel
+        self.dt, self.h, self.halo = float(dt), float(h), int(halo)
+        self.src_idx, self.src_amp = src_idx, src_amp
+
+
+class BatchPlan:
+    """Many shots advanced together, one batched kernel launch per step
+    (gbs_batch_plan_create / gbs_batch_run).  After ``run(n, t0)`` each shot's
+    ``u`` holds u^{t0+n} and ``u_prev`` u^{t0+n-1}; the next run continues
+    with ``t0 + n``.  ``tile_y = zchunk = 0`` lets the plan time the tilings
+    and keep the fastest."""
+
+    def __init__(self, shots: Sequence[Shot], *, storage="f32", tile_y: int = 0, zchunk: int = 0, stream=None):
+        lib = load()
+        arr = (_Shot * len(shots))()
+        self._keep = list(shots)
+        for k, sh in enumerate(shots):
+            p = [_field(t, n) for t, n in ((sh.u_prev, "u_prev"), (sh.u, "u"), (sh.vel, "vel"))]
+            _same_shape(sh.u, sh.u_prev, sh.vel)
+            nx, ny, nz = _dims(sh.u, sh.halo)
+            src = _make_src(sh.src_idx, sh.src_amp) or _Src(0, None, None, 0)
+            arr[k] = _Shot(nx, ny, nz, sh.halo, p[0], p[1], p[2], sh.dt, sh.h, src)
+        self._plan = ctypes.c_void_p()
+        opts = _opts(0, tile_y, zchunk, False)
+        _check(lib.gbs_batch_plan_create(ctypes.byref(self._plan), arr, len(shots), _STORAGE[storage],
+                                         ctypes.byref(opts), _stream(stream)))
+
+    def run(self, nsteps: int, t0: int = 0, *, use_graph: bool = False, stream=None) -> None:
+        if not self._plan:
+            raise RuntimeError("plan is closed")
+        _check(load().gbs_batch_run(self._plan, int(nsteps), int(t0), 1 if use_graph else 0, _stream(stream)))
+
+    def info(self) -> dict:
+        ty, zc, items, pts = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().gbs_batch_plan_info(self._plan, ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(items),
+                                          ctypes.byref(pts)))
+        return {"tile_y": ty.value, "zchunk": zc.value, "items": items.value, "points": pts.value}
+
+    def close(self) -> None:
+        if getattr(self, "_plan", None):
+            load().gbs_batch_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 NORM_KEYS = ("max_abs", "ref_max", "sum_sq_diff", "sum_sq_ref", "npoints", "norm_max_rel", "l2_rel", "rmsd")

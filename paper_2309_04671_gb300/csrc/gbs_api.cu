@@ -250,7 +250,8 @@ gbs_status run_step(const StepPlan &sp, const Grid &g, const void *u_prev, const
         StepParams p;
         memset(&p, 0, sizeof(p));
         p.g = g;
-        p.out = u_next;
+        p.out[0] = u_next;
+        p.out[1] = u_next;
         p.cf = wave_coeffs();
         p.s = s;
         p.dt = dt;
@@ -259,16 +260,12 @@ gbs_status run_step(const StepPlan &sp, const Grid &g, const void *u_prev, const
         p.iny = gx.ny;
         if (fused && has_src) {
             p.src_idx = src->idx;
-            p.src_amp = src->amp + t * src->n;
+            p.src_amp = src->amp;
+            p.src_nt = src->nt;
             p.nsrc = (int)src->n;
         }
-        if (meta) {
-            p.meta = meta;
-            p.slot_u = (int)(t % kMetaSlots);
-            p.slot_next = (int)((t + 1) % kMetaSlots);
-            p.slot_prev = (int)((t + 2) % kMetaSlots);
-        }
-        e = launch_tma(4, kWave, sp.tile_y, sp.storage, sp.tma, p, st);
+        p.meta = meta;
+        e = launch_tma(4, kWave, sp.tile_y, sp.storage, sp.tma, p, t, st);
     } else {
         WaveArgs w{static_cast<const float *>(u_prev), vel, s};
         e = launch_generic(4, kWave, g, static_cast<const float *>(u), static_cast<float *>(u_next), wave_coeffs(), w,
@@ -373,6 +370,26 @@ gbs_status check_wave_fields(const Grid &g, const float *u_prev, const float *u,
 }
 
 }  // namespace
+
+gbs_status set_error(gbs_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(t_err, sizeof(t_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+gbs_status set_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+void clear_error() { t_err[0] = 0; }
+Coeffs wave_weights() { return wave_coeffs(); }
+gbs_status make_tensor_map(CUtensorMap *m, const void *base, const Grid &g, int bw, int bh, gbs_dtype dt)
+{
+    return make_map(m, base, g, bw, bh, dt);
+}
+Grid internal_grid(int64_t nx, int64_t ny, int64_t nz) { return lp_layout(nx, ny, nz).g; }
+Grid dense_layout(int64_t nx, int64_t ny, int64_t nz, int halo) { return dense_grid(nx, ny, nz, halo); }
+int64_t grid_elems(const Grid &g) { return field_elems(g); }
+
 }  // namespace gbs
 
 using namespace gbs;
@@ -419,9 +436,10 @@ extern "C" gbs_status gbs_stencil_apply(const float *in, float *out, int64_t nx,
         StepParams p;
         memset(&p, 0, sizeof(p));
         p.g = g;
-        p.out = out;
+        p.out[0] = out;
+        p.out[1] = out;
         p.cf = cf;
-        e = launch_tma(radius, kStencil, 16, GBS_F32, plan, p, st);
+        e = launch_tma(radius, kStencil, 16, GBS_F32, plan, p, 0, st);
     } else {
         WaveArgs w{nullptr, nullptr, 0.f};
         e = launch_generic(radius, kStencil, g, in, out, cf, w, 0, st);

@@ -81,21 +81,31 @@ __device__ __forceinline__ int lp_scale_exponent(float m)
     return s < -100 ? -100 : (s > 100 ? 100 : s);
 }
 
-// Arguments of one launch of the TMA kernel.
+// Arguments of the TMA kernel for one field (one shot).  A launch also
+// gets the time level t of u (the step writes u^{t+1}) and the ping-pong
+// parity, which selects the output buffer.
 struct StepParams {
     Grid g;                    // geometry of u, u_prev, vel and out
-    void *out;                 // storage type of the launch
+    void *out[2];              // output buffer for parity 0 / 1 (storage type of the launch)
     Coeffs cf;
     float s;                   // dt / h
     float dt;
-    int zchunk;                // planes per CTA (0 = default)
-    int tiles_x;               // set by the launcher
+    int zchunk;                // planes per CTA (0 = default; single-field launches)
+    int tiles_x;               // set by the launcher (single-field launches)
     const int64_t *src_idx;    // fused sources: interior linear indices
-    const float *src_amp;      // this step's row f^n (nullptr: no injection this step)
+    const float *src_amp;      // source function, rows [src_nt][nsrc]; row t is injected if t < src_nt
+    int64_t src_nt;
     int nsrc;                  // <= kMaxFusedSrc
-    int *meta;                 // 16-bit storage state (kMetaSlots x kMetaInts), else nullptr
-    int slot_prev, slot_u, slot_next;
+    int *meta;                 // 16-bit storage state (kMetaSlots x kMetaInts; slot of level t = t % 3), else nullptr
     int64_t inx, iny;          // interior sizes that interior linear indices refer to
+};
+
+// One CTA's work in a batched launch: a 64 x TY tile of shot `shot`,
+// output planes [z0, z1).
+struct BatchItem {
+    int shot;
+    int tx0, ty0;
+    int z0, z1;
 };
 
 // Launchers (return a cudaError_t of the launch).
@@ -108,7 +118,13 @@ struct TmaPlan {
     CUtensorMap vel;     // box 64 x TY x 1 (wave mode), FP32
 };
 cudaError_t launch_tma(int radius, Mode mode, int tile_y, gbs_dtype storage, const TmaPlan &plan,
-                       const StepParams &p, cudaStream_t st);
+                       const StepParams &p, int64_t t, cudaStream_t st);
+// Batched wave steps: one CTA per item; shots[i] and maps[(i*2 + parity)*3 + {0,1,2}]
+// (u, u_prev, vel descriptors) live in device memory.
+cudaError_t launch_tma_batch(int tile_y, gbs_dtype storage, const BatchItem *items, int nitems,
+                             const StepParams *shots, const CUtensorMap *maps, int parity, int64_t t,
+                             cudaStream_t st);
+cudaError_t tma_prepare_batch(gbs_dtype storage, int tile_y);
 int tma_default_zchunk(int radius, Mode mode, int tile_y, gbs_dtype storage, const Grid &g);
 // Sets the wave kernel's shared-memory attribute (call before stream capture).
 cudaError_t tma_prepare_wave(gbs_dtype storage, int tile_y);
@@ -122,6 +138,20 @@ cudaError_t launch_lp_encode(gbs_dtype storage, const Grid &gc, const float *x, 
 cudaError_t launch_lp_decode(gbs_dtype storage, const Grid &gi, const void *q, const int *meta_slot,
                              const Grid &gc, float *x, cudaStream_t st);
 cudaError_t launch_copy_f32(const Grid &gc, const float *x, const Grid &gi, float *y, cudaStream_t st);
+cudaError_t launch_copy_back_f32(const Grid &gi, const float *y, const Grid &gc, float *x, cudaStream_t st);
+
+// Shared by the API files: status helpers, the weights, TMA descriptors and
+// the internal layout of library-owned fields.
+gbs_status set_error(gbs_status s, const char *fmt, ...);
+gbs_status set_cuda_error(cudaError_t e, const char *what);
+void clear_error();
+Coeffs wave_weights();
+gbs_status make_tensor_map(CUtensorMap *m, const void *base, const Grid &g, int bw, int bh, gbs_dtype dt);
+// interior (nx, ny, nz), halo 4, nx rounded up to a multiple of 4 (dead
+// columns), rows padded to a multiple of 8 elements
+Grid internal_grid(int64_t nx, int64_t ny, int64_t nz);
+Grid dense_layout(int64_t nx, int64_t ny, int64_t nz, int halo);
+int64_t grid_elems(const Grid &g);
 cudaError_t launch_lp_record(gbs_dtype storage, const Grid &gc, const Grid &gi, const void *q,
                              const int *meta_slot, const gbs_rec *rec, int64_t step, cudaStream_t st);
 

@@ -84,9 +84,10 @@ __global__ void __launch_bounds__(kThreads) k_decode(Grid gi, const T *q, const 
     GBS_ROW_LOOP(gc) { x[row_index(gc, i, row, gc.ny)] = get(q + row_index(gi, i, row, gc.ny)) * sc; }
 }
 
-__global__ void __launch_bounds__(kThreads) k_copy(Grid gc, const float *x, Grid gi, float *y)
+// copy the interior of gc's extent (nx, ny, nz) from layout gs to layout gd
+__global__ void __launch_bounds__(kThreads) k_copy(Grid gc, Grid gs, const float *x, Grid gd, float *y)
 {
-    GBS_ROW_LOOP(gc) { y[row_index(gi, i, row, gc.ny)] = x[row_index(gc, i, row, gc.ny)]; }
+    GBS_ROW_LOOP(gc) { y[row_index(gd, i, row, gc.ny)] = x[row_index(gs, i, row, gc.ny)]; }
 }
 
 template <typename T>
@@ -151,7 +152,13 @@ cudaError_t launch_lp_decode(gbs_dtype storage, const Grid &gi, const void *q, c
 
 cudaError_t launch_copy_f32(const Grid &gc, const float *x, const Grid &gi, float *y, cudaStream_t st)
 {
-    k_copy<<<grid_for(gc), kThreads, 0, st>>>(gc, x, gi, y);
+    k_copy<<<grid_for(gc), kThreads, 0, st>>>(gc, gc, x, gi, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_back_f32(const Grid &gi, const float *y, const Grid &gc, float *x, cudaStream_t st)
+{
+    k_copy<<<grid_for(gc), kThreads, 0, st>>>(gc, gi, y, gc, x);
     return cudaGetLastError();
 }
 

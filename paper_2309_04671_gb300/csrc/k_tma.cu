@@ -216,10 +216,13 @@ __device__ __forceinline__ f2 xpair(const float4 &lf, const float4 &cen, const f
     return pk(w[i], w[i + 1]);
 }
 
+// One CTA's work: the output planes [z0, z1) of the 64 x TY tile at (tx0, ty0)
+// of the field described by p; t = time level of u, parity selects p.out.
 template <int R, int MODE, int TY, typename T>
-__global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::MIN_BLOCKS)
-    k_tma(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_prev,
-          const __grid_constant__ CUtensorMap tm_vel, const StepParams p)
+__device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, const CUtensorMap *__restrict__ pm_prev,
+                                         const CUtensorMap *__restrict__ pm_vel, const StepParams &p,
+                                         const int64_t tx0, const int64_t ty0, const int z0, const int z1,
+                                         const int64_t t, const int parity)
 {
     using C = Cfg<R, MODE, TY, T>;
     constexpr bool kLow = C::LOW;
@@ -240,10 +243,6 @@ __global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::
     const Grid &g = p.g;
     const int tid = threadIdx.x;
     const int tx = tid % C::NTX, ty = tid / C::NTX;
-    const int64_t tx0 = (int64_t)(blockIdx.x % p.tiles_x) * kTX;
-    const int64_t ty0 = (int64_t)(blockIdx.x / p.tiles_x) * TY;
-    const int z0 = blockIdx.y * p.zchunk;
-    const int z1 = (int)min((int64_t)z0 + p.zchunk, g.nz);
     const int nzc = z1 - z0;                   // output planes of this CTA
     const int H = g.halo;
     const int pfirst = z0 - R;                 // first u plane streamed
@@ -263,10 +262,10 @@ __global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::
     }
 
     if (tid == 0) {
-        prefetch_tmap(&tm_u);
+        prefetch_tmap(pm_u);
         if (MODE == kWave) {
-            prefetch_tmap(&tm_prev);
-            prefetch_tmap(&tm_vel);
+            prefetch_tmap(pm_prev);
+            prefetch_tmap(pm_vel);
         }
         for (int i = 0; i < C::SL; ++i)
             mbar_init(&full_u[i], 1);
@@ -278,7 +277,10 @@ __global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::
     __syncthreads();
 
     // point sources inside this CTA's box (fused injection)
-    if (MODE == kWave && p.src_amp != nullptr && tid < p.nsrc) {
+    const float *amp_row = (MODE == kWave && p.src_amp != nullptr && t >= 0 && t < p.src_nt)
+                               ? p.src_amp + t * p.nsrc
+                               : nullptr;
+    if (amp_row != nullptr && tid < p.nsrc) {
         const int64_t lin = p.src_idx[tid];
         if (lin < 0 || lin >= p.inx * p.iny * g.nz) {
             atomicCAS(&g_status_tma, 0u, (unsigned)GBS_EINVAL);
@@ -289,25 +291,27 @@ __global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::
                 s_src_x[slot] = (int)(i - tx0);
                 s_src_y[slot] = (int)(j - ty0);
                 s_src_z[slot] = (int)k;
-                s_src_f[slot] = p.src_amp[tid];
+                s_src_f[slot] = amp_row[tid];
             }
         }
     }
 
-    // epilogue constants (identity scales for FP32)
+    // epilogue constants (identity scales for FP32); 16-bit state slot of level t is t % 3
+    const int slot_u = (int)(t % kMetaSlots), slot_next = (int)((t + 1) % kMetaSlots),
+              slot_prev = (int)((t + 2) % kMetaSlots);
     float k_u = 1.f, k_p = 1.f, k_o = 1.f, sc_out = 1.f;
     if constexpr (kLow) {
         const int *m = p.meta;
-        const int s_u = m[p.slot_u * kMetaInts + kMetaScale];
-        const int s_p = m[p.slot_prev * kMetaInts + kMetaScale];
-        const int s_n = lp_scale_exponent(__int_as_float(m[p.slot_u * kMetaInts + kMetaMax]));
+        const int s_u = m[slot_u * kMetaInts + kMetaScale];
+        const int s_p = m[slot_prev * kMetaInts + kMetaScale];
+        const int s_n = lp_scale_exponent(__int_as_float(m[slot_u * kMetaInts + kMetaMax]));
         k_u = pow2f(s_u - s_n);
         k_p = pow2f(s_p - s_n);
         k_o = pow2f(-s_n);
         sc_out = pow2f(s_n);
-        if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
-            p.meta[p.slot_next * kMetaInts + kMetaScale] = s_n;
-            p.meta[p.slot_prev * kMetaInts + kMetaMax] = 0;   // the slot the next step accumulates into
+        if (tx0 == 0 && ty0 == 0 && z0 == 0 && tid == 0) {   // one CTA per field
+            p.meta[slot_next * kMetaInts + kMetaScale] = s_n;
+            p.meta[slot_prev * kMetaInts + kMetaMax] = 0;   // the slot the next step accumulates into
         }
     }
     __syncthreads();
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::
     auto issue_u = [&]() {
         const int st = n_u % C::SL;
         mbar_arrive_expect_tx(&full_u[st], C::L_BYTES);
-        tma_load_3d(land + st * C::L_STRIDE, &tm_u, (int)(H + tx0 - 4), (int)(H + ty0 - R), H + pfirst + n_u,
+        tma_load_3d(land + st * C::L_STRIDE, pm_u, (int)(H + tx0 - 4), (int)(H + ty0 - R), H + pfirst + n_u,
                     &full_u[st]);
         ++n_u;
     };
@@ -327,8 +331,8 @@ __global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::
         const int st = n_pv % C::SP;
         unsigned char *dst = pv + st * C::PV_STRIDE;
         mbar_arrive_expect_tx(&full_pv[st], C::PV_STRIDE);
-        tma_load_3d(dst, &tm_prev, (int)(H + tx0 - C::PVU_X0), (int)(H + ty0), H + z0 + n_pv, &full_pv[st]);
-        tma_load_3d(dst + C::PVU_BYTES, &tm_vel, (int)(H + tx0), (int)(H + ty0), H + z0 + n_pv, &full_pv[st]);
+        tma_load_3d(dst, pm_prev, (int)(H + tx0 - C::PVU_X0), (int)(H + ty0), H + z0 + n_pv, &full_pv[st]);
+        tma_load_3d(dst + C::PVU_BYTES, pm_vel, (int)(H + tx0), (int)(H + ty0), H + z0 + n_pv, &full_pv[st]);
         ++n_pv;
     };
     if (tid == 0) {
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::
         const int64_t gx = tx0 + 4 * tx;
         const int64_t gy = ty0 + kVY * ty;
         const bool xin = gx < g.nx;
-        T *out_base = static_cast<T *>(p.out) + (H + gx) + g.px * (H + gy);
+        T *out_base = static_cast<T *>(p.out[parity]) + (H + gx) + g.px * (H + gy);
         const int64_t plane_stride = g.px * g.py;
 
         // 16-bit: halo groups of 4 elements this thread converts each plane
@@ -605,10 +609,35 @@ __global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::
             float mx = 0.f;
             for (int w = 0; w < NCW; ++w)
                 mx = fmaxf(mx, s_red[w]);
-            atomicMax(reinterpret_cast<unsigned *>(p.meta + p.slot_next * kMetaInts + kMetaMax),
+            atomicMax(reinterpret_cast<unsigned *>(p.meta + slot_next * kMetaInts + kMetaMax),
                       __float_as_uint(rounded(mx, (T *)nullptr) * sc_out));
         }
     }
+}
+
+// One field: grid x = tiles (x fastest), grid y = z-chunks.
+template <int R, int MODE, int TY, typename T>
+__global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::MIN_BLOCKS)
+    k_tma(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_prev,
+          const __grid_constant__ CUtensorMap tm_vel, const __grid_constant__ StepParams p, const int64_t t)
+{
+    const int64_t tx0 = (int64_t)(blockIdx.x % p.tiles_x) * kTX;
+    const int64_t ty0 = (int64_t)(blockIdx.x / p.tiles_x) * TY;
+    const int z0 = blockIdx.y * p.zchunk;
+    const int z1 = (int)min((int64_t)z0 + p.zchunk, p.g.nz);
+    tma_body<R, MODE, TY, T>(&tm_u, &tm_prev, &tm_vel, p, tx0, ty0, z0, z1, t, 0);
+}
+
+// Many fields (shots) in one launch: CTA i does items[i].  Per-shot
+// parameters and TMA descriptors are read from device memory.
+template <int TY, typename T>
+__global__ void __launch_bounds__(Cfg<4, kWave, TY, T>::NT, Cfg<4, kWave, TY, T>::MIN_BLOCKS)
+    k_tma_batch(const BatchItem *__restrict__ items, const StepParams *__restrict__ shots,
+                const CUtensorMap *__restrict__ maps, const int parity, const int64_t t)
+{
+    const BatchItem it = items[blockIdx.x];
+    const CUtensorMap *m = maps + ((int64_t)it.shot * 2 + parity) * 3;
+    tma_body<4, kWave, TY, T>(m, m + 1, m + 2, shots[it.shot], it.tx0, it.ty0, it.z0, it.z1, t, parity);
 }
 
 // The dynamic shared-memory opt-in, set once per instantiation and device
@@ -630,8 +659,39 @@ cudaError_t prepare_cfg()
     return e;
 }
 
+template <int TY, typename T>
+cudaError_t prepare_batch_cfg()
+{
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev >= 0 && dev < 64 && done[dev])
+        return cudaSuccess;
+    e = cudaFuncSetAttribute(k_tma_batch<TY, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg<4, kWave, TY, T>::SMEM);
+    if (e == cudaSuccess && dev >= 0 && dev < 64)
+        done[dev] = true;
+    return e;
+}
+
+template <int TY, typename T>
+cudaError_t launch_batch_cfg(const BatchItem *items, int nitems, const StepParams *shots, const CUtensorMap *maps,
+                             int parity, int64_t t, cudaStream_t st)
+{
+    cudaError_t e = prepare_batch_cfg<TY, T>();
+    if (e != cudaSuccess)
+        return e;
+    if (nitems <= 0)
+        return cudaSuccess;
+    using C = Cfg<4, kWave, TY, T>;
+    k_tma_batch<TY, T><<<(unsigned)nitems, C::NT, C::SMEM, st>>>(items, shots, maps, parity, t);
+    return cudaGetLastError();
+}
+
 template <int R, int MODE, int TY, typename T>
-cudaError_t launch_cfg(const TmaPlan &plan, const StepParams &p0, cudaStream_t st)
+cudaError_t launch_cfg(const TmaPlan &plan, const StepParams &p0, int64_t t, cudaStream_t st)
 {
     using C = Cfg<R, MODE, TY, T>;
     cudaError_t e = prepare_cfg<R, MODE, TY, T>();
@@ -646,7 +706,7 @@ cudaError_t launch_cfg(const TmaPlan &plan, const StepParams &p0, cudaStream_t s
         return cudaErrorInvalidConfiguration;
     p.tiles_x = (int)tiles_x;
     dim3 grid((unsigned)(tiles_x * tiles_y), (unsigned)nchunks);
-    k_tma<R, MODE, TY, T><<<grid, C::NT, C::SMEM, st>>>(plan.u, plan.prev, plan.vel, p);
+    k_tma<R, MODE, TY, T><<<grid, C::NT, C::SMEM, st>>>(plan.u, plan.prev, plan.vel, p, t);
     return cudaGetLastError();
 }
 
@@ -654,24 +714,24 @@ template <int MODE, int TY>
 cudaError_t launch_stencil_r(int radius, const TmaPlan &plan, const StepParams &p, cudaStream_t st)
 {
     switch (radius) {
-    case 1: return launch_cfg<1, MODE, TY, float>(plan, p, st);
-    case 2: return launch_cfg<2, MODE, TY, float>(plan, p, st);
-    case 3: return launch_cfg<3, MODE, TY, float>(plan, p, st);
-    case 4: return launch_cfg<4, MODE, TY, float>(plan, p, st);
+    case 1: return launch_cfg<1, MODE, TY, float>(plan, p, 0, st);
+    case 2: return launch_cfg<2, MODE, TY, float>(plan, p, 0, st);
+    case 3: return launch_cfg<3, MODE, TY, float>(plan, p, 0, st);
+    case 4: return launch_cfg<4, MODE, TY, float>(plan, p, 0, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename T>
-cudaError_t launch_wave_t(int tile_y, const TmaPlan &plan, const StepParams &p, cudaStream_t st)
+cudaError_t launch_wave_t(int tile_y, const TmaPlan &plan, const StepParams &p, int64_t t, cudaStream_t st)
 {
-    return tile_y == 32 ? launch_cfg<4, kWave, 32, T>(plan, p, st) : launch_cfg<4, kWave, 16, T>(plan, p, st);
+    return tile_y == 32 ? launch_cfg<4, kWave, 32, T>(plan, p, t, st) : launch_cfg<4, kWave, 16, T>(plan, p, t, st);
 }
 
 }  // namespace
 
 cudaError_t launch_tma(int radius, Mode mode, int tile_y, gbs_dtype storage, const TmaPlan &plan,
-                       const StepParams &p0, cudaStream_t st)
+                       const StepParams &p0, int64_t t, cudaStream_t st)
 {
     StepParams p = p0;
     if (p.zchunk <= 0)
@@ -680,9 +740,9 @@ cudaError_t launch_tma(int radius, Mode mode, int tile_y, gbs_dtype storage, con
         if (radius != 4)
             return cudaErrorInvalidValue;
         switch (storage) {
-        case GBS_F32: return launch_wave_t<float>(tile_y, plan, p, st);
-        case GBS_BF16: return launch_wave_t<__nv_bfloat16>(tile_y, plan, p, st);
-        case GBS_F16: return launch_wave_t<__half>(tile_y, plan, p, st);
+        case GBS_F32: return launch_wave_t<float>(tile_y, plan, p, t, st);
+        case GBS_BF16: return launch_wave_t<__nv_bfloat16>(tile_y, plan, p, t, st);
+        case GBS_F16: return launch_wave_t<__half>(tile_y, plan, p, t, st);
         default: return cudaErrorInvalidValue;
         }
     }
@@ -690,6 +750,36 @@ cudaError_t launch_tma(int radius, Mode mode, int tile_y, gbs_dtype storage, con
         return cudaErrorInvalidValue;
     return tile_y == 32 ? launch_stencil_r<kStencil, 32>(radius, plan, p, st)
                         : launch_stencil_r<kStencil, 16>(radius, plan, p, st);
+}
+
+cudaError_t launch_tma_batch(int tile_y, gbs_dtype storage, const BatchItem *items, int nitems,
+                             const StepParams *shots, const CUtensorMap *maps, int parity, int64_t t,
+                             cudaStream_t st)
+{
+    const bool t32 = tile_y == 32;
+    switch (storage) {
+    case GBS_F32:
+        return t32 ? launch_batch_cfg<32, float>(items, nitems, shots, maps, parity, t, st)
+                   : launch_batch_cfg<16, float>(items, nitems, shots, maps, parity, t, st);
+    case GBS_BF16:
+        return t32 ? launch_batch_cfg<32, __nv_bfloat16>(items, nitems, shots, maps, parity, t, st)
+                   : launch_batch_cfg<16, __nv_bfloat16>(items, nitems, shots, maps, parity, t, st);
+    case GBS_F16:
+        return t32 ? launch_batch_cfg<32, __half>(items, nitems, shots, maps, parity, t, st)
+                   : launch_batch_cfg<16, __half>(items, nitems, shots, maps, parity, t, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t tma_prepare_batch(gbs_dtype storage, int tile_y)
+{
+    const bool t32 = tile_y == 32;
+    switch (storage) {
+    case GBS_F32: return t32 ? prepare_batch_cfg<32, float>() : prepare_batch_cfg<16, float>();
+    case GBS_BF16: return t32 ? prepare_batch_cfg<32, __nv_bfloat16>() : prepare_batch_cfg<16, __nv_bfloat16>();
+    case GBS_F16: return t32 ? prepare_batch_cfg<32, __half>() : prepare_batch_cfg<16, __half>();
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t tma_prepare_wave(gbs_dtype storage, int tile_y)

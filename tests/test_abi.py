@@ -127,3 +127,30 @@ def test_norms_workspace_and_validation(lib):
     assert lib.gbs_field_norms(x, None, 8, 8, 8, 4, out, small, 8, None) == gbs.GBS_EINVAL
     assert b"workspace" in lib.gbs_last_error()
     assert lib.gbs_field_norms(x, None, 8, 8, 8, 4, None, small, 64, None) == gbs.GBS_EINVAL
+
+
+def test_batch_validation_before_device(lib):
+    fake = [ctypes.c_void_p(1 << 20), ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20)]
+    plan = ctypes.c_void_p()
+
+    def shot(nx=8, halo=4, up=fake[0], u=fake[1], dt=1e-3, nsrc=0):
+        return gbs._Shot(nx, 8, 8, halo, up, u, fake[2], dt, 10.0, gbs._Src(nsrc, None, None, 4))
+
+    def create(shots, opts=None, storage=gbs.GBS_F32):
+        arr = (gbs._Shot * max(1, len(shots)))(*shots)
+        return lib.gbs_batch_plan_create(ctypes.byref(plan), arr, len(shots), storage,
+                                         ctypes.byref(opts) if opts else None, None)
+
+    assert create([]) == gbs.GBS_EINVAL
+    assert create([shot(halo=2)]) == gbs.GBS_EINVAL
+    assert create([shot(nx=0)]) == gbs.GBS_EINVAL
+    assert create([shot(), shot(up=fake[1])]) == gbs.GBS_EINVAL
+    assert b"shot 1" in lib.gbs_last_error()
+    assert create([shot(dt=0.0)]) == gbs.GBS_EINVAL
+    assert create([shot(nsrc=17)]) == gbs.GBS_EINVAL
+    assert create([shot(nsrc=2)]) == gbs.GBS_EINVAL   # n > 0 without arrays
+    assert create([shot()], opts=gbs._Opts(0, 8, 0, 0)) == gbs.GBS_EINVAL
+    assert create([shot()], storage=7) == gbs.GBS_EINVAL
+    assert not plan.value
+    assert lib.gbs_batch_run(None, 3, 0, 0, None) == gbs.GBS_EINVAL
+    lib.gbs_batch_plan_destroy(None)

@@ -125,6 +125,60 @@ def layered_velocity(nx, ny, nz, halo, seed, *, nlayers=8, vmin=1500.0, vmax=450
     return v
 
 
+def layered_velocity_torch(nx, ny, nz, halo, seed, device, *, nlayers=8, vmin=1500.0, vmax=4500.0, ngauss=16,
+                           amp=0.10):
+    """The same recipe as :func:`layered_velocity` (same random parameters
+    for the same seed), evaluated with torch on ``device`` in FP64 and
+    returned as an FP32 tensor; for inputs too large to generate quickly on
+    the host.  Values can differ from the NumPy version in the last bits."""
+    import torch
+    rng = np.random.default_rng(seed)
+    n = min(nx, ny, nz)
+    centre = np.stack([rng.uniform(0, nx - 1, ngauss), rng.uniform(0, ny - 1, ngauss),
+                       rng.uniform(0, nz - 1, ngauss)], axis=1)
+    a = rng.uniform(-amp, amp, ngauss)
+    sigma = rng.uniform(n / 32.0, n / 8.0, ngauss)
+    f64 = dict(dtype=torch.float64, device=device)
+    xs, ys, zs = (torch.arange(m, **f64) for m in (nx, ny, nz))
+    layer = torch.clamp((torch.arange(nz, device=device) * nlayers) // nz, max=nlayers - 1).to(torch.float64)
+    vlayer = vmin + layer * (vmax - vmin) / (nlayers - 1)
+    pert = torch.ones((nz, ny, nx), **f64)
+    for q in range(ngauss):
+        gx = torch.exp(-(xs - centre[q, 0]) ** 2 / (2 * sigma[q] ** 2))
+        gy = torch.exp(-(ys - centre[q, 1]) ** 2 / (2 * sigma[q] ** 2))
+        gz = torch.exp(-(zs - centre[q, 2]) ** 2 / (2 * sigma[q] ** 2))
+        pert += a[q] * (gz[:, None, None] * (gy[None, :, None] * gx[None, None, :]))
+    pert *= vlayer[:, None, None]
+    v = torch.nn.functional.pad(pert.to(torch.float32)[None, None], (halo,) * 6, mode="replicate")[0, 0]
+    return v.contiguous()
+
+
+@dataclass
+class ShotSpec:
+    """One shot of a batch: interior sizes, velocity seed, source cell, h, CFL."""
+    nx: int
+    ny: int
+    nz: int
+    vel_seed: int
+    src: tuple
+    h: float = 10.0
+    cfl: float = 0.4
+
+
+def batch_specs(nshots: int = 64, lo: int = 96, hi: int = 320, seed_offset: int = 4,
+                src_depth: int = 8) -> list:
+    """Shots with side lengths uniform in [lo, hi] per axis (seeded), each
+    with its own layered velocity seed and a source at a seeded surface
+    position ``src_depth`` cells deep."""
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    out = []
+    for s in range(nshots):
+        nx, ny, nz = (int(v) for v in rng.integers(lo, hi + 1, 3))
+        i, j = int(rng.integers(0, nx)), int(rng.integers(0, ny))
+        out.append(ShotSpec(nx, ny, nz, SEED_BASE + 1000 + s + 1000 * seed_offset, (i, j, min(src_depth, nz - 1))))
+    return out
+
+
 def _edge_fill_halo(a: np.ndarray, h: int) -> None:
     if h == 0:
         return
