@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip BF16/FP16 storage and the radius sweep")
     ap.add_argument("--no-errors", action="store_true", help="skip the FP64-oracle error runs of the storage forms")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-shot form")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--ref-leapfrog", type=int, default=2, help="oracle leapfrog steps per reference step")
     return ap.parse_args()
@@ -318,6 +319,73 @@ def precision_errors(stream, n=256, nsteps=500):
     return out
 
 
+def batched_forms(args, stream, hbm, nshots=64, nsteps=200):
+    """Many shots of uneven size (sides uniform in 96-320 per axis, own
+    layered velocity and Ricker source each, 200 steps): one batch plan (one
+    launch per step for all shots, autotuned tiling, graph-captured loop) in
+    FP32 and BF16 storage, against the same shots advanced one after the
+    other by the single-shot entry points."""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    import workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    specs = W.batch_specs(nshots)
+    shots = []
+    for s in specs:
+        vel = W.layered_velocity_torch(s.nx, s.ny, s.nz, 4, s.vel_seed, dev)
+        dt = W.dt_for_cfl(s.cfl, s.h, float(vel.max()))
+        idx = torch.tensor([W.linear_index(*s.src, s.nx, s.ny)], dtype=torch.int64, device=dev)
+        amp = torch.from_numpy(W.ricker(nsteps, dt, 15.0).astype(np.float32).reshape(nsteps, 1)).to(dev)
+        z = torch.zeros_like(vel)
+        shots.append(gbs.Shot(z, z.clone(), vel, dt, s.h, 4, idx, amp))
+    pts = sum(s.nx * s.ny * s.nz for s in specs)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    out = {"workload": f"{nshots} shots, sides uniform in 96-320 per axis (seeded), halo 4, own layered velocity "
+                       f"and 15 Hz Ricker source each, CFL 0.4, {nsteps} leapfrog steps per step",
+           "points_per_step_leapfrog": pts, "leapfrog_steps": nsteps}
+    k = 3
+    for fmt in ("f32", "bf16"):
+        for sh in shots:
+            sh.u.zero_(), sh.u_prev.zero_()
+        t0 = time.perf_counter()
+        plan = gbs.BatchPlan(shots, storage=fmt, stream=side)
+        t_plan = time.perf_counter() - t0
+        info = plan.info()
+        with torch.cuda.stream(side):
+            plan.run(nsteps, use_graph=True)        # warm-up; builds the cached graph
+            ms, _, _ = time_calls(lambda: plan.run(nsteps, use_graph=True), k, side)
+            # kernel time per launch: the same run without the graph (the profiler skips captured launches)
+            _, kms, kl = time_calls(lambda: plan.run(nsteps), 1, side)
+        side.synchronize()
+        gbs.device_status()
+        bpp = 16 if fmt == "f32" else 10
+        ach = bpp * pts / (kms * 1e-3) / 1e9
+        out[fmt] = {"value": pts * nsteps / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms, "calls": k,
+                    "plan_create_s": t_plan, "autotuned": info,
+                    "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                                 "bytes_per_point": bpp, "kernel_ms_per_launch": kms, "kernel_launches": kl}}
+        plan.close()
+
+        def seq():
+            for sh in shots:
+                if fmt == "f32":
+                    gbs.wave_propagate(sh.u_prev, sh.u, sh.vel, sh.dt, sh.h, 4, nsteps, src_idx=sh.src_idx,
+                                       src_amp=sh.src_amp)
+                else:
+                    gbs.wave_propagate_lp(sh.u_prev, sh.u, sh.vel, sh.dt, sh.h, 4, nsteps, storage=fmt,
+                                          src_idx=sh.src_idx, src_amp=sh.src_amp)
+        seq()
+        ms_seq, _, _ = time_calls(seq, 1, stream)
+        gbs.device_status()
+        out[fmt]["sequential_single_shot"] = {"value": pts * nsteps / (ms_seq * 1e-3) / 1e9, "unit": UNIT,
+                                              "ms_per_step": ms_seq}
+        out[fmt]["speedup_vs_sequential"] = ms_seq / ms
+    del shots
+    torch.cuda.empty_cache()
+    return out
+
+
 def W_padded(prob):
     import workloads as W
     return W.padded_shape(prob.nx, prob.ny, prob.nz, prob.halo)
@@ -460,6 +528,8 @@ def run_ours(args):
         forms = {"storage": storage_forms(prob, args, stream, hbm), "radius_sweep": radius_sweep(args, stream, hbm)}
         if not args.no_errors:
             forms["error_vs_fp64_oracle"] = precision_errors(stream)
+        if not args.no_batch:
+            forms["batched"] = batched_forms(args, stream, hbm)
 
     if rank == 0:
         line = {

@@ -275,7 +275,7 @@ gbs_status gbs_fd2_coeffs(int radius, float *out);
 
 /*
  * Kernel timing.  While enabled (on != 0), every launch of the stencil /
- * wave-step kernel made outside stream capture is bracketed by two CUDA
+ * wave-step kernel (single-shot or batched) made outside stream capture is bracketed by two CUDA
  * events recorded on the launch's own stream.  gbs_profile_take()
  * synchronises on those events and returns the summed elapsed time (ms)
  * and the number of launches since the last take, then forgets them.

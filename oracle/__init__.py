@@ -23,6 +23,10 @@ What each function follows (arXiv 2309.04671):
   definition; the scale rule; one step of Eq. 2 on stored fields).  The
   paper computes in FP32 (``st.f32``); the 16-bit storage is this library's
   addition, pinned here against numpy/torch conversions.
+* :func:`forward_states`, :func:`adjoint_gradient`, :func:`fwi_misfit`,
+  :func:`fwi_gradient` -- the discrete adjoint of Algorithm 1 and the
+  gradient of a trace functional with respect to the velocity (the paper
+  has no adjoint; the derivation is written out above the functions).
 * :func:`err_norms` -- the paper's accuracy metrics (Sec. 11.1: maximum
   absolute error and RMSD against a reference), plus the normwise relative
   maximum and L2 errors.
@@ -30,7 +34,9 @@ What each function follows (arXiv 2309.04671):
 Pins (tests/test_oracle_*.py): moment conditions and a published table of the
 weights, polynomial exactness, the plane-wave symbol, operator symmetry, a
 Kronecker-sum brute force, the stencil footprint against the paper's Table 4,
-discrete energy conservation, time reversal and special cases of the step.
+discrete energy conservation, time reversal and special cases of the step;
+for the gradient: central finite differences of the misfit, a dot-product
+test with the linearised traces, a one-step closed form and causality.
 """
 from __future__ import annotations
 
@@ -325,6 +331,91 @@ def lp_wave_step(u_prev_st, u_st, vel, dt: float, h: float, halo: int, fmt: str,
     out = np.zeros_like(nxt)
     out[hh:-hh, hh:-hh, hh:-hh] = round_to_format(np.ldexp(nxt[hh:-hh, hh:-hh, hh:-hh], -s), fmt) * 2.0 ** s
     return out, s
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of Algorithm 1 and the velocity gradient.  The paper has no adjoint;
+# this is the discrete adjoint of the time loop as implemented by wave_step:
+#   u^{m+1} = 2u^m - u^{m-1} + D (L u^m + S f^m),  D = diag((v dt)^2),
+#   u^0 = u^{-1} = 0, trace row m = R u^{m+1},  m = 0..N-1,
+# for a scalar J of the trace with a_m = dJ/d(trace row m).  With
+# mu^m = dJ/du^m (mu^{N+1} = mu^{N+2} = 0) and L symmetric (zero halo):
+#   mu^m = R^T a_{m-1} + (2 + L D) mu^{m+1} - mu^{m+2};
+# nu = D mu turns this into the forward step itself,
+#   nu^{m+1} = 2 nu^{m+2} - nu^{m+3} + D (L nu^{m+2} + R^T a_m),
+# i.e. Algorithm 1 run backwards with the receivers as sources of amplitude
+# a_m; and since d(D)/dv = 2 v dt^2,
+#   dJ/dv(x) = sum_m 2 nu^{m+1}(x) (L u^m + S f^m)(x) / v(x).
+# ---------------------------------------------------------------------------
+def forward_states(vel, dt: float, h: float, halo: int, nsteps: int, *, src_idx=None, src_amp=None,
+                   rec_idx=None):
+    """Algorithm 1 from rest, keeping every state: returns ([u^0, ..., u^N],
+    trace) with trace row m = u^{m+1} at the receivers (FP64)."""
+    v = _f64(vel)
+    si = None if src_idx is None else np.ascontiguousarray(src_idx, np.int64).reshape(-1)
+    sa = None if src_amp is None else _f64(np.asarray(src_amp).reshape(-1, si.size))
+    ri = np.zeros(0, np.int64) if rec_idx is None else np.ascontiguousarray(rec_idx, np.int64).reshape(-1)
+    states = [np.zeros_like(v)]
+    prev = np.zeros_like(v)
+    trace = np.zeros((nsteps, ri.size), np.float64)
+    for m in range(nsteps):
+        f = None if si is None or m >= sa.shape[0] else sa[m]
+        nxt, rv = wave_step(prev, states[-1], v, dt, h, halo, src_idx=si if f is not None else None, src_f=f,
+                            rec_idx=ri)
+        trace[m] = rv
+        prev = states[-1]
+        states.append(nxt)
+    return states, trace
+
+
+def _interior_flat(nx, ny, halo, shape, idx):
+    """Padded flat offsets of interior linear indices (x fastest)."""
+    idx = np.asarray(idx, np.int64)
+    i, j, k = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    return (i + halo) + shape[2] * ((j + halo) + shape[1] * (k + halo))
+
+
+def adjoint_gradient(vel, dt: float, h: float, halo: int, nsteps: int, adj_src, *, src_idx=None, src_amp=None,
+                     rec_idx=None, states=None):
+    """dJ/dv (padded FP64 array, zero halo) for a scalar J of the trace whose
+    derivative with respect to trace row m is ``adj_src[m]`` (nsteps, nrec)."""
+    v = _f64(vel)
+    nx, ny, nz = _dims(v, halo)
+    if states is None:
+        states, _ = forward_states(v, dt, h, halo, nsteps, src_idx=src_idx, src_amp=src_amp, rec_idx=rec_idx)
+    ri = np.ascontiguousarray(rec_idx, np.int64).reshape(-1)
+    a = _f64(np.asarray(adj_src).reshape(nsteps, ri.size))
+    si = None if src_idx is None else np.ascontiguousarray(src_idx, np.int64).reshape(-1)
+    sa = None if src_amp is None else _f64(np.asarray(src_amp).reshape(-1, si.size))
+    c = axis_coeffs(4, h)
+    inner = (slice(halo, halo + nz), slice(halo, halo + ny), slice(halo, halo + nx))
+    g = np.zeros_like(v)
+    nu_far = np.zeros_like(v)    # nu^{m+3}
+    nu_near = np.zeros_like(v)   # nu^{m+2}
+    for m in range(nsteps - 1, -1, -1):
+        nu, _ = wave_step(nu_far, nu_near, v, dt, h, halo, src_idx=ri, src_f=a[m])   # nu^{m+1}
+        q = stencil_apply(states[m], 4, c, c, c, halo)                                 # L u^m
+        if si is not None and m < sa.shape[0]:
+            np.add.at(q.reshape(-1), _interior_flat(nx, ny, halo, v.shape, si), sa[m])  # + S f^m
+        g[inner] += 2.0 * nu[inner] * q[inner] / v[inner]
+        nu_far, nu_near = nu_near, nu
+    return g
+
+
+def fwi_misfit(vel, dt: float, h: float, halo: int, nsteps: int, d_obs, *, src_idx, src_amp, rec_idx):
+    """J = 1/2 sum_m |R u^{m+1} - d_m|^2 (FP64)."""
+    _, tr = forward_states(vel, dt, h, halo, nsteps, src_idx=src_idx, src_amp=src_amp, rec_idx=rec_idx)
+    r = tr - _f64(np.asarray(d_obs).reshape(tr.shape))
+    return 0.5 * float(np.sum(r * r))
+
+
+def fwi_gradient(vel, dt: float, h: float, halo: int, nsteps: int, d_obs, *, src_idx, src_amp, rec_idx):
+    """(J, dJ/dv) of the L2 trace misfit: the adjoint source is the residual."""
+    states, tr = forward_states(vel, dt, h, halo, nsteps, src_idx=src_idx, src_amp=src_amp, rec_idx=rec_idx)
+    r = tr - _f64(np.asarray(d_obs).reshape(tr.shape))
+    g = adjoint_gradient(vel, dt, h, halo, nsteps, r, src_idx=src_idx, src_amp=src_amp, rec_idx=rec_idx,
+                         states=states)
+    return 0.5 * float(np.sum(r * r)), g
 
 
 # ---------------------------------------------------------------------------

@@ -382,6 +382,8 @@ gbs_status set_error(gbs_status s, const char *fmt, ...)
 gbs_status set_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
 void clear_error() { t_err[0] = 0; }
 Coeffs wave_weights() { return wave_coeffs(); }
+cudaEvent_t profile_begin(cudaStream_t st) { return prof_begin(st); }
+void profile_end(cudaEvent_t e0, cudaStream_t st) { prof_end(e0, st); }
 gbs_status make_tensor_map(CUtensorMap *m, const void *base, const Grid &g, int bw, int bh, gbs_dtype dt)
 {
     return make_map(m, base, g, bw, bh, dt);

@@ -118,8 +118,10 @@ gbs_status configure(gbs_batch_plan &P, int tile_y, int zchunk, cudaStream_t st)
 gbs_status enqueue_steps(gbs_batch_plan &P, int64_t nsteps, int64_t t0, cudaStream_t st)
 {
     for (int64_t q = 0; q < nsteps; ++q) {
+        cudaEvent_t e0 = profile_begin(st);
         cudaError_t e = launch_tma_batch(P.tile_y, P.storage, P.d_items, P.nitems, P.d_params, P.d_maps,
                                          (int)(q & 1), t0 + q, st);
+        profile_end(e0, st);
         if (e != cudaSuccess)
             return set_cuda_error(e, "batched step launch");
     }

@@ -146,6 +146,9 @@ gbs_status set_error(gbs_status s, const char *fmt, ...);
 gbs_status set_cuda_error(cudaError_t e, const char *what);
 void clear_error();
 Coeffs wave_weights();
+// event profiler of gbs_profile_enable: bracket one launch (no-op when off or capturing)
+cudaEvent_t profile_begin(cudaStream_t st);
+void profile_end(cudaEvent_t e0, cudaStream_t st);
 gbs_status make_tensor_map(CUtensorMap *m, const void *base, const Grid &g, int bw, int bh, gbs_dtype dt);
 // interior (nx, ny, nz), halo 4, nx rounded up to a multiple of 4 (dead
 // columns), rows padded to a multiple of 8 elements
