@@ -220,6 +220,52 @@ gbs_status gbs_batch_plan_info(const gbs_batch_plan *plan, int *tile_y, int *zch
 void gbs_batch_plan_destroy(gbs_batch_plan *plan);
 
 /*
+ * Adjoint of the time loop and the gradient of a trace functional with
+ * respect to the velocity (the paper has no adjoint; this is the discrete
+ * adjoint of Algorithm 1 as implemented here).  Forward model: zero initial
+ * state, u^{m+1} = 2u^m - u^{m-1} + (v dt)^2 (L u^m + S f^m), trace row m =
+ * u^{m+1} at the receivers, m = 0..nsteps-1.  For a scalar J of the trace
+ * with a_m = dJ/d(trace row m), nu^{m+1} = 2nu^{m+2} - nu^{m+3} +
+ * (v dt)^2 (L nu^{m+2} + R^T a_m) is the same step run backwards, and
+ *   dJ/dv(x) = sum_m 2 nu^{m+1}(x) (L u^m + S f^m)(x) / v(x),
+ * accumulated in FP64 (fields and steps in FP32).
+ *
+ * Checkpointing: the forward pass keeps (u^{sK-1}, u^{sK}) every K =
+ * ckpt_every steps (0: K = ceil(sqrt(nsteps))); the backward pass recomputes
+ * each segment's K states from its checkpoint.  All state lives in the
+ * caller's workspace (gbs_adjoint_workspace_bytes: velocity, 4 fields,
+ * 2*ceil(nsteps/K) checkpoints, K-1 segment fields, each (nx rounded up to
+ * 4, plus 8) * (ny+8) * (nz+8) FP32 values with rows padded to 8, plus one
+ * FP64 field and 8 KiB), 256-byte aligned.  The halo of vel is not read.
+ *
+ * gbs_adjoint_forward: runs the forward model, writes rec->trace (nt >=
+ *   nsteps rows) and leaves the checkpoints in `work`.
+ * gbs_adjoint_backward: given adj_src = a (DEVICE [nsteps][nrec]) for the
+ *   same receivers, ADDS dJ/dv to grad (DEVICE FP64, the padded layout of
+ *   vel; the halo is not written).  Must follow gbs_adjoint_forward with the
+ *   same arguments and an untouched workspace.
+ * gbs_fwi_gradient: both passes for the L2 misfit J = 1/2 sum |trace - d_obs|^2:
+ *   writes trace and resid = trace - d_obs (DEVICE [nsteps][nrec], distinct
+ *   buffers), ADDS J to *misfit (DEVICE FP64) and dJ/dv to grad.
+ * Sources: as gbs_wave_propagate (more than 16 take a separate kernel).
+ * Nothing is allocated; calls enqueue on `stream`.
+ * Errors: GBS_EINVAL (sizes, halo < 4, nsteps <= 0, null or unaligned
+ * workspace, too small a workspace), GBS_ECUDA.
+ */
+size_t gbs_adjoint_workspace_bytes(int64_t nx, int64_t ny, int64_t nz, int64_t nsteps, int64_t ckpt_every);
+gbs_status gbs_adjoint_forward(const float *vel, float dt, float h, int64_t nx, int64_t ny, int64_t nz, int halo,
+                               int64_t nsteps, const gbs_src *src, const gbs_rec *rec, int64_t ckpt_every,
+                               void *work, size_t work_bytes, const gbs_opts *opts, void *stream);
+gbs_status gbs_adjoint_backward(const float *vel, float dt, float h, int64_t nx, int64_t ny, int64_t nz, int halo,
+                                int64_t nsteps, const gbs_src *src, const int64_t *rec_idx, int64_t nrec,
+                                const float *adj_src, int64_t ckpt_every, void *work, size_t work_bytes,
+                                double *grad, const gbs_opts *opts, void *stream);
+gbs_status gbs_fwi_gradient(const float *vel, float dt, float h, int64_t nx, int64_t ny, int64_t nz, int halo,
+                            int64_t nsteps, const gbs_src *src, const int64_t *rec_idx, int64_t nrec,
+                            const float *d_obs, float *trace, float *resid, int64_t ckpt_every, void *work,
+                            size_t work_bytes, double *grad, double *misfit, const gbs_opts *opts, void *stream);
+
+/*
  * Error norms of a field against a reference over the interior, accumulated
  * in FP64 (the accuracy metrics of Sec. 11.1: maximum absolute error and RMSD
  * against a reference implementation, plus scale-free versions).

@@ -30,6 +30,7 @@ STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4
 EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
            "gbs_wave_propagate_lp", "gbs_norms_workspace_bytes", "gbs_field_norms", "gbs_field_norms_noalloc",
            "gbs_batch_plan_create", "gbs_batch_run", "gbs_batch_plan_info", "gbs_batch_plan_destroy",
+           "gbs_adjoint_workspace_bytes", "gbs_adjoint_forward", "gbs_adjoint_backward", "gbs_fwi_gradient",
            "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take",
            "gbs_device_status", "gbs_last_error", "gbs_version")
 
@@ -113,6 +114,17 @@ def load() -> ctypes.CDLL:
         lib.gbs_batch_plan_info.restype = c_int
         lib.gbs_batch_plan_destroy.argtypes = [vp]
         lib.gbs_batch_plan_destroy.restype = None
+        lib.gbs_adjoint_workspace_bytes.argtypes = [i64, i64, i64, i64, i64]
+        lib.gbs_adjoint_workspace_bytes.restype = ctypes.c_size_t
+        lib.gbs_adjoint_forward.argtypes = [vp, c_float, c_float, i64, i64, i64, c_int, i64, ctypes.POINTER(_Src),
+                                            ctypes.POINTER(_Rec), i64, vp, ctypes.c_size_t, ctypes.POINTER(_Opts), vp]
+        lib.gbs_adjoint_forward.restype = c_int
+        lib.gbs_adjoint_backward.argtypes = [vp, c_float, c_float, i64, i64, i64, c_int, i64, ctypes.POINTER(_Src),
+                                             vp, i64, vp, i64, vp, ctypes.c_size_t, vp, ctypes.POINTER(_Opts), vp]
+        lib.gbs_adjoint_backward.restype = c_int
+        lib.gbs_fwi_gradient.argtypes = [vp, c_float, c_float, i64, i64, i64, c_int, i64, ctypes.POINTER(_Src), vp,
+                                         i64, vp, vp, vp, i64, vp, ctypes.c_size_t, vp, vp, ctypes.POINTER(_Opts), vp]
+        lib.gbs_fwi_gradient.restype = c_int
         lib.gbs_fd2_coeffs.argtypes = [c_int, fp]
         lib.gbs_profile_enable.argtypes = [c_int]
         lib.gbs_profile_take.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -121,8 +133,7 @@ def load() -> ctypes.CDLL:
         lib.gbs_last_error.argtypes = []
         lib.gbs_version.argtypes = []
         for f in ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_wave_propagate_lp",
-                  "gbs_batch_plan_create", "gbs_batch_run", "gbs_batch_plan_info", "gbs_batch_plan_destroy",
-           "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take", "gbs_device_status", "gbs_version"):
+                  "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take", "gbs_device_status", "gbs_version"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -373,6 +384,130 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# adjoint / velocity gradient
+# ---------------------------------------------------------------------------
+def adjoint_workspace_bytes(nx: int, ny: int, nz: int, nsteps: int, ckpt_every: int = 0) -> int:
+    """Bytes of device workspace the adjoint calls need (checkpoints included)."""
+    return int(load().gbs_adjoint_workspace_bytes(int(nx), int(ny), int(nz), int(nsteps), int(ckpt_every)))
+
+
+def adjoint_workspace(vel: torch.Tensor, halo: int, nsteps: int, ckpt_every: int = 0) -> torch.Tensor:
+    nx, ny, nz = _dims(vel, halo)
+    return torch.empty(adjoint_workspace_bytes(nx, ny, nz, nsteps, ckpt_every) + 256, dtype=torch.uint8,
+                       device=vel.device)
+
+
+def _aligned(work: torch.Tensor):
+    base = work.data_ptr()
+    off = (-base) % 256
+    return base + off, work.numel() - off
+
+
+def adjoint_forward(vel: torch.Tensor, dt: float, h: float, halo: int, nsteps: int, *, src_idx=None, src_amp=None,
+                    rec_idx=None, trace: Optional[torch.Tensor] = None, ckpt_every: int = 0,
+                    work: Optional[torch.Tensor] = None, tile_y: int = 0, zchunk: int = 0, stream=None):
+    """Forward model from rest, recording the trace (nsteps, nrec) and keeping
+    checkpoints in ``work`` for :func:`adjoint_backward`.  Returns (trace, work)."""
+    pv = _field(vel, "vel")
+    nx, ny, nz = _dims(vel, halo)
+    if work is None:
+        work = adjoint_workspace(vel, halo, nsteps, ckpt_every)
+    if rec_idx is not None and trace is None:
+        trace = torch.zeros((nsteps, rec_idx.numel()), dtype=torch.float32, device=vel.device)
+    src = _make_src(src_idx, src_amp)
+    rec = _make_rec(rec_idx, trace)
+    wp, wn = _aligned(work)
+    opts = _opts(0, tile_y, zchunk, False)
+    _check(load().gbs_adjoint_forward(pv, float(dt), float(h), nx, ny, nz, halo, int(nsteps), _ptr(src), _ptr(rec),
+                                      int(ckpt_every), wp, wn, ctypes.byref(opts), _stream(stream)))
+    return trace, work
+
+
+def adjoint_backward(vel: torch.Tensor, dt: float, h: float, halo: int, nsteps: int, adj_src: torch.Tensor,
+                     work: torch.Tensor, *, src_idx=None, src_amp=None, rec_idx=None, ckpt_every: int = 0,
+                     grad: Optional[torch.Tensor] = None, tile_y: int = 0, zchunk: int = 0, stream=None):
+    """Adds dJ/dv to ``grad`` (float64, shaped like vel) for the trace
+    cotangent ``adj_src`` (nsteps, nrec); needs the workspace of the
+    matching :func:`adjoint_forward`."""
+    pv = _field(vel, "vel")
+    nx, ny, nz = _dims(vel, halo)
+    if grad is None:
+        grad = torch.zeros(vel.shape, dtype=torch.float64, device=vel.device)
+    if not (grad.is_cuda and grad.dtype == torch.float64 and grad.is_contiguous() and grad.shape == vel.shape):
+        raise TypeError("grad must be a contiguous float64 CUDA tensor shaped like vel")
+    _idx(rec_idx, "rec_idx")
+    a = adj_src.contiguous()
+    if not (a.is_cuda and a.dtype == torch.float32 and a.numel() == nsteps * rec_idx.numel()):
+        raise TypeError("adj_src must be a float32 CUDA tensor of shape (nsteps, nrec)")
+    src = _make_src(src_idx, src_amp)
+    wp, wn = _aligned(work)
+    opts = _opts(0, tile_y, zchunk, False)
+    _check(load().gbs_adjoint_backward(pv, float(dt), float(h), nx, ny, nz, halo, int(nsteps), _ptr(src),
+                                       rec_idx.data_ptr(), rec_idx.numel(), a.data_ptr(), int(ckpt_every), wp, wn,
+                                       grad.data_ptr(), ctypes.byref(opts), _stream(stream)))
+    return grad
+
+
+def fwi_gradient(vel: torch.Tensor, dt: float, h: float, halo: int, nsteps: int, d_obs: torch.Tensor, *,
+                 src_idx=None, src_amp=None, rec_idx=None, ckpt_every: int = 0, work: Optional[torch.Tensor] = None,
+                 grad: Optional[torch.Tensor] = None, misfit: Optional[torch.Tensor] = None, tile_y: int = 0,
+                 zchunk: int = 0, stream=None):
+    """L2 trace misfit and its velocity gradient (both passes).  Returns
+    (misfit, grad, trace, resid); misfit (float64, 1 value) and grad are
+    accumulated into when given."""
+    pv = _field(vel, "vel")
+    nx, ny, nz = _dims(vel, halo)
+    _idx(rec_idx, "rec_idx")
+    nrec = rec_idx.numel()
+    d = d_obs.contiguous()
+    if not (d.is_cuda and d.dtype == torch.float32 and d.numel() == nsteps * nrec):
+        raise TypeError("d_obs must be a float32 CUDA tensor of shape (nsteps, nrec)")
+    if work is None:
+        work = adjoint_workspace(vel, halo, nsteps, ckpt_every)
+    if grad is None:
+        grad = torch.zeros(vel.shape, dtype=torch.float64, device=vel.device)
+    if misfit is None:
+        misfit = torch.zeros(1, dtype=torch.float64, device=vel.device)
+    trace = torch.empty((nsteps, nrec), dtype=torch.float32, device=vel.device)
+    resid = torch.empty_like(trace)
+    src = _make_src(src_idx, src_amp)
+    wp, wn = _aligned(work)
+    opts = _opts(0, tile_y, zchunk, False)
+    _check(load().gbs_fwi_gradient(pv, float(dt), float(h), nx, ny, nz, halo, int(nsteps), _ptr(src),
+                                   rec_idx.data_ptr(), nrec, d.data_ptr(), trace.data_ptr(), resid.data_ptr(),
+                                   int(ckpt_every), wp, wn, grad.data_ptr(), misfit.data_ptr(), ctypes.byref(opts),
+                                   _stream(stream)))
+    return misfit, grad, trace, resid
+
+
+class WavePropagate(torch.autograd.Function):
+    """Receiver traces of the forward model as a differentiable function of
+    the velocity: ``WavePropagate.apply(vel, dt, h, halo, nsteps, src_idx,
+    src_amp, rec_idx, ckpt_every)`` returns the (nsteps, nrec) trace; its
+    backward runs the adjoint with sqrt(N) checkpoints and returns dL/dvel
+    (accumulated in FP64, returned in vel's dtype)."""
+
+    @staticmethod
+    def forward(ctx, vel, dt, h, halo, nsteps, src_idx, src_amp, rec_idx, ckpt_every=0):
+        v = vel.detach().contiguous()
+        trace, work = adjoint_forward(v, dt, h, halo, nsteps, src_idx=src_idx, src_amp=src_amp, rec_idx=rec_idx,
+                                      ckpt_every=ckpt_every)
+        ctx.save_for_backward(v, src_idx, src_amp, rec_idx)
+        ctx.work = work
+        ctx.args = (dt, h, halo, nsteps, ckpt_every)
+        return trace
+
+    @staticmethod
+    def backward(ctx, grad_trace):
+        v, src_idx, src_amp, rec_idx = ctx.saved_tensors
+        dt, h, halo, nsteps, ckpt_every = ctx.args
+        g = adjoint_backward(v, dt, h, halo, nsteps, grad_trace.float(), ctx.work, src_idx=src_idx, src_amp=src_amp,
+                             rec_idx=rec_idx, ckpt_every=ckpt_every)
+        ctx.work = None
+        return g.to(v.dtype), None, None, None, None, None, None, None, None
 
 
 NORM_KEYS = ("max_abs", "ref_max", "sum_sq_diff", "sum_sq_ref", "npoints", "norm_max_rel", "l2_rel", "rmsd")

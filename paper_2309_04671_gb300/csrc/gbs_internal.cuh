@@ -36,7 +36,10 @@ struct Coeffs {
 // What the epilogue computes from the Laplacian `lap` at a point:
 //   kStencil: out = lap
 //   kWave:    out = 2u - u_prev + (vel * s)^2 * lap   with s = dt/h
-enum Mode { kStencil = 0, kWave = 1 };
+//   kImage:   g += (double)(lap * nu * s / vel), s = 2/h^2, nu read through
+//             the u_prev map, g = out[0] an FP64 field in the same layout
+//             (0 where vel == 0); the imaging condition of the adjoint
+enum Mode { kStencil = 0, kWave = 1, kImage = 2 };
 
 struct WaveArgs {
     const float *u_prev;   // read at the point only (may alias out)
@@ -163,10 +166,24 @@ cudaError_t launch_lp_record(gbs_dtype storage, const Grid &gc, const Grid &gi, 
 unsigned tma_status_take(cudaStream_t st);
 unsigned misc_status_take(cudaStream_t st);
 
+// Sources / receivers of a field in layout g; gidx (default g) is the grid
+// whose interior the linear indices count (the caller's, for internal layouts).
 cudaError_t launch_inject(const Grid &g, float *u_next, const float *vel, float dt,
-                          const gbs_src *src, int64_t step, cudaStream_t st);
+                          const gbs_src *src, int64_t step, cudaStream_t st, const Grid *gidx = nullptr);
 cudaError_t launch_record(const Grid &g, const float *u_next, const gbs_rec *rec, int64_t step,
-                          cudaStream_t st);
+                          cudaStream_t st, const Grid *gidx = nullptr);
+// Imaging condition, source cells: grad(x_s) += 2 nu(x_s) f_s / v(x_s) (row `step` of src->amp)
+cudaError_t launch_image_src(const Grid &gc, const Grid &g, double *grad, const float *nu, const float *vel,
+                             const gbs_src *src, int64_t step, cudaStream_t st);
+
+// Adjoint helpers (k_adjoint.cu).  Residual r = trace - d_obs (n values) with
+// FP64 partial sums of r^2 (kMisfitBlocks doubles in `part`), then
+// *misfit += sum / 2 in a fixed order; and grad_c += g over the interior
+// (g in layout gi, grad_c in gc, both FP64).
+constexpr int kMisfitBlocks = 1024;
+cudaError_t launch_residual_misfit(const float *trace, const float *d_obs, int64_t n, float *resid, double *part,
+                                   double *misfit, cudaStream_t st);
+cudaError_t launch_grad_add(const Grid &gi, const double *g, const Grid &gc, double *grad_c, cudaStream_t st);
 
 // Error norms (k_norms.cu): one FP64 partial record of 4 doubles per block
 // of kNormRowsPerBlock rows; `out` receives kNormOut doubles.

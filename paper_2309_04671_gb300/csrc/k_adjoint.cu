@@ -1,0 +1,86 @@
+// Small kernels of the adjoint / gradient path: the trace residual with the
+// L2 misfit J = 1/2 sum r^2 (FP64, deterministic two-pass reduction), and
+// the FP64 gradient added from the internal layout into the caller's.
+#include "gbs_internal.cuh"
+
+namespace gbs {
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads) k_residual(const float *trace, const float *d_obs, int64_t n,
+                                                      float *resid, double *part)
+{
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const float r = trace[i] - d_obs[i];
+        resid[i] = r;
+        acc += (double)r * (double)r;
+    }
+    __shared__ double sh[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0)
+        sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w)
+            s += sh[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_misfit_final(const double *part, int nparts, double *misfit)
+{
+    __shared__ double sh[kThreads];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += kThreads)
+        acc += part[b];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int t = 0; t < kThreads; ++t)
+            s += sh[t];
+        *misfit += 0.5 * s;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_grad_add(Grid gi, const double *g, Grid gc, double *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= gc.nx)
+        return;
+    const int64_t rows = gc.ny * gc.nz;
+    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
+        const int64_t j = row % gc.ny, k = row / gc.ny;
+        const int64_t a = (i + gi.halo) + gi.px * ((j + gi.halo) + gi.py * (k + gi.halo));
+        const int64_t b = (i + gc.halo) + gc.px * ((j + gc.halo) + gc.py * (k + gc.halo));
+        out[b] += g[a];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_residual_misfit(const float *trace, const float *d_obs, int64_t n, float *resid, double *part,
+                                   double *misfit, cudaStream_t st)
+{
+    k_residual<<<kMisfitBlocks, kThreads, 0, st>>>(trace, d_obs, n, resid, part);
+    k_misfit_final<<<1, kThreads, 0, st>>>(part, kMisfitBlocks, misfit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_add(const Grid &gi, const double *g, const Grid &gc, double *grad_c, cudaStream_t st)
+{
+    if (gc.nx <= 0 || gc.ny <= 0 || gc.nz <= 0)
+        return cudaSuccess;
+    const int64_t bx = (gc.nx + kThreads - 1) / kThreads;
+    const int64_t rows = gc.ny * gc.nz;
+    const unsigned by = (unsigned)(rows < 4096 ? rows : 4096);
+    k_grad_add<<<dim3((unsigned)bx, by), kThreads, 0, st>>>(gi, g, gc, grad_c);
+    return cudaGetLastError();
+}
+
+}  // namespace gbs

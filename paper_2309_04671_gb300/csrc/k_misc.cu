@@ -13,65 +13,96 @@ namespace {
 
 __device__ unsigned g_status_misc = 0;
 
-__device__ __forceinline__ int64_t padded_of(int64_t lin, const Grid &g)
+// lin counts points of gc's interior (x fastest); the result addresses g
+__device__ __forceinline__ int64_t padded_of(int64_t lin, const Grid &gc, const Grid &g)
 {
-    const int64_t i = lin % g.nx;
-    const int64_t j = (lin / g.nx) % g.ny;
-    const int64_t k = lin / (g.nx * g.ny);
+    const int64_t i = lin % gc.nx;
+    const int64_t j = (lin / gc.nx) % gc.ny;
+    const int64_t k = lin / (gc.nx * gc.ny);
     return (i + g.halo) + g.px * ((j + g.halo) + g.py * (k + g.halo));
 }
 
-__global__ void k_inject(Grid g, float *u_next, const float *vel, float dt, const int64_t *idx,
+__global__ void k_inject(Grid gc, Grid g, float *u_next, const float *vel, float dt, const int64_t *idx,
                          const float *amp_row, int64_t n)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n)
         return;
     const int64_t lin = idx[s];
-    if (lin < 0 || lin >= g.nx * g.ny * g.nz) {
+    if (lin < 0 || lin >= gc.nx * gc.ny * gc.nz) {
         atomicCAS(&g_status_misc, 0u, (unsigned)GBS_EINVAL);
         return;
     }
-    const int64_t p = padded_of(lin, g);
+    const int64_t p = padded_of(lin, gc, g);
     const float vdt = vel[p] * dt;
     atomicAdd(u_next + p, vdt * vdt * amp_row[s]);
 }
 
-__global__ void k_record(Grid g, const float *u_next, const int64_t *idx, float *trace_row, int64_t n)
+__global__ void k_record(Grid gc, Grid g, const float *u_next, const int64_t *idx, float *trace_row, int64_t n)
 {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n)
         return;
     const int64_t lin = idx[r];
-    if (lin < 0 || lin >= g.nx * g.ny * g.nz) {
+    if (lin < 0 || lin >= gc.nx * gc.ny * gc.nz) {
         atomicCAS(&g_status_misc, 0u, (unsigned)GBS_EINVAL);
         trace_row[r] = 0.f;
         return;
     }
-    trace_row[r] = u_next[padded_of(lin, g)];
+    trace_row[r] = u_next[padded_of(lin, gc, g)];
+}
+
+// Source term of the imaging condition: g(x_s) += 2 nu(x_s) f_s / v(x_s).
+__global__ void k_image_src(Grid gc, Grid g, double *grad, const float *nu, const float *vel, const int64_t *idx,
+                            const float *amp_row, int64_t n)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n)
+        return;
+    const int64_t lin = idx[s];
+    if (lin < 0 || lin >= gc.nx * gc.ny * gc.nz) {
+        atomicCAS(&g_status_misc, 0u, (unsigned)GBS_EINVAL);
+        return;
+    }
+    const int64_t p = padded_of(lin, gc, g);
+    const float v = vel[p];
+    if (v > 0.f)
+        atomicAdd(grad + p, (double)(2.f * nu[p] * amp_row[s] / v));
 }
 
 }  // namespace
 
 cudaError_t launch_inject(const Grid &g, float *u_next, const float *vel, float dt, const gbs_src *src,
-                          int64_t step, cudaStream_t st)
+                          int64_t step, cudaStream_t st, const Grid *gidx)
 {
     if (!src || src->n <= 0 || step < 0 || step >= src->nt)
         return cudaSuccess;
     const int threads = 128;
     const unsigned blocks = (unsigned)((src->n + threads - 1) / threads);
-    k_inject<<<blocks, threads, 0, st>>>(g, u_next, vel, dt, src->idx, src->amp + step * src->n, src->n);
+    k_inject<<<blocks, threads, 0, st>>>(gidx ? *gidx : g, g, u_next, vel, dt, src->idx, src->amp + step * src->n,
+                                         src->n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_record(const Grid &g, const float *u_next, const gbs_rec *rec, int64_t step,
-                          cudaStream_t st)
+                          cudaStream_t st, const Grid *gidx)
 {
     if (!rec || rec->n <= 0 || step < 0 || step >= rec->nt)
         return cudaSuccess;
     const int threads = 256;
     const unsigned blocks = (unsigned)((rec->n + threads - 1) / threads);
-    k_record<<<blocks, threads, 0, st>>>(g, u_next, rec->idx, rec->trace + step * rec->n, rec->n);
+    k_record<<<blocks, threads, 0, st>>>(gidx ? *gidx : g, g, u_next, rec->idx, rec->trace + step * rec->n, rec->n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_image_src(const Grid &gc, const Grid &g, double *grad, const float *nu, const float *vel,
+                             const gbs_src *src, int64_t step, cudaStream_t st)
+{
+    if (!src || src->n <= 0 || step < 0 || step >= src->nt)
+        return cudaSuccess;
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((src->n + threads - 1) / threads);
+    k_image_src<<<blocks, threads, 0, st>>>(gc, g, grad, nu, vel, src->idx, src->amp + step * src->n, src->n);
     return cudaGetLastError();
 }
 

@@ -91,7 +91,7 @@ struct Cfg {
     static constexpr int SP = LOW ? 3 : 5;
     static constexpr size_t SMEM_L = (size_t)SL * L_STRIDE;
     static constexpr size_t SMEM_F = (size_t)SF * F_STRIDE;
-    static constexpr size_t SMEM_PV = MODE == kWave ? (size_t)SP * PV_STRIDE : 0;
+    static constexpr size_t SMEM_PV = MODE != kStencil ? (size_t)SP * PV_STRIDE : 0;
     static constexpr size_t SMEM = SMEM_L + SMEM_F + SMEM_PV + (SL + SP) * 8;
     static constexpr int MIN_BLOCKS = NT > 128 ? 1 : (LOW ? 3 : 2);
     // halo groups of 4 elements converted by all threads (16-bit): 2 side
@@ -254,7 +254,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
     // returns before issuing any copy.
     {
         const int64_t xu = (H + tx0 - 4) * C::ES, xp = (H + tx0 - C::PVU_X0) * C::ES, xv = (H + tx0) * 4;
-        if ((xu & 15) != 0 || (MODE == kWave && ((xp & 15) != 0 || (xv & 15) != 0))) {
+        if ((xu & 15) != 0 || (MODE != kStencil && ((xp & 15) != 0 || (xv & 15) != 0))) {
             if (tid == 0)
                 atomicCAS(&g_status_tma, 0u, (unsigned)GBS_EALIGN);
             return;
@@ -263,7 +263,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
 
     if (tid == 0) {
         prefetch_tmap(pm_u);
-        if (MODE == kWave) {
+        if (MODE != kStencil) {
             prefetch_tmap(pm_prev);
             prefetch_tmap(pm_vel);
         }
@@ -338,7 +338,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
     if (tid == 0) {
         while (n_u < min(C::SL, nplanes))
             issue_u();
-        if (MODE == kWave)
+        if (MODE != kStencil)
             while (n_pv < min(C::SP, nzc))
                 issue_pv();
     }
@@ -353,8 +353,8 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
 #pragma unroll
         for (int m = 1; m <= R; ++m) {
             CX[m] = pk(p.cf.c[0][m], p.cf.c[0][m]);
-            CY[m] = MODE == kWave ? CX[m] : pk(p.cf.c[1][m], p.cf.c[1][m]);
-            CZ[m] = MODE == kWave ? CX[m] : pk(p.cf.c[2][m], p.cf.c[2][m]);
+            CY[m] = MODE != kStencil ? CX[m] : pk(p.cf.c[1][m], p.cf.c[1][m]);
+            CZ[m] = MODE != kStencil ? CX[m] : pk(p.cf.c[2][m], p.cf.c[2][m]);
         }
         const f2 S2 = pk(p.s, p.s);
         const f2 KU = pk(k_u, k_u);
@@ -448,7 +448,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                     const T *pvu = nullptr;
                     const float *pvv = nullptr;
                     const int sp = cj % C::SP;
-                    if (MODE == kWave) {
+                    if (MODE != kStencil) {
                         if (mbar_wait_bounded(&full_pv[sp], (uint32_t)((cj / C::SP) & 1), &g_status_tma))
                             consumed_pv = cj + 1;
                         else
@@ -457,7 +457,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                         pvv = reinterpret_cast<const float *>(pv + sp * C::PV_STRIDE + C::PVU_BYTES);
                     }
                     f2 res_l[kVY], res_h[kVY];
-                    float4 vel4[kVY];
+                    float4 vel4[kVY], nu4[kVY];
 #pragma unroll
                     for (int r = 0; r < kVY; ++r) {
                         const float4 cen = P[rho + R][r];
@@ -487,7 +487,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                             const f2 zs_l = add2(lo(zp), lo(zm)), zs_h = add2(hi(zp), hi(zm));
                             f2 &al = (m & 1) ? acc_l : acc2_l;
                             f2 &ah = (m & 1) ? acc_h : acc2_h;
-                            if (MODE == kWave) {
+                            if (MODE != kStencil) {
                                 // one weight per distance on every axis (the wave operator)
                                 al = fma2(CX[m], add2(add2(xs_l, ys_l), zs_l), al);
                                 ah = fma2(CX[m], add2(add2(xs_h, ys_h), zs_h), ah);
@@ -516,6 +516,9 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                             }
                             acc_l = fma2(c_l, acc_l, t_l);
                             acc_h = fma2(c_h, acc_h, t_h);
+                        } else if (MODE == kImage) {
+                            nu4[r] = ld4(pvu + (kVY * ty + r) * C::PVU_W + C::PVU_X0 + 4 * tx);
+                            vel4[r] = ld4(pvv + (kVY * ty + r) * kTX + 4 * tx);
                         }
                         res_l[r] = acc_l;
                         res_h[r] = acc_h;
@@ -541,11 +544,28 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                         }
                     }
                     T *dst = out_base + plane_stride * (int64_t)(H + k);
+                    (void)dst;   // unused by the imaging mode
 #pragma unroll
                     for (int r = 0; r < kVY; ++r) {
                         if (!(xin && gy + r < g.ny))
                             continue;
-                        if constexpr (kLow) {
+                        if constexpr (MODE == kImage) {
+                            // g += lap * nu * (2/h^2) / v in FP32, accumulated in FP64
+                            float4 lap;
+                            upk(res_l[r], lap.x, lap.y);
+                            upk(res_h[r], lap.z, lap.w);
+                            const float4 v = vel4[r], nu = nu4[r];
+                            double *gd = static_cast<double *>(p.out[0]) +
+                                         ((H + gx) + g.px * (H + gy + r) + plane_stride * (int64_t)(H + k));
+                            double2 g0 = *reinterpret_cast<const double2 *>(gd);
+                            double2 g1 = *reinterpret_cast<const double2 *>(gd + 2);
+                            g0.x += v.x > 0.f ? (double)(lap.x * nu.x * (p.s / v.x)) : 0.0;
+                            g0.y += v.y > 0.f ? (double)(lap.y * nu.y * (p.s / v.y)) : 0.0;
+                            g1.x += v.z > 0.f ? (double)(lap.z * nu.z * (p.s / v.z)) : 0.0;
+                            g1.y += v.w > 0.f ? (double)(lap.w * nu.w * (p.s / v.w)) : 0.0;
+                            *reinterpret_cast<double2 *>(gd) = g0;
+                            *reinterpret_cast<double2 *>(gd + 2) = g1;
+                        } else if constexpr (kLow) {
                             float4 v;
                             upk(res_l[r], v.x, v.y);
                             upk(res_h[r], v.z, v.w);
@@ -568,7 +588,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                         const int rel_u = kLow ? j + 1 : max(0, j - R + 1);
                         while (n_u < nplanes && n_u < rel_u + C::SL)
                             issue_u();
-                        if (MODE == kWave) {
+                        if (MODE != kStencil) {
                             const int rel_pv = max(0, j - 2 * R + 1);
                             while (n_pv < nzc && n_pv < rel_pv + C::SP)
                                 issue_pv();
@@ -722,6 +742,12 @@ cudaError_t launch_stencil_r(int radius, const TmaPlan &plan, const StepParams &
     }
 }
 
+cudaError_t launch_image_t(int tile_y, const TmaPlan &plan, const StepParams &p, cudaStream_t st)
+{
+    return tile_y == 32 ? launch_cfg<4, kImage, 32, float>(plan, p, 0, st)
+                        : launch_cfg<4, kImage, 16, float>(plan, p, 0, st);
+}
+
 template <typename T>
 cudaError_t launch_wave_t(int tile_y, const TmaPlan &plan, const StepParams &p, int64_t t, cudaStream_t st)
 {
@@ -748,6 +774,8 @@ cudaError_t launch_tma(int radius, Mode mode, int tile_y, gbs_dtype storage, con
     }
     if (storage != GBS_F32)
         return cudaErrorInvalidValue;
+    if (mode == kImage)
+        return radius == 4 ? launch_image_t(tile_y, plan, p, st) : cudaErrorInvalidValue;
     return tile_y == 32 ? launch_stencil_r<kStencil, 32>(radius, plan, p, st)
                         : launch_stencil_r<kStencil, 16>(radius, plan, p, st);
 }
@@ -806,7 +834,7 @@ int tma_default_zchunk(int radius, Mode mode, int tile_y, gbs_dtype storage, con
     const int per_sm = (tile_y == 32) ? 1 : (storage == GBS_F32 ? 2 : 3);
     const int64_t slots = (int64_t)sms * per_sm;
     const int64_t tiles = ((g.nx + kTX - 1) / kTX) * ((g.ny + tile_y - 1) / tile_y);
-    const double halo_cost = (mode == kWave ? 0.25 : 0.5) * 2 * radius;
+    const double halo_cost = (mode != kStencil ? 0.25 : 0.5) * 2 * radius;
     int best = (int)g.nz;
     double best_cost = 1e300;
     for (int64_t c = 1; c <= g.nz && c <= 65535; ++c) {

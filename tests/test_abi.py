@@ -154,3 +154,30 @@ def test_batch_validation_before_device(lib):
     assert not plan.value
     assert lib.gbs_batch_run(None, 3, 0, 0, None) == gbs.GBS_EINVAL
     lib.gbs_batch_plan_destroy(None)
+
+
+def test_adjoint_workspace_and_validation(lib):
+    # internal layout: nx rounded up to 4, row pitch (nx4 + 8) rounded to 8
+    nx, ny, nz, n = 13, 10, 9, 30
+    k = 6   # ceil(sqrt(30))
+    px = ((nx + 3) // 4 * 4 + 8 + 7) // 8 * 8
+    e = px * (ny + 8) * (nz + 8)
+    fld = (e * 4 + 255) // 256 * 256
+    want = fld * (5 + 2 * 5 + (k - 1)) + (e * 8 + 255) // 256 * 256 + 1024 * 8
+    assert lib.gbs_adjoint_workspace_bytes(nx, ny, nz, n, 0) == want
+    assert lib.gbs_adjoint_workspace_bytes(nx, ny, nz, n, 1) == fld * (5 + 2 * 30) + (e * 8 + 255) // 256 * 256 + 8192
+    assert lib.gbs_adjoint_workspace_bytes(nx, ny, nz, 0, 0) == 0
+    vel = ctypes.c_void_p(1 << 20)
+    work = ctypes.c_void_p(1 << 24)
+    args = (vel, ctypes.c_float(1e-3), ctypes.c_float(10.0), nx, ny, nz)
+    # halo < 4, nsteps <= 0, unaligned or small workspace: all rejected before any device call
+    assert lib.gbs_adjoint_forward(*args, 2, n, None, None, 0, work, want, None, None) == gbs.GBS_EINVAL
+    assert lib.gbs_adjoint_forward(*args, 4, 0, None, None, 0, work, want, None, None) == gbs.GBS_EINVAL
+    assert lib.gbs_adjoint_forward(*args, 4, n, None, None, 0, ctypes.c_void_p((1 << 24) + 8), want, None,
+                                   None) == gbs.GBS_EINVAL
+    assert lib.gbs_adjoint_forward(*args, 4, n, None, None, 0, work, want - 1, None, None) == gbs.GBS_EINVAL
+    assert b"workspace" in lib.gbs_last_error()
+    assert lib.gbs_adjoint_backward(*args, 4, n, None, None, 3, None, 0, work, want, None, None,
+                                    None) == gbs.GBS_EINVAL
+    assert lib.gbs_fwi_gradient(*args, 4, n, None, None, 0, None, None, None, 0, work, want, None, None, None,
+                                None) == gbs.GBS_EINVAL

@@ -1,0 +1,127 @@
+"""GPU parity of the adjoint / velocity-gradient path against the FP64 oracle.
+
+* gbs_fwi_gradient (forward with checkpoints, residual + misfit, adjoint
+  steps, imaging condition in FP64) against oracle.fwi_gradient on ragged
+  grids, with few receivers (fused injection) and many (separate kernel);
+* the checkpoint interval changes nothing: K = 1, 3, sqrt(N) and N give
+  bit-identical gradients (recomputed states are the same FP32 values and
+  the FP64 sum runs in the same order);
+* WavePropagate (torch.autograd.Function) gives the same gradient as
+  gbs_fwi_gradient, and its backward for an arbitrary cotangent matches the
+  oracle's adjoint_gradient.
+
+Tolerance: the gradient's normwise error is bounded by the FP32 error of
+the residual it is driven by (the residual is a few per cent of the trace,
+so trace errors count ~30x) plus the propagation bound: 40 * 2e-6 * N.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2309_04671_gb300 as gbs
+import workloads as W
+from gpu_util import need_gpu, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+H = 10.0
+HALO = 4
+
+
+def grad_tol(n):
+    return 40 * 2e-6 * n
+
+
+def _problem(nx, ny, nz, nsteps, nrec, seed):
+    rng = np.random.default_rng(seed)
+    vel = W.layered_velocity(nx, ny, nz, HALO, seed)
+    dt = W.dt_for_cfl(0.4, H, float(W.interior(vel, HALO).max()))
+    n = nx * ny * nz
+    cells = rng.choice(n, 2 + nrec, replace=False).astype(np.int64)
+    src, rec = cells[:2], cells[2:]
+    amp = np.stack([W.ricker(nsteps, dt, 15.0, t0=0.012 + 0.004 * q) for q in range(2)], axis=1).astype(np.float32)
+    pert = np.zeros_like(vel)
+    W.interior(pert, HALO)[...] = rng.uniform(-0.03, 0.03, (nz, ny, nx))
+    vtrue = (vel * (1.0 + pert)).astype(np.float32)
+    _, d_obs = oracle.forward_states(vtrue, dt, H, HALO, nsteps, src_idx=src, src_amp=amp, rec_idx=rec)
+    return dict(vel=vel, dt=dt, nsteps=nsteps, src=src, amp=amp, rec=rec, d_obs=d_obs.astype(np.float32))
+
+
+def _gpu_fwi(p, ckpt_every=0):
+    return gbs.fwi_gradient(to_dev(p["vel"]), p["dt"], H, HALO, p["nsteps"], to_dev(p["d_obs"]),
+                            src_idx=to_dev(p["src"]), src_amp=to_dev(p["amp"]), rec_idx=to_dev(p["rec"]),
+                            ckpt_every=ckpt_every)
+
+
+@pytest.mark.parametrize("shape,nsteps,nrec", [((37, 29, 24), 60, 40), ((32, 32, 32), 48, 9), ((13, 70, 9), 30, 17)])
+def test_fwi_gradient_against_oracle(shape, nsteps, nrec):
+    need_gpu()
+    p = _problem(*shape, nsteps, nrec, seed=sum(shape) + nsteps)
+    misfit, grad, trace, resid = _gpu_fwi(p)
+    gbs.device_status()
+    J, g = oracle.fwi_gradient(p["vel"], p["dt"], H, HALO, nsteps, p["d_obs"], src_idx=p["src"], src_amp=p["amp"],
+                               rec_idx=p["rec"])
+    got_J = float(misfit.cpu()[0])
+    e = oracle.err_norms(grad.cpu().numpy(), g)
+    print(shape, nsteps, nrec, "J", got_J, J, "grad", e)
+    assert abs(got_J - J) <= grad_tol(nsteps) * J
+    assert e["norm_max_rel"] <= grad_tol(nsteps), e
+    assert e["l2_rel"] <= grad_tol(nsteps), e
+    # resid = trace - d_obs exactly (FP32 subtraction)
+    assert torch.equal(resid, trace - to_dev(p["d_obs"]))
+    # the halo of the gradient is not written
+    gh = grad.cpu().numpy()
+    inner = W.interior(gh, HALO).copy()
+    gh[HALO:-HALO, HALO:-HALO, HALO:-HALO] = 0
+    assert np.all(gh == 0) and np.any(inner != 0)
+
+
+def test_checkpoint_interval_is_invisible():
+    need_gpu()
+    p = _problem(21, 18, 17, 27, 12, seed=3)
+    ref = None
+    for k in (0, 1, 3, 27, 50):
+        _, grad, trace, _ = _gpu_fwi(p, ckpt_every=k)
+        gbs.device_status()
+        if ref is None:
+            ref = (grad.clone(), trace.clone())
+        else:
+            assert torch.equal(grad, ref[0]), k
+            assert torch.equal(trace, ref[1]), k
+
+
+def test_autograd_function_matches_fwi_gradient_and_oracle():
+    need_gpu()
+    p = _problem(24, 20, 19, 36, 14, seed=8)
+    vel = to_dev(p["vel"]).requires_grad_(True)
+    si, sa, ri = to_dev(p["src"]), to_dev(p["amp"]), to_dev(p["rec"])
+    trace = gbs.WavePropagate.apply(vel, p["dt"], H, HALO, p["nsteps"], si, sa, ri, 0)
+    d = to_dev(p["d_obs"])
+    loss = 0.5 * ((trace - d) ** 2).sum()
+    loss.backward()
+    gbs.device_status()
+    _, grad, _, _ = _gpu_fwi(p)
+    assert torch.equal(vel.grad, grad.float())
+    # an arbitrary cotangent against the oracle's adjoint
+    w = np.random.default_rng(2).standard_normal((p["nsteps"], p["rec"].size)).astype(np.float32)
+    vel2 = to_dev(p["vel"]).requires_grad_(True)
+    tr2 = gbs.WavePropagate.apply(vel2, p["dt"], H, HALO, p["nsteps"], si, sa, ri, 5)
+    (tr2 * to_dev(w)).sum().backward()
+    gbs.device_status()
+    g = oracle.adjoint_gradient(p["vel"], p["dt"], H, HALO, p["nsteps"], w, src_idx=p["src"], src_amp=p["amp"],
+                                rec_idx=p["rec"])
+    e = oracle.err_norms(vel2.grad.double().cpu().numpy(), g)
+    assert e["norm_max_rel"] <= 2e-6 * 4 * p["nsteps"], e
+
+
+def test_adjoint_rejects_bad_input():
+    need_gpu()
+    vel = torch.full((16, 16, 16), 1500.0, device="cuda")
+    ri = torch.zeros(1, dtype=torch.int64, device="cuda")
+    d = torch.zeros((4, 1), device="cuda")
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.fwi_gradient(vel, 1e-3, 10.0, 4, 4, d, rec_idx=ri, work=small)
+    assert e.value.status == gbs.GBS_EINVAL
+    with pytest.raises(gbs.GbsError):
+        gbs.fwi_gradient(vel, 1e-3, 10.0, 2, 4, d, rec_idx=ri)
