@@ -53,9 +53,15 @@ def parse():
     ap.add_argument("--graph", action="store_true", help="replay the step loop as a CUDA graph")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip BF16/FP16 storage and the radius sweep")
-    ap.add_argument("--no-errors", action="store_true", help="skip the FP64-oracle error runs of the storage forms")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched multi-shot form")
+    ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
+                    help="wave-field storage of the main timed path (arithmetic is FP32 in all)")
+    ap.add_argument("--forms", default="storage,radius,errors,batched,adjoint",
+                    help="comma list of extra forms to measure after the main line, or 'none'")
+    ap.add_argument("--no-forms", action="store_true", help="same as --forms none")
+    ap.add_argument("--adj-n", type=int, default=256, help="adjoint form: interior side")
+    ap.add_argument("--adj-steps", type=int, default=1000, help="adjoint form: time steps")
+    ap.add_argument("--adj-shots", type=int, default=8, help="adjoint form: shots")
+    ap.add_argument("--batch-shots", type=int, default=64, help="batched form: shots")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--ref-leapfrog", type=int, default=2, help="oracle leapfrog steps per reference step")
     return ap.parse_args()
@@ -386,6 +392,142 @@ def batched_forms(args, stream, hbm, nshots=64, nsteps=200):
     return out
 
 
+def _plain_gradient(vel, dt, h, nsteps, src, amp, rec, resid, ckpt):
+    """The same gradient assembled from the library's single-step calls
+    (gbs_wave_step for the forward, recomputation and adjoint steps,
+    gbs_stencil_apply for L u^m) with the imaging product in torch FP64: the
+    unfused way to compute it.  Same sqrt(N) checkpoints."""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    halo = 4
+    c = [w / (h * h) for w in gbs.fd2_coeffs(4)]
+    a, b = torch.zeros_like(vel), torch.zeros_like(vel)
+    cks = []
+    for m in range(nsteps):
+        if m % ckpt == 0:
+            cks.append((a.clone(), b.clone()))
+        gbs.wave_step(a, b, a, vel, dt, h, halo, src_idx=src, src_amp=amp, step=m)
+        a, b = b, a
+    g = torch.zeros(vel.shape, dtype=torch.float64, device=vel.device)
+    v64 = vel.double()
+    na, nb = torch.zeros_like(vel), torch.zeros_like(vel)
+    lap = torch.zeros_like(vel)
+    flat = src.clone()
+    nx = vel.shape[2] - 2 * halo
+    ny = vel.shape[1] - 2 * halo
+    pidx = (flat % nx + halo) + vel.shape[2] * ((flat // nx) % ny + halo + vel.shape[1] * (flat // (nx * ny) + halo))
+    for s in range(len(cks) - 1, -1, -1):
+        m0, m1 = s * ckpt, min(s * ckpt + ckpt, nsteps)
+        states = [cks[s][0], cks[s][1]]
+        for m in range(m0 + 1, m1):
+            nxt = torch.zeros_like(vel)
+            gbs.wave_step(states[-2], states[-1], nxt, vel, dt, h, halo, src_idx=src, src_amp=amp, step=m - 1)
+            states.append(nxt)
+        for m in range(m1 - 1, m0 - 1, -1):
+            gbs.wave_step(na, nb, na, vel, dt, h, halo, src_idx=rec, src_amp=resid, step=m)
+            gbs.stencil_apply(states[m - m0 + 1], lap, radius=4, cx=c, cy=c, cz=c, halo=halo)
+            g += 2.0 * na.double() * lap.double() / v64
+            if m < amp.shape[0]:
+                g.view(-1).index_add_(0, pidx, 2.0 * na.view(-1)[pidx].double() * amp[m].double() / v64.view(-1)[pidx])
+            na, nb = nb, na
+    g[:halo] = 0
+    g[-halo:] = 0
+    g[:, :halo] = 0
+    g[:, -halo:] = 0
+    g[:, :, :halo] = 0
+    g[:, :, -halo:] = 0
+    return g
+
+
+def adjoint_form(args, stream, hbm, n=256, nsteps=1000, nshots=8):
+    """Velocity gradient of the L2 trace misfit: n^3 layered + Gaussian model,
+    nshots sources at seeded surface positions (depth 2), receivers on the
+    full n x n plane at depth 8, data from a model with a +5% Gaussian
+    anomaly, nsteps FP32 steps, sqrt(N) checkpoints, FP64 accumulation."""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    import workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    halo, h = 4, 10.0
+    vel = W.layered_velocity_torch(n, n, n, halo, W.SEED_BASE + 5, dev)
+    zz, yy, xx = torch.meshgrid(*(torch.arange(n + 2 * halo, device=dev, dtype=torch.float32) - halo - n / 2
+                                  for _ in range(3)), indexing="ij")
+    vtrue = vel * (1.0 + 0.05 * torch.exp(-(xx * xx + yy * yy + zz * zz) / (2 * (n / 8) ** 2)))
+    del zz, yy, xx
+    dt = W.dt_for_cfl(0.4, h, float(vtrue.max()))
+    rng = np.random.default_rng(W.SEED_BASE + 5)
+    pos = [(int(rng.integers(0, n)), int(rng.integers(0, n))) for _ in range(nshots)]
+    rec = torch.tensor([W.linear_index(i, j, 8, n, n) for j in range(n) for i in range(n)], dtype=torch.int64,
+                       device=dev)
+    amp = torch.from_numpy(W.ricker(nsteps, dt, 15.0).astype(np.float32).reshape(nsteps, 1)).to(dev)
+    srcs = [torch.tensor([W.linear_index(i, j, 2, n, n)], dtype=torch.int64, device=dev) for i, j in pos]
+    d_obs = []
+    for si in srcs:
+        tr = torch.zeros((nsteps, rec.numel()), device=dev)
+        gbs.wave_propagate(torch.zeros_like(vel), torch.zeros_like(vel), vtrue, dt, h, halo, nsteps, src_idx=si,
+                           src_amp=amp, rec_idx=rec, rec_trace=tr)
+        d_obs.append(tr)
+    work = gbs.adjoint_workspace(vel, halo, nsteps)
+    grad = torch.zeros(vel.shape, dtype=torch.float64, device=dev)
+    misfit = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def gradient():
+        grad.zero_()
+        misfit.zero_()
+        for si, d in zip(srcs, d_obs):
+            gbs.fwi_gradient(vel, dt, h, halo, nsteps, d, src_idx=si, src_amp=amp, rec_idx=rec, work=work,
+                             grad=grad, misfit=misfit)
+
+    def forward_only():
+        tr = torch.empty((nsteps, rec.numel()), device=dev)
+        for si in srcs:
+            gbs.wave_propagate(torch.zeros_like(vel), torch.zeros_like(vel), vel, dt, h, halo, nsteps, src_idx=si,
+                               src_amp=amp, rec_idx=rec, rec_trace=tr)
+    gradient()
+    ms_g, kms, kl = time_calls(gradient, 1, stream)
+    gbs.device_status()
+    forward_only()
+    ms_f, _, _ = time_calls(forward_only, 1, stream)
+    k = int(np.ceil(np.sqrt(nsteps)))
+    pts = n ** 3
+    # algorithmic bytes per point per step: forward 16, recomputation 16 (K-1)/K,
+    # adjoint step 16, imaging 20 (u^m, nu, w, FP32 partial read + write) and
+    # the FP64 fold every 32 steps (FP32 read + write, FP64 read + write: 24/32)
+    bpp = 16 + 16 * (k - 1) / k + 16 + 20 + 24 / 32
+    alg = pts * nshots * nsteps * bpp
+    kernel_ms = kms * kl            # summed duration of the step and imaging launches
+    ach = alg / (kernel_ms * 1e-3) / 1e9
+    out = {"workload": f"{n}^3 layered+16 Gaussians, {nshots} shots (depth 2, seeded x/y), {n}x{n} receivers at "
+                       f"depth 8, {nsteps} steps FP32, CFL 0.4, data from a +5% Gaussian anomaly, checkpoints every "
+                       f"{k} steps, FP64 gradient",
+           "value": pts * nsteps * nshots / (ms_g * 1e-3) / 1e9, "unit": "gradient point-steps/s (x1e9)",
+           "ms_per_gradient": ms_g, "shots": nshots, "forward_only_ms": ms_f, "gradient_over_forward": ms_g / ms_f,
+           "misfit": float(misfit.cpu()[0]),
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                        "bytes_per_point_step": bpp, "kernel_ms": kernel_ms,
+                        "kernel_launches": kl}}
+    # the unfused composition of single-step calls, one shot
+    g_fused = torch.zeros_like(grad)
+    m1 = torch.zeros_like(misfit)
+    _, _, _, resid = gbs.fwi_gradient(vel, dt, h, halo, nsteps, d_obs[0], src_idx=srcs[0], src_amp=amp,
+                                      rec_idx=rec, work=work, grad=g_fused, misfit=m1)
+    torch.cuda.synchronize()
+    del work
+    torch.cuda.empty_cache()
+    res = {}
+
+    def plain():
+        res["g"] = _plain_gradient(vel, dt, h, nsteps, srcs[0], amp, rec, resid, k)
+    ms_p, _, _ = time_calls(plain, 1, stream)
+    gbs.device_status()
+    diff = float((res["g"] - g_fused).abs().max() / g_fused.abs().max())
+    out["unfused_single_step_calls"] = {"ms_one_shot": ms_p, "fused_ms_one_shot": ms_g / nshots,
+                                        "speedup_fused": ms_p / (ms_g / nshots), "grad_norm_max_rel_diff": diff}
+    del res, d_obs
+    torch.cuda.empty_cache()
+    return out
+
+
 def W_padded(prob):
     import workloads as W
     return W.padded_shape(prob.nx, prob.ny, prob.nz, prob.halo)
@@ -454,13 +596,20 @@ def run_ours(args):
     vel = torch.from_numpy(prob.vel).to(dev)
     si = torch.from_numpy(prob.src_idx).to(dev)
     sa = torch.from_numpy(prob.src_amp).to(dev)
-    kw = dict(src_idx=si, src_amp=sa, kernel=args.kernel, tile_y=args.tile_y, zchunk=args.zchunk,
-              use_graph=args.graph)
     stream = torch.cuda.current_stream()
+    if args.storage == "f32":
+        kw = dict(src_idx=si, src_amp=sa, kernel=args.kernel, tile_y=args.tile_y, zchunk=args.zchunk,
+                  use_graph=args.graph)
+        propagate = gbs.wave_propagate
+    else:
+        kw = dict(src_idx=si, src_amp=sa, tile_y=args.tile_y, zchunk=args.zchunk, use_graph=args.graph,
+                  storage=args.storage, work=gbs.lp_workspace(a, halo))
+        propagate = gbs.wave_propagate_lp
+    bytes_per_point = BYTES_PER_POINT if args.storage == "f32" else 10
 
     # warm-up (also builds the wavefield)
     for _ in range(max(3, args.warmup)):
-        a, b = gbs.wave_propagate(a, b, vel, prob.dt, prob.h, halo, ns, **kw)
+        a, b = propagate(a, b, vel, prob.dt, prob.h, halo, ns, **kw)
     gbs.device_status()
 
     clocks = ClockSampler(local)
@@ -474,7 +623,7 @@ def run_ours(args):
     w0 = time.time()
     ev0.record(stream)
     for _ in range(args.steps):
-        a, b = gbs.wave_propagate(a, b, vel, prob.dt, prob.h, halo, ns, **kw)
+        a, b = propagate(a, b, vel, prob.dt, prob.h, halo, ns, **kw)
     ev1.record(stream)
     torch.cuda.synchronize()
     w1 = time.time()
@@ -490,14 +639,14 @@ def run_ours(args):
     value = points / (elapsed_ms * 1e-3) / 1e9
     hbm, peak_kind = peaks()
     per_launch_ms = kernel_ms / max(1, kernel_launches)
-    alg_bytes = BYTES_PER_POINT * prob.npoints
+    alg_bytes = bytes_per_point * prob.npoints
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9 if kernel_launches else None
-    traffic = traffic_per_launch(n)
+    traffic = traffic_per_launch(n) if args.storage == "f32" else None
     inject_launches = 0   # sources are added inside the step kernel (at most 16)
 
     # end to end through host buffers (pinned), same call a user makes
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.storage == "f32":
         hp = torch.zeros(shape, dtype=torch.float32).pin_memory()
         hu = torch.zeros(shape, dtype=torch.float32).pin_memory()
         hv = torch.from_numpy(prob.vel).pin_memory()
@@ -524,12 +673,20 @@ def run_ours(args):
                "sample": f"{steps} FP64 leapfrog steps of the full {n}^3 grid ({secs:.1f} s), after 1 untimed step"}
 
     forms = None
-    if rank == 0 and not args.no_forms:
-        forms = {"storage": storage_forms(prob, args, stream, hbm), "radius_sweep": radius_sweep(args, stream, hbm)}
-        if not args.no_errors:
+    wanted = set() if args.no_forms or args.forms == "none" else set(args.forms.split(","))
+    if rank == 0 and wanted:
+        forms = {}
+        if "storage" in wanted:
+            forms["storage"] = storage_forms(prob, args, stream, hbm)
+        if "radius" in wanted:
+            forms["radius_sweep"] = radius_sweep(args, stream, hbm)
+        if "errors" in wanted:
             forms["error_vs_fp64_oracle"] = precision_errors(stream)
-        if not args.no_batch:
-            forms["batched"] = batched_forms(args, stream, hbm)
+        if "batched" in wanted:
+            forms["batched"] = batched_forms(args, stream, hbm, nshots=args.batch_shots)
+        if "adjoint" in wanted:
+            forms["adjoint"] = adjoint_form(args, stream, hbm, n=args.adj_n, nsteps=args.adj_steps,
+                                            nshots=args.adj_shots)
 
     if rank == 0:
         line = {
@@ -540,7 +697,9 @@ def run_ours(args):
                        "leapfrog_steps_per_step": ns, "dt": prob.dt, "h": prob.h,
                        "l2": "no flush: each of the 3 fields (562 MB) exceeds the 129 MB L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "kernel": "k_tma<R=4,wave>" if args.kernel != 2 else "k_generic<R=4,wave>",
+                       "kernel": ("k_tma<R=4,wave>" if args.kernel != 2 else "k_generic<R=4,wave>")
+                       if args.storage == "f32" else f"k_tma<R=4,wave,{args.storage} storage>",
+                       "storage": args.storage,
                        "tile_y": args.tile_y or 16, "zchunk": args.zchunk or "auto", "graph": args.graph},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None, "traffic": traffic,

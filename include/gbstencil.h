@@ -227,16 +227,19 @@ void gbs_batch_plan_destroy(gbs_batch_plan *plan);
  * u^{m+1} at the receivers, m = 0..nsteps-1.  For a scalar J of the trace
  * with a_m = dJ/d(trace row m), nu^{m+1} = 2nu^{m+2} - nu^{m+3} +
  * (v dt)^2 (L nu^{m+2} + R^T a_m) is the same step run backwards, and
- *   dJ/dv(x) = sum_m 2 nu^{m+1}(x) (L u^m + S f^m)(x) / v(x),
- * accumulated in FP64 (fields and steps in FP32).
+ *   dJ/dv(x) = sum_m 2 nu^{m+1}(x) (L u^m + S f^m)(x) / v(x).
+ * Fields and steps are FP32; the sum over m runs in FP32 over runs of at
+ * most 32 consecutive steps, each folded into an FP64 accumulator (FP64
+ * arithmetic is a small fraction of FP32 throughput on this GPU).
  *
  * Checkpointing: the forward pass keeps (u^{sK-1}, u^{sK}) every K =
  * ckpt_every steps (0: K = ceil(sqrt(nsteps))); the backward pass recomputes
  * each segment's K states from its checkpoint.  All state lives in the
- * caller's workspace (gbs_adjoint_workspace_bytes: velocity, 4 fields,
- * 2*ceil(nsteps/K) checkpoints, K-1 segment fields, each (nx rounded up to
- * 4, plus 8) * (ny+8) * (nz+8) FP32 values with rows padded to 8, plus one
- * FP64 field and 8 KiB), 256-byte aligned.  The halo of vel is not read.
+ * caller's workspace (gbs_adjoint_workspace_bytes: velocity, imaging
+ * weight, FP32 partial gradient, 4 wave fields, 2*ceil(nsteps/K) checkpoint
+ * fields, K-1 segment fields, each (nx rounded up to 4, plus 8) * (ny+8) *
+ * (nz+8) FP32 values with rows padded to 8, plus one FP64 field and 8 KiB),
+ * 256-byte aligned.  The halo of vel is not read.
  *
  * gbs_adjoint_forward: runs the forward model, writes rec->trace (nt >=
  *   nsteps rows) and leaves the checkpoints in `work`.

@@ -12,9 +12,9 @@
 // has no adjoint; this is the discrete adjoint of the step as implemented.)
 //
 // The adjoint step is the forward wave-step kernel; the imaging condition is
-// the same TMA kernel in its kImage mode (stencil of u^m, FP64 accumulation
-// of the product with nu^{m+1}); the source cells get their term from a
-// small kernel.  The forward pass stores (u^{sK-1}, u^{sK}) every K steps;
+// the same TMA kernel in its kImage mode (stencil of u^m times nu^{m+1},
+// summed in FP32 over at most 32 steps, then folded into the FP64
+// gradient); the source cells get their term from a small kernel.  The forward pass stores (u^{sK-1}, u^{sK}) every K steps;
 // the backward pass walks the segments last to first, recomputes the K
 // states of a segment from its checkpoint into a segment buffer, and runs
 // the adjoint steps of the segment against them.  All fields live in the
@@ -38,13 +38,23 @@ int64_t default_ckpt(int64_t nsteps)
     return k < 1 ? 1 : k;
 }
 
-// Workspace: velocity, forward and adjoint ping-pong pairs, checkpoints,
-// segment buffer, FP64 gradient, misfit partials.
+// The imaging sum runs in FP32 over at most kFoldEvery consecutive steps and
+// is folded into the FP64 gradient after each such run (FP64 arithmetic is
+// a small fraction of FP32 throughput on this GPU; ~32-term FP32 partial
+// sums lose ~1e-6 relative, far below the FP32 field error).  The fold
+// points depend on m only, so results do not depend on the checkpoint
+// interval.
+constexpr int64_t kFoldEvery = 32;
+
+// Workspace: velocity, imaging weight, FP32 partial gradient, forward and
+// adjoint ping-pong pairs, checkpoints, segment buffer, FP64 gradient,
+// misfit partials.
 struct AdjLayout {
     Grid gi;
     int64_t K = 1, nck = 0;
     size_t field = 0;   // bytes of one FP32 field
-    size_t off_vel = 0, off_f[2] = {0, 0}, off_n[2] = {0, 0}, off_ck = 0, off_seg = 0, off_g = 0, off_part = 0;
+    size_t off_vel = 0, off_w = 0, off_gp = 0, off_f[2] = {0, 0}, off_n[2] = {0, 0}, off_ck = 0, off_seg = 0,
+           off_g = 0, off_part = 0;
     size_t total = 0;
 };
 
@@ -58,6 +68,10 @@ AdjLayout adj_layout(int64_t nx, int64_t ny, int64_t nz, int64_t nsteps, int64_t
     L.field = up256(E * sizeof(float));
     size_t off = 0;
     L.off_vel = off;
+    off += L.field;
+    L.off_w = off;
+    off += L.field;
+    L.off_gp = off;
     off += L.field;
     for (int i = 0; i < 2; ++i) {
         L.off_f[i] = off;
@@ -83,8 +97,8 @@ struct Ctx {
     Grid gc, gi;
     const AdjLayout *L;
     unsigned char *w;
-    float *vel;
-    CUtensorMap vel_map;
+    float *vel, *wt, *gp;   // velocity, imaging weight 2/(h^2 v), FP32 partial gradient
+    CUtensorMap vel_map, w_map, gp_map;
     int tile_y, zchunk;
     float dt, h;
     cudaStream_t st;
@@ -133,7 +147,8 @@ gbs_status step(const Ctx &c, const float *prev, const float *u, float *out, con
     return GBS_OK;
 }
 
-// Imaging condition at step m: g += 2 nu (L u^m + S f^m) / v.
+// Imaging condition at step m: g += 2 nu (L u^m + S f^m) / v (the stencil
+// part into the FP32 partial, the source cells straight into FP64).
 gbs_status image(const Ctx &c, const float *u_m, const float *nu, const gbs_src *src, int64_t m)
 {
     TmaPlan plan;
@@ -142,13 +157,13 @@ gbs_status image(const Ctx &c, const float *u_m, const float *nu, const gbs_src 
         s = make_tensor_map(&plan.prev, nu, c.gi, 64, c.tile_y, GBS_F32);
     if (s != GBS_OK)
         return s;
-    plan.vel = c.vel_map;
+    plan.vel = c.w_map;
+    plan.g = c.gp_map;
     StepParams p;
     memset(&p, 0, sizeof(p));
     p.g = c.gi;
-    p.out[0] = p.out[1] = c.grad();
+    p.out[0] = p.out[1] = c.gp;
     p.cf = wave_weights();
-    p.s = (float)(2.0 / ((double)c.h * (double)c.h));
     p.zchunk = c.zchunk;
     p.inx = c.gc.nx;
     p.iny = c.gc.ny;
@@ -195,6 +210,8 @@ Ctx make_ctx(const AdjLayout &L, int64_t nx, int64_t ny, int64_t nz, int halo, v
     c.L = &L;
     c.w = static_cast<unsigned char *>(work);
     c.vel = c.fld(L.off_vel);
+    c.wt = c.fld(L.off_w);
+    c.gp = c.fld(L.off_gp);
     c.tile_y = (opts && opts->tile_y == 32) ? 32 : 16;
     c.zchunk = (opts && opts->zchunk > 0) ? opts->zchunk : tma_default_zchunk(4, kWave, c.tile_y, GBS_F32, c.gi);
     c.dt = dt;
@@ -203,15 +220,24 @@ Ctx make_ctx(const AdjLayout &L, int64_t nx, int64_t ny, int64_t nz, int halo, v
     return c;
 }
 
-// Copy the velocity into the internal layout (zero elsewhere) and map it.
+// Copy the velocity into the internal layout (zero elsewhere), derive the
+// imaging weight w = 2 / (h^2 v) (0 where v = 0), and map both.
 gbs_status load_velocity(Ctx &c, const float *vel)
 {
+    const int64_t E = grid_elems(c.gi);
     cudaError_t e = cudaMemsetAsync(c.vel, 0, c.L->field, c.st);
     if (e == cudaSuccess)
         e = launch_copy_f32(c.gc, vel, c.gi, c.vel, c.st);
+    if (e == cudaSuccess)
+        e = launch_image_weight(c.vel, (float)(2.0 / ((double)c.h * (double)c.h)), c.wt, E, c.st);
     if (e != cudaSuccess)
         return set_cuda_error(e, "velocity copy");
-    return make_tensor_map(&c.vel_map, c.vel, c.gi, 64, c.tile_y, GBS_F32);
+    gbs_status s = make_tensor_map(&c.vel_map, c.vel, c.gi, 64, c.tile_y, GBS_F32);
+    if (s == GBS_OK)
+        s = make_tensor_map(&c.w_map, c.wt, c.gi, 64, c.tile_y, GBS_F32);
+    if (s == GBS_OK)
+        s = make_tensor_map(&c.gp_map, c.gp, c.gi, 64, c.tile_y, GBS_F32);
+    return s;
 }
 
 gbs_status forward(Ctx &c, int64_t nsteps, const gbs_src *src, const gbs_rec *rec)
@@ -247,6 +273,8 @@ gbs_status backward(Ctx &c, int64_t nsteps, const gbs_src *src, const gbs_src *a
     cudaError_t e = cudaMemsetAsync(a, 0, 2 * L.field, c.st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(c.grad(), 0, (size_t)grid_elems(c.gi) * sizeof(double), c.st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c.gp, 0, L.field, c.st);
     // the steps never write halos (or, with zero velocity, change the dead
     // columns), so zero segment buffers keep them zero for every recomputed state
     const size_t nseg = (size_t)std::max<int64_t>(0, std::min(L.K, nsteps) - 1);
@@ -274,6 +302,8 @@ gbs_status backward(Ctx &c, int64_t nsteps, const gbs_src *src, const gbs_src *a
                 r = image(c, u_at(m), a, src, m);
             if (r != GBS_OK)
                 return r;
+            if (m % kFoldEvery == 0 && (e = launch_fold(c.gp, c.grad(), grid_elems(c.gi), c.st)) != cudaSuccess)
+                return set_cuda_error(e, "gradient fold");
             std::swap(a, b);
         }
     }

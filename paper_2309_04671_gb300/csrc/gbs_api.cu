@@ -57,14 +57,17 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// Tensor map over a padded field (px x py x pz) of the given storage type, box bw x bh x 1.
-gbs_status make_map(CUtensorMap *m, const void *base, const Grid &g, int bw, int bh, gbs_dtype dt = GBS_F32)
+// Tensor map over a padded field (px x py x pz) of the given storage type, box
+// bw x bh x 1; f64 = true maps an FP64 field (dt ignored).
+gbs_status make_map(CUtensorMap *m, const void *base, const Grid &g, int bw, int bh, gbs_dtype dt = GBS_F32,
+                    bool f64 = false)
 {
     EncodeTiledFn enc = encode_fn();
     if (!enc)
         return fail(GBS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    const int es = dt == GBS_F32 ? 4 : 2;
-    const CUtensorMapDataType ty = dt == GBS_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+    const int es = f64 ? 8 : dt == GBS_F32 ? 4 : 2;
+    const CUtensorMapDataType ty = f64             ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                   : dt == GBS_F32  ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : dt == GBS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)(g.nz + 2 * g.halo)};
@@ -387,6 +390,10 @@ void profile_end(cudaEvent_t e0, cudaStream_t st) { prof_end(e0, st); }
 gbs_status make_tensor_map(CUtensorMap *m, const void *base, const Grid &g, int bw, int bh, gbs_dtype dt)
 {
     return make_map(m, base, g, bw, bh, dt);
+}
+gbs_status make_tensor_map_f64(CUtensorMap *m, const double *base, const Grid &g, int bw, int bh)
+{
+    return make_map(m, base, g, bw, bh, GBS_F32, true);
 }
 Grid internal_grid(int64_t nx, int64_t ny, int64_t nz) { return lp_layout(nx, ny, nz).g; }
 Grid dense_layout(int64_t nx, int64_t ny, int64_t nz, int halo) { return dense_grid(nx, ny, nz, halo); }

@@ -36,9 +36,11 @@ struct Coeffs {
 // What the epilogue computes from the Laplacian `lap` at a point:
 //   kStencil: out = lap
 //   kWave:    out = 2u - u_prev + (vel * s)^2 * lap   with s = dt/h
-//   kImage:   g += (double)(lap * nu * s / vel), s = 2/h^2, nu read through
-//             the u_prev map, g = out[0] an FP64 field in the same layout
-//             (0 where vel == 0); the imaging condition of the adjoint
+//   kImage:   g += lap * nu * w in FP32, nu read through the u_prev map and
+//             w = 2 / (h^2 vel) (0 where vel == 0) through the vel map; g =
+//             out[0], an FP32 partial sum in the same layout, staged through
+//             the g map (the imaging condition of the adjoint; the caller
+//             folds the partial into its FP64 gradient every few steps)
 enum Mode { kStencil = 0, kWave = 1, kImage = 2 };
 
 struct WaveArgs {
@@ -116,9 +118,10 @@ cudaError_t launch_generic(int radius, Mode mode, const Grid &g, const float *in
                            const Coeffs &cf, const WaveArgs &w, int zchunk, cudaStream_t st);
 
 struct TmaPlan {
-    CUtensorMap u;       // box (64+8) x (TY+2R) x 1 over the padded field
-    CUtensorMap prev;    // box 64 x TY x 1 (wave mode)
-    CUtensorMap vel;     // box 64 x TY x 1 (wave mode), FP32
+    CUtensorMap u{};     // box (64+8) x (TY+2R) x 1 over the padded field
+    CUtensorMap prev{};  // box 64 x TY x 1 (wave mode)
+    CUtensorMap vel{};   // box 64 x TY x 1 (wave mode), FP32
+    CUtensorMap g{};     // box 64 x TY x 1 (imaging mode), FP32 partial sum
 };
 cudaError_t launch_tma(int radius, Mode mode, int tile_y, gbs_dtype storage, const TmaPlan &plan,
                        const StepParams &p, int64_t t, cudaStream_t st);
@@ -153,6 +156,7 @@ Coeffs wave_weights();
 cudaEvent_t profile_begin(cudaStream_t st);
 void profile_end(cudaEvent_t e0, cudaStream_t st);
 gbs_status make_tensor_map(CUtensorMap *m, const void *base, const Grid &g, int bw, int bh, gbs_dtype dt);
+gbs_status make_tensor_map_f64(CUtensorMap *m, const double *base, const Grid &g, int bw, int bh);
 // interior (nx, ny, nz), halo 4, nx rounded up to a multiple of 4 (dead
 // columns), rows padded to a multiple of 8 elements
 Grid internal_grid(int64_t nx, int64_t ny, int64_t nz);
@@ -184,6 +188,10 @@ constexpr int kMisfitBlocks = 1024;
 cudaError_t launch_residual_misfit(const float *trace, const float *d_obs, int64_t n, float *resid, double *part,
                                    double *misfit, cudaStream_t st);
 cudaError_t launch_grad_add(const Grid &gi, const double *g, const Grid &gc, double *grad_c, cudaStream_t st);
+// w = (2/h^2) / v where v > 0, else 0, over all n values of a field
+cudaError_t launch_image_weight(const float *vel, float two_over_h2, float *w, int64_t n, cudaStream_t st);
+// g += (double)gp; gp = 0, over all n values (n a multiple of 4, 16-byte aligned)
+cudaError_t launch_fold(float *gp, double *g, int64_t n, cudaStream_t st);
 
 // Error norms (k_norms.cu): one FP64 partial record of 4 doubles per block
 // of kNormRowsPerBlock rows; `out` receives kNormOut doubles.

@@ -1,6 +1,8 @@
 // Small kernels of the adjoint / gradient path: the trace residual with the
-// L2 misfit J = 1/2 sum r^2 (FP64, deterministic two-pass reduction), and
-// the FP64 gradient added from the internal layout into the caller's.
+// L2 misfit J = 1/2 sum r^2 (FP64, deterministic two-pass reduction), the
+// imaging weight 2 / (h^2 v), the fold of an FP32 partial gradient into the
+// FP64 one, and the FP64 gradient added from the internal layout into the
+// caller's.
 #include "gbs_internal.cuh"
 
 namespace gbs {
@@ -62,7 +64,56 @@ __global__ void __launch_bounds__(kThreads) k_grad_add(Grid gi, const double *g,
     }
 }
 
+__global__ void __launch_bounds__(kThreads) k_image_weight(const float *vel, float c, float *w, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const float v = vel[i];
+        w[i] = v > 0.f ? c / v : 0.f;
+    }
+}
+
+// g += gp, gp = 0 (4 values per thread and iteration)
+__global__ void __launch_bounds__(kThreads) k_fold(float4 *gp, double2 *g, int64_t n4)
+{
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
+        const float4 a = gp[i];
+        double2 lo = g[2 * i], hi = g[2 * i + 1];
+        lo.x += (double)a.x;
+        lo.y += (double)a.y;
+        hi.x += (double)a.z;
+        hi.y += (double)a.w;
+        g[2 * i] = lo;
+        g[2 * i + 1] = hi;
+        gp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+unsigned grid_blocks(int64_t n)
+{
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (n + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)sms * 8;
+    return (unsigned)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
 }  // namespace
+
+cudaError_t launch_image_weight(const float *vel, float two_over_h2, float *w, int64_t n, cudaStream_t st)
+{
+    k_image_weight<<<grid_blocks(n), kThreads, 0, st>>>(vel, two_over_h2, w, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fold(float *gp, double *g, int64_t n, cudaStream_t st)
+{
+    if ((n & 3) != 0 || (reinterpret_cast<uintptr_t>(gp) & 15u) != 0 || (reinterpret_cast<uintptr_t>(g) & 15u) != 0)
+        return cudaErrorInvalidValue;
+    k_fold<<<grid_blocks(n / 4), kThreads, 0, st>>>(reinterpret_cast<float4 *>(gp), reinterpret_cast<double2 *>(g),
+                                                    n / 4);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_residual_misfit(const float *trace, const float *d_obs, int64_t n, float *resid, double *part,
                                    double *misfit, cudaStream_t st)

@@ -87,8 +87,12 @@ struct Cfg {
     static constexpr int PVU_W = kTX + 2 * PVU_X0;
     static constexpr int PVU_BYTES = PVU_W * TY * ES;
     static constexpr int PVV_BYTES = kTX * TY * 4;     // vel tile (FP32)
-    static constexpr int PV_STRIDE = PVU_BYTES + PVV_BYTES;
-    static constexpr int SP = LOW ? 3 : 5;
+    // imaging mode: the FP32 partial-sum tile rides in the same stage
+    static constexpr int PVG_BYTES = MODE == kImage ? kTX * TY * 4 : 0;
+    static constexpr int PV_STRIDE = PVU_BYTES + PVV_BYTES + PVG_BYTES;
+    // stages of (u_prev|nu, vel|w[, g]); imaging stages are 1.5x as large,
+    // so fewer keep two CTAs per SM
+    static constexpr int SP = LOW ? 3 : (MODE == kImage ? 4 : 5);
     static constexpr size_t SMEM_L = (size_t)SL * L_STRIDE;
     static constexpr size_t SMEM_F = (size_t)SF * F_STRIDE;
     static constexpr size_t SMEM_PV = MODE != kStencil ? (size_t)SP * PV_STRIDE : 0;
@@ -220,7 +224,8 @@ __device__ __forceinline__ f2 xpair(const float4 &lf, const float4 &cen, const f
 // of the field described by p; t = time level of u, parity selects p.out.
 template <int R, int MODE, int TY, typename T>
 __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, const CUtensorMap *__restrict__ pm_prev,
-                                         const CUtensorMap *__restrict__ pm_vel, const StepParams &p,
+                                         const CUtensorMap *__restrict__ pm_vel, const CUtensorMap *__restrict__ pm_g,
+                                         const StepParams &p,
                                          const int64_t tx0, const int64_t ty0, const int z0, const int z1,
                                          const int64_t t, const int parity)
 {
@@ -267,6 +272,8 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
             prefetch_tmap(pm_prev);
             prefetch_tmap(pm_vel);
         }
+        if (MODE == kImage)
+            prefetch_tmap(pm_g);
         for (int i = 0; i < C::SL; ++i)
             mbar_init(&full_u[i], 1);
         for (int i = 0; i < C::SP; ++i)
@@ -333,6 +340,9 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
         mbar_arrive_expect_tx(&full_pv[st], C::PV_STRIDE);
         tma_load_3d(dst, pm_prev, (int)(H + tx0 - C::PVU_X0), (int)(H + ty0), H + z0 + n_pv, &full_pv[st]);
         tma_load_3d(dst + C::PVU_BYTES, pm_vel, (int)(H + tx0), (int)(H + ty0), H + z0 + n_pv, &full_pv[st]);
+        if (MODE == kImage)
+            tma_load_3d(dst + C::PVU_BYTES + C::PVV_BYTES, pm_g, (int)(H + tx0), (int)(H + ty0), H + z0 + n_pv,
+                        &full_pv[st]);
         ++n_pv;
     };
     if (tid == 0) {
@@ -447,6 +457,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                     }
                     const T *pvu = nullptr;
                     const float *pvv = nullptr;
+                    const float *pvg = nullptr;
                     const int sp = cj % C::SP;
                     if (MODE != kStencil) {
                         if (mbar_wait_bounded(&full_pv[sp], (uint32_t)((cj / C::SP) & 1), &g_status_tma))
@@ -455,6 +466,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                             fail = true;
                         pvu = reinterpret_cast<const T *>(pv + sp * C::PV_STRIDE);
                         pvv = reinterpret_cast<const float *>(pv + sp * C::PV_STRIDE + C::PVU_BYTES);
+                        pvg = reinterpret_cast<const float *>(pv + sp * C::PV_STRIDE + C::PVU_BYTES + C::PVV_BYTES);
                     }
                     f2 res_l[kVY], res_h[kVY];
                     float4 vel4[kVY], nu4[kVY];
@@ -550,21 +562,13 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                         if (!(xin && gy + r < g.ny))
                             continue;
                         if constexpr (MODE == kImage) {
-                            // g += lap * nu * (2/h^2) / v in FP32, accumulated in FP64
-                            float4 lap;
-                            upk(res_l[r], lap.x, lap.y);
-                            upk(res_h[r], lap.z, lap.w);
-                            const float4 v = vel4[r], nu = nu4[r];
-                            double *gd = static_cast<double *>(p.out[0]) +
-                                         ((H + gx) + g.px * (H + gy + r) + plane_stride * (int64_t)(H + k));
-                            double2 g0 = *reinterpret_cast<const double2 *>(gd);
-                            double2 g1 = *reinterpret_cast<const double2 *>(gd + 2);
-                            g0.x += v.x > 0.f ? (double)(lap.x * nu.x * (p.s / v.x)) : 0.0;
-                            g0.y += v.y > 0.f ? (double)(lap.y * nu.y * (p.s / v.y)) : 0.0;
-                            g1.x += v.z > 0.f ? (double)(lap.z * nu.z * (p.s / v.z)) : 0.0;
-                            g1.y += v.w > 0.f ? (double)(lap.w * nu.w * (p.s / v.w)) : 0.0;
-                            *reinterpret_cast<double2 *>(gd) = g0;
-                            *reinterpret_cast<double2 *>(gd + 2) = g1;
+                            // g += (lap * nu) * w, w = 2 / (h^2 v): FP32 partial sum
+                            const float4 gv = ld4(pvg + (kVY * ty + r) * kTX + 4 * tx);   // staged by TMA
+                            const f2 g_l = fma2(mul2(res_l[r], lo(nu4[r])), lo(vel4[r]), lo(gv));
+                            const f2 g_h = fma2(mul2(res_h[r], hi(nu4[r])), hi(vel4[r]), hi(gv));
+                            float *gd = static_cast<float *>(p.out[0]) +
+                                        ((H + gx) + g.px * (H + gy + r) + plane_stride * (int64_t)(H + k));
+                            st_pairs(gd, g_l, g_h);
                         } else if constexpr (kLow) {
                             float4 v;
                             upk(res_l[r], v.x, v.y);
@@ -639,13 +643,14 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
 template <int R, int MODE, int TY, typename T>
 __global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::MIN_BLOCKS)
     k_tma(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_prev,
-          const __grid_constant__ CUtensorMap tm_vel, const __grid_constant__ StepParams p, const int64_t t)
+          const __grid_constant__ CUtensorMap tm_vel, const __grid_constant__ CUtensorMap tm_g,
+          const __grid_constant__ StepParams p, const int64_t t)
 {
     const int64_t tx0 = (int64_t)(blockIdx.x % p.tiles_x) * kTX;
     const int64_t ty0 = (int64_t)(blockIdx.x / p.tiles_x) * TY;
     const int z0 = blockIdx.y * p.zchunk;
     const int z1 = (int)min((int64_t)z0 + p.zchunk, p.g.nz);
-    tma_body<R, MODE, TY, T>(&tm_u, &tm_prev, &tm_vel, p, tx0, ty0, z0, z1, t, 0);
+    tma_body<R, MODE, TY, T>(&tm_u, &tm_prev, &tm_vel, &tm_g, p, tx0, ty0, z0, z1, t, 0);
 }
 
 // Many fields (shots) in one launch: CTA i does items[i].  Per-shot
@@ -657,7 +662,7 @@ __global__ void __launch_bounds__(Cfg<4, kWave, TY, T>::NT, Cfg<4, kWave, TY, T>
 {
     const BatchItem it = items[blockIdx.x];
     const CUtensorMap *m = maps + ((int64_t)it.shot * 2 + parity) * 3;
-    tma_body<4, kWave, TY, T>(m, m + 1, m + 2, shots[it.shot], it.tx0, it.ty0, it.z0, it.z1, t, parity);
+    tma_body<4, kWave, TY, T>(m, m + 1, m + 2, nullptr, shots[it.shot], it.tx0, it.ty0, it.z0, it.z1, t, parity);
 }
 
 // The dynamic shared-memory opt-in, set once per instantiation and device
@@ -726,7 +731,7 @@ cudaError_t launch_cfg(const TmaPlan &plan, const StepParams &p0, int64_t t, cud
         return cudaErrorInvalidConfiguration;
     p.tiles_x = (int)tiles_x;
     dim3 grid((unsigned)(tiles_x * tiles_y), (unsigned)nchunks);
-    k_tma<R, MODE, TY, T><<<grid, C::NT, C::SMEM, st>>>(plan.u, plan.prev, plan.vel, p, t);
+    k_tma<R, MODE, TY, T><<<grid, C::NT, C::SMEM, st>>>(plan.u, plan.prev, plan.vel, plan.g, p, t);
     return cudaGetLastError();
 }
 
