@@ -190,6 +190,12 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def job_value(points_per_rank, world, elapsed_ms):
+    """Whole-job throughput (Gpoint-updates/s): the points every rank
+    processed over the slowest rank's timed region."""
+    return points_per_rank * world / (elapsed_ms * 1e-3) / 1e9
+
+
 def cpu_oracle_rate(prob, target_s):
     """FP64 oracle (C, OpenMP over z) on the host cores: leapfrog steps of the
     same grid, timed; returns (Gpt/s, steps, seconds, threads)."""
@@ -635,8 +641,7 @@ def run_ours(args):
     elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     clk = clocks.stop()
 
-    points = prob.npoints * ns * args.steps * world
-    value = points / (elapsed_ms * 1e-3) / 1e9
+    value = job_value(prob.npoints * ns * args.steps, world, elapsed_ms)
     hbm, peak_kind = peaks()
     per_launch_ms = kernel_ms / max(1, kernel_launches)
     alg_bytes = bytes_per_point * prob.npoints
