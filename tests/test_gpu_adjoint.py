@@ -1,11 +1,14 @@
 """GPU parity of the adjoint / velocity-gradient path against the FP64 oracle.
 
 * gbs_fwi_gradient (forward with checkpoints, residual + misfit, adjoint
-  steps, imaging condition in FP64) against oracle.fwi_gradient on ragged
-  grids, with few receivers (fused injection) and many (separate kernel);
+  steps, imaging condition summed in FP32 over runs of <= 32 steps and
+  folded into FP64) against oracle.fwi_gradient on ragged grids, with few
+  receivers (fused injection) and many (separate kernel);
 * the checkpoint interval changes nothing: K = 1, 3, sqrt(N) and N give
   bit-identical gradients (recomputed states are the same FP32 values and
-  the FP64 sum runs in the same order);
+  the fold points depend on the step index only);
+* at the benchmark's full size (256^3, 1000 steps): the trace against the
+  oracle's forward run, the misfit, and checkpoint invariance;
 * WavePropagate (torch.autograd.Function) gives the same gradient as
   gbs_fwi_gradient, and its backward for an arbitrary cotangent matches the
   oracle's adjoint_gradient.
@@ -125,3 +128,37 @@ def test_adjoint_rejects_bad_input():
     assert e.value.status == gbs.GBS_EINVAL
     with pytest.raises(gbs.GbsError):
         gbs.fwi_gradient(vel, 1e-3, 10.0, 2, 4, d, rec_idx=ri)
+
+
+def test_config5_full_size_properties():
+    """The benchmark's gradient workload (256^3, 1000 steps, 65,536 receivers
+    on the plane at depth 8, one shot): the recorded trace against the FP64
+    oracle's forward run, the misfit against 1/2 sum r^2 of the returned
+    residual, and bit-identical gradients for two checkpoint intervals."""
+    need_gpu()
+    n, N, halo = 256, 1000, 4
+    vel = W.layered_velocity_torch(n, n, n, halo, W.SEED_BASE + 5, "cuda")
+    dt = W.dt_for_cfl(0.4, H, float(vel.max()) * 1.05)
+    rec = torch.tensor([W.linear_index(i, j, 8, n, n) for j in range(n) for i in range(n)], dtype=torch.int64,
+                       device="cuda")
+    src = torch.tensor([W.linear_index(77, 140, 2, n, n)], dtype=torch.int64, device="cuda")
+    amp = torch.from_numpy(W.ricker(N, dt, 15.0).astype(np.float32).reshape(N, 1)).cuda()
+    d_obs = torch.zeros((N, rec.numel()), device="cuda")
+    gbs.wave_propagate(torch.zeros_like(vel), torch.zeros_like(vel), vel * 1.01, dt, H, halo, N, src_idx=src,
+                       src_amp=amp, rec_idx=rec, rec_trace=d_obs)
+    grads = []
+    for k in (0, 50):
+        misfit, grad, trace, resid = gbs.fwi_gradient(vel, dt, H, halo, N, d_obs, src_idx=src, src_amp=amp,
+                                                      rec_idx=rec, ckpt_every=k)
+        gbs.device_status()
+        grads.append(grad)
+    assert torch.equal(grads[0], grads[1])
+    r = resid.double()
+    assert float(misfit[0]) == pytest.approx(0.5 * float((r * r).sum()), rel=1e-12)
+    v = vel.cpu().numpy()
+    z = np.zeros_like(v)
+    _, _, ref = oracle.wave_propagate(z, z, v, dt, H, halo, N, src_idx=src.cpu().numpy(),
+                                      src_amp=amp.cpu().numpy(), rec_idx=rec.cpu().numpy())
+    e = oracle.err_norms(trace.cpu().numpy(), ref)
+    assert e["norm_max_rel"] <= 2e-6 * N, e
+    assert bool(torch.isfinite(grads[0]).all()) and float(grads[0].abs().max()) > 0

@@ -204,3 +204,43 @@ def test_batch_rejects_bad_input():
         gbs.BatchPlan([good, gbs.Shot(z, z.clone(), z.clone(), 1e-3, 10.0, 4, idx, amp)])
     with pytest.raises(gbs.GbsError):
         gbs.BatchPlan([gbs.Shot(z, z, z.clone(), 1e-3, 10.0, 4)])
+
+
+def test_config4_full_size_sampled_shots():
+    """The benchmark's batch: 64 shots with sides uniform in 96-320, 200 steps,
+    autotuned plan, graph-captured run.  Three shots (smallest, median,
+    largest volume) are checked whole against the FP64 oracle; every shot
+    must stay finite with an untouched halo."""
+    need_gpu()
+    nsteps = 200
+    specs = W.batch_specs(64)
+    shots = []
+    for s in specs:
+        vel = W.layered_velocity_torch(s.nx, s.ny, s.nz, 4, s.vel_seed, dev())
+        dt = W.dt_for_cfl(s.cfl, s.h, float(vel.max()))
+        idx = torch.tensor([W.linear_index(*s.src, s.nx, s.ny)], dtype=torch.int64, device=dev())
+        amp = torch.from_numpy(W.ricker(nsteps, dt, 15.0).astype(np.float32).reshape(nsteps, 1)).to(dev())
+        z = torch.zeros_like(vel)
+        shots.append(gbs.Shot(z, z.clone(), vel, dt, s.h, 4, idx, amp))
+    plan = gbs.BatchPlan(shots, storage="f32")
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        plan.run(nsteps, use_graph=True)
+    st.synchronize()
+    gbs.device_status()
+    vols = [s.nx * s.ny * s.nz for s in specs]
+    order = np.argsort(vols)
+    for k in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        s, sh = specs[k], shots[k]
+        vel = sh.vel.cpu().numpy()
+        z = np.zeros_like(vel)
+        _, ru, _ = oracle.wave_propagate(z, z, vel, sh.dt, sh.h, 4, nsteps, src_idx=sh.src_idx.cpu().numpy(),
+                                         src_amp=sh.src_amp.cpu().numpy())
+        e = oracle.err_norms(sh.u.cpu().numpy(), ru)
+        assert e["norm_max_rel"] <= tol_steps(nsteps), (k, (s.nx, s.ny, s.nz), e)
+    for sh in shots:
+        u = sh.u
+        assert bool(torch.isfinite(u).all())
+        assert float(u[:4].abs().max()) == 0 and float(u[:, :, -4:].abs().max()) == 0
+    plan.close()
