@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
                     help="wave-field storage of the main timed path (arithmetic is FP32 in all)")
-    ap.add_argument("--forms", default="storage,radius,errors,batched,adjoint",
+    ap.add_argument("--forms", default="storage,radius,errors,precision,batched,adjoint",
                     help="comma list of extra forms to measure after the main line, or 'none'")
     ap.add_argument("--no-forms", action="store_true", help="same as --forms none")
     ap.add_argument("--adj-n", type=int, default=256, help="adjoint form: interior side")
@@ -270,6 +270,51 @@ def storage_forms(prob, args, stream, hbm):
                     "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                                  "kernel_ms_per_launch": kms, "kernel_launches": kl}}
         del a, b, work, st
+    torch.cuda.empty_cache()
+    return out
+
+
+def precision_form(args, stream, hbm, n=1024, nsteps=500):
+    """The precision configuration: n^3 layered model, nsteps steps per call,
+    wave fields stored in FP32, BF16 and FP16 (FP32 arithmetic in all).  One
+    untimed call, then one timed call each; kernel roofline at 16 / 10 B/pt.
+    (The FP64-oracle errors of the same setup are taken at 256^3.)"""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    import workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    halo, h = 4, 10.0
+    vel = W.layered_velocity_torch(n, n, n, halo, W.SEED_BASE + 3, dev)
+    dt = W.dt_for_cfl(0.4, h, float(vel.max()))
+    si = torch.tensor([W.linear_index(n // 2, n // 2, 20, n, n)], dtype=torch.int64, device=dev)
+    sa = torch.from_numpy(W.ricker(nsteps, dt, 15.0).astype(np.float32).reshape(nsteps, 1)).to(dev)
+    out = {"workload": f"{n}^3 interior + halo 4, {nsteps} leapfrog steps per call, layered 1500-4500 m/s + 16 "
+                       f"Gaussians, CFL 0.4, 15 Hz Ricker at depth 20"}
+    a, b = torch.zeros_like(vel), torch.zeros_like(vel)
+    work = None
+    for fmt in ("f32", "bf16", "f16"):
+        if fmt != "f32" and work is None:
+            work = gbs.lp_workspace(a, halo)
+
+        def run():
+            a.zero_()
+            b.zero_()
+            if fmt == "f32":
+                gbs.wave_propagate(a, b, vel, dt, h, halo, nsteps, src_idx=si, src_amp=sa)
+            else:
+                gbs.wave_propagate_lp(a, b, vel, dt, h, halo, nsteps, storage=fmt, work=work, src_idx=si,
+                                      src_amp=sa)
+        run()
+        ms, kms, kl = time_calls(run, 1, stream)
+        gbs.device_status()
+        bpp = 16 if fmt == "f32" else 10
+        ach = bpp * n ** 3 / (kms * 1e-3) / 1e9
+        out[fmt] = {"value": n ** 3 * nsteps / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_call": ms,
+                    "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                                 "bytes_per_point": bpp, "kernel_ms_per_launch": kms, "kernel_launches": kl}}
+    for fmt in ("bf16", "f16"):
+        out[fmt]["speedup_vs_f32"] = out["f32"]["ms_per_call"] / out[fmt]["ms_per_call"]
+    del a, b, work, vel
     torch.cuda.empty_cache()
     return out
 
@@ -687,6 +732,8 @@ def run_ours(args):
             forms["radius_sweep"] = radius_sweep(args, stream, hbm)
         if "errors" in wanted:
             forms["error_vs_fp64_oracle"] = precision_errors(stream)
+        if "precision" in wanted:
+            forms["precision_1024"] = precision_form(args, stream, hbm)
         if "batched" in wanted:
             forms["batched"] = batched_forms(args, stream, hbm, nshots=args.batch_shots)
         if "adjoint" in wanted:

@@ -162,3 +162,27 @@ def test_config5_full_size_properties():
     e = oracle.err_norms(trace.cpu().numpy(), ref)
     assert e["norm_max_rel"] <= 2e-6 * N, e
     assert bool(torch.isfinite(grads[0]).all()) and float(grads[0].abs().max()) > 0
+
+
+def test_gpu_gradient_matches_gpu_finite_differences_32():
+    """Central differences of the GPU misfit itself on a 32^3 grid (the FD
+    check of the gradient configuration): J(v +- eps delta) with a relative
+    perturbation eps = 1e-3, against <g, delta>.  FP32 fields limit the FD
+    quotient to ~1e-4 relative; the bound is 2e-3."""
+    need_gpu()
+    p = _problem(32, 32, 32, 80, 48, seed=32)
+    rng = np.random.default_rng(5)
+    delta = np.zeros_like(p["vel"])
+    W.interior(delta, HALO)[...] = rng.uniform(-1, 1, (32, 32, 32)) * W.interior(p["vel"], HALO)
+    _, grad, _, _ = _gpu_fwi(p)
+    gbs.device_status()
+    an = float((grad.cpu().double() * torch.from_numpy(delta).double()).sum())
+    eps = 1e-3
+
+    def J(v):
+        m, _, _, _ = gbs.fwi_gradient(to_dev(v.astype(np.float32)), p["dt"], H, HALO, p["nsteps"], to_dev(p["d_obs"]),
+                                      src_idx=to_dev(p["src"]), src_amp=to_dev(p["amp"]), rec_idx=to_dev(p["rec"]))
+        return float(m.cpu()[0])
+    fd = (J(p["vel"] + eps * delta) - J(p["vel"] - eps * delta)) / (2 * eps)
+    gbs.device_status()
+    assert abs(fd - an) <= 2e-3 * abs(an), (fd, an)

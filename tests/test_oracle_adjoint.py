@@ -160,3 +160,14 @@ def test_gradient_vanishes_outside_reach():
     gi = W.interior(g, HALO)
     assert np.all(gi[:, :, 2 + 4 * N:] == 0)         # beyond the forward field's reach in x
     assert np.any(gi[:, :, : 2 + 4 * N] != 0)
+
+
+def test_gradient_finite_differences_32():
+    """The same central-difference pin on a 32^3 grid with 40 steps."""
+    s = _setup(nx=32, ny=32, nz=32, nsteps=40, seed=17, nsrc=1, nrec=24)
+    J, g = _grad(s)
+    delta = np.zeros_like(s["vel"])
+    W.interior(delta, HALO)[...] = s["rng"].uniform(-1, 1, W.interior(delta, HALO).shape) * W.interior(s["vel"], HALO)
+    fd = _fd(s, delta, 1e-6)
+    an = float(np.sum(g * delta))
+    assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
