@@ -23,6 +23,10 @@ What each function follows (arXiv 2309.04671):
   definition; the scale rule; one step of Eq. 2 on stored fields).  The
   paper computes in FP32 (``st.f32``); the 16-bit storage is this library's
   addition, pinned here against numpy/torch conversions.
+* :func:`footprint`, :func:`suite_flops`, :func:`stencil_general` -- the
+  kernels of the numerical-accuracy suite (Sec. 11.1, Table 4): star / box
+  footprints in 2D and 3D of order 1..4 and the j* kernels, as a weighted
+  sum over the footprint divided by a constant (C, ``oracle.c``).
 * :func:`forward_states`, :func:`adjoint_gradient`, :func:`fwi_misfit`,
   :func:`fwi_gradient` -- the discrete adjoint of Algorithm 1 and the
   gradient of a trace functional with respect to the velocity (the paper
@@ -94,6 +98,9 @@ def _load():
                                                   _i64, _i64, _i64, _i64, ctypes.c_int, _dp, _i64, _i64,
                                                   _i64, _ip, _dp, _i64, _i64, _ip, _dp, _i64]
             lib.oracle_wave_propagate.restype = ctypes.c_int
+            lib.oracle_stencil_general.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _i64, _i64, _i64,
+                                                   ctypes.c_void_p, _dp, ctypes.c_double]
+            lib.oracle_stencil_general.restype = None
             _lib = lib
     return _lib
 
@@ -203,6 +210,67 @@ def stencil_points(inp_f32: np.ndarray, radius: int, cx, cy, cz, halo: int,
     _load().oracle_stencil_points_f32(_f(x), nx, ny, nz, halo, radius, _d(c[0]), _d(c[1]), _d(c[2]),
                                       idx.size, _i(idx), _d(out))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Sec. 11.1, Table 4: the numerical-accuracy suite of stencil kernels
+# ---------------------------------------------------------------------------
+# name -> (shape, dimensions, order, divides by a constant)
+SUITE = {
+    **{f"star{d}d{r}r": ("star", d, r, False) for d in (2, 3) for r in (1, 2, 3, 4)},
+    **{f"box{d}d{r}r": ("box", d, r, False) for d in (2, 3) for r in (1, 2, 3, 4)},
+    "j2d5pt": ("star", 2, 1, True),
+    "j2d9pt": ("star", 2, 2, True),
+    "j2d9pt-gol": ("box", 2, 1, True),
+    "j3d27pt": ("box", 3, 1, True),
+}
+
+
+def footprint(shape: str, dims: int, radius: int) -> np.ndarray:
+    """Offsets (dx, dy, dz) of a star or box footprint, (npts, 3) int32, in
+    lexicographic order of (dz, dy, dx) with dx fastest.  A star holds the
+    points on the coordinate axes within ``radius``; a box every point of
+    the cube; 2D footprints have dz = 0."""
+    rz = radius if dims == 3 else 0
+    pts = []
+    for dz in range(-rz, rz + 1):
+        for dy in range(-radius, radius + 1):
+            for dx in range(-radius, radius + 1):
+                nonzero = (dx != 0) + (dy != 0) + (dz != 0)
+                if shape == "box" or nonzero <= 1:
+                    pts.append((dx, dy, dz))
+    return np.array(pts, dtype=np.int32)
+
+
+def suite_flops(name: str) -> int:
+    """Floating-point operations per output point: one multiply per
+    footprint point, one add per point but the first, one division for the
+    j* kernels."""
+    shape, dims, r, div = SUITE[name]
+    n = len(footprint(shape, dims, r))
+    return 2 * n - 1 + (1 if div else 0)
+
+
+def stencil_general(inp: np.ndarray, offsets, weights, halo, divisor: float = 1.0,
+                    out: np.ndarray | None = None) -> np.ndarray:
+    """out = (sum_q w_q inp(p + off_q)) / divisor on the interior (FP64).
+    ``halo`` is (hx, hy, hz); the halo of ``out`` is left as given (zeros when
+    ``out`` is None)."""
+    x = _f64(inp)
+    hx, hy, hz = (int(v) for v in halo)
+    nz, ny, nx = x.shape[0] - 2 * hz, x.shape[1] - 2 * hy, x.shape[2] - 2 * hx
+    if min(nx, ny, nz) < 0:
+        raise ValueError("halo larger than the field")
+    off = np.ascontiguousarray(offsets, dtype=np.int32).reshape(-1, 3)
+    w = _f64(np.asarray(weights).reshape(-1))
+    if w.size != off.shape[0]:
+        raise ValueError("one weight per offset")
+    if np.any(np.abs(off[:, 0]) > hx) or np.any(np.abs(off[:, 1]) > hy) or np.any(np.abs(off[:, 2]) > hz):
+        raise ValueError("footprint reaches beyond the halo")
+    o = np.zeros_like(x) if out is None else out
+    _load().oracle_stencil_general(_d(x), _d(o), nx, ny, nz, hx, hy, hz, off.shape[0],
+                                   off.ctypes.data_as(ctypes.c_void_p), _d(w), float(divisor))
+    return o
 
 
 # ---------------------------------------------------------------------------

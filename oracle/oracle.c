@@ -202,3 +202,30 @@ int oracle_wave_propagate(double *u_prev, double *u, const double *vel, double d
     free(a); free(b); free(nxt); free(zero_f); free(rec_tmp);
     return 0;
 }
+
+/*
+ * The kernels of the paper's numerical-accuracy suite (Sec. 11.1, Table 4):
+ * star / box stencils in 2D and 3D of order 1..4 and the j2d5pt, j2d9pt,
+ * j2d9pt-gol and j3d27pt kernels, as one definition:
+ *     out(i,j,k) = ( sum_q w_q in(i+dx_q, j+dy_q, k+dz_q) ) / divisor
+ * over the footprint offsets q (divisor 1 for the plain star / box
+ * kernels).  Halo widths are per axis (hz = 0 for 2D kernels applied plane
+ * by plane); the halo is read as given and out's halo is left untouched.
+ * The sum runs in the order the offsets are listed, in FP64.
+ */
+void oracle_stencil_general(const double *in, double *out, i64 nx, i64 ny, i64 nz, i64 hx, i64 hy, i64 hz,
+                            i64 npts, const int *off, const double *w, double divisor)
+{
+    const i64 Nx = nx + 2 * hx, Ny = ny + 2 * hy;
+#pragma omp parallel for schedule(static)
+    for (i64 k = 0; k < nz; ++k)
+        for (i64 j = 0; j < ny; ++j)
+            for (i64 i = 0; i < nx; ++i) {
+                double s = 0.0;
+                for (i64 q = 0; q < npts; ++q) {
+                    const i64 x = i + hx + off[3 * q], y = j + hy + off[3 * q + 1], z = k + hz + off[3 * q + 2];
+                    s += w[q] * in[x + Nx * (y + Ny * z)];
+                }
+                out[(i + hx) + Nx * ((j + hy) + Ny * (k + hz))] = s / divisor;
+            }
+}
