@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
                     help="wave-field storage of the main timed path (arithmetic is FP32 in all)")
-    ap.add_argument("--forms", default="storage,radius,errors,precision,batched,adjoint",
+    ap.add_argument("--forms", default="storage,radius,errors,precision,batched,adjoint,suite",
                     help="comma list of extra forms to measure after the main line, or 'none'")
     ap.add_argument("--no-forms", action="store_true", help="same as --forms none")
     ap.add_argument("--adj-n", type=int, default=256, help="adjoint form: interior side")
@@ -315,6 +315,62 @@ def precision_form(args, stream, hbm, n=1024, nsteps=500):
     for fmt in ("bf16", "f16"):
         out[fmt]["speedup_vs_f32"] = out["f32"]["ms_per_call"] / out[fmt]["ms_per_call"]
     del a, b, work, vel
+    torch.cuda.empty_cache()
+    return out
+
+
+FP32_FMA_LANES_PER_SM = 128      # FP32 FMA lanes per SM (4 partitions x 32)
+
+
+def fp32_peak_tflops(sm_mhz=2070.0):
+    """FP32 peak from unit counts and clock: SMs x 128 lanes x 2 FLOP x clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * FP32_FMA_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def suite_form(args, stream, hbm):
+    """The 20 kernels of the paper's numerical-accuracy suite (Table 4) on
+    uniform[0,1) fields with seeded weights: 3D kernels on 512^3 (256^3 for
+    box3d3r / box3d4r), 2D kernels on one 8192^2 plane.  Star and j* kernels
+    are HBM-bound (8 B/pt); the box kernels of order >= 2 are bound by FP32
+    FMA throughput (2 FLOP per footprint point)."""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    dev = torch.device("cuda", torch.cuda.current_device())
+    H = 4
+    peak_f = fp32_peak_tflops()
+    out = {"fp32_peak_tflops": peak_f, "fp32_peak_basis": "SMs x 128 FMA lanes x 2 FLOP x 2070 MHz"}
+    g = torch.Generator(device=dev).manual_seed(11)
+    for name, (shape, dims, r, div) in gbs.SUITE.items():
+        n = 512 if dims == 3 else 8192
+        if shape == "box" and dims == 3 and r >= 3:
+            n = 256
+        nz, hz = (n, H) if dims == 3 else (1, 0)
+        x = torch.rand((nz + 2 * hz, n + 2 * H, n + 2 * H), device=dev, generator=g)
+        y = torch.zeros_like(x)
+        npts = gbs.suite_points(dims, shape, r)
+        w = np.random.default_rng(npts).uniform(-1, 1, npts)
+
+        def run():
+            gbs.stencil_suite(x, y, dims=dims, shape=shape, radius=r, weights=w, halo=H,
+                              divisor=7.0 if div else 1.0)
+        for _ in range(3):
+            run()
+        ms, _, _ = time_calls(run, 10, stream)
+        gbs.device_status()
+        pts = n * n * nz
+        flops = 2 * npts - 1 + (1 if div else 0)
+        gbs_s = 8 * pts / (ms * 1e-3) / 1e9
+        tf = flops * pts / (ms * 1e-3) / 1e12
+        compute = shape == "box" and r >= 2
+        out[name] = {"grid": [n, n, nz], "value": pts / (ms * 1e-3) / 1e9, "unit": UNIT, "us_per_call": ms * 1e3,
+                     "flops_per_point": flops,
+                     "roofline": ({"bound": "alu", "achieved": tf, "peak": peak_f, "unit": "TFLOP/s",
+                                   "frac": tf / peak_f} if compute else
+                                  {"bound": "hbm", "achieved": gbs_s, "peak": hbm, "unit": "GB/s",
+                                   "frac": gbs_s / hbm})}
+        del x, y
     torch.cuda.empty_cache()
     return out
 
@@ -736,6 +792,8 @@ def run_ours(args):
             forms["precision_1024"] = precision_form(args, stream, hbm)
         if "batched" in wanted:
             forms["batched"] = batched_forms(args, stream, hbm, nshots=args.batch_shots)
+        if "suite" in wanted:
+            forms["suite"] = suite_form(args, stream, hbm)
         if "adjoint" in wanted:
             forms["adjoint"] = adjoint_form(args, stream, hbm, n=args.adj_n, nsteps=args.adj_steps,
                                             nshots=args.adj_shots)

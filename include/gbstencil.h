@@ -175,6 +175,30 @@ gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float *vel, floa
                                  const gbs_opts *opts, void *stream);
 
 /*
+ * The kernels of the paper's numerical-accuracy suite (Sec. 11.1, Table 4):
+ *   out(i,j,k) = ( sum_q w_q in(i+dx_q, j+dy_q, k+dz_q) ) / divisor
+ * over the interior, for a star (shape 0: the points on the axes within
+ * `radius`) or box (shape 1: the whole cube) footprint of radius 1..4, in 3D
+ * (dims 3) or in 2D (dims 2: every z plane is an independent 2D problem and
+ * the field has no z halo).  star2d1r..box3d4r are divisor 1; j2d5pt,
+ * j2d9pt, j2d9pt-gol and j3d27pt are star2d1r, star2d2r, box2d1r and box3d1r
+ * with their divisor.  No symmetry is assumed: every offset has its own
+ * weight.
+ *   in, out     DEVICE float, padded layout of gbs_stencil_apply with halo
+ *               `halo` in x and y and, for dims 3, in z; must not overlap.
+ *               The halo of `in` is read as given, that of `out` untouched.
+ *   weights     HOST float[gbs_suite_points(dims, shape, radius)], in the
+ *               lexicographic order of the offsets (dz, dy, dx), dx fastest.
+ *   divisor     the constant the sum is divided by (1 for none).
+ * Requirements: halo >= radius, halo % 4 == 0, nx % 4 == 0, 16-byte aligned
+ * fields (GBS_EALIGN otherwise).  The sum runs in FP32 in the order of the
+ * offsets.  Errors: GBS_EINVAL, GBS_EALIGN, GBS_ECUDA.
+ */
+int gbs_suite_points(int dims, int shape, int radius);   /* footprint size, -1 if invalid */
+gbs_status gbs_stencil_suite(const float *in, float *out, int64_t nx, int64_t ny, int64_t nz, int halo, int dims,
+                             int shape, int radius, const float *weights, float divisor, void *stream);
+
+/*
  * Batched propagation: many independent shots -- each its own grid sizes,
  * velocity model, dt, h and up to 16 point sources -- advanced together, one
  * kernel launch per time step covering every shot (Algorithm 1 per shot).

@@ -101,6 +101,9 @@ def _load():
             lib.oracle_stencil_general.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _i64, _i64, _i64,
                                                    ctypes.c_void_p, _dp, ctypes.c_double]
             lib.oracle_stencil_general.restype = None
+            lib.oracle_stencil_general_points_f32.argtypes = [_fp, _i64, _i64, _i64, _i64, _i64, _i64, _i64,
+                                                              ctypes.c_void_p, _dp, ctypes.c_double, _i64, _ip, _dp]
+            lib.oracle_stencil_general_points_f32.restype = None
             _lib = lib
     return _lib
 
@@ -271,6 +274,21 @@ def stencil_general(inp: np.ndarray, offsets, weights, halo, divisor: float = 1.
     _load().oracle_stencil_general(_d(x), _d(o), nx, ny, nz, hx, hy, hz, off.shape[0],
                                    off.ctypes.data_as(ctypes.c_void_p), _d(w), float(divisor))
     return o
+
+
+def stencil_general_points(inp_f32: np.ndarray, offsets, weights, halo, idx, divisor: float = 1.0) -> np.ndarray:
+    """The suite definition at interior linear indices ``idx`` of an FP32 field, in FP64."""
+    x = np.ascontiguousarray(inp_f32, dtype=np.float32)
+    hx, hy, hz = (int(v) for v in halo)
+    nz, ny, nx = x.shape[0] - 2 * hz, x.shape[1] - 2 * hy, x.shape[2] - 2 * hx
+    off = np.ascontiguousarray(offsets, dtype=np.int32).reshape(-1, 3)
+    w = _f64(np.asarray(weights).reshape(-1))
+    idx = np.ascontiguousarray(idx, np.int64)
+    res = np.empty(idx.size, np.float64)
+    _load().oracle_stencil_general_points_f32(_f(x), nx, ny, nz, hx, hy, hz, off.shape[0],
+                                              off.ctypes.data_as(ctypes.c_void_p), _d(w), float(divisor),
+                                              idx.size, _i(idx), _d(res))
+    return res
 
 
 # ---------------------------------------------------------------------------

@@ -229,3 +229,23 @@ void oracle_stencil_general(const double *in, double *out, i64 nx, i64 ny, i64 n
                 out[(i + hx) + Nx * ((j + hy) + Ny * (k + hz))] = s / divisor;
             }
 }
+
+/* The suite definition above at interior linear indices idx[0..n) of an
+ * FP32 field (x fastest), in FP64. */
+void oracle_stencil_general_points_f32(const float *in, i64 nx, i64 ny, i64 nz, i64 hx, i64 hy, i64 hz, i64 npts,
+                                       const int *off, const double *w, double divisor, i64 n, const i64 *idx,
+                                       double *res)
+{
+    const i64 Nx = nx + 2 * hx, Ny = ny + 2 * hy;
+    (void)nz;
+#pragma omp parallel for schedule(static)
+    for (i64 t = 0; t < n; ++t) {
+        const i64 i = idx[t] % nx, j = (idx[t] / nx) % ny, k = idx[t] / (nx * ny);
+        double s = 0.0;
+        for (i64 q = 0; q < npts; ++q) {
+            const i64 x = i + hx + off[3 * q], y = j + hy + off[3 * q + 1], z = k + hz + off[3 * q + 2];
+            s += w[q] * (double)in[x + Nx * (y + Ny * z)];
+        }
+        res[t] = s / divisor;
+    }
+}

@@ -31,6 +31,7 @@ EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_w
            "gbs_wave_propagate_lp", "gbs_norms_workspace_bytes", "gbs_field_norms", "gbs_field_norms_noalloc",
            "gbs_batch_plan_create", "gbs_batch_run", "gbs_batch_plan_info", "gbs_batch_plan_destroy",
            "gbs_adjoint_workspace_bytes", "gbs_adjoint_forward", "gbs_adjoint_backward", "gbs_fwi_gradient",
+           "gbs_suite_points", "gbs_stencil_suite",
            "gbs_fd2_coeffs", "gbs_profile_enable", "gbs_profile_take",
            "gbs_device_status", "gbs_last_error", "gbs_version")
 
@@ -125,6 +126,10 @@ def load() -> ctypes.CDLL:
         lib.gbs_fwi_gradient.argtypes = [vp, c_float, c_float, i64, i64, i64, c_int, i64, ctypes.POINTER(_Src), vp,
                                          i64, vp, vp, vp, i64, vp, ctypes.c_size_t, vp, vp, ctypes.POINTER(_Opts), vp]
         lib.gbs_fwi_gradient.restype = c_int
+        lib.gbs_suite_points.argtypes = [c_int, c_int, c_int]
+        lib.gbs_suite_points.restype = c_int
+        lib.gbs_stencil_suite.argtypes = [vp, vp, i64, i64, i64, c_int, c_int, c_int, c_int, fp, c_float, vp]
+        lib.gbs_stencil_suite.restype = c_int
         lib.gbs_fd2_coeffs.argtypes = [c_int, fp]
         lib.gbs_profile_enable.argtypes = [c_int]
         lib.gbs_profile_take.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -240,6 +245,50 @@ def wave_step(u_prev: torch.Tensor, u: torch.Tensor, u_next: torch.Tensor, vel: 
     _check(load().gbs_wave_step(p[0], p[1], p[2], p[3], float(dt), float(h), nx, ny, nz, halo,
                                 _ptr(src), _ptr(rec), int(step), _stream(stream)))
     return u_next
+
+
+SUITE_SHAPES = {"star": 0, "box": 1}
+# Table 4 of the paper: name -> (shape, dims, order, divides by a constant)
+SUITE = {
+    **{f"star{d}d{r}r": ("star", d, r, False) for d in (2, 3) for r in (1, 2, 3, 4)},
+    **{f"box{d}d{r}r": ("box", d, r, False) for d in (2, 3) for r in (1, 2, 3, 4)},
+    "j2d5pt": ("star", 2, 1, True),
+    "j2d9pt": ("star", 2, 2, True),
+    "j2d9pt-gol": ("box", 2, 1, True),
+    "j3d27pt": ("box", 3, 1, True),
+}
+
+
+def suite_points(dims: int, shape: str, radius: int) -> int:
+    """Number of footprint points (= weights) of a suite kernel."""
+    n = int(load().gbs_suite_points(int(dims), SUITE_SHAPES[shape], int(radius)))
+    if n < 0:
+        raise ValueError("invalid dims / shape / radius")
+    return n
+
+
+def stencil_suite(inp: torch.Tensor, out: Optional[torch.Tensor] = None, *, dims: int, shape: str, radius: int,
+                  weights: Sequence[float], halo: int, divisor: float = 1.0, stream=None) -> torch.Tensor:
+    """A kernel of the paper's numerical-accuracy suite (Table 4):
+    out = (sum_q w_q inp(p + off_q)) / divisor over a star or box footprint.
+    3D fields are (nz+2h, ny+2h, nx+2h); 2D fields are (nz, ny+2h, nx+2h),
+    each z plane an independent 2D problem.  ``weights`` follow the offsets
+    in lexicographic (dz, dy, dx) order."""
+    if out is None:
+        out = torch.zeros_like(inp)
+    pin, pout = _field(inp, "inp"), _field(out, "out")
+    _same_shape(inp, out)
+    hz = halo if dims == 3 else 0
+    nz, ny, nx = inp.shape[0] - 2 * hz, inp.shape[1] - 2 * halo, inp.shape[2] - 2 * halo
+    if min(nx, ny, nz) < 0:
+        raise ValueError("halo larger than the field")
+    w = [float(v) for v in weights]
+    if len(w) != suite_points(dims, shape, radius):
+        raise ValueError("one weight per footprint point")
+    arr = (ctypes.c_float * len(w))(*w)
+    _check(load().gbs_stencil_suite(pin, pout, nx, ny, nz, int(halo), int(dims), SUITE_SHAPES[shape], int(radius),
+                                    arr, float(divisor), _stream(stream)))
+    return out
 
 
 def _opts(kernel, tile_y, zchunk, use_graph):

@@ -395,6 +395,23 @@ gbs_status make_tensor_map_f64(CUtensorMap *m, const double *base, const Grid &g
 {
     return make_map(m, base, g, bw, bh, GBS_F32, true);
 }
+gbs_status make_tensor_map_f32_dims(CUtensorMap *m, const float *base, int64_t px, int64_t py, int64_t pz, int bw,
+                                    int bh)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc)
+        return fail(GBS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[3] = {(cuuint64_t)px, (cuuint64_t)py, (cuuint64_t)pz};
+    const cuuint64_t strides[2] = {(cuuint64_t)px * 4, (cuuint64_t)(px * py) * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(GBS_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GBS_OK;
+}
 Grid internal_grid(int64_t nx, int64_t ny, int64_t nz) { return lp_layout(nx, ny, nz).g; }
 Grid dense_layout(int64_t nx, int64_t ny, int64_t nz, int halo) { return dense_grid(nx, ny, nz, halo); }
 int64_t grid_elems(const Grid &g) { return field_elems(g); }
@@ -717,7 +734,8 @@ extern "C" gbs_status gbs_device_status(void *stream)
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const unsigned a = tma_status_take(st);
     const unsigned b = misc_status_take(st);
-    const unsigned v = a ? a : b;
+    const unsigned c = suite_status_take(st);
+    const unsigned v = a ? a : (b ? b : c);
     if (v != 0)
         return fail((gbs_status)v, "device status %u", v);
     return GBS_OK;

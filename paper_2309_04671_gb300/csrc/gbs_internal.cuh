@@ -157,6 +157,28 @@ cudaEvent_t profile_begin(cudaStream_t st);
 void profile_end(cudaEvent_t e0, cudaStream_t st);
 gbs_status make_tensor_map(CUtensorMap *m, const void *base, const Grid &g, int bw, int bh, gbs_dtype dt);
 gbs_status make_tensor_map_f64(CUtensorMap *m, const double *base, const Grid &g, int bw, int bh);
+// FP32 tensor map over an array of px x py x pz elements (x fastest), box bw x bh x 1
+gbs_status make_tensor_map_f32_dims(CUtensorMap *m, const float *base, int64_t px, int64_t py, int64_t pz, int bw,
+                                    int bh);
+
+// Kernels of the numerical-accuracy suite (k_suite.cu): out = (sum_q w_q in(p + off_q)) / divisor over
+// a star or box footprint of radius R in 2D (plane by plane) or 3D.  Weights are dense over the
+// (2RZ+1) x (2R+1) x (2R+1) cube of offsets, dz slowest, dx fastest (zero off the footprint), RZ = R in
+// 3D and 0 in 2D.
+constexpr int kSuiteMaxW = 729;
+struct SuiteParams {
+    int64_t nx, ny, nz;      // interior
+    int64_t px, py;          // row pitch, rows per plane (elements)
+    int hxy, hz;             // halo in x/y and in z
+    int zchunk, tiles_x;
+    int has_div;
+    float divisor;
+    float w[kSuiteMaxW];
+};
+int suite_default_zchunk(int radius, bool d3, const SuiteParams &p);
+cudaError_t launch_suite(int radius, bool box, bool d3, const CUtensorMap &map, const SuiteParams &p, float *out,
+                         cudaStream_t st);
+unsigned suite_status_take(cudaStream_t st);
 // interior (nx, ny, nz), halo 4, nx rounded up to a multiple of 4 (dead
 // columns), rows padded to a multiple of 8 elements
 Grid internal_grid(int64_t nx, int64_t ny, int64_t nz);

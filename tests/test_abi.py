@@ -181,3 +181,22 @@ def test_adjoint_workspace_and_validation(lib):
                                     None) == gbs.GBS_EINVAL
     assert lib.gbs_fwi_gradient(*args, 4, n, None, None, 0, None, None, None, 0, work, want, None, None, None,
                                 None) == gbs.GBS_EINVAL
+
+
+def test_suite_points_and_validation(lib):
+    assert lib.gbs_suite_points(3, 1, 4) == 729
+    assert lib.gbs_suite_points(2, 0, 4) == 17
+    assert lib.gbs_suite_points(3, 0, 1) == 7
+    assert lib.gbs_suite_points(4, 0, 1) == -1 and lib.gbs_suite_points(3, 2, 1) == -1
+    assert lib.gbs_suite_points(3, 0, 5) == -1
+    w = (ctypes.c_float * 729)(*([1.0] * 729))
+    a, b = ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 28)
+    call = lib.gbs_stencil_suite
+    assert call(a, b, 8, 8, 8, 4, 4, 0, 1, w, ctypes.c_float(1.0), None) == gbs.GBS_EINVAL      # dims
+    assert call(a, b, 8, 8, 8, 4, 3, 2, 1, w, ctypes.c_float(1.0), None) == gbs.GBS_EINVAL      # shape
+    assert call(a, b, 8, 8, 8, 2, 3, 1, 4, w, ctypes.c_float(1.0), None) == gbs.GBS_EINVAL      # halo < radius
+    assert call(a, b, 8, 8, 8, 4, 3, 1, 4, None, ctypes.c_float(1.0), None) == gbs.GBS_EINVAL   # weights
+    assert call(a, b, 8, 8, 8, 4, 3, 1, 4, w, ctypes.c_float(0.0), None) == gbs.GBS_EINVAL      # divisor
+    assert call(a, a, 8, 8, 8, 4, 3, 1, 4, w, ctypes.c_float(1.0), None) == gbs.GBS_EINVAL      # overlap
+    assert call(a, b, 6, 8, 8, 4, 3, 1, 4, w, ctypes.c_float(1.0), None) == gbs.GBS_EALIGN      # nx % 4
+    assert call(a, b, 0, 8, 8, 4, 3, 1, 4, w, ctypes.c_float(1.0), None) == gbs.GBS_OK         # empty
