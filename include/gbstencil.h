@@ -191,8 +191,9 @@ gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float *vel, floa
  *               lexicographic order of the offsets (dz, dy, dx), dx fastest.
  *   divisor     the constant the sum is divided by (1 for none).
  * Requirements: halo >= radius, halo % 4 == 0, nx % 4 == 0, 16-byte aligned
- * fields (GBS_EALIGN otherwise).  The sum runs in FP32 in the order of the
- * offsets.  Errors: GBS_EINVAL, GBS_EALIGN, GBS_ECUDA.
+ * fields (GBS_EALIGN otherwise).  The sum runs in FP32 (3D stars: centre,
+ * then the points at distance 1..R; the others in the order of the offsets).
+ * Errors: GBS_EINVAL, GBS_EALIGN, GBS_ECUDA.
  */
 int gbs_suite_points(int dims, int shape, int radius);   /* footprint size, -1 if invalid */
 gbs_status gbs_stencil_suite(const float *in, float *out, int64_t nx, int64_t ny, int64_t nz, int halo, int dims,

@@ -28,9 +28,12 @@ struct Grid {
 };
 
 // Per-axis weights of Eq. 3: c[a][0] is axis a's share of the centre
-// weight, c[a][m] the weight at distance m (m <= 4).
+// weight, c[a][m] the weight at distance m (m <= 4) -- of both points at
+// distance m, except in kStencilAsym mode, where c[a][m] weighs the point
+// at +m and cm[a][m] the point at -m.
 struct Coeffs {
     float c[3][5];
+    float cm[3][5];
 };
 
 // What the epilogue computes from the Laplacian `lap` at a point:
@@ -41,7 +44,9 @@ struct Coeffs {
 //             out[0], an FP32 partial sum in the same layout, staged through
 //             the g map (the imaging condition of the adjoint; the caller
 //             folds the partial into its FP64 gradient every few steps)
-enum Mode { kStencil = 0, kWave = 1, kImage = 2 };
+//   kStencilAsym: out = (sum_a c[a][0]) u + sum_a sum_m c[a][m] u(+m) + cm[a][m] u(-m)
+//             (a star with one weight per point: the suite's star3d kernels)
+enum Mode { kStencil = 0, kWave = 1, kImage = 2, kStencilAsym = 3 };
 
 struct WaveArgs {
     const float *u_prev;   // read at the point only (may alias out)

@@ -70,6 +70,40 @@ extern "C" gbs_status gbs_stencil_suite(const float *in, float *out, int64_t nx,
     if (halo % 4 != 0 || nx % 4 != 0 || (reinterpret_cast<uintptr_t>(in) & 15u) != 0 ||
         (reinterpret_cast<uintptr_t>(out) & 15u) != 0)
         return set_error(GBS_EALIGN, "the suite kernels need halo %% 4 == 0, nx %% 4 == 0 and 16-byte aligned fields");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (dims == 3 && shape == 0 && divisor == 1.f) {
+        // 3D stars take the leapfrog's streaming kernel (z values in a register
+        // queue) with one weight per point
+        const Grid g = dense_layout(nx, ny, nz, halo);
+        Coeffs cf;
+        memset(&cf, 0, sizeof(cf));
+        for_footprint(dims, shape, radius, [&](int64_t q, int dx, int dy, int dz) {
+            const int a = dx != 0 ? 0 : (dy != 0 ? 1 : 2);
+            const int m = dx + dy + dz;
+            if (m == 0)
+                cf.c[0][0] = weights[q];
+            else if (m > 0)
+                cf.c[a][m] = weights[q];
+            else
+                cf.cm[a][-m] = weights[q];
+        });
+        TmaPlan plan;
+        gbs_status s = make_tensor_map(&plan.u, in, g, 64 + 8, 16 + 2 * radius, GBS_F32);
+        if (s != GBS_OK)
+            return s;
+        plan.prev = plan.vel = plan.g = plan.u;
+        StepParams p;
+        memset(&p, 0, sizeof(p));
+        p.g = g;
+        p.out[0] = p.out[1] = out;
+        p.cf = cf;
+        cudaEvent_t e0 = profile_begin(st);
+        cudaError_t e = launch_tma(radius, kStencilAsym, 16, GBS_F32, plan, p, 0, st);
+        profile_end(e0, st);
+        if (e != cudaSuccess)
+            return set_cuda_error(e, "suite star kernel launch");
+        return GBS_OK;
+    }
     SuiteParams p;
     memset(&p, 0, sizeof(p));
     p.nx = nx;
@@ -90,7 +124,9 @@ extern "C" gbs_status gbs_stencil_suite(const float *in, float *out, int64_t nx,
     gbs_status s = make_tensor_map_f32_dims(&map, in, px, py, pz, 64 + 8, 16 + 2 * radius);
     if (s != GBS_OK)
         return s;
-    cudaError_t e = launch_suite(radius, shape == 1, dims == 3, map, p, out, static_cast<cudaStream_t>(stream));
+    cudaEvent_t e0 = profile_begin(st);
+    cudaError_t e = launch_suite(radius, shape == 1, dims == 3, map, p, out, st);
+    profile_end(e0, st);
     if (e != cudaSuccess)
         return set_cuda_error(e, "suite kernel launch");
     return GBS_OK;

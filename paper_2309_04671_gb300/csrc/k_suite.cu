@@ -16,9 +16,12 @@
 // 16-byte loads) once and uses it for both output rows.  The weights sit in
 // shared memory as a dense (2RZ+1) x (2R+1) x (2R+1) array; all threads read
 // the same weight at once (broadcast).  The sum runs in the footprint's
-// lexicographic order (dz, dy, dx) in FP32.  Box stencils of high order are
-// bound by FP32 FMA throughput (box3d4r: 729 FMAs per point), star stencils
-// by HBM bandwidth (8 bytes per point).
+// lexicographic order (dz, dy, dx) in FP32, as scalar FMAs with eight
+// independent accumulators per thread (packed f32x2 FMAs measured slower
+// here).  Box stencils of high order are bound by FP32 FMA throughput
+// (box3d4r: 729 FMAs per point), star stencils by HBM bandwidth (8 bytes per
+// point).  3D stars with divisor 1 go to the leapfrog's streaming kernel
+// instead (gbs_suite.cu).
 #include "gbs_internal.cuh"
 
 namespace gbs {

@@ -95,7 +95,8 @@ struct Cfg {
     static constexpr int SP = LOW ? 3 : (MODE == kImage ? 4 : 5);
     static constexpr size_t SMEM_L = (size_t)SL * L_STRIDE;
     static constexpr size_t SMEM_F = (size_t)SF * F_STRIDE;
-    static constexpr size_t SMEM_PV = MODE != kStencil ? (size_t)SP * PV_STRIDE : 0;
+    static constexpr bool PV = MODE == kWave || MODE == kImage;   // second ring (u_prev|nu, vel|w[, g])
+    static constexpr size_t SMEM_PV = PV ? (size_t)SP * PV_STRIDE : 0;
     static constexpr size_t SMEM = SMEM_L + SMEM_F + SMEM_PV + (SL + SP) * 8;
     static constexpr int MIN_BLOCKS = NT > 128 ? 1 : (LOW ? 3 : 2);
     // halo groups of 4 elements converted by all threads (16-bit): 2 side
@@ -259,7 +260,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
     // returns before issuing any copy.
     {
         const int64_t xu = (H + tx0 - 4) * C::ES, xp = (H + tx0 - C::PVU_X0) * C::ES, xv = (H + tx0) * 4;
-        if ((xu & 15) != 0 || (MODE != kStencil && ((xp & 15) != 0 || (xv & 15) != 0))) {
+        if ((xu & 15) != 0 || (C::PV && ((xp & 15) != 0 || (xv & 15) != 0))) {
             if (tid == 0)
                 atomicCAS(&g_status_tma, 0u, (unsigned)GBS_EALIGN);
             return;
@@ -268,7 +269,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
 
     if (tid == 0) {
         prefetch_tmap(pm_u);
-        if (MODE != kStencil) {
+        if (C::PV) {
             prefetch_tmap(pm_prev);
             prefetch_tmap(pm_vel);
         }
@@ -348,7 +349,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
     if (tid == 0) {
         while (n_u < min(C::SL, nplanes))
             issue_u();
-        if (MODE != kStencil)
+        if (C::PV)
             while (n_pv < min(C::SP, nzc))
                 issue_pv();
     }
@@ -363,8 +364,15 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
 #pragma unroll
         for (int m = 1; m <= R; ++m) {
             CX[m] = pk(p.cf.c[0][m], p.cf.c[0][m]);
-            CY[m] = MODE != kStencil ? CX[m] : pk(p.cf.c[1][m], p.cf.c[1][m]);
-            CZ[m] = MODE != kStencil ? CX[m] : pk(p.cf.c[2][m], p.cf.c[2][m]);
+            CY[m] = C::PV ? CX[m] : pk(p.cf.c[1][m], p.cf.c[1][m]);
+            CZ[m] = C::PV ? CX[m] : pk(p.cf.c[2][m], p.cf.c[2][m]);
+        }
+        f2 CXm[R + 1], CYm[R + 1], CZm[R + 1];   // -m weights (kStencilAsym)
+#pragma unroll
+        for (int m = 1; m <= R; ++m) {
+            CXm[m] = pk(p.cf.cm[0][m], p.cf.cm[0][m]);
+            CYm[m] = pk(p.cf.cm[1][m], p.cf.cm[1][m]);
+            CZm[m] = pk(p.cf.cm[2][m], p.cf.cm[2][m]);
         }
         const f2 S2 = pk(p.s, p.s);
         const f2 KU = pk(k_u, k_u);
@@ -459,7 +467,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                     const float *pvv = nullptr;
                     const float *pvg = nullptr;
                     const int sp = cj % C::SP;
-                    if (MODE != kStencil) {
+                    if (C::PV) {
                         if (mbar_wait_bounded(&full_pv[sp], (uint32_t)((cj / C::SP) & 1), &g_status_tma))
                             consumed_pv = cj + 1;
                         else
@@ -484,6 +492,22 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                             const float4 ym = (r - m >= 0) ? P[rho + R][r - m] : ld4(sc + (ly + r - m) * C::BW + lx);
                             const float4 zp = P[rho + R + m][r];
                             const float4 zm = P[rho + R - m][r];
+                            if constexpr (MODE == kStencilAsym) {
+                                // one weight per point: +m and -m apart on every axis
+                                const float w[12] = {lf.x, lf.y, lf.z, lf.w, cen.x, cen.y, cen.z, cen.w,
+                                                     rt.x, rt.y, rt.z, rt.w};
+                                f2 &al = (m & 1) ? acc_l : acc2_l;
+                                f2 &ah = (m & 1) ? acc_h : acc2_h;
+                                al = fma2(CX[m], pk(w[4 + m], w[5 + m]), al);
+                                ah = fma2(CX[m], pk(w[6 + m], w[7 + m]), ah);
+                                al = fma2(CXm[m], pk(w[4 - m], w[5 - m]), al);
+                                ah = fma2(CXm[m], pk(w[6 - m], w[7 - m]), ah);
+                                al = fma2(CYm[m], lo(ym), fma2(CY[m], lo(yp), al));
+                                ah = fma2(CYm[m], hi(ym), fma2(CY[m], hi(yp), ah));
+                                al = fma2(CZm[m], lo(zm), fma2(CZ[m], lo(zp), al));
+                                ah = fma2(CZm[m], hi(zm), fma2(CZ[m], hi(zp), ah));
+                                continue;
+                            }
                             f2 xs_l, xs_h;
                             if (m & 1) {
                                 // odd distance: the neighbour pairs straddle register pairs, add per point
@@ -499,7 +523,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                             const f2 zs_l = add2(lo(zp), lo(zm)), zs_h = add2(hi(zp), hi(zm));
                             f2 &al = (m & 1) ? acc_l : acc2_l;
                             f2 &ah = (m & 1) ? acc_h : acc2_h;
-                            if (MODE != kStencil) {
+                            if (C::PV) {
                                 // one weight per distance on every axis (the wave operator)
                                 al = fma2(CX[m], add2(add2(xs_l, ys_l), zs_l), al);
                                 ah = fma2(CX[m], add2(add2(xs_h, ys_h), zs_h), ah);
@@ -592,7 +616,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                         const int rel_u = kLow ? j + 1 : max(0, j - R + 1);
                         while (n_u < nplanes && n_u < rel_u + C::SL)
                             issue_u();
-                        if (MODE != kStencil) {
+                        if (C::PV) {
                             const int rel_pv = max(0, j - 2 * R + 1);
                             while (n_pv < nzc && n_pv < rel_pv + C::SP)
                                 issue_pv();
@@ -781,6 +805,9 @@ cudaError_t launch_tma(int radius, Mode mode, int tile_y, gbs_dtype storage, con
         return cudaErrorInvalidValue;
     if (mode == kImage)
         return radius == 4 ? launch_image_t(tile_y, plan, p, st) : cudaErrorInvalidValue;
+    if (mode == kStencilAsym)
+        return tile_y == 32 ? launch_stencil_r<kStencilAsym, 32>(radius, plan, p, st)
+                            : launch_stencil_r<kStencilAsym, 16>(radius, plan, p, st);
     return tile_y == 32 ? launch_stencil_r<kStencil, 32>(radius, plan, p, st)
                         : launch_stencil_r<kStencil, 16>(radius, plan, p, st);
 }
@@ -839,7 +866,7 @@ int tma_default_zchunk(int radius, Mode mode, int tile_y, gbs_dtype storage, con
     const int per_sm = (tile_y == 32) ? 1 : (storage == GBS_F32 ? 2 : 3);
     const int64_t slots = (int64_t)sms * per_sm;
     const int64_t tiles = ((g.nx + kTX - 1) / kTX) * ((g.ny + tile_y - 1) / tile_y);
-    const double halo_cost = (mode != kStencil ? 0.25 : 0.5) * 2 * radius;
+    const double halo_cost = ((mode == kWave || mode == kImage) ? 0.25 : 0.5) * 2 * radius;
     int best = (int)g.nz;
     double best_cost = 1e300;
     for (int64_t c = 1; c <= g.nz && c <= 65535; ++c) {
