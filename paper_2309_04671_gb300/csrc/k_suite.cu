@@ -18,7 +18,8 @@
 // the same weight at once (broadcast).  The sum runs in the footprint's
 // lexicographic order (dz, dy, dx) in FP32, as scalar FMAs with eight
 // independent accumulators per thread (packed f32x2 FMAs measured slower
-// here).  Box stencils of high order are bound by FP32 FMA throughput
+// here); box kernels take their weights as constant-bank operands of the
+// FMAs (see below).  Box stencils of high order are bound by FP32 FMA throughput
 // (box3d4r: 729 FMAs per point), star stencils by HBM bandwidth (8 bytes per
 // point).  3D stars with divisor 1 go to the leapfrog's streaming kernel
 // instead (gbs_suite.cu).
@@ -125,7 +126,12 @@ __global__ void __launch_bounds__(kSNT, 2)
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
                     acc[r][e] = 0.f;
-#pragma unroll 1
+            // box weights straight from the constant-bank parameter (compile-time
+            // indices, no load instruction) with the window fully unrolled,
+            // except box3d3r, where the unrolled code measured slower
+            constexpr bool kConstW = BOX && !(D3 && R == 3);
+            constexpr int kDzUnroll = kConstW ? 2 * RZ + 1 : 1;
+#pragma unroll(kDzUnroll)
             for (int dz = 0; dz <= 2 * RZ; ++dz) {
                 const float *pl = reinterpret_cast<const float *>(smem + ((c + dz) % C::SL) * C::L_STRIDE);
                 const float *wz = ws + dz * W1 * W1;
@@ -153,7 +159,8 @@ __global__ void __launch_bounds__(kSNT, 2)
                             if (BOX || dy == 0) {
 #pragma unroll
                                 for (int dx = -R; dx <= R; ++dx) {
-                                    const float wv = wz[(dy + R) * W1 + dx + R];
+                                    const float wv = kConstW ? p.w[(dz * W1 + dy + R) * W1 + dx + R]
+                                                             : wz[(dy + R) * W1 + dx + R];
 #pragma unroll
                                     for (int e = 0; e < 4; ++e)
                                         acc[r][e] = fmaf(wv, win[4 + e + dx], acc[r][e]);
