@@ -17,6 +17,11 @@ What each function follows (arXiv 2309.04671):
 * :func:`wave_step` / :func:`wave_propagate` -- Eq. 2 and Algorithm 1 with a
   zero (Dirichlet) halo; the source enters as dt^2 V^2 f^n after the stencil
   update (C, ``oracle.c``).
+* :func:`absorbing_eta`, :func:`wave_step_damped`, :func:`wave_propagate_damped`
+  -- the step inside an absorbing (damping) layer: the damped wave
+  equation u_tt + 2 eta u_t = V^2 lap u with a centred u_t and a quadratic
+  damping profile near the faces (the paper surrounds its domain with an
+  absorbing boundary, Sec. 2.2, but gives no equations for it).
 * :func:`round_to_format`, :func:`lp_scale_exponent`, :func:`lp_encode`,
   :func:`lp_wave_step` -- wave fields stored in BF16/FP16 with a per-field
   power-of-two scale (IEEE round-to-nearest-even from the format's
@@ -101,6 +106,9 @@ def _load():
             lib.oracle_stencil_general.argtypes = [_dp, _dp, _i64, _i64, _i64, _i64, _i64, _i64, _i64,
                                                    ctypes.c_void_p, _dp, ctypes.c_double]
             lib.oracle_stencil_general.restype = None
+            lib.oracle_wave_step_damped.argtypes = [_dp, _dp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                                    _i64, _i64, _i64, _i64, ctypes.c_int, _dp, _i64, _ip, _dp]
+            lib.oracle_wave_step_damped.restype = None
             lib.oracle_stencil_general_points_f32.argtypes = [_fp, _i64, _i64, _i64, _i64, _i64, _i64, _i64,
                                                               ctypes.c_void_p, _dp, ctypes.c_double, _i64, _ip, _dp]
             lib.oracle_stencil_general_points_f32.restype = None
@@ -308,6 +316,54 @@ def wave_step(u_prev, u, vel, dt: float, h: float, halo: int, *, radius: int = 4
     _load().oracle_wave_step(_d(up), _d(uc), _d(nxt), _d(v), dt, h, nx, ny, nz, halo, radius, _d(c),
                              si.size, _i(si), _d(sf), ri.size, _i(ri), _d(ro))
     return nxt, ro[: ri.size]
+
+
+def absorbing_eta(nx: int, ny: int, nz: int, halo: int, width: int, eta_max: float,
+                  free_surface: bool = False) -> np.ndarray:
+    """Damping profile of the absorbing layer on the padded grid (FP64):
+    eta = eta_max ((W - d) / W)^2 at interior points whose distance d (in
+    cells) to the nearest interior face is below W, else 0; with
+    ``free_surface`` the top face (z = 0) does not absorb.  Zero in the halo."""
+    eta = np.zeros((nz + 2 * halo, ny + 2 * halo, nx + 2 * halo))
+    if width <= 0:
+        return eta
+    i = np.arange(nx)
+    j = np.arange(ny)
+    k = np.arange(nz)
+    dx = np.minimum(i, nx - 1 - i)
+    dy = np.minimum(j, ny - 1 - j)
+    dz = (nz - 1 - k) if free_surface else np.minimum(k, nz - 1 - k)
+    d = np.minimum(np.minimum(dz[:, None, None], dy[None, :, None]), dx[None, None, :])
+    inner = np.where(d < width, eta_max * ((width - d) / width) ** 2, 0.0)
+    eta[halo:halo + nz, halo:halo + ny, halo:halo + nx] = inner
+    return eta
+
+
+def wave_step_damped(u_prev, u, vel, eta, dt: float, h: float, halo: int, *, radius: int = 4, coeffs=None,
+                     src_idx=None, src_f=None) -> np.ndarray:
+    """One leapfrog step of the damped wave equation (absorbing layer); returns u_next."""
+    up, uc, v, e = _f64(u_prev), _f64(u), _f64(vel), _f64(eta)
+    nx, ny, nz = _dims(uc, halo)
+    c = fd2_coeffs(radius) if coeffs is None else _f64(coeffs)
+    nxt = up.copy()
+    si = np.zeros(0, np.int64) if src_idx is None else np.ascontiguousarray(src_idx, np.int64)
+    sf = np.zeros(si.size, np.float64) if src_f is None else _f64(np.asarray(src_f).reshape(-1))
+    _load().oracle_wave_step_damped(_d(up), _d(uc), _d(nxt), _d(v), _d(e), dt, h, nx, ny, nz, halo, radius, _d(c),
+                                    si.size, _i(si), _d(sf))
+    return nxt
+
+
+def wave_propagate_damped(u_prev, u, vel, eta, dt: float, h: float, halo: int, nsteps: int, *, t0: int = 0,
+                          src_idx=None, src_amp=None):
+    """Algorithm 1 with the absorbing layer: returns (u^{t0+nsteps-1}, u^{t0+nsteps})."""
+    a, b = _f64(u_prev).copy(), _f64(u).copy()
+    si = None if src_idx is None else np.ascontiguousarray(src_idx, np.int64).reshape(-1)
+    sa = None if src_amp is None else _f64(np.asarray(src_amp).reshape(-1, si.size))
+    for n in range(t0, t0 + nsteps):
+        f = None if (si is None or n >= sa.shape[0]) else sa[n]
+        nxt = wave_step_damped(a, b, vel, eta, dt, h, halo, src_idx=si if f is not None else None, src_f=f)
+        a, b = b, nxt
+    return a, b
 
 
 def wave_points(u_prev_f32, u_f32, vel_f32, dt: float, h: float, halo: int, idx, *, radius: int = 4,

@@ -249,3 +249,39 @@ void oracle_stencil_general_points_f32(const float *in, i64 nx, i64 ny, i64 nz, 
         res[t] = s / divisor;
     }
 }
+
+/*
+ * The leapfrog step with an absorbing (damping) layer.  The paper runs its
+ * simulations inside an absorbing boundary (a PML, Sec. 2.2) without giving
+ * its equations; this is the damped wave equation
+ *     u_tt + 2 eta(x) u_t = V^2 lap u,
+ * with u_t centred as (u^{n+1} - u^{n-1}) / (2 dt):
+ *     u^{n+1} = [2u^n - (1 - eta dt) u^{n-1} + dt^2 V^2 lap u^n] / (1 + eta dt),
+ * then the source added as in oracle_wave_step.  eta >= 0 per padded point
+ * (eta = 0 gives oracle_wave_step).  u_next may alias u_prev.
+ */
+void oracle_wave_step_damped(const double *u_prev, const double *u, double *u_next, const double *vel,
+                             const double *eta, double dt, double h, i64 nx, i64 ny, i64 nz, i64 H, int R,
+                             const double *c, i64 nsrc, const i64 *src_idx, const double *src_f)
+{
+    const i64 Nx = nx + 2 * H, Ny = ny + 2 * H;
+    const i64 sy = Nx, sz = Nx * Ny;
+    double ch[5] = {0, 0, 0, 0, 0};
+    for (int m = 0; m <= R; ++m)
+        ch[m] = c[m] / (h * h);
+#pragma omp parallel for schedule(static)
+    for (i64 k = 0; k < nz; ++k)
+        for (i64 j = 0; j < ny; ++j)
+            for (i64 i = 0; i < nx; ++i) {
+                i64 p = (i + H) + Nx * ((j + H) + Ny * (k + H));
+                double lap = star_at(u, p, sy, sz, R, ch, ch, ch);
+                double vdt = vel[p] * dt;
+                double ed = eta[p] * dt;
+                u_next[p] = (2.0 * u[p] - (1.0 - ed) * u_prev[p] + vdt * vdt * lap) / (1.0 + ed);
+            }
+    for (i64 s = 0; s < nsrc; ++s) {
+        i64 p = pad_of_interior(src_idx[s], nx, ny, H);
+        double vdt = vel[p] * dt;
+        u_next[p] += vdt * vdt * src_f[s];
+    }
+}
