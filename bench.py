@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
                     help="wave-field storage of the main timed path (arithmetic is FP32 in all)")
-    ap.add_argument("--forms", default="storage,radius,errors,precision,batched,adjoint,suite",
+    ap.add_argument("--forms", default="storage,radius,errors,precision,absorb,batched,adjoint,suite",
                     help="comma list of extra forms to measure after the main line, or 'none'")
     ap.add_argument("--no-forms", action="store_true", help="same as --forms none")
     ap.add_argument("--adj-n", type=int, default=256, help="adjoint form: interior side")
@@ -317,6 +317,36 @@ def precision_form(args, stream, hbm, n=1024, nsteps=500):
     del a, b, work, vel
     torch.cuda.empty_cache()
     return out
+
+
+def absorb_form(prob, args, stream, hbm, width=20):
+    """The headline workload inside an absorbing layer of `width` cells on
+    every face (damped wave equation, eta_max for a 1e-3 reflection target):
+    whole-call throughput and the step kernel's roofline at 16 B/pt."""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    dev = torch.device("cuda", torch.cuda.current_device())
+    vel = torch.from_numpy(prob.vel).to(dev)
+    si, sa = torch.from_numpy(prob.src_idx).to(dev), torch.from_numpy(prob.src_amp).to(dev)
+    vmax = float(prob.meta.get("vmax", vel.max().item()))
+    eta_max = 3 * vmax * np.log(1e3) / (2 * width * prob.h)
+    st = {"a": torch.zeros_like(vel), "b": torch.zeros_like(vel)}
+
+    def run():
+        st["a"], st["b"] = gbs.wave_propagate(st["a"], st["b"], vel, prob.dt, prob.h, prob.halo, prob.nsteps,
+                                              src_idx=si, src_amp=sa, absorb=(width, eta_max))
+    for _ in range(2):
+        run()
+    k = max(3, args.steps // 4)
+    ms, kms, kl = time_calls(run, k, stream)
+    gbs.device_status()
+    ach = 16 * prob.npoints / (kms * 1e-3) / 1e9
+    del st
+    torch.cuda.empty_cache()
+    return {"width": width, "eta_max": eta_max, "value": prob.npoints * prob.nsteps / (ms * 1e-3) / 1e9,
+            "unit": UNIT, "ms_per_step": ms, "calls": k,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "kernel_ms_per_launch": kms, "kernel_launches": kl}}
 
 
 FP32_FMA_LANES_PER_SM = 128      # FP32 FMA lanes per SM (4 partitions x 32)
@@ -792,6 +822,8 @@ def run_ours(args):
             forms["precision_1024"] = precision_form(args, stream, hbm)
         if "batched" in wanted:
             forms["batched"] = batched_forms(args, stream, hbm, nshots=args.batch_shots)
+        if "absorb" in wanted:
+            forms["absorbing_layer"] = absorb_form(prob, args, stream, hbm)
         if "suite" in wanted:
             forms["suite"] = suite_form(args, stream, hbm)
         if "adjoint" in wanted:

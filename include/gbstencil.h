@@ -95,6 +95,18 @@ typedef struct {
     int tile_y;     /* rows per CTA tile of the TMA kernel: 16 or 32 (x is always 64) */
     int zchunk;     /* planes streamed per CTA (>= 1) */
     int use_graph;  /* wave_propagate: 1 = capture the step loop in a CUDA graph and replay it */
+    /* gbs_wave_propagate (FP32, TMA kernel) only: an absorbing layer of
+     * absorb_width cells (<= 64) inside every face of the interior, the
+     * damped wave equation u_tt + 2 eta u_t = V^2 lap u with a centred u_t:
+     *   u^{n+1} = [2u^n - (1 - eta dt) u^{n-1} + dt^2 V^2 lap u^n] / (1 + eta dt)
+     * (sources added after), eta = absorb_eta ((W - d) / W)^2 [1/s] at
+     * distance d < W cells from the nearest absorbing face, 0 elsewhere.
+     * absorb_free_top = 1 leaves the face z = 0 reflecting (a free surface).
+     * The paper surrounds its domain with an absorbing boundary (Sec. 2.2)
+     * without giving its equations; this layer is one published choice. */
+    int absorb_width;
+    float absorb_eta;
+    int absorb_free_top;
 } gbs_opts;
 
 /*

@@ -58,7 +58,8 @@ class _Rec(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("tile_y", ctypes.c_int), ("zchunk", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("absorb_width", ctypes.c_int), ("absorb_eta", ctypes.c_float),
+                ("absorb_free_top", ctypes.c_int)]
 
 
 class _Shot(ctypes.Structure):
@@ -291,24 +292,29 @@ def stencil_suite(inp: torch.Tensor, out: Optional[torch.Tensor] = None, *, dims
     return out
 
 
-def _opts(kernel, tile_y, zchunk, use_graph):
-    return _Opts(int(kernel), int(tile_y), int(zchunk), 1 if use_graph else 0)
+def _opts(kernel, tile_y, zchunk, use_graph, absorb=None):
+    w, eta, free = absorb if absorb else (0, 0.0, False)
+    return _Opts(int(kernel), int(tile_y), int(zchunk), 1 if use_graph else 0, int(w), float(eta), 1 if free else 0)
 
 
 def wave_propagate(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, dt: float, h: float,
                    halo: int, nsteps: int, *, t0: int = 0, src_idx=None, src_amp=None, rec_idx=None,
                    rec_trace=None, kernel: int = 0, tile_y: int = 0, zchunk: int = 0,
-                   use_graph: bool = False, stream=None):
+                   use_graph: bool = False, absorb=None, stream=None):
     """Algorithm 1: nsteps leapfrog steps, in place in the two buffers.
 
     Returns (prev, cur): the tensors that now hold u^{t0+nsteps-1} and
     u^{t0+nsteps} (the two input buffers, swapped when nsteps is odd).
+    ``absorb = (width, eta_max[, free_top])`` adds the absorbing layer
+    (damped wave equation near the faces; FP32 TMA kernel only).
 
     With CPU tensors (ideally pinned) the call copies the inputs to the
     device, runs, and copies both fields (and the trace) back; it then
     returns CPU tensors.
     """
     if not u.is_cuda:
+        if absorb:
+            raise ValueError("the absorbing layer takes device tensors")
         return _wave_propagate_host(u_prev, u, vel, dt, h, halo, nsteps, t0=t0, src_idx=src_idx,
                                     src_amp=src_amp, rec_idx=rec_idx, rec_trace=rec_trace, kernel=kernel,
                                     tile_y=tile_y, zchunk=zchunk, use_graph=use_graph, stream=stream)
@@ -317,7 +323,10 @@ def wave_propagate(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, dt:
     nx, ny, nz = _dims(u, halo)
     src = _make_src(src_idx, src_amp)
     rec = _make_rec(rec_idx, rec_trace)
-    opts = _opts(kernel, tile_y, zchunk, use_graph)
+    ab = None
+    if absorb:
+        ab = (absorb[0], absorb[1], absorb[2] if len(absorb) > 2 else False)
+    opts = _opts(kernel, tile_y, zchunk, use_graph, ab)
     _check(load().gbs_wave_propagate(p[0], p[1], p[2], float(dt), float(h), nx, ny, nz, halo, int(nsteps),
                                      int(t0), _ptr(src), _ptr(rec), ctypes.byref(opts), _stream(stream)))
     return (u, u_prev) if nsteps % 2 else (u_prev, u)

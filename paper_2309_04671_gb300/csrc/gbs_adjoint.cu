@@ -332,6 +332,8 @@ extern "C" gbs_status gbs_adjoint_forward(const float *vel, float dt, float h, i
     gbs_status s = check_common(vel, dt, h, nx, ny, nz, halo, nsteps, src, ckpt_every, work);
     if (s != GBS_OK)
         return s;
+    if (opts && opts->absorb_width != 0)
+        return set_error(GBS_EINVAL, "the adjoint has no absorbing layer");
     if (rec && (rec->n < 0 || (rec->n > 0 && (!rec->idx || !rec->trace || rec->nt < nsteps))))
         return set_error(GBS_EINVAL, "receiver list needs idx and a trace of >= nsteps rows");
     const AdjLayout L = adj_layout(nx, ny, nz, nsteps, ckpt_every);
@@ -352,6 +354,8 @@ extern "C" gbs_status gbs_adjoint_backward(const float *vel, float dt, float h, 
     gbs_status s = check_common(vel, dt, h, nx, ny, nz, halo, nsteps, src, ckpt_every, work);
     if (s != GBS_OK)
         return s;
+    if (opts && opts->absorb_width != 0)
+        return set_error(GBS_EINVAL, "the adjoint has no absorbing layer");
     if (nrec < 0 || (nrec > 0 && (!rec_idx || !adj_src)))
         return set_error(GBS_EINVAL, "receiver indices and adjoint source needed");
     if (!grad)
@@ -381,6 +385,8 @@ extern "C" gbs_status gbs_fwi_gradient(const float *vel, float dt, float h, int6
     gbs_status s = check_common(vel, dt, h, nx, ny, nz, halo, nsteps, src, ckpt_every, work);
     if (s != GBS_OK)
         return s;
+    if (opts && opts->absorb_width != 0)
+        return set_error(GBS_EINVAL, "the adjoint has no absorbing layer");
     if (nrec <= 0 || !rec_idx || !d_obs || !trace || !resid || !grad || !misfit)
         return set_error(GBS_EINVAL, "receivers, d_obs, trace, resid, grad and misfit are required");
     if (trace == resid)

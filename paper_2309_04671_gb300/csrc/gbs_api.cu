@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cmath>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -217,7 +218,35 @@ struct StepPlan {
     int zchunk;
     gbs_dtype storage;    // of u, u_prev, u_next (vel is FP32)
     TmaPlan tma;
+    Absorb ab{};          // absorbing layer (TMA FP32 only)
 };
+
+// Validate the absorbing-layer options and tabulate A, B by distance.
+gbs_status absorb_plan(const gbs_opts *o, float dt, int kernel, Absorb *ab)
+{
+    memset(ab, 0, sizeof(*ab));
+    if (!o || o->absorb_width == 0)
+        return GBS_OK;
+    if (o->absorb_width < 0 || o->absorb_width > kMaxAbsorb)
+        return fail(GBS_EINVAL, "absorb_width must be in 0..%d", kMaxAbsorb);
+    if (!(o->absorb_eta >= 0.f) || !std::isfinite(o->absorb_eta))
+        return fail(GBS_EINVAL, "absorb_eta must be finite and >= 0");
+    if (kernel != 1)
+        return fail(GBS_EALIGN, "the absorbing layer runs on the TMA kernel (halo %% 4 == 0, nx %% 4 == 0, "
+                                "16-byte aligned fields)");
+    const int w = o->absorb_width;
+    ab->width = w;
+    ab->free_top = o->absorb_free_top != 0;
+    for (int d = 0; d < w; ++d) {
+        const double r = (double)(w - d) / (double)w;
+        const double ed = (double)o->absorb_eta * r * r * (double)dt;
+        ab->A[d] = (float)(1.0 / (1.0 + ed));
+        ab->B[d] = (float)(1.0 - ed);
+    }
+    return GBS_OK;
+}
+
+bool absorb_requested(const gbs_opts *o) { return o && o->absorb_width != 0; }
 
 gbs_status plan_step(StepPlan *sp, const Grid &g, const void *u_prev, const void *u, const float *vel,
                      int kernel, int tile_y, int zchunk, gbs_dtype storage = GBS_F32)
@@ -268,7 +297,8 @@ gbs_status run_step(const StepPlan &sp, const Grid &g, const void *u_prev, const
             p.nsrc = (int)src->n;
         }
         p.meta = meta;
-        e = launch_tma(4, kWave, sp.tile_y, sp.storage, sp.tma, p, t, st);
+        p.ab = sp.ab;
+        e = launch_tma(4, sp.ab.width > 0 ? kWaveAbsorb : kWave, sp.tile_y, sp.storage, sp.tma, p, t, st);
     } else {
         WaveArgs w{static_cast<const float *>(u_prev), vel, s};
         e = launch_generic(4, kWave, g, static_cast<const float *>(u), static_cast<float *>(u_next), wave_coeffs(), w,
@@ -526,6 +556,9 @@ extern "C" gbs_status gbs_wave_propagate(float *u_prev, float *u, const float *v
     const int kernel = pick_kernel(opts, tma_ok, &s);
     if (s != GBS_OK)
         return s;
+    Absorb ab;
+    if ((s = absorb_plan(opts, dt, kernel, &ab)) != GBS_OK)
+        return s;
     const int tile_y = pick_tile_y(opts);
     const int zchunk = (opts && opts->zchunk > 0) ? opts->zchunk
                        : kernel == 1                ? tma_default_zchunk(4, kWave, tile_y, GBS_F32, g)
@@ -537,6 +570,7 @@ extern "C" gbs_status gbs_wave_propagate(float *u_prev, float *u, const float *v
         return s;
     if ((s = plan_step(&plan[1], g, buf[1], buf[0], vel, kernel, tile_y, zchunk)) != GBS_OK)
         return s;
+    plan[0].ab = plan[1].ab = ab;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool graph = opts && opts->use_graph && st != nullptr;
 
@@ -551,7 +585,7 @@ extern "C" gbs_status gbs_wave_propagate(float *u_prev, float *u, const float *v
         return GBS_OK;
     };
     if (kernel == 1 && graph) {
-        cudaError_t e = tma_prepare_wave(GBS_F32, tile_y);
+        cudaError_t e = plan[0].ab.width > 0 ? tma_prepare_wave_absorb(tile_y) : tma_prepare_wave(GBS_F32, tile_y);
         if (e != cudaSuccess)
             return cuda_fail(e, "kernel attributes");
     }
@@ -587,6 +621,8 @@ extern "C" gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float
                     (long long)src->n);
     if (opts && (opts->zchunk < 0 || opts->kernel == 2))
         return fail(GBS_EINVAL, "16-bit storage runs the TMA kernel only; zchunk must be >= 0");
+    if (absorb_requested(opts))
+        return fail(GBS_EINVAL, "the absorbing layer is available with FP32 storage only");
     if (nx == 0 || ny == 0 || nz == 0 || nsteps == 0)
         return GBS_OK;
     const Grid gc = dense_grid(nx, ny, nz, halo);

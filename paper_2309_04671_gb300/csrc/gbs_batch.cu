@@ -267,6 +267,8 @@ extern "C" gbs_status gbs_batch_plan_create(gbs_batch_plan **plan, const gbs_sho
         return set_error(GBS_EINVAL, "opts.tile_y must be 0, 16 or 32");
     if (opts && opts->zchunk < 0)
         return set_error(GBS_EINVAL, "opts.zchunk must be >= 0");
+    if (opts && opts->absorb_width != 0)
+        return set_error(GBS_EINVAL, "batch plans have no absorbing layer");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     gbs_batch_plan *P = new gbs_batch_plan();
     P->nshots = nshots;

@@ -46,7 +46,8 @@ struct Coeffs {
 //             folds the partial into its FP64 gradient every few steps)
 //   kStencilAsym: out = (sum_a c[a][0]) u + sum_a sum_m c[a][m] u(+m) + cm[a][m] u(-m)
 //             (a star with one weight per point: the suite's star3d kernels)
-enum Mode { kStencil = 0, kWave = 1, kImage = 2, kStencilAsym = 3 };
+//   kWaveAbsorb: kWave with the absorbing layer of StepParams::ab (FP32)
+enum Mode { kStencil = 0, kWave = 1, kImage = 2, kStencilAsym = 3, kWaveAbsorb = 4 };
 
 struct WaveArgs {
     const float *u_prev;   // read at the point only (may alias out)
@@ -94,6 +95,18 @@ __device__ __forceinline__ int lp_scale_exponent(float m)
 // Arguments of the TMA kernel for one field (one shot).  A launch also
 // gets the time level t of u (the step writes u^{t+1}) and the ping-pong
 // parity, which selects the output buffer.
+// Absorbing layer of the leapfrog (damped wave equation, centred u_t):
+//   u^{n+1} = A (2u^n - B u^{n-1} + (V dt)^2 lap u^n) [+ sources after],
+// A = 1 / (1 + eta dt), B = 1 - eta dt, tabulated by the distance d < width
+// (cells) from a point to the nearest absorbing interior face.
+constexpr int kMaxAbsorb = 64;
+struct Absorb {
+    int width;                 // 0 = no layer
+    int free_top;              // 1 = the face z = 0 does not absorb
+    float A[kMaxAbsorb];
+    float B[kMaxAbsorb];
+};
+
 struct StepParams {
     Grid g;                    // geometry of u, u_prev, vel and out
     void *out[2];              // output buffer for parity 0 / 1 (storage type of the launch)
@@ -108,6 +121,7 @@ struct StepParams {
     int nsrc;                  // <= kMaxFusedSrc
     int *meta;                 // 16-bit storage state (kMetaSlots x kMetaInts; slot of level t = t % 3), else nullptr
     int64_t inx, iny;          // interior sizes that interior linear indices refer to
+    Absorb ab;                 // absorbing layer (FP32 wave mode; width 0 = none)
 };
 
 // One CTA's work in a batched launch: a 64 x TY tile of shot `shot`,
@@ -138,6 +152,7 @@ cudaError_t launch_tma_batch(int tile_y, gbs_dtype storage, const BatchItem *ite
 cudaError_t tma_prepare_batch(gbs_dtype storage, int tile_y);
 int tma_default_zchunk(int radius, Mode mode, int tile_y, gbs_dtype storage, const Grid &g);
 // Sets the wave kernel's shared-memory attribute (call before stream capture).
+cudaError_t tma_prepare_wave_absorb(int tile_y);
 cudaError_t tma_prepare_wave(gbs_dtype storage, int tile_y);
 
 // 16-bit storage helpers (k_lp.cu).  Grids: `gc` the caller's FP32 layout,

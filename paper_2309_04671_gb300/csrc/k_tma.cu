@@ -95,7 +95,8 @@ struct Cfg {
     static constexpr int SP = LOW ? 3 : (MODE == kImage ? 4 : 5);
     static constexpr size_t SMEM_L = (size_t)SL * L_STRIDE;
     static constexpr size_t SMEM_F = (size_t)SF * F_STRIDE;
-    static constexpr bool PV = MODE == kWave || MODE == kImage;   // second ring (u_prev|nu, vel|w[, g])
+    static constexpr bool WAVE = MODE == kWave || MODE == kWaveAbsorb;
+    static constexpr bool PV = WAVE || MODE == kImage;   // second ring (u_prev|nu, vel|w[, g])
     static constexpr size_t SMEM_PV = PV ? (size_t)SP * PV_STRIDE : 0;
     static constexpr size_t SMEM = SMEM_L + SMEM_F + SMEM_PV + (SL + SP) * 8;
     static constexpr int MIN_BLOCKS = NT > 128 ? 1 : (LOW ? 3 : 2);
@@ -285,7 +286,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
     __syncthreads();
 
     // point sources inside this CTA's box (fused injection)
-    const float *amp_row = (MODE == kWave && p.src_amp != nullptr && t >= 0 && t < p.src_nt)
+    const float *amp_row = (C::WAVE && p.src_amp != nullptr && t >= 0 && t < p.src_nt)
                                ? p.src_amp + t * p.nsrc
                                : nullptr;
     if (amp_row != nullptr && tid < p.nsrc) {
@@ -534,7 +535,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                         }
                         acc_l = add2(acc_l, acc2_l);
                         acc_h = add2(acc_h, acc2_h);
-                        if (MODE == kWave) {
+                        if (C::WAVE) {
                             const float4 up = ld4(pvu + (kVY * ty + r) * C::PVU_W + C::PVU_X0 + 4 * tx);
                             vel4[r] = ld4(pvv + (kVY * ty + r) * kTX + 4 * tx);
                             const f2 vs_l = mul2(lo(vel4[r]), S2), vs_h = mul2(hi(vel4[r]), S2);
@@ -550,8 +551,37 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                                 t_l = sub2(add2(lo(cen), lo(cen)), lo(up));
                                 t_h = sub2(add2(hi(cen), hi(cen)), hi(up));
                             }
-                            acc_l = fma2(c_l, acc_l, t_l);
-                            acc_h = fma2(c_h, acc_h, t_h);
+                            bool damp = false;
+                            if constexpr (!kLow && MODE == kWaveAbsorb) {
+                                // absorbing layer: u_next = A (2u - B u_prev + c lap), A, B by the
+                                // distance d < width to the nearest absorbing face (rare, uniform test first)
+                                const int aw = p.ab.width;
+                                if (aw > 0) {
+                                    const int64_t yy = gy + r;
+                                    const int64_t dzk = p.ab.free_top ? (g.nz - 1 - k) : min((int64_t)k, g.nz - 1 - k);
+                                    const int64_t dyz = min(min(yy, g.ny - 1 - yy), dzk);
+                                    if (dyz < aw || gx < aw || gx + 3 >= g.nx - aw) {
+                                        float4 A4, B4;
+                                        float *pa = &A4.x, *pb = &B4.x;
+#pragma unroll
+                                        for (int e = 0; e < 4; ++e) {
+                                            int64_t d = min(dyz, min(gx + e, g.nx - 1 - gx - e));
+                                            d = d < 0 ? 0 : d;   // lanes past the interior are not stored
+                                            pa[e] = d < aw ? p.ab.A[d] : 1.f;
+                                            pb[e] = d < aw ? p.ab.B[d] : 1.f;
+                                        }
+                                        t_l = sub2(add2(lo(cen), lo(cen)), mul2(lo(B4), lo(up)));
+                                        t_h = sub2(add2(hi(cen), hi(cen)), mul2(hi(B4), hi(up)));
+                                        acc_l = mul2(lo(A4), fma2(c_l, acc_l, t_l));
+                                        acc_h = mul2(hi(A4), fma2(c_h, acc_h, t_h));
+                                        damp = true;
+                                    }
+                                }
+                            }
+                            if (!damp) {
+                                acc_l = fma2(c_l, acc_l, t_l);
+                                acc_h = fma2(c_h, acc_h, t_h);
+                            }
                         } else if (MODE == kImage) {
                             nu4[r] = ld4(pvu + (kVY * ty + r) * C::PVU_W + C::PVU_X0 + 4 * tx);
                             vel4[r] = ld4(pvv + (kVY * ty + r) * kTX + 4 * tx);
@@ -559,7 +589,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                         res_l[r] = acc_l;
                         res_h[r] = acc_h;
                     }
-                    if (MODE == kWave && nsrc_cta > 0) {
+                    if (C::WAVE && nsrc_cta > 0) {
                         // rare: this CTA holds a source cell
                         for (int i = 0; i < nsrc_cta; ++i) {
                             if (s_src_z[i] != k || (s_src_x[i] >> 2) != tx)
@@ -791,6 +821,12 @@ cudaError_t launch_tma(int radius, Mode mode, int tile_y, gbs_dtype storage, con
     StepParams p = p0;
     if (p.zchunk <= 0)
         p.zchunk = tma_default_zchunk(radius, mode, tile_y, storage, p.g);
+    if (mode == kWaveAbsorb) {
+        if (radius != 4 || storage != GBS_F32)
+            return cudaErrorInvalidValue;
+        return tile_y == 32 ? launch_cfg<4, kWaveAbsorb, 32, float>(plan, p, t, st)
+                            : launch_cfg<4, kWaveAbsorb, 16, float>(plan, p, t, st);
+    }
     if (mode == kWave) {
         if (radius != 4)
             return cudaErrorInvalidValue;
@@ -840,6 +876,11 @@ cudaError_t tma_prepare_batch(gbs_dtype storage, int tile_y)
     case GBS_F16: return t32 ? prepare_batch_cfg<32, __half>() : prepare_batch_cfg<16, __half>();
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t tma_prepare_wave_absorb(int tile_y)
+{
+    return tile_y == 32 ? prepare_cfg<4, kWaveAbsorb, 32, float>() : prepare_cfg<4, kWaveAbsorb, 16, float>();
 }
 
 cudaError_t tma_prepare_wave(gbs_dtype storage, int tile_y)

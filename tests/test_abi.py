@@ -200,3 +200,16 @@ def test_suite_points_and_validation(lib):
     assert call(a, a, 8, 8, 8, 4, 3, 1, 4, w, ctypes.c_float(1.0), None) == gbs.GBS_EINVAL      # overlap
     assert call(a, b, 6, 8, 8, 4, 3, 1, 4, w, ctypes.c_float(1.0), None) == gbs.GBS_EALIGN      # nx % 4
     assert call(a, b, 0, 8, 8, 4, 3, 1, 4, w, ctypes.c_float(1.0), None) == gbs.GBS_OK         # empty
+
+
+def test_absorb_validation_before_device(lib):
+    fake = [ctypes.c_void_p(1 << 20), ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20)]
+    args = (fake[0], fake[1], fake[2], ctypes.c_float(1e-3), ctypes.c_float(10.0), 8, 8, 8, 4, 3, 0, None, None)
+    assert lib.gbs_wave_propagate(*args, ctypes.byref(gbs._Opts(0, 0, 0, 0, 65, 10.0, 0)), None) == gbs.GBS_EINVAL
+    assert lib.gbs_wave_propagate(*args, ctypes.byref(gbs._Opts(0, 0, 0, 0, 4, -1.0, 0)), None) == gbs.GBS_EINVAL
+    assert lib.gbs_wave_propagate(*args, ctypes.byref(gbs._Opts(2, 0, 0, 0, 4, 10.0, 0)), None) == gbs.GBS_EALIGN
+    work = ctypes.c_void_p(1 << 24)
+    lp = lib.gbs_wave_propagate_lp(fake[0], fake[1], fake[2], ctypes.c_float(1e-3), ctypes.c_float(10.0), 8, 8, 8,
+                                   4, 3, 0, None, None, 1, work, 1 << 30,
+                                   ctypes.byref(gbs._Opts(0, 0, 0, 0, 4, 10.0, 0)), None)
+    assert lp == gbs.GBS_EINVAL
