@@ -138,3 +138,44 @@ def test_fp32_many_sources_take_the_injection_kernel():
         _, ru, _ = oracle.wave_propagate(z, z, vel, dt, 10.0, halo, nsteps, src_idx=src, src_amp=amp)
         e = oracle.err_norms(cur.cpu().numpy(), ru)
         assert e["norm_max_rel"] <= tol_steps(nsteps), (kernel, e)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_full_size_one_step_sampled(fmt):
+    """The benchmark's 512^3 layered workload, one 16-bit step in the launch
+    configuration the benchmark times, checked at sampled points (tile seams,
+    faces, random interior): the stored inputs are the library's decoded
+    u^0 and u^{-1} rounded by torch's own conversion at the encode scale; the
+    oracle steps them in FP64 and rounds at the lagged scale of u^0."""
+    need_gpu()
+    prob = W.layered_problem(n=512, nsteps=1)
+    n, halo = 512, prob.halo
+    g = torch.Generator(device=dev()).manual_seed(3)
+    shape = W.padded_shape(n, n, n, halo)
+    inner = (slice(halo, -halo),) * 3
+    a = torch.zeros(shape, device=dev())
+    b = torch.zeros(shape, device=dev())
+    a[inner] = (torch.rand((n, n, n), device=dev(), generator=g) * 2 - 1) * 0.02
+    b[inner] = (torch.rand((n, n, n), device=dev(), generator=g) * 2 - 1) * 0.03
+    tdt = torch.bfloat16 if fmt == "bf16" else torch.float16
+    # stored u^{-1}: RN at the encode scale of its own max (torch's conversion)
+    s_p = oracle.lp_scale_exponent(float(a.abs().max()))
+    stored_prev = ((a * 2.0 ** -s_p).to(tdt).float() * 2.0 ** s_p).cpu().numpy()
+    prev, cur = gbs.wave_propagate_lp(a, b, torch.from_numpy(prob.vel).to(dev()), prob.dt, prob.h, halo, 1,
+                                      storage=fmt)
+    gbs.device_status()
+    u0 = prev.cpu().numpy()                               # the stored u^0, decoded
+    rng = np.random.default_rng(2)
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (63, 15, 200), (64, 16, 201), (511, 0, 255)]
+    pts += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(600)]
+    idx = np.array([i + n * (j + n * k) for i, j, k in pts], np.int64)
+    ref = oracle.wave_points(stored_prev, u0, prob.vel, prob.dt, prob.h, halo, idx)
+    s = oracle.lp_scale_exponent(float(np.abs(W.interior(u0, halo)).max()))   # lagged scale of u^{n+1}
+    want = oracle.round_to_format(ref * 2.0 ** -s, fmt) * 2.0 ** s
+    c = cur.cpu().numpy()
+    got = np.array([c[k + halo, j + halo, i + halo] for i, j, k in pts], np.float64)
+    gi, ri = got * 2.0 ** -s, ref * 2.0 ** -s
+    big = np.maximum(np.abs(gi), np.abs(ri))
+    spacing = 2.0 ** (np.floor(np.log2(np.maximum(big, 2.0 ** -30))) - (FMT_P[fmt] - 1))
+    assert np.all(np.abs(gi - ri) <= spacing + TOL_ONE * np.abs(ri).max())
+    assert np.mean(got != want) < 0.02
