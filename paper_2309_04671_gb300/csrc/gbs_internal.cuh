@@ -190,7 +190,8 @@ struct SuiteParams {
     int64_t nx, ny, nz;      // interior
     int64_t px, py;          // row pitch, rows per plane (elements)
     int hxy, hz;             // halo in x/y and in z
-    int zchunk, tiles_x;
+    int zchunk, tiles_x;     // planes (3D) or (plane, y tile) items (2D) per CTA; x tiles (set by the launcher)
+    int ty_tiles;            // y tiles (set by the launcher)
     int has_div;
     float divisor;
     float w[kSuiteMaxW];

@@ -63,12 +63,18 @@ __global__ void __launch_bounds__(kSNT, 2)
 
     const int tid = threadIdx.x;
     const int tx = tid % (kSX / 4), ty = tid / (kSX / 4);
-    const int64_t tx0 = (int64_t)(blockIdx.x % p.tiles_x) * kSX;
-    const int64_t ty0 = (int64_t)(blockIdx.x / p.tiles_x) * kSY;
-    const int z0 = blockIdx.y * p.zchunk;
-    const int z1 = (int)min((int64_t)z0 + p.zchunk, p.nz);
-    const int nzc = z1 - z0;
+    // 3D: the CTA owns the tile (tx0, ty0) and streams the planes of its
+    // z-chunk.  2D: the CTA owns an x tile and streams a chunk of items
+    // q = (z plane, y tile), each an independent one-tile 2D problem.
+    const int64_t tx0 = (int64_t)(D3 ? blockIdx.x % p.tiles_x : blockIdx.x) * kSX;
+    const int64_t ty0_3d = D3 ? (int64_t)(blockIdx.x / p.tiles_x) * kSY : 0;
+    const int64_t total = D3 ? p.nz : p.nz * (int64_t)p.ty_tiles;
+    const int64_t z0 = (int64_t)blockIdx.y * p.zchunk;
+    const int64_t z1 = min(z0 + p.zchunk, total);
+    const int nzc = (int)(z1 - z0);
     const int nplanes = nzc + 2 * RZ;
+    auto item_y = [&](int64_t q) -> int64_t { return D3 ? ty0_3d : (q % p.ty_tiles) * kSY; };
+    auto item_z = [&](int64_t q) -> int64_t { return D3 ? q : q / p.ty_tiles; };
     const int H = p.hxy;
 
     // a box must start on a 16-byte boundary in x; the host launches only
@@ -88,12 +94,13 @@ __global__ void __launch_bounds__(kSNT, 2)
     }
     __syncthreads();
 
-    int n_issued = 0;   // planes z0 - RZ + [0, n_issued) requested (thread 0 only)
+    int n_issued = 0;   // planes (items) z0 - RZ + [0, n_issued) requested (thread 0 only)
     auto issue = [&]() {
         const int st = n_issued % C::SL;
+        const int64_t q = z0 - RZ + n_issued;
         mbar_arrive_expect_tx(&full[st], C::L_BYTES);
-        tma_load_3d(smem + st * C::L_STRIDE, &tm, (int)(H + tx0 - 4), (int)(H + ty0 - R), p.hz + z0 - RZ + n_issued,
-                    &full[st]);
+        tma_load_3d(smem + st * C::L_STRIDE, &tm, (int)(H + tx0 - 4), (int)(H + item_y(q) - R),
+                    (int)(p.hz + item_z(q)), &full[st]);
         ++n_issued;
     };
     if (tid == 0)
@@ -102,7 +109,7 @@ __global__ void __launch_bounds__(kSNT, 2)
 
     const int lx = 4 + 4 * tx;                 // stage column of the thread's first point
     const int ly = R + kSVY * ty;              // stage row of the thread's first row
-    const int64_t gx = tx0 + 4 * tx, gy = ty0 + kSVY * ty;
+    const int64_t gx = tx0 + 4 * tx;
     const bool xin = gx < p.nx;
     const int64_t plane = p.px * p.py;
     bool fail = false, aborted = false;
@@ -186,7 +193,8 @@ __global__ void __launch_bounds__(kSNT, 2)
                     }
                 }
             }
-            float *dst = out + (H + gx) + p.px * (H + gy) + plane * (int64_t)(p.hz + z0 + c);
+            const int64_t gy = item_y(z0 + c) + kSVY * ty;
+            float *dst = out + (H + gx) + p.px * (H + gy) + plane * (p.hz + item_z(z0 + c));
 #pragma unroll
             for (int r = 0; r < kSVY; ++r) {
                 if (!(xin && gy + r < p.ny))
@@ -235,11 +243,14 @@ cudaError_t launch_one(const CUtensorMap &map, const SuiteParams &p0, float *out
     }
     SuiteParams p = p0;
     const int64_t tiles_x = (p.nx + kSX - 1) / kSX, tiles_y = (p.ny + kSY - 1) / kSY;
-    const int64_t nchunks = (p.nz + p.zchunk - 1) / p.zchunk;
-    if (tiles_x * tiles_y > 0x7fffffff || nchunks > 65535)
-        return cudaErrorInvalidConfiguration;
     p.tiles_x = (int)tiles_x;
-    k_suite<R, BOX, D3><<<dim3((unsigned)(tiles_x * tiles_y), (unsigned)nchunks), kSNT, C::SMEM, st>>>(map, p, out);
+    p.ty_tiles = (int)tiles_y;
+    const int64_t total = D3 ? p.nz : p.nz * tiles_y;         // planes (3D) or (plane, y tile) items (2D)
+    const int64_t nchunks = (total + p.zchunk - 1) / p.zchunk;
+    const int64_t gx = D3 ? tiles_x * tiles_y : tiles_x;
+    if (gx > 0x7fffffff || nchunks > 65535 || total > 0x7fffffff)
+        return cudaErrorInvalidConfiguration;
+    k_suite<R, BOX, D3><<<dim3((unsigned)gx, (unsigned)nchunks), kSNT, C::SMEM, st>>>(map, p, out);
     return cudaGetLastError();
 }
 
@@ -265,12 +276,15 @@ int suite_default_zchunk(int radius, bool d3, const SuiteParams &p)
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t slots = (int64_t)sms * 2;
-    const int64_t tiles = ((p.nx + kSX - 1) / kSX) * ((p.ny + kSY - 1) / kSY);
+    const int64_t tx = (p.nx + kSX - 1) / kSX, ty = (p.ny + kSY - 1) / kSY;
+    // 3D: tiles x z-chunks of planes; 2D: x tiles x chunks of (plane, y tile) items
+    const int64_t tiles = d3 ? tx * ty : tx;
+    const int64_t n = d3 ? p.nz : p.nz * ty;
     const double extra = d3 ? 0.5 * 2 * radius : 0.0;
-    int best = (int)(p.nz > 0 ? p.nz : 1);
+    int best = (int)(n > 0 ? (n < 0x7fffffff ? n : 0x7fffffff) : 1);
     double best_cost = 1e300;
-    for (int64_t c = 1; c <= p.nz && c <= 65535; ++c) {
-        const int64_t z = (p.nz + c - 1) / c;
+    for (int64_t c = 1; c <= n && c <= 65535; ++c) {
+        const int64_t z = (n + c - 1) / c;
         if (c > 1 && z < 8)
             break;
         const int64_t waves = (tiles * c + slots - 1) / slots;
