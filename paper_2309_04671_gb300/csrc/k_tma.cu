@@ -186,6 +186,44 @@ __device__ __forceinline__ void st4(__half *p, float4 v)
     *reinterpret_cast<uint2 *>(p) = raw;
 }
 
+// Store 4 values as 16-bit codes and fold their magnitudes into a running
+// two-lane max (max.xorsign.abs: the magnitude is max(|a|,|b|), the sign is
+// meaningless and dropped at the end).
+__device__ __forceinline__ void st4_max(__nv_bfloat16 *p, float4 v, unsigned &m)
+{
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 raw;
+    raw.x = *reinterpret_cast<const unsigned *>(&a);
+    raw.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = raw;
+    asm("max.xorsign.abs.bf16x2 %0, %0, %1;" : "+r"(m) : "r"(raw.x));
+    asm("max.xorsign.abs.bf16x2 %0, %0, %1;" : "+r"(m) : "r"(raw.y));
+}
+__device__ __forceinline__ void st4_max(__half *p, float4 v, unsigned &m)
+{
+    const __half2 a = __floats2half2_rn(v.x, v.y);
+    const __half2 b = __floats2half2_rn(v.z, v.w);
+    uint2 raw;
+    raw.x = *reinterpret_cast<const unsigned *>(&a);
+    raw.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = raw;
+    asm("max.xorsign.abs.f16x2 %0, %0, %1;" : "+r"(m) : "r"(raw.x));
+    asm("max.xorsign.abs.f16x2 %0, %0, %1;" : "+r"(m) : "r"(raw.y));
+}
+__device__ __forceinline__ void st4_max(float *p, float4 v, unsigned &) { st4(p, v); }
+// the larger magnitude of the two lanes, as a float
+__device__ __forceinline__ float code_absmax(unsigned m, __nv_bfloat16 *)
+{
+    return fmaxf(fabsf(__uint_as_float(m << 16)), fabsf(__uint_as_float(m & 0xffff0000u)));
+}
+__device__ __forceinline__ float code_absmax(unsigned m, __half *)
+{
+    const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&m));
+    return fmaxf(fabsf(f.x), fabsf(f.y));
+}
+__device__ __forceinline__ float code_absmax(unsigned, float *) { return 0.f; }
+
 // The value a float takes once rounded to the storage type.
 __device__ __forceinline__ float rounded(float v, float *) { return v; }
 __device__ __forceinline__ float rounded(float v, __nv_bfloat16 *) { return __bfloat162float(__float2bfloat16_rn(v)); }
@@ -324,7 +362,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
         }
     }
     __syncthreads();
-    float lmax = 0.f;
+    unsigned lmax2 = 0u;   // 16-bit: running max |code| of the stored values, two lanes
 
     // Loads issued so far (thread 0 only): u planes pfirst + [0, n_u) into
     // landing stage j % SL (use j / SL), pv planes z0 + [0, n_pv) into j % SP.
@@ -359,12 +397,14 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
     int consumed_u = 0, consumed_pv = 0;
 
     {
-        const float c0 = p.cf.c[0][0] + p.cf.c[1][0] + p.cf.c[2][0];
+        // 16-bit: the weights carry k_u (a power of two, so the products are exact)
+        const float ku = kLow ? k_u : 1.f;
+        const float c0 = (p.cf.c[0][0] + p.cf.c[1][0] + p.cf.c[2][0]) * ku;
         const f2 C0 = pk(c0, c0);
         f2 CX[R + 1], CY[R + 1], CZ[R + 1];
 #pragma unroll
         for (int m = 1; m <= R; ++m) {
-            CX[m] = pk(p.cf.c[0][m], p.cf.c[0][m]);
+            CX[m] = pk(p.cf.c[0][m] * ku, p.cf.c[0][m] * ku);
             CY[m] = C::PV ? CX[m] : pk(p.cf.c[1][m], p.cf.c[1][m]);
             CZ[m] = C::PV ? CX[m] : pk(p.cf.c[2][m], p.cf.c[2][m]);
         }
@@ -378,7 +418,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
         const f2 S2 = pk(p.s, p.s);
         const f2 KU = pk(k_u, k_u);
         const f2 TWO_KU = pk(2.f * k_u, 2.f * k_u);
-        const f2 KP = pk(k_p, k_p);
+        const f2 NKP = pk(-k_p, -k_p);
         const int nsrc_cta = s_nsrc;               // uniform over the CTA
         const int lx = 4 + 4 * tx;                 // stage column of the thread's first point
         const int ly = R + kVY * ty;               // stage row of the thread's first row
@@ -450,7 +490,8 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                             *reinterpret_cast<float4 *>(fs + (ly + r) * C::BW + lx) = P[Q - 1 + rho][r];
 #pragma unroll
                         for (int h = 0; h < kHaloPer; ++h)
-                            *reinterpret_cast<float4 *>(fs + hoff[h]) = ld4(su + hoff[h]);
+                            if (C::NT * h + tid < C::HALO_GROUPS)
+                                *reinterpret_cast<float4 *>(fs + hoff[h]) = ld4(su + hoff[h]);
                     }
                 }
 
@@ -541,10 +582,11 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                             const f2 vs_l = mul2(lo(vel4[r]), S2), vs_h = mul2(hi(vel4[r]), S2);
                             f2 c_l, c_h, t_l, t_h;
                             if (kLow) {
-                                c_l = mul2(mul2(vs_l, KU), vs_l);
-                                c_h = mul2(mul2(vs_h, KU), vs_h);
-                                t_l = sub2(mul2(TWO_KU, lo(cen)), mul2(KP, lo(up)));
-                                t_h = sub2(mul2(TWO_KU, hi(cen)), mul2(KP, hi(up)));
+                                // lap already carries k_u (scaled weights)
+                                c_l = mul2(vs_l, vs_l);
+                                c_h = mul2(vs_h, vs_h);
+                                t_l = fma2(TWO_KU, lo(cen), mul2(NKP, lo(up)));
+                                t_h = fma2(TWO_KU, hi(cen), mul2(NKP, hi(up)));
                             } else {
                                 c_l = mul2(vs_l, vs_l);
                                 c_h = mul2(vs_h, vs_h);
@@ -627,8 +669,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                             float4 v;
                             upk(res_l[r], v.x, v.y);
                             upk(res_h[r], v.z, v.w);
-                            lmax = fmaxf(lmax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-                            st4(dst + r * g.px, v);
+                            st4_max(dst + r * g.px, v, lmax2);
                         } else {
                             st_pairs(dst + r * g.px, res_l[r], res_h[r]);
                         }
@@ -675,8 +716,8 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
     }
 
     if constexpr (kLow) {
-        // max |value| of this CTA before rounding; rounding is monotone, so the
-        // rounded maximum is the largest stored code -> state slot of u^{n+1}
+        // max |stored code| of this CTA -> state slot of u^{n+1} (in field units)
+        float lmax = code_absmax(lmax2, (T *)nullptr);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
@@ -688,7 +729,7 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
             for (int w = 0; w < NCW; ++w)
                 mx = fmaxf(mx, s_red[w]);
             atomicMax(reinterpret_cast<unsigned *>(p.meta + slot_next * kMetaInts + kMetaMax),
-                      __float_as_uint(rounded(mx, (T *)nullptr) * sc_out));
+                      __float_as_uint(mx * sc_out));
         }
     }
 }
