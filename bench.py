@@ -651,6 +651,26 @@ def adjoint_form(args, stream, hbm, n=256, nsteps=1000, nshots=8):
     torch.cuda.synchronize()
     del work
     torch.cuda.empty_cache()
+    # every state kept in HBM (K = 1: no recomputation), one shot, if it fits
+    need = gbs.adjoint_workspace_bytes(n, n, n, nsteps, 1)
+    free, _ = torch.cuda.mem_get_info()
+    if need < 0.8 * free:
+        work1 = gbs.adjoint_workspace(vel, halo, nsteps, ckpt_every=1)
+        g1 = torch.zeros_like(grad)
+
+        def store_all():
+            g1.zero_()
+            gbs.fwi_gradient(vel, dt, h, halo, nsteps, d_obs[0], src_idx=srcs[0], src_amp=amp, rec_idx=rec,
+                             work=work1, grad=g1, ckpt_every=1)
+        store_all()
+        ms1, _, _ = time_calls(store_all, 1, stream)
+        gbs.device_status()
+        out["store_all_states"] = {"workspace_gb": need / 1e9, "ms_one_shot": ms1,
+                                   "checkpointed_ms_one_shot": ms_g / nshots,
+                                   "gradient_over_forward": ms1 / (ms_f / nshots),
+                                   "bit_identical_to_checkpointed": bool(torch.equal(g1, g_fused))}
+        del work1, g1
+        torch.cuda.empty_cache()
     res = {}
 
     def plain():

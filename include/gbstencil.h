@@ -271,12 +271,14 @@ void gbs_batch_plan_destroy(gbs_batch_plan *plan);
  *
  * Checkpointing: the forward pass keeps (u^{sK-1}, u^{sK}) every K =
  * ckpt_every steps (0: K = ceil(sqrt(nsteps))); the backward pass recomputes
- * each segment's K states from its checkpoint.  All state lives in the
- * caller's workspace (gbs_adjoint_workspace_bytes: velocity, imaging
- * weight, FP32 partial gradient, 4 wave fields, 2*ceil(nsteps/K) checkpoint
- * fields, K-1 segment fields, each (nx rounded up to 4, plus 8) * (ny+8) *
- * (nz+8) FP32 values with rows padded to 8, plus one FP64 field and 8 KiB),
- * 256-byte aligned.  The halo of vel is not read.
+ * each segment's K states from its checkpoint.  K = 1 keeps every state once
+ * (nsteps+1 fields) and recomputes nothing.  All state lives in the caller's
+ * workspace (gbs_adjoint_workspace_bytes: velocity, imaging weight, FP32
+ * partial gradient, 4 wave fields, 2*ceil(nsteps/K) checkpoint fields and
+ * K-1 segment fields -- or nsteps+1 state fields for K = 1 -- each (nx
+ * rounded up to 4, plus 8) * (ny+8) * (nz+8) FP32 values with rows padded to
+ * 8, plus one FP64 field and 8 KiB), 256-byte aligned.  The halo of vel is
+ * not read.
  *
  * gbs_adjoint_forward: runs the forward model, writes rec->trace (nt >=
  *   nsteps rows) and leaves the checkpoints in `work`.

@@ -11,6 +11,9 @@
 // and dJ/dv(x) = sum_m 2 nu^{m+1}(x) (L u^m + S f^m)(x) / v(x).  (The paper
 // has no adjoint; this is the discrete adjoint of the step as implemented.)
 //
+// With K = 1 every state is kept once instead (N+1 fields: 74 GB for 1000
+// steps at 256^3, which HBM holds) and nothing is recomputed.
+//
 // The adjoint step is the forward wave-step kernel; the imaging condition is
 // the same TMA kernel in its kImage mode (stencil of u^m times nu^{m+1},
 // summed in FP32 over at most 32 steps, then folded into the FP64
@@ -55,6 +58,7 @@ struct AdjLayout {
     size_t field = 0;   // bytes of one FP32 field
     size_t off_vel = 0, off_w = 0, off_gp = 0, off_f[2] = {0, 0}, off_n[2] = {0, 0}, off_ck = 0, off_seg = 0,
            off_g = 0, off_part = 0;
+    bool store_all = false;   // K = 1: every state u^0..u^N kept once (at off_ck), nothing recomputed
     size_t total = 0;
 };
 
@@ -81,10 +85,11 @@ AdjLayout adj_layout(int64_t nx, int64_t ny, int64_t nz, int64_t nsteps, int64_t
         L.off_n[i] = off;
         off += L.field;
     }
+    L.store_all = L.K == 1;
     L.off_ck = off;
-    off += (size_t)L.nck * 2 * L.field;
+    off += (size_t)(L.store_all ? nsteps + 1 : L.nck * 2) * L.field;
     L.off_seg = off;
-    off += (size_t)std::max<int64_t>(0, std::min(L.K, nsteps) - 1) * L.field;
+    off += (size_t)(L.store_all ? 0 : std::max<int64_t>(0, std::min(L.K, nsteps) - 1)) * L.field;
     L.off_g = off;
     off += up256(E * sizeof(double));
     L.off_part = off;
@@ -105,6 +110,7 @@ struct Ctx {
 
     float *fld(size_t off) const { return reinterpret_cast<float *>(w + off); }
     float *ckpt(int64_t s, int which) const { return fld(L->off_ck + ((size_t)s * 2 + which) * L->field); }
+    float *state(int64_t m) const { return fld(L->off_ck + (size_t)m * L->field); }   // store_all: u^m
     float *seg(int64_t i) const { return fld(L->off_seg + (size_t)i * L->field); }
     double *grad() const { return reinterpret_cast<double *>(w + L->off_g); }
 };
@@ -247,6 +253,23 @@ gbs_status forward(Ctx &c, int64_t nsteps, const gbs_src *src, const gbs_rec *re
     cudaError_t e = cudaMemsetAsync(a, 0, 2 * L.field, c.st);
     if (e != cudaSuccess)
         return set_cuda_error(e, "forward init");
+    if (L.store_all) {
+        // every state in its own slot: u^0 = 0 in slot 0, the step writes the
+        // next slot's interior; everything else of the slots is zeroed first
+        e = cudaMemsetAsync(c.state(0), 0, L.field, c.st);
+        if (e == cudaSuccess)
+            e = launch_zero_shell(c.state(1), (int64_t)(L.field / sizeof(float)), (int)nsteps, c.gi, c.st);
+        if (e != cudaSuccess)
+            return set_cuda_error(e, "state init");
+        for (int64_t m = 0; m < nsteps; ++m) {
+            gbs_status r = step(c, m == 0 ? a : c.state(m - 1), c.state(m), c.state(m + 1), src, m);
+            if (r != GBS_OK)
+                return r;
+            if (rec && (e = launch_record(c.gi, c.state(m + 1), rec, m, c.st, &c.gc)) != cudaSuccess)
+                return set_cuda_error(e, "receiver launch");
+        }
+        return GBS_OK;
+    }
     for (int64_t m = 0; m < nsteps; ++m) {
         if (m % L.K == 0) {
             const int64_t s = m / L.K;
@@ -282,6 +305,19 @@ gbs_status backward(Ctx &c, int64_t nsteps, const gbs_src *src, const gbs_src *a
         e = cudaMemsetAsync(c.seg(0), 0, nseg * L.field, c.st);
     if (e != cudaSuccess)
         return set_cuda_error(e, "adjoint init");
+    if (L.store_all) {
+        for (int64_t m = nsteps - 1; m >= 0; --m) {
+            gbs_status r = step(c, a, b, a, adj, m);   // a <- nu^{m+1}
+            if (r == GBS_OK)
+                r = image(c, c.state(m), a, src, m);
+            if (r != GBS_OK)
+                return r;
+            if (m % kFoldEvery == 0 && (e = launch_fold(c.gp, c.grad(), grid_elems(c.gi), c.st)) != cudaSuccess)
+                return set_cuda_error(e, "gradient fold");
+            std::swap(a, b);
+        }
+        return GBS_OK;
+    }
     for (int64_t s = L.nck - 1; s >= 0; --s) {
         const int64_t m0 = s * L.K, m1 = std::min(m0 + L.K, nsteps);
         auto u_at = [&](int64_t m) -> float * {   // u^m for m in [m0-1, m1)

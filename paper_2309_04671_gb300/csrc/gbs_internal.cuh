@@ -235,6 +235,8 @@ cudaError_t launch_grad_add(const Grid &gi, const double *g, const Grid &gc, dou
 cudaError_t launch_image_weight(const float *vel, float two_over_h2, float *w, int64_t n, cudaStream_t st);
 // g += (double)gp; gp = 0, over all n values (n a multiple of 4, 16-byte aligned)
 cudaError_t launch_fold(float *gp, double *g, int64_t n, cudaStream_t st);
+// zero all of nfields fields (stride elements apart, layout g) outside the box a step writes
+cudaError_t launch_zero_shell(float *base, int64_t stride, int nfields, const Grid &g, cudaStream_t st);
 
 // Error norms (k_norms.cu): one FP64 partial record of 4 doubles per block
 // of kNormRowsPerBlock rows; `out` receives kNormOut doubles.

@@ -88,6 +88,34 @@ __global__ void __launch_bounds__(kThreads) k_fold(float4 *gp, double2 *g, int64
     }
 }
 
+// Zero everything of nf consecutive fields (stride elements apart) except
+// the box the step kernel writes: x < H + g.nx, rows and planes of the
+// interior.  One warp per row.
+__global__ void __launch_bounds__(kThreads) k_zero_shell(float *base, int64_t stride, int nf, Grid g)
+{
+    const int64_t pz = g.nz + 2 * g.halo;
+    const int64_t rows = (int64_t)nf * pz * g.py;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+    const int64_t H = g.halo;
+    for (int64_t row = warp0; row < rows; row += nwarps) {
+        const int64_t f = row / (pz * g.py), rem = row % (pz * g.py);
+        const int64_t z = rem / g.py, y = rem % g.py;
+        float *r = base + f * stride + (z * g.py + y) * g.px;
+        const bool shell = z < H || z >= H + g.nz || y < H || y >= H + g.ny;
+        if (shell) {
+            for (int64_t x = lane; x < g.px; x += 32)
+                r[x] = 0.f;
+        } else {
+            for (int64_t x = lane; x < H; x += 32)
+                r[x] = 0.f;
+            for (int64_t x = H + g.nx + lane; x < g.px; x += 32)
+                r[x] = 0.f;
+        }
+    }
+}
+
 unsigned grid_blocks(int64_t n)
 {
     int dev = 0, sms = 152;
@@ -112,6 +140,15 @@ cudaError_t launch_fold(float *gp, double *g, int64_t n, cudaStream_t st)
         return cudaErrorInvalidValue;
     k_fold<<<grid_blocks(n / 4), kThreads, 0, st>>>(reinterpret_cast<float4 *>(gp), reinterpret_cast<double2 *>(g),
                                                     n / 4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_shell(float *base, int64_t stride, int nfields, const Grid &g, cudaStream_t st)
+{
+    if (nfields <= 0)
+        return cudaSuccess;
+    k_zero_shell<<<grid_blocks((int64_t)nfields * (g.nz + 2 * g.halo) * g.py * 32), kThreads, 0, st>>>(base, stride,
+                                                                                                     nfields, g);
     return cudaGetLastError();
 }
 

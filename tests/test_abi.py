@@ -165,7 +165,7 @@ def test_adjoint_workspace_and_validation(lib):
     fld = (e * 4 + 255) // 256 * 256
     want = fld * (7 + 2 * 5 + (k - 1)) + (e * 8 + 255) // 256 * 256 + 1024 * 8
     assert lib.gbs_adjoint_workspace_bytes(nx, ny, nz, n, 0) == want
-    assert lib.gbs_adjoint_workspace_bytes(nx, ny, nz, n, 1) == fld * (7 + 2 * 30) + (e * 8 + 255) // 256 * 256 + 8192
+    assert lib.gbs_adjoint_workspace_bytes(nx, ny, nz, n, 1) == fld * (7 + 30 + 1) + (e * 8 + 255) // 256 * 256 + 8192
     assert lib.gbs_adjoint_workspace_bytes(nx, ny, nz, 0, 0) == 0
     vel = ctypes.c_void_p(1 << 20)
     work = ctypes.c_void_p(1 << 24)
