@@ -284,6 +284,12 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
     __shared__ int s_src_x[kMaxFusedSrc], s_src_y[kMaxFusedSrc], s_src_z[kMaxFusedSrc];
     __shared__ float s_src_f[kMaxFusedSrc];
     __shared__ float s_red[C::NT / 32];
+    // absorbing layer: A, B by distance, in shared memory (threads look up
+    // different distances; divergent constant-bank reads would serialise)
+    __shared__ float2 s_ab[MODE == kWaveAbsorb ? kMaxAbsorb : 1];
+    if constexpr (MODE == kWaveAbsorb)
+        for (int i = threadIdx.x; i < p.ab.width; i += C::NT)
+            s_ab[i] = make_float2(p.ab.A[i], p.ab.B[i]);
 
     const Grid &g = p.g;
     const int tid = threadIdx.x;
@@ -427,6 +433,12 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
         const bool xin = gx < g.nx;
         T *out_base = static_cast<T *>(p.out[parity]) + (H + gx) + g.px * (H + gy);
         const int64_t plane_stride = g.px * g.py;
+        // absorbing layer (kWaveAbsorb): sizes in 32 bits and whether the tile
+        // lies inside the layer's inner boundary in x and y
+        const int ab_nx = (int)g.nx, ab_ny = (int)g.ny, ab_nz = (int)g.nz;
+        const bool ab_tile_in = MODE == kWaveAbsorb && tx0 >= p.ab.width && tx0 + kTX <= g.nx - p.ab.width &&
+                                ty0 >= p.ab.width && ty0 + TY <= g.ny - p.ab.width;
+        (void)ab_nx; (void)ab_ny; (void)ab_nz; (void)ab_tile_in;
 
         // 16-bit: halo groups of 4 elements this thread converts each plane
         // (element offsets in the box); slots past the last group repeat earlier
@@ -598,19 +610,22 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
                                 // absorbing layer: u_next = A (2u - B u_prev + c lap), A, B by the
                                 // distance d < width to the nearest absorbing face (rare, uniform test first)
                                 const int aw = p.ab.width;
-                                if (aw > 0) {
-                                    const int64_t yy = gy + r;
-                                    const int64_t dzk = p.ab.free_top ? (g.nz - 1 - k) : min((int64_t)k, g.nz - 1 - k);
-                                    const int64_t dyz = min(min(yy, g.ny - 1 - yy), dzk);
-                                    if (dyz < aw || gx < aw || gx + 3 >= g.nx - aw) {
+                                const int dzk = p.ab.free_top ? ab_nz - 1 - k : min(k, ab_nz - 1 - k);
+                                // uniform over the CTA: the whole tile of this plane is inside
+                                if (!(ab_tile_in && dzk >= aw)) {
+                                    const int yy = (int)gy + r;
+                                    const int dyz = min(min(yy, ab_ny - 1 - yy), dzk);
+                                    const int gxi = (int)gx;
+                                    if (dyz < aw || gxi < aw || gxi + 3 >= ab_nx - aw) {
                                         float4 A4, B4;
                                         float *pa = &A4.x, *pb = &B4.x;
 #pragma unroll
                                         for (int e = 0; e < 4; ++e) {
-                                            int64_t d = min(dyz, min(gx + e, g.nx - 1 - gx - e));
+                                            int d = min(dyz, min(gxi + e, ab_nx - 1 - gxi - e));
                                             d = d < 0 ? 0 : d;   // lanes past the interior are not stored
-                                            pa[e] = d < aw ? p.ab.A[d] : 1.f;
-                                            pb[e] = d < aw ? p.ab.B[d] : 1.f;
+                                            const float2 ab = d < aw ? s_ab[d] : make_float2(1.f, 1.f);
+                                            pa[e] = ab.x;
+                                            pb[e] = ab.y;
                                         }
                                         t_l = sub2(add2(lo(cen), lo(cen)), mul2(lo(B4), lo(up)));
                                         t_h = sub2(add2(hi(cen), hi(cen)), mul2(hi(B4), hi(up)));
