@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--adj-shots", type=int, default=8, help="adjoint form: shots")
     ap.add_argument("--batch-shots", type=int, default=64, help="batched form: shots")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--ref-leapfrog", type=int, default=2, help="oracle leapfrog steps per reference step")
+    ap.add_argument("--ref-leapfrog", type=int, default=16, help="oracle leapfrog steps per reference step")
     return ap.parse_args()
 
 
