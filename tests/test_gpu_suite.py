@@ -122,3 +122,20 @@ def test_full_size_sampled(name, n):
     got = np.array([oh[k + hz, j + H, i + H] for i, j, k in pts], np.float64)
     bound = len(fp) * U * absum / abs(divisor) + U * np.abs(want) + 1e-37
     assert np.all(np.abs(got - want) <= bound), float(np.max(np.abs(got - want) / bound))
+
+
+@pytest.mark.parametrize("r", [1, 3])
+def test_star3d_with_divisor_takes_the_window_kernel(r):
+    """3D stars with a divisor run on the window kernel (the others on the
+    streaming kernel): both against the oracle."""
+    need_gpu()
+    nx, ny, nz = 68, 37, 21
+    rng = np.random.default_rng(50 + r)
+    x = rng.uniform(-1, 1, (nz + 2 * H, ny + 2 * H, nx + 2 * H)).astype(np.float32)
+    fp = oracle.footprint("star", 3, r)
+    w = rng.uniform(-1, 1, len(fp)).astype(np.float32)
+    name = f"star3d{r}r"
+    for divisor in (1.0, 3.0):
+        out = gbs.stencil_suite(to_dev(x), dims=3, shape="star", radius=r, weights=w, halo=H, divisor=divisor)
+        gbs.device_status()
+        _check(name, x, w, divisor, out.cpu().numpy())

@@ -174,3 +174,32 @@ def test_full_size_time_reversal(layered512):
     scale = float(torch.max(torch.abs(c0c)))
     err = max(float(torch.max(torch.abs(p2 - c0c))), float(torch.max(torch.abs(c2 - p0c))))
     assert err <= tol_steps(100) * scale, (err, scale)
+
+
+def test_precision_size_1024_one_step_sampled():
+    """The precision configuration's 1024^3 grid (FP32 storage): one step in
+    the launch configuration the benchmark times, at sampled points."""
+    need_gpu()
+    n, halo, h = 1024, 4, 10.0
+    vel = W.layered_velocity_torch(n, n, n, halo, W.SEED_BASE + 3, dev())
+    dt = W.dt_for_cfl(0.4, h, float(vel.max()))
+    g = torch.Generator(device=dev()).manual_seed(8)
+    inner = (slice(halo, -halo),) * 3
+    a = torch.zeros_like(vel)
+    b = torch.zeros_like(vel)
+    a[inner] = torch.rand((n, n, n), device=dev(), generator=g) * 2 - 1
+    b[inner] = torch.rand((n, n, n), device=dev(), generator=g) * 2 - 1
+    up, u = a.cpu().numpy(), b.cpu().numpy()
+    prev, cur = gbs.wave_propagate(a, b, vel, dt, h, halo, 1)
+    gbs.device_status()
+    rng = np.random.default_rng(6)
+    idx = rng.integers(0, n ** 3, 20000).astype(np.int64)
+    ii = np.array([0, 1, 63, 64, 511, 512, n - 2, n - 1])
+    extra = W.linear_index(ii[:, None, None], ii[None, :, None], ii[None, None, :], n, n).reshape(-1)
+    idx = np.concatenate([idx, extra])
+    ref = oracle.wave_points(up, u, vel.cpu().numpy(), dt, h, halo, idx)
+    c = cur.cpu().numpy()
+    i, j, k = idx % n, (idx // n) % n, idx // (n * n)
+    got = c[k + halo, j + halo, i + halo].astype(np.float64)
+    e = oracle.err_norms(got, ref)
+    assert e["norm_max_rel"] <= TOL_ONE, e
