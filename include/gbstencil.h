@@ -187,6 +187,45 @@ gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float *vel, floa
                                  const gbs_opts *opts, void *stream);
 
 /*
+ * Algorithm 1 with 2-step temporal blocking (the paper's temporal blocking,
+ * Sec. 3): the fields of gbs_wave_propagate, computed two steps per launch.
+ * In one launch every CTA streams its tile twice: one group of warps writes
+ * u^{t+1}, the other computes u^{t+2} from it as soon as the tile and its
+ * four neighbours have stored the planes it needs (block counters in the
+ * workspace; a cooperative launch keeps every CTA resident).  The second
+ * step's reads of u^{t+1}, u^t and vel are served from L2, so a pair of
+ * steps moves 20 bytes per point through DRAM instead of 32.  Both steps sum
+ * Eq. 3 in the semi-stencil order along z (the paper's `semi` template,
+ * Sec. 8), so the fields agree with gbs_wave_propagate to FP32 rounding, not
+ * bit for bit.
+ *   u_prev, u, vel, dt, h, sizes, halo, nsteps, t0, src, rec, opts
+ *                 as gbs_wave_propagate, with the same parity rule on return
+ *                 (no absorbing layer).
+ *   work          DEVICE scratch of at least gbs_tb_workspace_bytes(nx, ny,
+ *                 nz, halo) bytes (two fields and the block counters),
+ *                 16-byte aligned, not overlapping the fields, owned by the
+ *                 caller; contents on entry do not matter.
+ * Pairs of steps run fused when gbs_tb_supported() says so for the sizes,
+ * the fields are 16-byte aligned, there are at most 16 sources and
+ * opts->kernel is not 2; they run in an even number, and the remaining steps
+ * (all of them otherwise) run as gbs_wave_propagate.
+ * Errors: GBS_EINVAL (as gbs_wave_propagate, a small, misaligned or
+ * overlapping workspace, an absorbing layer), GBS_EALIGN, GBS_ECUDA.
+ */
+size_t gbs_tb_workspace_bytes(int64_t nx, int64_t ny, int64_t nz, int halo);
+gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float *vel, float dt, float h,
+                                 int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                                 int64_t t0, const gbs_src *src, const gbs_rec *rec, void *work,
+                                 size_t work_bytes, const gbs_opts *opts, void *stream);
+/*
+ * 1 when pairs of steps on this grid run fused on the current device (halo %
+ * 4 == 0 and >= 4, nx % 4 == 0, and the 64 x tile_y tiles times z-chunks fit
+ * on the device at once), with the tile height and CTA count chosen; else 0.
+ * tile_y and ctas may be NULL.
+ */
+int gbs_tb_supported(int64_t nx, int64_t ny, int64_t nz, int halo, int *tile_y, int *ctas);
+
+/*
  * The kernels of the paper's numerical-accuracy suite (Sec. 11.1, Table 4):
  *   out(i,j,k) = ( sum_q w_q in(i+dx_q, j+dy_q, k+dz_q) ) / divisor
  * over the interior, for a star (shape 0: the points on the axes within

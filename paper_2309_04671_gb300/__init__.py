@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4
 
 # Entry points declared in include/gbstencil.h (checked by the tests).
 EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
-           "gbs_wave_propagate_lp", "gbs_norms_workspace_bytes", "gbs_field_norms", "gbs_field_norms_noalloc",
+           "gbs_wave_propagate_lp", "gbs_tb_workspace_bytes", "gbs_wave_propagate_tb", "gbs_tb_supported",
+           "gbs_norms_workspace_bytes", "gbs_field_norms", "gbs_field_norms_noalloc",
            "gbs_batch_plan_create", "gbs_batch_run", "gbs_batch_plan_info", "gbs_batch_plan_destroy",
            "gbs_adjoint_workspace_bytes", "gbs_adjoint_forward", "gbs_adjoint_backward", "gbs_fwi_gradient",
            "gbs_suite_points", "gbs_stencil_suite",
@@ -100,6 +101,14 @@ def load() -> ctypes.CDLL:
         lib.gbs_wave_propagate_lp.argtypes = [vp, vp, vp, c_float, c_float, i64, i64, i64, c_int, i64, i64,
                                               ctypes.POINTER(_Src), ctypes.POINTER(_Rec), c_int, vp, ctypes.c_size_t,
                                               ctypes.POINTER(_Opts), vp]
+        lib.gbs_tb_workspace_bytes.argtypes = [i64, i64, i64, c_int]
+        lib.gbs_tb_workspace_bytes.restype = ctypes.c_size_t
+        lib.gbs_wave_propagate_tb.argtypes = [vp, vp, vp, c_float, c_float, i64, i64, i64, c_int, i64, i64,
+                                              ctypes.POINTER(_Src), ctypes.POINTER(_Rec), vp, ctypes.c_size_t,
+                                              ctypes.POINTER(_Opts), vp]
+        lib.gbs_wave_propagate_tb.restype = c_int
+        lib.gbs_tb_supported.argtypes = [i64, i64, i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+        lib.gbs_tb_supported.restype = c_int
         lib.gbs_norms_workspace_bytes.argtypes = [i64, i64]
         lib.gbs_norms_workspace_bytes.restype = ctypes.c_size_t
         lib.gbs_field_norms.argtypes = [vp, vp, i64, i64, i64, c_int, vp, vp, ctypes.c_size_t, vp]
@@ -352,6 +361,51 @@ def _wave_propagate_host(u_prev, u, vel, dt, h, halo, nsteps, *, t0, src_idx, sr
         rec_trace.copy_(d_tr, non_blocking=True)
     torch.cuda.current_stream().synchronize()
     return u_prev, u
+
+
+def tb_workspace_bytes(nx: int, ny: int, nz: int, halo: int) -> int:
+    """Bytes of device scratch gbs_wave_propagate_tb needs (two fields and the progress words)."""
+    return int(load().gbs_tb_workspace_bytes(int(nx), int(ny), int(nz), int(halo)))
+
+
+def tb_workspace(u: torch.Tensor, halo: int) -> torch.Tensor:
+    """A device byte tensor large enough for wave_propagate_tb on fields shaped like u."""
+    nx, ny, nz = _dims(u, halo)
+    return torch.empty(tb_workspace_bytes(nx, ny, nz, halo), dtype=torch.uint8, device=u.device)
+
+
+def tb_supported(nx: int, ny: int, nz: int, halo: int) -> tuple[bool, int, int]:
+    """(fused, tile_y, ctas): whether pairs of steps run fused on this grid on the current device."""
+    ty, ctas = ctypes.c_int(0), ctypes.c_int(0)
+    ok = load().gbs_tb_supported(int(nx), int(ny), int(nz), int(halo), ctypes.byref(ty), ctypes.byref(ctas))
+    return bool(ok), int(ty.value), int(ctas.value)
+
+
+def wave_propagate_tb(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, dt: float, h: float,
+                      halo: int, nsteps: int, *, t0: int = 0, src_idx=None, src_amp=None, rec_idx=None,
+                      rec_trace=None, work: Optional[torch.Tensor] = None, kernel: int = 0,
+                      use_graph: bool = False, stream=None):
+    """Algorithm 1 with 2-step temporal blocking: the fields of wave_propagate
+    (to FP32 rounding: the z sums run in the semi-stencil order), with pairs
+    of steps fused into one launch.
+
+    Returns (prev, cur) as wave_propagate.  ``work`` is device scratch of at
+    least tb_workspace_bytes(...) bytes (allocated per call if None).
+    """
+    p = [_field(t, n) for t, n in ((u_prev, "u_prev"), (u, "u"), (vel, "vel"))]
+    _same_shape(u, u_prev, vel)
+    nx, ny, nz = _dims(u, halo)
+    if work is None:
+        work = tb_workspace(u, halo)
+    if not (work.is_cuda and work.is_contiguous()):
+        raise ValueError("work must be a contiguous device tensor")
+    src = _make_src(src_idx, src_amp)
+    rec = _make_rec(rec_idx, rec_trace)
+    opts = _opts(kernel, 0, 0, use_graph)
+    _check(load().gbs_wave_propagate_tb(p[0], p[1], p[2], float(dt), float(h), nx, ny, nz, halo, int(nsteps),
+                                        int(t0), _ptr(src), _ptr(rec), work.data_ptr(),
+                                        work.numel() * work.element_size(), ctypes.byref(opts), _stream(stream)))
+    return (u, u_prev) if nsteps % 2 else (u_prev, u)
 
 
 def lp_workspace_bytes(nx: int, ny: int, nz: int) -> int:

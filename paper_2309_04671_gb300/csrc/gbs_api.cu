@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "gbs_internal.cuh"
+#include "gbs_wf.cuh"
 
 namespace gbs {
 namespace {
@@ -592,6 +593,160 @@ extern "C" gbs_status gbs_wave_propagate(float *u_prev, float *u, const float *v
     return graph ? run_captured(st, enqueue) : enqueue();
 }
 
+namespace gbs {
+namespace {
+// Workspace of the time-blocked propagation: two fields in the caller's
+// layout (u^{t+1}, u^{t+2} of every other pair) and the block counters.
+struct TbLayout {
+    size_t off_w1, off_w2, off_words, total;
+};
+TbLayout tb_layout(const Grid &g)
+{
+    const size_t n = (size_t)field_elems(g) * 4;
+    TbLayout L;
+    L.off_w1 = 0;
+    L.off_w2 = round256(n);
+    L.off_words = L.off_w2 + round256(n);
+    L.total = L.off_words + (size_t)kWfMaxWords * 4;
+    return L;
+}
+}  // namespace
+}  // namespace gbs
+
+extern "C" size_t gbs_tb_workspace_bytes(int64_t nx, int64_t ny, int64_t nz, int halo)
+{
+    if (check_dims(nx, ny, nz, halo) != GBS_OK)
+        return 0;
+    return tb_layout(dense_grid(nx, ny, nz, halo)).total;
+}
+
+extern "C" int gbs_tb_supported(int64_t nx, int64_t ny, int64_t nz, int halo, int *tile_y, int *ctas)
+{
+    t_err[0] = 0;
+    if (check_dims(nx, ny, nz, halo) != GBS_OK || halo < 4 || nx == 0 || ny == 0 || nz == 0)
+        return 0;
+    const Grid g = dense_grid(nx, ny, nz, halo);
+    WfShape sh;
+    if (!tma_shape_ok(g) || !wf_shape(g, &sh))
+        return 0;
+    if (tile_y)
+        *tile_y = sh.tile_y;
+    if (ctas)
+        *ctas = sh.ctas;
+    return 1;
+}
+
+extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float *vel, float dt, float h,
+                                            int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                                            int64_t t0, const gbs_src *src, const gbs_rec *rec, void *work,
+                                            size_t work_bytes, const gbs_opts *opts, void *stream)
+{
+    t_err[0] = 0;
+    gbs_status s = check_dims(nx, ny, nz, halo);
+    if (s != GBS_OK)
+        return s;
+    if (nsteps < 0 || t0 < 0)
+        return fail(GBS_EINVAL, "nsteps and t0 must be >= 0");
+    if ((s = check_src_rec(src, rec)) != GBS_OK)
+        return s;
+    if (absorb_requested(opts))
+        return fail(GBS_EINVAL, "the time-blocked propagation has no absorbing layer");
+    if (nx == 0 || ny == 0 || nz == 0 || nsteps == 0)
+        return GBS_OK;
+    const Grid g = dense_grid(nx, ny, nz, halo);
+    if (u_prev == u)
+        return fail(GBS_EINVAL, "u_prev and u are the same buffer");
+    if ((s = check_wave_fields(g, u_prev, u, u_prev, vel, dt, h)) != GBS_OK)
+        return s;
+    if (overlap(u_prev, u, field_elems(g)))
+        return fail(GBS_EINVAL, "u_prev and u overlap");
+    const TbLayout L = tb_layout(g);
+    if (!work || work_bytes < L.total || !aligned16(work))
+        return fail(GBS_EINVAL, "workspace needs %zu bytes, 16-byte aligned (gbs_tb_workspace_bytes)", L.total);
+    const char *wb = static_cast<const char *>(work);
+    const int64_t fe = field_elems(g);
+    for (const float *f : {static_cast<const float *>(u_prev), static_cast<const float *>(u), vel}) {
+        const char *fb = reinterpret_cast<const char *>(f);
+        if (fb < wb + L.total && wb < fb + fe * 4)
+            return fail(GBS_EINVAL, "workspace overlaps a field");
+    }
+    WfShape sh{};
+    const bool fused = tma_shape_ok(g) && aligned16(u_prev) && aligned16(u) && aligned16(vel) &&
+                       (!src || src->n <= kMaxFusedSrc) && !(opts && opts->kernel == 2) && wf_shape(g, &sh);
+    // pairs run in an even number so the levels end in (u_prev, u); the rest are single steps
+    int64_t npairs = fused ? nsteps / 2 : 0;
+    if (npairs & 1)
+        --npairs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (npairs > 0) {
+        float *w1 = reinterpret_cast<float *>(static_cast<char *>(work) + L.off_w1);
+        float *w2 = reinterpret_cast<float *>(static_cast<char *>(work) + L.off_w2);
+        unsigned *words = reinterpret_cast<unsigned *>(static_cast<char *>(work) + L.off_words);
+        const int ty = sh.tile_y;
+        // parity 0 reads (u_prev, u) and writes (w1, w2); parity 1 the reverse
+        float *lv[2][4] = {{u_prev, u, w1, w2}, {w1, w2, u_prev, u}};
+        WfMaps maps[2];
+        for (int q = 0; q < 2; ++q) {
+            float *pr = lv[q][0], *cu = lv[q][1], *c1 = lv[q][2];
+            if ((s = make_map(&maps[q].ua, cu, g, 64 + 8, ty + 8)) != GBS_OK ||
+                (s = make_map(&maps[q].pa, pr, g, 64, ty)) != GBS_OK ||
+                (s = make_map(&maps[q].ub, c1, g, 64 + 8, ty + 8)) != GBS_OK ||
+                (s = make_map(&maps[q].pb, cu, g, 64, ty)) != GBS_OK ||
+                (s = make_map(&maps[q].vel, vel, g, 64, ty)) != GBS_OK)
+                return s;
+        }
+        WfParams p;
+        memset(&p, 0, sizeof(p));
+        p.g = g;
+        p.cf = wave_coeffs();
+        p.s = (float)((double)dt / (double)h);
+        p.dt = dt;
+        if (src && src->n > 0) {
+            p.src_idx = src->idx;
+            p.src_amp = src->amp;
+            p.src_nt = src->nt;
+            p.nsrc = (int)src->n;
+        }
+        p.inx = nx;
+        p.iny = ny;
+        p.words = words;
+        cudaError_t e = wf_prepare(ty);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "kernel attributes");
+        auto enqueue = [&]() -> gbs_status {
+            cudaError_t r = cudaMemsetAsync(words, 0, (size_t)sh.ctas * sh.nblk * 4, st);
+            if (r != cudaSuccess)
+                return cuda_fail(r, "block counters");
+            if ((r = launch_zero_shell(w1, (int64_t)((L.off_w2 - L.off_w1) / 4), 2, g, st)) != cudaSuccess)
+                return cuda_fail(r, "workspace halo");
+            for (int64_t i = 0; i < npairs; ++i) {
+                const int q = (int)(i & 1);
+                WfParams pi = p;
+                pi.out[0] = lv[q][2];
+                pi.out[1] = lv[q][3];
+                pi.epoch = (unsigned)(i + 1);
+                pi.t = t0 + 2 * i;
+                cudaEvent_t e0 = prof_begin(st);
+                r = launch_wf(sh, maps[q], pi, st);
+                prof_end(e0, st);
+                if (r != cudaSuccess)
+                    return cuda_fail(r, "time-blocked launch");
+                if ((r = launch_record(g, lv[q][2], rec, pi.t, st)) != cudaSuccess ||
+                    (r = launch_record(g, lv[q][3], rec, pi.t + 1, st)) != cudaSuccess)
+                    return cuda_fail(r, "receiver launch");
+            }
+            return GBS_OK;
+        };
+        const bool graph = opts && opts->use_graph && st != nullptr;
+        if ((s = graph ? run_captured(st, enqueue) : enqueue()) != GBS_OK)
+            return s;
+    }
+    const int64_t rest = nsteps - 2 * npairs;
+    if (rest == 0)
+        return GBS_OK;
+    return gbs_wave_propagate(u_prev, u, vel, dt, h, nx, ny, nz, halo, rest, t0 + 2 * npairs, src, rec, opts, stream);
+}
+
 extern "C" size_t gbs_lp_workspace_bytes(int64_t nx, int64_t ny, int64_t nz)
 {
     if (nx < 0 || ny < 0 || nz < 0)
@@ -771,7 +926,8 @@ extern "C" gbs_status gbs_device_status(void *stream)
     const unsigned a = tma_status_take(st);
     const unsigned b = misc_status_take(st);
     const unsigned c = suite_status_take(st);
-    const unsigned v = a ? a : (b ? b : c);
+    const unsigned d = wf_status_take(st);
+    const unsigned v = a ? a : (b ? b : (c ? c : d));
     if (v != 0)
         return fail((gbs_status)v, "device status %u", v);
     return GBS_OK;

@@ -1,0 +1,762 @@
+// Two leapfrog steps (Eq. 2, Algorithm 1) fused in one launch on sm_103a:
+// 2-step temporal blocking (the paper's temporal blocking, Sec. 3) without
+// recomputing a halo.
+//
+// Each CTA owns a 64 x TY tile of the interior xy plane and a z range, and
+// runs two TMA-fed 2.5D streaming pipelines over it:
+//   stage A computes u^{t+1} = 2u^t - u^{t-1} + (V dt)^2 lap u^t (+ sources)
+//           from u^t, u^{t-1} and vel and stores it;
+//   stage B computes u^{t+2} from u^{t+1}, u^t and vel.  A u^{t+1} box
+//           reaches 4 points into the four neighbouring tiles (its corners
+//           belong to diagonal tiles, which the star never reads), so stage
+//           B copies a block of planes only once this tile and those
+//           neighbours have stored it.
+// Each stage has compute warps and one copy-issuing warp (warp
+// specialisation).  The issuing thread keeps the rings full: it waits
+// (non-blocking tests) for a free stage, issues the TMA copy, and for stage
+// A publishes stored blocks; the compute warps wait only on "full"
+// mbarriers and release stages on "empty" mbarriers.
+//
+// Publication.  Stage-A compute threads fence their u^{t+1} stores for the
+// async proxy (fence.proxy.async.global) and arrive on a "block stored"
+// barrier; the issuing thread then executes one GPU-scope fence and adds 1
+// to the block's counter of every tile that reads it.  Stage B's issuing
+// thread copies a block once its counter equals (tiles it covers) x
+// (launches so far) (acquire, then fence.proxy.async.global).
+//
+// The grid is launched cooperatively, so every CTA is resident and every
+// wait ends once the stage-A warps it waits for have run; all waits are
+// bounded.  Stage B reads u^{t+1} soon after stage A stored it and u^t, vel
+// soon after stage A read them; those copies carry an L2 evict_last policy
+// and the last reads evict_first, so stage B is served from L2 and DRAM
+// moves u^t, u^{t-1}, vel (12 B) and u^{t+1}, u^{t+2} (8 B) per point: 20 B
+// per two updates instead of 32.
+//
+// Semi-stencil z sweep (the paper's `semi` template, Sec. 8).  A thread
+// uses each plane only when it lands: for its points it forms the new
+// accumulator c0 u(j) + sum_m c_m [x, y neighbours at distance m of plane j
+// + u(j - m)], and adds c_m u(j) to the pending accumulators of planes
+// j - m, so the accumulator of plane j - R is complete.  A u stage is free
+// right after its plane lands (no R-plane residency), which leaves room for
+// deep rings of both stages in shared memory.  The sums are those of Eq. 3
+// in another order than the single-step kernel, so the fields agree with it
+// to FP32 rounding.
+//
+// z-chunks.  When the tiles alone do not fill the device, the z range is
+// split; stage A of a chunk then also computes the R planes either side of
+// it (stage B's z halo).  Neighbouring chunks compute those planes from the
+// same inputs with the same arithmetic and store the same bits.
+#include "gbs_wf.cuh"
+
+namespace gbs {
+namespace {
+
+__device__ unsigned g_status_wf = 0;
+
+constexpr int kR = 4;       // radius of the wave operator
+constexpr int kTX = 64;     // tile width (16 threads x 4 points)
+constexpr int kVY = 2;      // rows per thread
+
+template <int TY>
+struct WfCfg {
+    static constexpr int NTX = kTX / 4;
+    static constexpr int NT = NTX * (TY / kVY);     // threads per stage
+    static constexpr int BW = kTX + 8;              // u box: 4-wide x halo each side
+    static constexpr int BH = TY + 2 * kR;
+    static constexpr int L_BYTES = BW * BH * 4;
+    static constexpr int L_STRIDE = (L_BYTES + 127) / 128 * 128;
+    static constexpr int PVU_BYTES = kTX * TY * 4;  // u_prev tile; the vel tile follows
+    static constexpr int PV_BYTES = 2 * PVU_BYTES;
+    static constexpr int PV_STRIDE = (PV_BYTES + 127) / 128 * 128;
+    // Ring depths.  A u stage holds a plane from its arrival until it has been
+    // the stencil centre (R planes later), so SL = R + 1 + planes in flight.
+    // Stage A streams from DRAM and keeps more planes in flight than stage B,
+    // whose loads are mostly served from L2.
+    static constexpr bool TALL = TY >= 24;
+    static constexpr int SL_A = TALL ? 6 : 8;
+    static constexpr int SP_A = TALL ? 5 : 6;
+    static constexpr int SL_B = TALL ? 4 : 6;
+    static constexpr int SP_B = TALL ? 3 : 4;
+    static constexpr size_t OFF_LA = 0;
+    static constexpr size_t OFF_PA = OFF_LA + (size_t)SL_A * L_STRIDE;
+    static constexpr size_t OFF_LB = OFF_PA + (size_t)SP_A * PV_STRIDE;
+    static constexpr size_t OFF_PB = OFF_LB + (size_t)SL_B * L_STRIDE;
+    static constexpr size_t OFF_BAR = OFF_PB + (size_t)SP_B * PV_STRIDE;
+    static constexpr size_t SMEM = OFF_BAR + (size_t)(2 * (SL_A + SP_A + SL_B + SP_B) + 8) * 8;
+    static_assert(NT % 32 == 0, "a stage is whole warps");
+    static_assert(SL_A >= 2 && SL_B >= 2 && SP_A >= 2 && SP_B >= 2, "one stage in use, one in flight");
+};
+
+// ---- packed FP32 pairs (f32x2) ----
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 r, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2 lo(const float4 &v) { return pk(v.x, v.y); }
+__device__ __forceinline__ f2 hi(const float4 &v) { return pk(v.z, v.w); }
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ f2 xpair(const float4 &lf, const float4 &cen, const float4 &rt, int i)
+{
+    const float w[12] = {lf.x, lf.y, lf.z, lf.w, cen.x, cen.y, cen.z, cen.w, rt.x, rt.y, rt.z, rt.w};
+    return pk(w[i], w[i + 1]);
+}
+__device__ __forceinline__ float at(const float4 &v, int e)
+{
+    return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void add_at(float4 &v, int e, float a)
+{
+    if (e == 0) v.x += a;
+    else if (e == 1) v.y += a;
+    else if (e == 2) v.z += a;
+    else v.w += a;
+}
+
+// ---- barriers, progress counters, proxy fence ----
+__device__ __forceinline__ void stage_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_add_relaxed(unsigned *p, unsigned v)
+{
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// L2 eviction priority of an access (createpolicy): data read for the last
+// time in a launch goes first, so that the data stage B re-reads stays.
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// 3D tiled TMA load with an L2 cache policy.
+__device__ __forceinline__ void tma_load_3d_pol(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar,
+                                                uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ void st_pairs_pol(float *p, f2 a, f2 b, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.b64 [%0], {%1, %2}, %3;" ::"l"(p), "l"(a), "l"(b), "l"(pol) : "memory");
+}
+
+// Non-blocking test of a barrier phase (try_wait may suspend the thread).
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+constexpr int kPB = kWfBlock;   // stage-A output planes per published block
+constexpr int kNS = 8;   // ring of "block stored" barriers
+
+// Planes of one stage of a CTA.  Stage A covers the chunk and R planes
+// either side of it (stage B's z halo), clamped to the interior.
+struct StageGeo {
+    int a0, a1;          // stage A's output planes
+    int o0, nzc;         // this stage's first output plane, count
+    int pfirst, nplanes; // first u plane streamed, count
+};
+__device__ __forceinline__ StageGeo stage_geo(const WfParams &p, int chunk, int stage)
+{
+    StageGeo s;
+    const int nz = (int)p.g.nz;
+    const int z0c = chunk * p.zchunk, z1c = min(nz, z0c + p.zchunk);
+    s.a0 = max(0, z0c - kR);
+    s.a1 = min(nz, z1c + kR);
+    s.o0 = stage == 0 ? s.a0 : z0c;
+    s.nzc = (stage == 0 ? s.a1 : z1c) - s.o0;
+    s.pfirst = s.o0 - kR;
+    s.nplanes = s.nzc + 2 * kR;
+    return s;
+}
+
+// Shared-memory rings and barriers of one stage.  full_*: the copy landed
+// (expect_tx).  empty_*: every consumer warp is done with the stage.
+// stored: every stage-A consumer thread has stored (and fenced) a block.
+struct Ring {
+    unsigned char *land, *pv;
+    uint64_t *full_u, *empty_u, *full_pv, *empty_pv, *stored;
+};
+
+// The tiles whose u^{t+1} a stage-B box of `tile` covers: itself and its x, y
+// neighbours (the relation is symmetric: they are also the tiles whose
+// stage B reads this tile's u^{t+1}).
+__device__ __forceinline__ int tile_deps(const WfParams &p, int tile, int *d)
+{
+    const int ix = tile % p.tiles_x, iy = tile / p.tiles_x;
+    int n = 0;
+    d[n++] = tile;
+    if (ix > 0) d[n++] = tile - 1;
+    if (ix + 1 < p.tiles_x) d[n++] = tile + 1;
+    if (iy > 0) d[n++] = tile - p.tiles_x;
+    if (iy + 1 < p.tiles_y) d[n++] = tile + p.tiles_x;
+    return n;
+}
+
+// Warp-uniform bounded wait on a full barrier.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
+{
+    const bool ok = mbar_wait_bounded(bar, parity, &g_status_wf);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Compute warps of one stage (STAGE 0 writes u^{t+1}, STAGE 1 u^{t+2}), in
+// the semi-stencil form: each plane is used only when it
+// arrives.  At arrival j a thread forms, for its points, the new accumulator
+//   acc(j) = c0 u(j) + sum_m c_m [x, y neighbours at distance m in plane j]
+//                    + sum_m c_m u(j - m)
+// and adds c_m u(j) to the pending accumulators of planes j - m; the
+// accumulator of plane j - R is then complete.  The queue holds u and the
+// accumulators of the last R planes; the u stage is free after the arrival.
+template <int TY, int STAGE>
+__device__ __forceinline__ void wf_consumer(const WfParams &p, const Ring &rg, const int64_t tx0, const int64_t ty0,
+                                            const int chunk, int *s_nsrc, int *s_src_x, int *s_src_y, int *s_src_z,
+                                            float *s_src_f)
+{
+    using C = WfCfg<TY>;
+    constexpr int SL = STAGE == 0 ? C::SL_A : C::SL_B;
+    constexpr int SP = STAGE == 0 ? C::SP_A : C::SP_B;
+    const Grid &g = p.g;
+    const int tid = threadIdx.x - STAGE * C::NT;
+    const int lane = threadIdx.x & 31;
+    const int tx = tid % C::NTX, ty = tid / C::NTX;
+    const int H = g.halo;
+    const StageGeo sg = stage_geo(p, chunk, STAGE);
+    const int o0 = sg.o0, nzc = sg.nzc, nplanes = sg.nplanes;
+    const int64_t t = p.t + STAGE;
+
+    const float *amp_row = (p.src_amp != nullptr && t >= 0 && t < p.src_nt) ? p.src_amp + t * p.nsrc : nullptr;
+    if (amp_row != nullptr && tid < p.nsrc) {
+        const int64_t lin = p.src_idx[tid];
+        if (lin < 0 || lin >= p.inx * p.iny * g.nz) {
+            atomicCAS(&g_status_wf, 0u, (unsigned)GBS_EINVAL);
+        } else {
+            const int64_t i = lin % p.inx, j = (lin / p.inx) % p.iny, k = lin / (p.inx * p.iny);
+            if (i >= tx0 && i < tx0 + kTX && j >= ty0 && j < ty0 + TY && k >= o0 && k < o0 + nzc) {
+                const int slot = atomicAdd(s_nsrc, 1);
+                s_src_x[slot] = (int)(i - tx0);
+                s_src_y[slot] = (int)(j - ty0);
+                s_src_z[slot] = (int)k;
+                s_src_f[slot] = amp_row[tid];
+            }
+        }
+    }
+    stage_sync(1 + STAGE, C::NT);
+
+    const float c0 = p.cf.c[0][0] + p.cf.c[1][0] + p.cf.c[2][0];
+    const f2 C0 = pk(c0, c0);
+    f2 CX[kR + 1];
+#pragma unroll
+    for (int m = 1; m <= kR; ++m)
+        CX[m] = pk(p.cf.c[0][m], p.cf.c[0][m]);
+    const f2 S2 = pk(p.s, p.s);
+    const int nsrc_cta = *s_nsrc;
+    const int lx = 4 + 4 * tx;
+    const int ly = kR + kVY * ty;
+    const int64_t gx = tx0 + 4 * tx;
+    const int64_t gy = ty0 + kVY * ty;
+    const bool xin = gx < g.nx;
+    float *out_base = p.out[STAGE] + (H + gx) + g.px * (H + gy);
+    const int64_t plane_stride = g.px * g.py;
+    const uint64_t pol_out = STAGE == 0 ? policy_evict_last() : policy_evict_first();
+
+    // V[a][r]: u of plane j - R + a; A*[a][r]: pending accumulator of plane j - R + a (a = 0..R-1)
+    float4 V[kR][kVY];
+    f2 AL[kR][kVY], AH[kR][kVY];
+#pragma unroll
+    for (int a = 0; a < kR; ++a)
+#pragma unroll
+        for (int r = 0; r < kVY; ++r) {
+            V[a][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            AL[a][r] = 0ull;
+            AH[a][r] = 0ull;
+        }
+
+    for (int j = 0; j < nplanes; ++j) {
+        const int st = j % SL;
+        if (!warp_wait(&rg.full_u[st], (uint32_t)((j / SL) & 1)))
+            return;
+        const float *su = reinterpret_cast<const float *>(rg.land + st * C::L_STRIDE);
+        float4 cu[kVY];
+#pragma unroll
+        for (int r = 0; r < kVY; ++r)
+            cu[r] = ld4(su + (ly + r) * C::BW + lx);
+        f2 NL[kVY], NH[kVY];
+#pragma unroll
+        for (int r = 0; r < kVY; ++r) {
+            const float4 lf = ld4(su + (ly + r) * C::BW + lx - 4);
+            const float4 rt = ld4(su + (ly + r) * C::BW + lx + 4);
+            const float4 cen = cu[r];
+            f2 acc_l = mul2(C0, lo(cen)), acc_h = mul2(C0, hi(cen));
+            f2 acc2_l = 0ull, acc2_h = 0ull;
+#pragma unroll
+            for (int m = 1; m <= kR; ++m) {
+                const float4 yp = (r + m < kVY) ? cu[r + m] : ld4(su + (ly + r + m) * C::BW + lx);
+                const float4 ym = (r - m >= 0) ? cu[r - m] : ld4(su + (ly + r - m) * C::BW + lx);
+                f2 xs_l, xs_h;
+                if (m & 1) {
+                    const float w[12] = {lf.x, lf.y, lf.z, lf.w, cen.x, cen.y, cen.z, cen.w, rt.x, rt.y, rt.z, rt.w};
+                    xs_l = pk(w[4 + m] + w[4 - m], w[5 + m] + w[5 - m]);
+                    xs_h = pk(w[6 + m] + w[6 - m], w[7 + m] + w[7 - m]);
+                } else {
+                    xs_l = add2(xpair(lf, cen, rt, 4 + m), xpair(lf, cen, rt, 4 - m));
+                    xs_h = add2(xpair(lf, cen, rt, 6 + m), xpair(lf, cen, rt, 6 - m));
+                }
+                const f2 ys_l = add2(lo(yp), lo(ym)), ys_h = add2(hi(yp), hi(ym));
+                const float4 zb = V[kR - m][r];   // u(j - m)
+                f2 &al = (m & 1) ? acc_l : acc2_l;
+                f2 &ah = (m & 1) ? acc_h : acc2_h;
+                al = fma2(CX[m], add2(add2(xs_l, ys_l), lo(zb)), al);
+                ah = fma2(CX[m], add2(add2(xs_h, ys_h), hi(zb)), ah);
+                // forward term of plane j - m
+                AL[kR - m][r] = fma2(CX[m], lo(cen), AL[kR - m][r]);
+                AH[kR - m][r] = fma2(CX[m], hi(cen), AH[kR - m][r]);
+            }
+            NL[r] = add2(acc_l, acc2_l);
+            NH[r] = add2(acc_h, acc2_h);
+        }
+        // this warp is done with plane j's stage
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(&rg.empty_u[st]);
+
+        if (j >= 2 * kR) {
+            // plane j - R is complete: output plane o0 + cj
+            const int cj = j - 2 * kR;
+            const int k = o0 + cj;
+            const int sp = cj % SP;
+            if (!warp_wait(&rg.full_pv[sp], (uint32_t)((cj / SP) & 1)))
+                return;
+            const float *pvu = reinterpret_cast<const float *>(rg.pv + sp * C::PV_STRIDE);
+            const float *pvv = reinterpret_cast<const float *>(rg.pv + sp * C::PV_STRIDE + C::PVU_BYTES);
+            f2 res_l[kVY], res_h[kVY];
+            float4 vel4[kVY];
+#pragma unroll
+            for (int r = 0; r < kVY; ++r) {
+                const float4 u0 = V[0][r];
+                const float4 up = ld4(pvu + (kVY * ty + r) * kTX + 4 * tx);
+                vel4[r] = ld4(pvv + (kVY * ty + r) * kTX + 4 * tx);
+                const f2 vs_l = mul2(lo(vel4[r]), S2), vs_h = mul2(hi(vel4[r]), S2);
+                const f2 c_l = mul2(vs_l, vs_l), c_h = mul2(vs_h, vs_h);
+                const f2 t_l = sub2(add2(lo(u0), lo(u0)), lo(up));
+                const f2 t_h = sub2(add2(hi(u0), hi(u0)), hi(up));
+                res_l[r] = fma2(c_l, AL[0][r], t_l);
+                res_h[r] = fma2(c_h, AH[0][r], t_h);
+            }
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&rg.empty_pv[sp]);
+            if (nsrc_cta > 0) {
+                for (int i = 0; i < nsrc_cta; ++i) {
+                    if (s_src_z[i] != k || (s_src_x[i] >> 2) != tx)
+                        continue;
+                    const int e = s_src_x[i] & 3;
+#pragma unroll
+                    for (int r = 0; r < kVY; ++r) {
+                        if (s_src_y[i] == kVY * ty + r) {
+                            const float vdt = at(vel4[r], e) * p.dt;
+                            float4 v;
+                            upk(res_l[r], v.x, v.y);
+                            upk(res_h[r], v.z, v.w);
+                            add_at(v, e, vdt * vdt * s_src_f[i]);
+                            res_l[r] = lo(v);
+                            res_h[r] = hi(v);
+                        }
+                    }
+                }
+            }
+            float *dst = out_base + plane_stride * (int64_t)(H + k);
+#pragma unroll
+            for (int r = 0; r < kVY; ++r)
+                if (xin && gy + r < g.ny)
+                    st_pairs_pol(dst + r * g.px, res_l[r], res_h[r], pol_out);
+            if (STAGE == 0 && (cj % kPB == kPB - 1 || cj == nzc - 1)) {
+                fence_proxy_async_global();
+                mbar_arrive(&rg.stored[(cj / kPB) % kNS]);
+            }
+        }
+        // shift: plane j becomes the newest entry
+#pragma unroll
+        for (int a = 0; a < kR - 1; ++a)
+#pragma unroll
+            for (int r = 0; r < kVY; ++r) {
+                V[a][r] = V[a + 1][r];
+                AL[a][r] = AL[a + 1][r];
+                AH[a][r] = AH[a + 1][r];
+            }
+#pragma unroll
+        for (int r = 0; r < kVY; ++r) {
+            V[kR - 1][r] = cu[r];
+            AL[kR - 1][r] = NL[r];
+            AH[kR - 1][r] = NH[r];
+        }
+    }
+}
+
+// Copy-issuing thread of one stage (lane 0 of the stage's producer warp).
+// Stage A also publishes its stored blocks: for each, one GPU-scope fence,
+// then +1 on the block's counter of every tile that reads it.  Stage B
+// issues a u^{t+1} copy once its block's counter reaches (tiles it covers)
+// x epoch.  Every wait is bounded; on a timeout the thread records
+// GBS_ETIMEOUT and waits (bounded) for the copies it issued before leaving.
+template <int TY, int STAGE>
+__device__ __forceinline__ void wf_producer(const CUtensorMap *__restrict__ pm_u,
+                                            const CUtensorMap *__restrict__ pm_prev,
+                                            const CUtensorMap *__restrict__ pm_vel, const WfParams &p,
+                                            const Ring &rg, const int64_t tx0, const int64_t ty0, const int tile,
+                                            const int chunk)
+{
+    using C = WfCfg<TY>;
+    constexpr int SL = STAGE == 0 ? C::SL_A : C::SL_B;
+    constexpr int SP = STAGE == 0 ? C::SP_A : C::SP_B;
+    const int H = p.g.halo;
+    const StageGeo sg = stage_geo(p, chunk, STAGE);
+    const int ntiles = p.tiles_x * p.tiles_y;
+    unsigned *words = p.words + (int64_t)chunk * ntiles * p.nblk;
+    int deps[5];
+    const int ndeps = tile_deps(p, tile, deps);
+    const unsigned need = (unsigned)ndeps * p.epoch;    // stage B: count of a published block
+    const int nblk_a = (sg.a1 - sg.a0 + kPB - 1) / kPB; // stage A's blocks
+    int n_u = 0, n_pv = 0, n_pub = 0, ok_blk = -1;
+    // stage A: u^t and vel are read again by stage B, u^{t-1} is not; stage B's reads are the last
+    const uint64_t pol_keep = STAGE == 0 ? policy_evict_last() : policy_evict_first();
+    const uint64_t pol_drop = policy_evict_first();
+    uint64_t t_idle = global_timer_ns();
+    bool fail = false;
+    while (n_u < sg.nplanes || n_pv < sg.nzc || (STAGE == 0 && n_pub < nblk_a)) {
+        bool prog = false;
+        if (n_u < sg.nplanes) {
+            const int st = n_u % SL;
+            bool ready = n_u < SL || mbar_test(&rg.empty_u[st], (uint32_t)((n_u / SL - 1) & 1));
+            if (ready && STAGE == 1) {
+                const int b = sg.pfirst + n_u;   // plane of u^{t+1}
+                if (b >= sg.a0 && b < sg.a1) {
+                    const int blk = (b - sg.a0) / kPB;
+                    if (blk > ok_blk) {
+                        if (ld_acquire(words + (int64_t)tile * p.nblk + blk) >= need) {
+                            ok_blk = blk;
+                            fence_proxy_async_global();
+                        } else {
+                            ready = false;
+                        }
+                    }
+                }
+            }
+            if (ready) {
+                mbar_arrive_expect_tx(&rg.full_u[st], C::L_BYTES);
+                tma_load_3d_pol(rg.land + st * C::L_STRIDE, pm_u, (int)(H + tx0 - 4), (int)(H + ty0 - kR),
+                                H + sg.pfirst + n_u, &rg.full_u[st], pol_keep);
+                ++n_u;
+                prog = true;
+            }
+        }
+        if (n_pv < sg.nzc) {
+            const int st = n_pv % SP;
+            if (n_pv < SP || mbar_test(&rg.empty_pv[st], (uint32_t)((n_pv / SP - 1) & 1))) {
+                unsigned char *dst = rg.pv + st * C::PV_STRIDE;
+                mbar_arrive_expect_tx(&rg.full_pv[st], C::PV_BYTES);
+                tma_load_3d_pol(dst, pm_prev, (int)(H + tx0), (int)(H + ty0), H + sg.o0 + n_pv, &rg.full_pv[st],
+                                pol_drop);
+                tma_load_3d_pol(dst + C::PVU_BYTES, pm_vel, (int)(H + tx0), (int)(H + ty0), H + sg.o0 + n_pv,
+                                &rg.full_pv[st], pol_keep);
+                ++n_pv;
+                prog = true;
+            }
+        }
+        if (STAGE == 0 && n_pub < nblk_a &&
+            mbar_test(&rg.stored[n_pub % kNS], (uint32_t)((n_pub / kNS) & 1))) {
+            fence_acq_rel_gpu();
+            for (int i = 0; i < ndeps; ++i)
+                red_add_relaxed(words + (int64_t)deps[i] * p.nblk + n_pub, 1u);
+            ++n_pub;
+            prog = true;
+        }
+        if (prog) {
+            t_idle = global_timer_ns();
+        } else if (global_timer_ns() - t_idle > kWaitLimitNs) {
+            atomicCAS(&g_status_wf, 0u, (unsigned)GBS_ETIMEOUT);
+            fail = true;
+            break;
+        } else {
+            __nanosleep(32);
+        }
+    }
+    if (fail) {
+        // let the copies still in flight land before the CTA's shared memory is released
+        for (int i = max(0, n_u - SL); i < n_u; ++i)
+            mbar_wait_bounded(&rg.full_u[i % SL], (uint32_t)((i / SL) & 1), &g_status_wf);
+        for (int i = max(0, n_pv - SP); i < n_pv; ++i)
+            mbar_wait_bounded(&rg.full_pv[i % SP], (uint32_t)((i / SP) & 1), &g_status_wf);
+    }
+}
+
+// CTA b: tile b % tiles, z-chunk b / tiles.  Warps: stage-A compute
+// [0, NT), stage-B compute [NT, 2 NT), then one copy-issuing warp per stage.
+template <int TY>
+__global__ void __launch_bounds__(2 * WfCfg<TY>::NT + 64, 1)
+    k_wf(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_pa,
+         const __grid_constant__ CUtensorMap tm_ub, const __grid_constant__ CUtensorMap tm_pb,
+         const __grid_constant__ CUtensorMap tm_vel, const __grid_constant__ WfParams p)
+{
+    using C = WfCfg<TY>;
+    constexpr int NW = C::NT / 32;   // compute warps per stage
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ int s_nsrc[2];
+    __shared__ int s_src_x[2][kMaxFusedSrc], s_src_y[2][kMaxFusedSrc], s_src_z[2][kMaxFusedSrc];
+    __shared__ float s_src_f[2][kMaxFusedSrc];
+    const int ntiles = p.tiles_x * p.tiles_y;
+    const int tile = (int)(blockIdx.x % (unsigned)ntiles);
+    const int chunk = (int)(blockIdx.x / (unsigned)ntiles);
+    const int64_t tx0 = (int64_t)(tile % p.tiles_x) * kTX;
+    const int64_t ty0 = (int64_t)(tile / p.tiles_x) * TY;
+
+    // Every TMA box must start on a 16-byte boundary in x.  The host only
+    // launches shapes that satisfy this; a CTA that would not records
+    // GBS_EALIGN and returns before issuing any copy (uniform over the CTA).
+    if ((((p.g.halo + tx0 - 4) * 4) & 15) != 0 || (((p.g.halo + tx0) * 4) & 15) != 0) {
+        if (threadIdx.x == 0)
+            atomicCAS(&g_status_wf, 0u, (unsigned)GBS_EALIGN);
+        return;
+    }
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
+    Ring ra, rb;
+    ra.land = smem + C::OFF_LA;
+    ra.pv = smem + C::OFF_PA;
+    ra.full_u = bars;
+    ra.empty_u = ra.full_u + C::SL_A;
+    ra.full_pv = ra.empty_u + C::SL_A;
+    ra.empty_pv = ra.full_pv + C::SP_A;
+    ra.stored = ra.empty_pv + C::SP_A;
+    rb.land = smem + C::OFF_LB;
+    rb.pv = smem + C::OFF_PB;
+    rb.full_u = ra.stored + kNS;
+    rb.empty_u = rb.full_u + C::SL_B;
+    rb.full_pv = rb.empty_u + C::SL_B;
+    rb.empty_pv = rb.full_pv + C::SP_B;
+    rb.stored = nullptr;
+    if (threadIdx.x == 0) {
+        prefetch_tmap(&tm_ua);
+        prefetch_tmap(&tm_pa);
+        prefetch_tmap(&tm_ub);
+        prefetch_tmap(&tm_pb);
+        prefetch_tmap(&tm_vel);
+        for (int i = 0; i < C::SL_A; ++i) {
+            mbar_init(&ra.full_u[i], 1);
+            mbar_init(&ra.empty_u[i], NW);
+        }
+        for (int i = 0; i < C::SP_A; ++i) {
+            mbar_init(&ra.full_pv[i], 1);
+            mbar_init(&ra.empty_pv[i], NW);
+        }
+        for (int i = 0; i < kNS; ++i)
+            mbar_init(&ra.stored[i], C::NT);
+        for (int i = 0; i < C::SL_B; ++i) {
+            mbar_init(&rb.full_u[i], 1);
+            mbar_init(&rb.empty_u[i], NW);
+        }
+        for (int i = 0; i < C::SP_B; ++i) {
+            mbar_init(&rb.full_pv[i], 1);
+            mbar_init(&rb.empty_pv[i], NW);
+        }
+        fence_mbar_init();
+        s_nsrc[0] = 0;
+        s_nsrc[1] = 0;
+    }
+    __syncthreads();
+    const int w = threadIdx.x / 32;
+    if (w < NW)
+        wf_consumer<TY, 0>(p, ra, tx0, ty0, chunk, &s_nsrc[0], s_src_x[0], s_src_y[0], s_src_z[0], s_src_f[0]);
+    else if (w < 2 * NW)
+        wf_consumer<TY, 1>(p, rb, tx0, ty0, chunk, &s_nsrc[1], s_src_x[1], s_src_y[1], s_src_z[1], s_src_f[1]);
+    else if (w == 2 * NW && (threadIdx.x & 31) == 0)
+        wf_producer<TY, 0>(&tm_ua, &tm_pa, &tm_vel, p, ra, tx0, ty0, tile, chunk);
+    else if (w == 2 * NW + 1 && (threadIdx.x & 31) == 0)
+        wf_producer<TY, 1>(&tm_ub, &tm_pb, &tm_vel, p, rb, tx0, ty0, tile, chunk);
+}
+
+template <int TY>
+cudaError_t prepare_t()
+{
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev >= 0 && dev < 64 && done[dev])
+        return cudaSuccess;
+    e = cudaFuncSetAttribute(k_wf<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WfCfg<TY>::SMEM);
+    if (e == cudaSuccess && dev >= 0 && dev < 64)
+        done[dev] = true;
+    return e;
+}
+
+// CTAs the device holds at once for tile height TY (0 on error).
+template <int TY>
+int slots_t()
+{
+    if (prepare_t<TY>() != cudaSuccess)
+        return 0;
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wf<TY>, 2 * WfCfg<TY>::NT + 64, WfCfg<TY>::SMEM) !=
+        cudaSuccess)
+        return 0;
+    return sms * per;
+}
+
+template <int TY>
+cudaError_t launch_t(const WfShape &s, const WfMaps &m, const WfParams &p, cudaStream_t st)
+{
+    cudaError_t e = prepare_t<TY>();
+    if (e != cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)s.ctas);
+    cfg.blockDim = dim3(2 * WfCfg<TY>::NT + 64);
+    cfg.dynamicSmemBytes = WfCfg<TY>::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_wf<TY>, m.ua, m.pa, m.ub, m.pb, m.vel, p);
+}
+
+}  // namespace
+
+// Shape choice.  A CTA streams its whole z range, and all CTAs run at once,
+// so the launch lasts as long as one CTA: about (planes + overhead) x tile
+// rows.  Among the tile heights and chunk counts whose CTAs all fit, take
+// the one with the least such work per CTA (a chunk adds stage A's 2R extra
+// planes; a tile row adds its 2R-row halo to the u boxes).
+bool wf_shape(const Grid &g, WfShape *s)
+{
+    const int heights[2] = {28, 16};
+    double best = 1e300;
+    bool found = false;
+    for (int h : heights) {
+        const int slots = h == 28 ? slots_t<28>() : slots_t<16>();
+        if (slots <= 0)
+            continue;
+        const int64_t tx = (g.nx + kTX - 1) / kTX, ty = (g.ny + h - 1) / h;
+        const int64_t tiles = tx * ty;
+        if (tiles <= 0 || tiles > slots)
+            continue;
+        for (int64_t c = 1; c <= g.nz && tiles * c <= slots; ++c) {
+            const int64_t zc = (g.nz + c - 1) / c;
+            if (c > 1 && zc < 16)
+                break;
+            const int64_t nblk = (zc + 2 * kR + kPB - 1) / kPB;
+            if (tiles * c * nblk > kWfMaxWords)
+                continue;
+            const double extra = c > 1 ? 2.0 * kR * 0.5 : 0.0;   // stage A's extra planes: one stage of two
+            const double cost = ((double)zc + extra) * (double)(h + kR);
+            if (cost < best * 0.999) {
+                best = cost;
+                found = true;
+                s->tile_y = h;
+                s->tiles_x = (int)tx;
+                s->tiles_y = (int)ty;
+                s->zchunk = (int)zc;
+                s->nchunks = (int)((g.nz + zc - 1) / zc);
+                s->ctas = (int)(tiles * s->nchunks);
+                s->nblk = (int)nblk;
+            }
+        }
+    }
+    return found;
+}
+
+cudaError_t wf_prepare(int tile_y) { return tile_y == 28 ? prepare_t<28>() : prepare_t<16>(); }
+
+cudaError_t launch_wf(const WfShape &s, const WfMaps &m, const WfParams &p, cudaStream_t st)
+{
+    if (s.ctas <= 0 || (int64_t)s.tiles_x * s.tiles_y * s.nchunks != s.ctas ||
+        (int64_t)s.ctas * s.nblk > kWfMaxWords || s.nblk * kPB < s.zchunk + 2 * kR)
+        return cudaErrorInvalidConfiguration;
+    WfParams q = p;
+    q.tiles_x = s.tiles_x;
+    q.tiles_y = s.tiles_y;
+    q.zchunk = s.zchunk;
+    q.nchunks = s.nchunks;
+    q.nblk = s.nblk;
+    switch (s.tile_y) {
+    case 28: return launch_t<28>(s, m, q, st);
+    case 16: return launch_t<16>(s, m, q, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+unsigned wf_status_take(cudaStream_t st)
+{
+    unsigned v = 0, zero = 0;
+    if (cudaStreamSynchronize(st) != cudaSuccess)
+        return GBS_ECUDA;
+    if (cudaMemcpyFromSymbol(&v, g_status_wf, sizeof(v)) != cudaSuccess)
+        return GBS_ECUDA;
+    if (v != 0)
+        cudaMemcpyToSymbol(g_status_wf, &zero, sizeof(zero));
+    return v;
+}
+
+}  // namespace gbs

@@ -213,3 +213,30 @@ def test_absorb_validation_before_device(lib):
                                    4, 3, 0, None, None, 1, work, 1 << 30,
                                    ctypes.byref(gbs._Opts(0, 0, 0, 0, 4, 10.0, 0)), None)
     assert lp == gbs.GBS_EINVAL
+
+
+def test_tb_workspace_and_validation(lib):
+    n = (8 + 8) ** 3 * 4
+    r256 = (n + 255) // 256 * 256
+    assert gbs.tb_workspace_bytes(8, 8, 8, 4) == 2 * r256 + (1 << 18) * 4
+    assert gbs.tb_workspace_bytes(-1, 8, 8, 4) == 0
+    # no device here: the fused path is never reported as available
+    assert gbs.tb_supported(64, 64, 64, 4) == (False, 0, 0)
+    fake = [ctypes.c_void_p(1 << 20), ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20)]
+    work = ctypes.c_void_p(1 << 26)
+    big = ctypes.c_size_t(1 << 30)
+    call = lib.gbs_wave_propagate_tb
+
+    def args(up, u, w, wb, nsteps=4, opts=None):
+        return (up, u, fake[2], ctypes.c_float(1e-3), ctypes.c_float(10.0), 8, 8, 8, 4, nsteps, 0, None, None,
+                w, wb, opts, None)
+
+    assert call(*args(fake[0], fake[0], work, big)) == gbs.GBS_EINVAL            # same buffer twice
+    assert call(*args(fake[0], fake[1], work, ctypes.c_size_t(1024))) == gbs.GBS_EINVAL   # small workspace
+    assert call(*args(fake[0], fake[1], None, big)) == gbs.GBS_EINVAL            # no workspace
+    assert call(*args(fake[0], fake[1], ctypes.c_void_p((1 << 26) + 4), big)) == gbs.GBS_EINVAL   # misaligned
+    assert call(*args(fake[0], fake[1], fake[1], big)) == gbs.GBS_EINVAL         # workspace over a field
+    absorb = ctypes.byref(gbs._Opts(0, 0, 0, 0, 4, 10.0, 0))
+    assert call(*args(fake[0], fake[1], work, big, opts=absorb)) == gbs.GBS_EINVAL
+    assert call(*args(fake[0], fake[1], work, big, nsteps=0)) == gbs.GBS_OK
+    assert call(*args(fake[0], fake[1], work, big, nsteps=-1)) == gbs.GBS_EINVAL

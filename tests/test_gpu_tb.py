@@ -1,0 +1,181 @@
+"""GPU parity of gbs_wave_propagate_tb (Algorithm 1 with 2-step temporal
+blocking) against the FP64 oracle and against the single-step path.
+
+Covers: the 64^3 constant-velocity Ricker problem with receivers, ragged
+and z-chunked grids with several sources (odd and even step counts, so
+pairs and trailing single steps both run), graph replay, restart at t0,
+the fallback for shapes the fused kernel does not take, workspace errors,
+and the full 512^3 layered workload in the launch configuration the
+benchmark times.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2309_04671_gb300 as gbs
+import workloads as W
+from gpu_util import dev, halo_mask, need_gpu, to_dev, tol_steps, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _ricker64(nsteps, nrec=64):
+    prob = W.small_constant_problem(n=64, nsteps=nsteps)
+    rng = np.random.default_rng(3)
+    rec = rng.integers(0, prob.npoints, nrec).astype(np.int64)
+    rec[0] = prob.src_idx[0]
+    return prob, rec
+
+
+def test_ricker_64_vs_oracle():
+    need_gpu()
+    prob, rec = _ricker64(20)
+    assert gbs.tb_supported(prob.nx, prob.ny, prob.nz, prob.halo)[0]
+    z = np.zeros(W.padded_shape(prob.nx, prob.ny, prob.nz, prob.halo), np.float32)
+    a, b = to_dev(z), to_dev(z)
+    trace = torch.zeros((prob.nsteps, rec.size), device=dev())
+    prev, cur = gbs.wave_propagate_tb(a, b, to_dev(prob.vel), prob.dt, prob.h, prob.halo, prob.nsteps,
+                                      src_idx=to_dev(prob.src_idx), src_amp=to_dev(prob.src_amp),
+                                      rec_idx=to_dev(rec), rec_trace=trace)
+    gbs.device_status()
+    rp, ru, rtr = oracle.wave_propagate(z, z, prob.vel, prob.dt, prob.h, prob.halo, prob.nsteps,
+                                        src_idx=prob.src_idx, src_amp=prob.src_amp, rec_idx=rec)
+    tol = tol_steps(prob.nsteps)
+    for got, ref in ((cur, ru), (prev, rp), (trace, rtr)):
+        e = oracle.err_norms(got.cpu().numpy(), ref)
+        assert e["finite"] and e["norm_max_rel"] <= tol, e
+    assert np.all(cur.cpu().numpy()[halo_mask(z.shape, prob.halo)] == 0)
+
+
+def _case(shape, nsteps, seed):
+    nx, ny, nz = shape
+    halo, h = 4, 10.0
+    up = W.uniform_field(nx, ny, nz, halo, seed, halo_random=False)
+    u = W.uniform_field(nx, ny, nz, halo, seed + 1, halo_random=False)
+    vel = W.layered_velocity(nx, ny, nz, halo, seed + 2)
+    dt = W.dt_for_cfl(0.4, h, float(W.interior(vel, halo).max()))
+    rng = np.random.default_rng(seed)
+    npts = nx * ny * nz
+    src = rng.integers(0, npts, 3).astype(np.int64)
+    amp = rng.standard_normal((nsteps, 3)).astype(np.float32)
+    rec = rng.integers(0, npts, 40).astype(np.int64)
+    return up, u, vel, dt, h, halo, src, amp, rec
+
+
+# (shape, steps): even and odd pair counts, a trailing single step, ragged
+# x/y/z extents, and a tall grid that the fused kernel splits into z-chunks
+@pytest.mark.parametrize("shape,nsteps", [((64, 64, 64), 21), ((68, 45, 37), 10), ((64, 64, 256), 12),
+                                          ((128, 100, 40), 22), ((132, 20, 9), 8)])
+def test_vs_oracle_and_single_step(shape, nsteps):
+    need_gpu()
+    up, u, vel, dt, h, halo, src, amp, rec = _case(shape, nsteps, 40 + nsteps)
+    assert gbs.tb_supported(*shape, halo)[0]
+    d_vel, d_src, d_amp, d_rec = to_dev(vel), to_dev(src), to_dev(amp), to_dev(rec)
+    outs = []
+    for fn in (gbs.wave_propagate, gbs.wave_propagate_tb):
+        trace = torch.zeros((nsteps, rec.size), device=dev())
+        p, c = fn(to_dev(up), to_dev(u), d_vel, dt, h, halo, nsteps, src_idx=d_src, src_amp=d_amp,
+                  rec_idx=d_rec, rec_trace=trace)
+        gbs.device_status()
+        outs.append((p.cpu().numpy(), c.cpu().numpy(), trace.cpu().numpy()))
+    rp, ru, rtr = oracle.wave_propagate(up, u, vel, dt, h, halo, nsteps, src_idx=src, src_amp=amp, rec_idx=rec)
+    tol = tol_steps(nsteps)
+    (sp, sc, st), (tp, tc, tt) = outs
+    for got, ref in ((tc, ru), (tp, rp), (tt, rtr)):
+        e = oracle.err_norms(got, ref)
+        assert e["finite"] and e["norm_max_rel"] <= tol, e
+    # the two GPU paths differ only in the order of the FP32 sums
+    for got, ref in ((tc, sc), (tp, sp), (tt, st)):
+        e = oracle.err_norms(got, ref)
+        assert e["norm_max_rel"] <= tol, e
+    assert np.all(tc[halo_mask(tc.shape, halo)] == 0)
+
+
+def test_graph_replay_and_restart():
+    """Graph replay gives the same bits; 8 + 6 steps (t0 = 8) agrees with
+    14 steps and with the oracle."""
+    need_gpu()
+    prob, _ = _ricker64(14, nrec=1)
+    z = np.zeros(W.padded_shape(prob.nx, prob.ny, prob.nz, prob.halo), np.float32)
+    vel, si, sa = to_dev(prob.vel), to_dev(prob.src_idx), to_dev(prob.src_amp)
+    work = gbs.tb_workspace(vel, prob.halo)
+    p1, c1 = gbs.wave_propagate_tb(to_dev(z), to_dev(z), vel, prob.dt, prob.h, prob.halo, 8, src_idx=si, src_amp=sa,
+                                   work=work)
+    p2, c2 = gbs.wave_propagate_tb(p1, c1, vel, prob.dt, prob.h, prob.halo, 6, t0=8, src_idx=si, src_amp=sa,
+                                   work=work)
+    p3, c3 = gbs.wave_propagate_tb(to_dev(z), to_dev(z), vel, prob.dt, prob.h, prob.halo, 14, src_idx=si,
+                                   src_amp=sa, work=work)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        g1, g2 = to_dev(z), to_dev(z)
+        p4, c4 = gbs.wave_propagate_tb(g1, g2, vel, prob.dt, prob.h, prob.halo, 14, src_idx=si, src_amp=sa,
+                                       use_graph=True, stream=s)
+    s.synchronize()
+    gbs.device_status()
+    assert torch.equal(c3, c4) and torch.equal(p3, p4)
+    _, ru, _ = oracle.wave_propagate(z, z, prob.vel, prob.dt, prob.h, prob.halo, 14,
+                                     src_idx=prob.src_idx, src_amp=prob.src_amp)
+    for c in (c2, c3):
+        assert oracle.err_norms(c.cpu().numpy(), ru)["norm_max_rel"] <= tol_steps(14)
+
+
+def test_unsupported_shape_runs_single_steps():
+    """nx % 4 != 0: no fused pairs; the call is gbs_wave_propagate exactly."""
+    need_gpu()
+    shape = (66, 30, 20)
+    assert not gbs.tb_supported(*shape, 4)[0]
+    up, u, vel, dt, h, halo, src, amp, rec = _case(shape, 6, 77)
+    d_vel = to_dev(vel)
+    p0, c0 = gbs.wave_propagate(to_dev(up), to_dev(u), d_vel, dt, h, halo, 6, src_idx=to_dev(src),
+                                src_amp=to_dev(amp))
+    p1, c1 = gbs.wave_propagate_tb(to_dev(up), to_dev(u), d_vel, dt, h, halo, 6, src_idx=to_dev(src),
+                                   src_amp=to_dev(amp))
+    gbs.device_status()
+    assert torch.equal(c0, c1) and torch.equal(p0, p1)
+
+
+def test_workspace_errors():
+    need_gpu()
+    z = torch.zeros(W.padded_shape(64, 64, 64, 4), device=dev())
+    small = torch.empty(1024, dtype=torch.uint8, device=dev())
+    with pytest.raises(gbs.GbsError):
+        gbs.wave_propagate_tb(z.clone(), z.clone(), z + 1500.0, 1e-3, 10.0, 4, 4, work=small)
+
+
+def test_full_size_pairs(layered512):
+    """512^3 layered model in the launch configuration the benchmark times:
+    4 steps as two fused pairs against 4 single steps (themselves checked
+    against the oracle at this size), and time reversal through fused pairs
+    (a property of Eq. 2 at any size)."""
+    prob = layered512
+    n, halo = prob.nx, prob.halo
+    ok, tile_y, ctas = gbs.tb_supported(n, n, n, halo)
+    sms = torch.cuda.get_device_properties(dev()).multi_processor_count
+    assert ok and ctas <= sms, (ok, tile_y, ctas, sms)
+    vel = to_dev(prob.vel)
+    si, sa = to_dev(prob.src_idx), to_dev(prob.src_amp)
+    up = W.uniform_field(n, n, n, halo, 601, halo_random=False)
+    u = W.uniform_field(n, n, n, halo, 602, halo_random=False)
+    work = gbs.tb_workspace(vel, halo)
+    p0, c0 = gbs.wave_propagate(to_dev(up), to_dev(u), vel, prob.dt, prob.h, halo, 4, src_idx=si, src_amp=sa)
+    p1, c1 = gbs.wave_propagate_tb(to_dev(up), to_dev(u), vel, prob.dt, prob.h, halo, 4, src_idx=si, src_amp=sa,
+                                   work=work)
+    gbs.device_status()
+    scale = float(torch.max(torch.abs(c0)))
+    err = max(float(torch.max(torch.abs(c1 - c0))), float(torch.max(torch.abs(p1 - p0))))
+    del p0, c0
+    assert err <= tol_steps(4) * scale, (err, scale)
+    # 8 steps forward, swap the pair, 8 steps back: the start returns
+    a, b = to_dev(up), to_dev(u)
+    pf, cf = gbs.wave_propagate_tb(a, b, vel, prob.dt, prob.h, halo, 8, work=work)
+    pb, cb = gbs.wave_propagate_tb(cf, pf, vel, prob.dt, prob.h, halo, 8, work=work)
+    gbs.device_status()
+    err = max(float(torch.max(torch.abs(pb - to_dev(u)))), float(torch.max(torch.abs(cb - to_dev(up)))))
+    assert err <= tol_steps(16), err
+
+
+@pytest.fixture(scope="module")
+def layered512():
+    need_gpu()
+    return W.layered_problem(n=512, nsteps=100)
