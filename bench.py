@@ -1,18 +1,27 @@
 #!/usr/bin/env python3
 """Throughput of the 25-point acoustic leapfrog on one GB300.
 
-Workload (default): wave_propagate on a 512^3 interior (halo 4), FP32,
+Workload (default): Algorithm 1 on a 512^3 interior (halo 4), FP32,
 radius-4 8th-order star Laplacian, layered velocity 1500-4500 m/s with 16
 seeded Gaussian perturbations, h = 10 m, dt at CFL 0.4, 15 Hz Ricker source
-at depth 20.  One benchmark "step" = one wave_propagate call of 100 leapfrog
-steps (Algorithm 1) over the whole grid.  Fields (3 x 562 MB) are larger
-than L2, so no flush is needed between steps.
+at depth 20.  One benchmark "step" = one propagation call of 100 leapfrog
+steps over the whole grid.  Fields (3 x 562 MB) are larger than L2, so no
+flush is needed between steps.
+
+The default path is wave_propagate_tb: pairs of steps fused in one launch
+(2-step temporal blocking, 20 algorithmic bytes per point per pair);
+--path single times wave_propagate (one launch per step, 16 bytes per point
+update).  Both compute the same fields (to FP32 rounding).
 
 Prints ONE JSON line (rank 0) with Gpoint-updates/s for the whole job, the
-roofline of the dominant kernel (HBM bound, 16 algorithmic bytes per point
-update), an end-to-end number through host buffers, the FP64 oracle timed on
-the host cores, SM clocks sampled during the timed region, and the number of
-kernel launches.  --impl reference times the FP64 oracle instead.
+roofline of the dominant kernel (HBM bound), an end-to-end number through
+host buffers, the FP64 oracle timed on the host cores, SM clocks sampled
+during the timed region, and the number of kernel launches.  The
+single-step path is reported beside it (forms.single_step).  Extra forms
+(--forms) measure the other rows: 16-bit storage, the radius sweep, errors
+against the FP64 oracle, the 1024^3 precision grid, the absorbing layer,
+batches of shots, the adjoint gradient and the Table 4 suite.  --impl
+reference times the FP64 oracle instead.
 """
 from __future__ import annotations
 
@@ -34,9 +43,16 @@ import numpy as np  # noqa: E402
 METRIC = "Gpoint-updates/s & % HBM roofline, 25-pt 512^3; BF16/batched vs plain FP32"
 UNIT = "Gpoint-updates/s"
 BYTES_PER_POINT = 16          # read u, u_prev, vel; write u_next (FP32)
+BYTES_PER_POINT_PAIR = 20     # two fused steps: read u^t, u^{t-1}, vel; write u^{t+1}, u^{t+2}
 FALLBACK_HBM_GBS = 6800.0
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_tma_wave_512_traffic.json")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_2309_04671_gb300", "csrc", f) for f in ("k_tma.cu", "gbs_internal.cuh")]
+CSRC = os.path.join(ROOT, "paper_2309_04671_gb300", "csrc")
+# committed ncu DRAM counts per launch, valid while the kernel sources hash the same
+TRAFFIC = {
+    "single": (os.path.join(ROOT, "profiles", "k_tma_wave_512_traffic.json"),
+               [os.path.join(CSRC, f) for f in ("k_tma.cu", "gbs_internal.cuh")]),
+    "tb": (os.path.join(ROOT, "profiles", "k_wf_pair_512_traffic.json"),
+           [os.path.join(CSRC, f) for f in ("k_wf.cu", "gbs_wf.cuh", "gbs_internal.cuh")]),
+}
 
 
 def parse():
@@ -50,12 +66,14 @@ def parse():
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--path", choices=["tb", "single"], default="tb",
+                    help="FP32 propagation: fused pairs of steps (tb) or one launch per step (single)")
     ap.add_argument("--graph", action="store_true", help="replay the step loop as a CUDA graph")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
                     help="wave-field storage of the main timed path (arithmetic is FP32 in all)")
-    ap.add_argument("--forms", default="storage,radius,errors,precision,absorb,batched,adjoint,suite",
+    ap.add_argument("--forms", default="single,storage,radius,errors,precision,absorb,batched,adjoint,suite",
                     help="comma list of extra forms to measure after the main line, or 'none'")
     ap.add_argument("--no-forms", action="store_true", help="same as --forms none")
     ap.add_argument("--adj-n", type=int, default=256, help="adjoint form: interior side")
@@ -142,23 +160,23 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_sha():
+def kernel_sha(path="single"):
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in TRAFFIC[path][1]:
         with open(p, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(n):
+def traffic_per_launch(n, path="single"):
     """DRAM bytes per launch from the committed ncu summary, if it matches
     the current kernel source and workload size."""
     try:
-        with open(TRAFFIC_FILE) as f:
+        with open(TRAFFIC[path][0]) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    if t.get("kernel_sha") != kernel_sha() or int(t.get("n", -1)) != n:
+    if t.get("kernel_sha") != kernel_sha(path) or int(t.get("n", -1)) != n:
         return None
     return float(t["dram_bytes_per_launch"])
 
@@ -734,6 +752,33 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def single_step_form(prob, args, stream, hbm, vel, si, sa):
+    """The same workload with one launch per step (wave_propagate): the
+    single-step kernel against its own 16-byte roofline."""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    halo, ns = prob.halo, prob.nsteps
+    shape = W_padded(prob)
+    a = torch.zeros(shape, device=vel.device)
+    b = torch.zeros(shape, device=vel.device)
+    st = {"a": a, "b": b}
+
+    def run():
+        st["a"], st["b"] = gbs.wave_propagate(st["a"], st["b"], vel, prob.dt, prob.h, halo, ns, src_idx=si,
+                                              src_amp=sa)
+    for _ in range(3):
+        run()
+    gbs.device_status()
+    k = max(3, min(10, args.steps))
+    ms, kms, kl = time_calls(run, k, stream)
+    gbs.device_status()
+    ach = BYTES_PER_POINT * prob.npoints / (kms * 1e-3) / 1e9 if kms else None
+    return {"value": prob.npoints * ns / ms / 1e6, "unit": UNIT, "ms_per_call": ms, "calls": k,
+            "kernel": "k_tma<R=4,wave,16,float>", "kernel_us": kms * 1e3 if kms else None,
+            "achieved_gbs": ach, "frac": ach / hbm if ach else None,
+            "traffic": traffic_per_launch(prob.nx, "single"), "alg_bytes_per_point": BYTES_PER_POINT}
+
+
 def run_ours(args):
     import torch
 
@@ -754,7 +799,11 @@ def run_ours(args):
     si = torch.from_numpy(prob.src_idx).to(dev)
     sa = torch.from_numpy(prob.src_amp).to(dev)
     stream = torch.cuda.current_stream()
-    if args.storage == "f32":
+    tb = args.storage == "f32" and args.path == "tb"
+    if tb:
+        kw = dict(src_idx=si, src_amp=sa, kernel=args.kernel, use_graph=args.graph, work=gbs.tb_workspace(a, halo))
+        propagate = gbs.wave_propagate_tb
+    elif args.storage == "f32":
         kw = dict(src_idx=si, src_amp=sa, kernel=args.kernel, tile_y=args.tile_y, zchunk=args.zchunk,
                   use_graph=args.graph)
         propagate = gbs.wave_propagate
@@ -762,7 +811,9 @@ def run_ours(args):
         kw = dict(src_idx=si, src_amp=sa, tile_y=args.tile_y, zchunk=args.zchunk, use_graph=args.graph,
                   storage=args.storage, work=gbs.lp_workspace(a, halo))
         propagate = gbs.wave_propagate_lp
-    bytes_per_point = BYTES_PER_POINT if args.storage == "f32" else 10
+    # algorithmic bytes per point of one launch of the dominant kernel
+    bytes_per_point = BYTES_PER_POINT_PAIR if tb else (BYTES_PER_POINT if args.storage == "f32" else 10)
+    tb_shape = gbs.tb_supported(n, n, n, halo) if tb else None
 
     # warm-up (also builds the wavefield)
     for _ in range(max(3, args.warmup)):
@@ -797,8 +848,10 @@ def run_ours(args):
     per_launch_ms = kernel_ms / max(1, kernel_launches)
     alg_bytes = bytes_per_point * prob.npoints
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9 if kernel_launches else None
-    traffic = traffic_per_launch(n) if args.storage == "f32" else None
-    inject_launches = 0   # sources are added inside the step kernel (at most 16)
+    traffic = traffic_per_launch(n, "tb" if tb else "single") if args.storage == "f32" else None
+    # sources are added inside the step kernels (at most 16); the fused path
+    # also zeroes its workspace halo with one kernel per call
+    inject_launches = args.steps if tb else 0
 
     # end to end through host buffers (pinned), same call a user makes
     e2e = None
@@ -808,13 +861,18 @@ def run_ours(args):
         hv = torch.from_numpy(prob.vel).pin_memory()
         hsi, hsa = torch.from_numpy(prob.src_idx), torch.from_numpy(prob.src_amp)
         e2e_steps = max(1, min(3, args.steps))
-        gbs.wave_propagate(hp, hu, hv, prob.dt, prob.h, halo, ns, src_idx=hsi, src_amp=hsa, kernel=args.kernel,
-                           tile_y=args.tile_y, zchunk=args.zchunk, use_graph=args.graph)
+        if tb:
+            hkw = dict(src_idx=hsi, src_amp=hsa, kernel=args.kernel, use_graph=args.graph, work=kw["work"])
+            hcall = gbs.wave_propagate_tb
+        else:
+            hkw = dict(src_idx=hsi, src_amp=hsa, kernel=args.kernel, tile_y=args.tile_y, zchunk=args.zchunk,
+                       use_graph=args.graph)
+            hcall = gbs.wave_propagate
+        hcall(hp, hu, hv, prob.dt, prob.h, halo, ns, **hkw)
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            gbs.wave_propagate(hp, hu, hv, prob.dt, prob.h, halo, ns, src_idx=hsi, src_amp=hsa,
-                               kernel=args.kernel, tile_y=args.tile_y, zchunk=args.zchunk, use_graph=args.graph)
+            hcall(hp, hu, hv, prob.dt, prob.h, halo, ns, **hkw)
         el = max_over_ranks(time.perf_counter() - t0, world)
         fb = prob.vel.nbytes
         e2e = {"value": prob.npoints * ns * e2e_steps * world / el / 1e9, "unit": UNIT,
@@ -832,6 +890,8 @@ def run_ours(args):
     wanted = set() if args.no_forms or args.forms == "none" else set(args.forms.split(","))
     if rank == 0 and wanted:
         forms = {}
+        if "single" in wanted and tb:
+            forms["single_step"] = single_step_form(prob, args, stream, hbm, vel, si, sa)
         if "storage" in wanted:
             forms["storage"] = storage_forms(prob, args, stream, hbm)
         if "radius" in wanted:
@@ -859,14 +919,23 @@ def run_ours(args):
                        "leapfrog_steps_per_step": ns, "dt": prob.dt, "h": prob.h,
                        "l2": "no flush: each of the 3 fields (562 MB) exceeds the 129 MB L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "kernel": ("k_tma<R=4,wave>" if args.kernel != 2 else "k_generic<R=4,wave>")
+                       "kernel": (f"k_wf<TY={tb_shape[1]}>: two fused leapfrog steps per launch "
+                                  f"(2-step temporal blocking, {tb_shape[2]} cooperative CTAs)" if tb else
+                                  ("k_tma<R=4,wave>" if args.kernel != 2 else "k_generic<R=4,wave>"))
                        if args.storage == "f32" else f"k_tma<R=4,wave,{args.storage} storage>",
+                       "path": "fused pairs of steps" if tb else "one launch per step",
                        "storage": args.storage,
-                       "tile_y": args.tile_y or 16, "zchunk": args.zchunk or "auto", "graph": args.graph},
+                       "tile_y": (tb_shape[1] if tb else args.tile_y or 16), "zchunk": args.zchunk or "auto",
+                       "graph": args.graph},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                          "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
-                         "kernel_ms_per_launch": per_launch_ms, "kernel_launches": kernel_launches},
+                         "alg_bytes_per_point_per_launch": bytes_per_point,
+                         "point_updates_per_launch": prob.npoints * (2 if tb else 1),
+                         "kernel_ms_per_launch": per_launch_ms, "kernel_launches": kernel_launches,
+                         # the throughput against the single-step minimum of 16 B per update (can exceed 1)
+                         "single_step_basis_frac": (value * BYTES_PER_POINT / hbm) if args.storage == "f32"
+                         else None},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,

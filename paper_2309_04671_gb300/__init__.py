@@ -390,8 +390,23 @@ def wave_propagate_tb(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, 
     of steps fused into one launch.
 
     Returns (prev, cur) as wave_propagate.  ``work`` is device scratch of at
-    least tb_workspace_bytes(...) bytes (allocated per call if None).
+    least tb_workspace_bytes(...) bytes (allocated per call if None).  With
+    CPU tensors (ideally pinned) the call copies the inputs to the device,
+    runs, copies both fields (and the trace) back, and returns CPU tensors.
     """
+    if not u.is_cuda:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        d = [None if x is None else x.to(dev, non_blocking=True)
+             for x in (u_prev, u, vel, src_idx, src_amp, rec_idx, rec_trace)]
+        a, b = wave_propagate_tb(d[0], d[1], d[2], dt, h, halo, nsteps, t0=t0, src_idx=d[3], src_amp=d[4],
+                                 rec_idx=d[5], rec_trace=d[6], work=work, kernel=kernel, use_graph=use_graph,
+                                 stream=stream)
+        u.copy_(b, non_blocking=True)
+        u_prev.copy_(a, non_blocking=True)
+        if rec_trace is not None:
+            rec_trace.copy_(d[6], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return u_prev, u
     p = [_field(t, n) for t, n in ((u_prev, "u_prev"), (u, "u"), (vel, "vel"))]
     _same_shape(u, u_prev, vel)
     nx, ny, nz = _dims(u, halo)

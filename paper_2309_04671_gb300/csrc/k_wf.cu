@@ -203,8 +203,14 @@ __device__ __forceinline__ void fence_proxy_async_global()
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// stage A issues u planes at most this far ahead of stage B's next plane
+// (more than a block plus R planes, so stage A can always publish what
+// stage B waits for)
+constexpr int kLead = 14;
+constexpr unsigned kPollSleepNs = 32;   // pause of an issuing thread that found nothing to do
 constexpr int kPB = kWfBlock;   // stage-A output planes per published block
 constexpr int kNS = 8;   // ring of "block stored" barriers
+static_assert(kLead > kWfBlock + 4 + 1, "stage A must be able to publish the block stage B waits for");
 
 // Planes of one stage of a CTA.  Stage A covers the chunk and R planes
 // either side of it (stage B's z halo), clamped to the interior.
@@ -461,7 +467,7 @@ __device__ __forceinline__ void wf_producer(const CUtensorMap *__restrict__ pm_u
                                             const CUtensorMap *__restrict__ pm_prev,
                                             const CUtensorMap *__restrict__ pm_vel, const WfParams &p,
                                             const Ring &rg, const int64_t tx0, const int64_t ty0, const int tile,
-                                            const int chunk)
+                                            const int chunk, volatile int *b_next)
 {
     using C = WfCfg<TY>;
     constexpr int SL = STAGE == 0 ? C::SL_A : C::SL_B;
@@ -485,6 +491,10 @@ __device__ __forceinline__ void wf_producer(const CUtensorMap *__restrict__ pm_u
         if (n_u < sg.nplanes) {
             const int st = n_u % SL;
             bool ready = n_u < SL || mbar_test(&rg.empty_u[st], (uint32_t)((n_u / SL - 1) & 1));
+            // stage A stays within kLead planes of stage B, so the data stage B
+            // reads again is still in L2 (stage B publishes its next plane)
+            if (STAGE == 0 && sg.pfirst + n_u > *b_next + kLead)
+                ready = false;
             if (ready && STAGE == 1) {
                 const int b = sg.pfirst + n_u;   // plane of u^{t+1}
                 if (b >= sg.a0 && b < sg.a1) {
@@ -504,6 +514,8 @@ __device__ __forceinline__ void wf_producer(const CUtensorMap *__restrict__ pm_u
                 tma_load_3d_pol(rg.land + st * C::L_STRIDE, pm_u, (int)(H + tx0 - 4), (int)(H + ty0 - kR),
                                 H + sg.pfirst + n_u, &rg.full_u[st], pol_keep);
                 ++n_u;
+                if (STAGE == 1)
+                    *b_next = n_u < sg.nplanes ? sg.pfirst + n_u : 1 << 30;
                 prog = true;
             }
         }
@@ -535,7 +547,7 @@ __device__ __forceinline__ void wf_producer(const CUtensorMap *__restrict__ pm_u
             fail = true;
             break;
         } else {
-            __nanosleep(32);
+            __nanosleep(kPollSleepNs);
         }
     }
     if (fail) {
@@ -561,6 +573,7 @@ __global__ void __launch_bounds__(2 * WfCfg<TY>::NT + 64, 1)
     __shared__ int s_nsrc[2];
     __shared__ int s_src_x[2][kMaxFusedSrc], s_src_y[2][kMaxFusedSrc], s_src_z[2][kMaxFusedSrc];
     __shared__ float s_src_f[2][kMaxFusedSrc];
+    __shared__ int s_bnext;   // stage B's next u^{t+1} plane to copy
     const int ntiles = p.tiles_x * p.tiles_y;
     const int tile = (int)(blockIdx.x % (unsigned)ntiles);
     const int chunk = (int)(blockIdx.x / (unsigned)ntiles);
@@ -618,6 +631,7 @@ __global__ void __launch_bounds__(2 * WfCfg<TY>::NT + 64, 1)
         fence_mbar_init();
         s_nsrc[0] = 0;
         s_nsrc[1] = 0;
+        s_bnext = stage_geo(p, chunk, 1).pfirst;
     }
     __syncthreads();
     const int w = threadIdx.x / 32;
@@ -626,9 +640,9 @@ __global__ void __launch_bounds__(2 * WfCfg<TY>::NT + 64, 1)
     else if (w < 2 * NW)
         wf_consumer<TY, 1>(p, rb, tx0, ty0, chunk, &s_nsrc[1], s_src_x[1], s_src_y[1], s_src_z[1], s_src_f[1]);
     else if (w == 2 * NW && (threadIdx.x & 31) == 0)
-        wf_producer<TY, 0>(&tm_ua, &tm_pa, &tm_vel, p, ra, tx0, ty0, tile, chunk);
+        wf_producer<TY, 0>(&tm_ua, &tm_pa, &tm_vel, p, ra, tx0, ty0, tile, chunk, &s_bnext);
     else if (w == 2 * NW + 1 && (threadIdx.x & 31) == 0)
-        wf_producer<TY, 1>(&tm_ub, &tm_pb, &tm_vel, p, rb, tx0, ty0, tile, chunk);
+        wf_producer<TY, 1>(&tm_ub, &tm_pb, &tm_vel, p, rb, tx0, ty0, tile, chunk, &s_bnext);
 }
 
 template <int TY>
