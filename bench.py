@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=512, help="interior side")
+    ap.add_argument("--nz", type=int, default=0, help="interior z extent (default: n; smaller for profiling runs)")
     ap.add_argument("--nsteps", type=int, default=100, help="leapfrog steps per benchmark step")
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--zchunk", type=int, default=0)
@@ -85,8 +86,9 @@ def parse():
     return ap.parse_args()
 
 
-def workload_desc(n, nsteps):
-    return (f"wave_propagate {n}^3 interior + halo 4, FP32, 25-pt radius-4 8th-order Laplacian, "
+def workload_desc(n, nsteps, nz=None):
+    size = f"{n}^3" if nz in (None, n) else f"{n}x{n}x{nz}"
+    return (f"wave_propagate {size} interior + halo 4, FP32, 25-pt radius-4 8th-order Laplacian, "
             f"{nsteps} leapfrog steps per step, layered 1500-4500 m/s + 16 Gaussians, h=10 m, CFL 0.4, "
             f"15 Hz Ricker at depth 20")
 
@@ -790,7 +792,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     gbs.load()
 
-    prob = W.layered_problem(n=args.n, nsteps=args.nsteps)
+    prob = W.layered_problem(n=args.n, nsteps=args.nsteps, nz=args.nz or None)
     n, halo, ns = prob.nx, prob.halo, prob.nsteps
     shape = W_padded(prob)
     a = torch.zeros(shape, device=dev)
@@ -813,7 +815,7 @@ def run_ours(args):
         propagate = gbs.wave_propagate_lp
     # algorithmic bytes per point of one launch of the dominant kernel
     bytes_per_point = BYTES_PER_POINT_PAIR if tb else (BYTES_PER_POINT if args.storage == "f32" else 10)
-    tb_shape = gbs.tb_supported(n, n, n, halo) if tb else None
+    tb_shape = gbs.tb_supported(prob.nx, prob.ny, prob.nz, halo) if tb else None
 
     # warm-up (also builds the wavefield)
     for _ in range(max(3, args.warmup)):
@@ -848,7 +850,8 @@ def run_ours(args):
     per_launch_ms = kernel_ms / max(1, kernel_launches)
     alg_bytes = bytes_per_point * prob.npoints
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9 if kernel_launches else None
-    traffic = traffic_per_launch(n, "tb" if tb else "single") if args.storage == "f32" else None
+    traffic = (traffic_per_launch(n, "tb" if tb else "single") if args.storage == "f32" and prob.nz == n
+               else None)
     # sources are added inside the step kernels (at most 16); the fused path
     # also zeroes its workspace halo with one kernel per call
     inject_launches = args.steps if tb else 0
@@ -915,9 +918,10 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(n, ns), "grid": [n, n, n], "halo": halo,
+            "config": {"workload": workload_desc(n, ns, prob.nz), "grid": [prob.nx, prob.ny, prob.nz], "halo": halo,
                        "leapfrog_steps_per_step": ns, "dt": prob.dt, "h": prob.h,
-                       "l2": "no flush: each of the 3 fields (562 MB) exceeds the 129 MB L2",
+                       "l2": f"no flush: each of the 3 fields ({4 * int(np.prod(shape)) / 1e6:.0f} MB) exceeds "
+                             "the 129 MB L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "kernel": (f"k_wf<TY={tb_shape[1]}>: two fused leapfrog steps per launch "
                                   f"(2-step temporal blocking, {tb_shape[2]} cooperative CTAs)" if tb else

@@ -13,13 +13,13 @@
  *         u^{n+1} = 2 u^n - u^{n-1} + dt^2 V^2 lap(u^n) + dt^2 V^2 f^n
  *   - Algorithm 1: the time loop over n, source added after the update.
  *
- * Grid layout (Sec. 10, GPU code generation: a flattened array with halo
+ * Grid layout (Secs. 11.1 and 11.3, code generation: a flattened array with halo
  * padding).  A field with interior nx*ny*nz and halo width `halo` is a dense
  * float array of (nx+2*halo)*(ny+2*halo)*(nz+2*halo) elements, x fastest,
  * z slowest; interior point (i,j,k) is element
  *     (i+halo) + (nx+2*halo) * ((j+halo) + (ny+2*halo) * (k+halo)).
  * The "interior linear index" of (i,j,k) is i + nx*(j + ny*k).
- * Interiors are the half-open boxes [0,nx)x[0,ny)x[0,nz) (Sec. 10, "map").
+ * Interiors are the half-open boxes [0,nx)x[0,ny)x[0,nz) (Sec. 11.1, "map").
  *
  * Conventions shared by every call:
  *   - Pointers to fields, index lists and traces are DEVICE pointers owned
@@ -196,7 +196,7 @@ gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float *vel, floa
  * step's reads of u^{t+1}, u^t and vel are served from L2, so a pair of
  * steps moves 20 bytes per point through DRAM instead of 32.  Both steps sum
  * Eq. 3 in the semi-stencil order along z (the paper's `semi` template,
- * Sec. 8), so the fields agree with gbs_wave_propagate to FP32 rounding, not
+ * Sec. 9.3), so the fields agree with gbs_wave_propagate to FP32 rounding, not
  * bit for bit.
  *   u_prev, u, vel, dt, h, sizes, halo, nsteps, t0, src, rec, opts
  *                 as gbs_wave_propagate, with the same parity rule on return
@@ -226,7 +226,7 @@ gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float *vel, floa
 int gbs_tb_supported(int64_t nx, int64_t ny, int64_t nz, int halo, int *tile_y, int *ctas);
 
 /*
- * The kernels of the paper's numerical-accuracy suite (Sec. 11.1, Table 4):
+ * The kernels of the paper's numerical-accuracy suite (Sec. 13.1, Table 4):
  *   out(i,j,k) = ( sum_q w_q in(i+dx_q, j+dy_q, k+dz_q) ) / divisor
  * over the interior, for a star (shape 0: the points on the axes within
  * `radius`) or box (shape 1: the whole cube) footprint of radius 1..4, in 3D
@@ -348,7 +348,7 @@ gbs_status gbs_fwi_gradient(const float *vel, float dt, float h, int64_t nx, int
 
 /*
  * Error norms of a field against a reference over the interior, accumulated
- * in FP64 (the accuracy metrics of Sec. 11.1: maximum absolute error and RMSD
+ * in FP64 (the accuracy metrics of Sec. 13.1: maximum absolute error and RMSD
  * against a reference implementation, plus scale-free versions).
  *   x, ref        DEVICE float fields, padded layout; ref may be NULL (norms
  *                 of x itself, as if ref were zero).

@@ -29,14 +29,14 @@ What each function follows (arXiv 2309.04671):
   paper computes in FP32 (``st.f32``); the 16-bit storage is this library's
   addition, pinned here against numpy/torch conversions.
 * :func:`footprint`, :func:`suite_flops`, :func:`stencil_general` -- the
-  kernels of the numerical-accuracy suite (Sec. 11.1, Table 4): star / box
+  kernels of the numerical-accuracy suite (Sec. 13.1, Table 4): star / box
   footprints in 2D and 3D of order 1..4 and the j* kernels, as a weighted
   sum over the footprint divided by a constant (C, ``oracle.c``).
 * :func:`forward_states`, :func:`adjoint_gradient`, :func:`fwi_misfit`,
   :func:`fwi_gradient` -- the discrete adjoint of Algorithm 1 and the
   gradient of a trace functional with respect to the velocity (the paper
   has no adjoint; the derivation is written out above the functions).
-* :func:`err_norms` -- the paper's accuracy metrics (Sec. 11.1: maximum
+* :func:`err_norms` -- the paper's accuracy metrics (Sec. 13.1: maximum
   absolute error and RMSD against a reference), plus the normwise relative
   maximum and L2 errors.
 
@@ -224,7 +224,7 @@ def stencil_points(inp_f32: np.ndarray, radius: int, cx, cy, cz, halo: int,
 
 
 # ---------------------------------------------------------------------------
-# Sec. 11.1, Table 4: the numerical-accuracy suite of stencil kernels
+# Sec. 13.1, Table 4: the numerical-accuracy suite of stencil kernels
 # ---------------------------------------------------------------------------
 # name -> (shape, dimensions, order, divides by a constant)
 SUITE = {
@@ -561,7 +561,7 @@ def fwi_gradient(vel, dt: float, h: float, halo: int, nsteps: int, d_obs, *, src
 
 
 # ---------------------------------------------------------------------------
-# Sec. 11.1 accuracy metrics
+# Sec. 13.1 accuracy metrics
 # ---------------------------------------------------------------------------
 def err_norms(x, ref) -> dict:
     """Errors of ``x`` against ``ref`` (same shape), computed in FP64.

@@ -14,7 +14,7 @@
  *                    + sum_{m=1..R} cxm [in(i+m,j,k) + in(i-m,j,k)]
  *                                 + cym [in(i,j+m,k) + in(i,j-m,k)]
  *                                 + czm [in(i,j,k+m) + in(i,j,k-m)]
- *     over the interior [0,nx)x[0,ny)x[0,nz) (half-open, Sec. 10 "map"),
+ *     over the interior [0,nx)x[0,ny)x[0,nz) (half-open, Sec. 11.1 "map"),
  *     reading the halo as given.
  *   - Sec. 2.2, Eq. 2: u^{n+1} = 2u^n - u^{n-1} + dt^2 V^2 (lap u^n)
  *                                + dt^2 V^2 f^n,
@@ -27,7 +27,7 @@
  * receivers are given by interior linear index i + nx*(j + ny*k).
  *
  * The loops are OpenMP "parallel for" over z, the shape of the paper's
- * "loop" template (Sec. 8, OpenMP backend table); each output point is
+ * "loop" template (Sec. 9.2, OpenMP backend table); each output point is
  * computed by exactly one thread, so the result does not depend on the
  * thread count.
  */
@@ -204,7 +204,7 @@ int oracle_wave_propagate(double *u_prev, double *u, const double *vel, double d
 }
 
 /*
- * The kernels of the paper's numerical-accuracy suite (Sec. 11.1, Table 4):
+ * The kernels of the paper's numerical-accuracy suite (Sec. 13.1, Table 4):
  * star / box stencils in 2D and 3D of order 1..4 and the j2d5pt, j2d9pt,
  * j2d9pt-gol and j3d27pt kernels, as one definition:
  *     out(i,j,k) = ( sum_q w_q in(i+dx_q, j+dy_q, k+dz_q) ) / divisor

@@ -8,7 +8,7 @@ path: if the library is missing or no GPU is present the calls raise.
 
 Fields are float32 CUDA tensors of shape (nz+2*halo, ny+2*halo, nx+2*halo),
 C-contiguous (x fastest), as in the paper's flattened grid with halo padding
-(Sec. 10).
+(Secs. 11.1 and 11.3).
 """
 from __future__ import annotations
 

@@ -1,4 +1,4 @@
-// Host entry of the numerical-accuracy suite kernels (Sec. 11.1, Table 4):
+// Host entry of the numerical-accuracy suite kernels (Sec. 13.1, Table 4):
 // validation, the dense weight cube, the TMA descriptor and the launch
 // (C ABI in include/gbstencil.h).
 #include <cmath>

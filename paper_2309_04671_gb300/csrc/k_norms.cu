@@ -1,5 +1,5 @@
 // Error norms of a field against a reference over the interior, accumulated
-// in FP64 (the paper's accuracy metrics, Sec. 11.1: maximum absolute error
+// in FP64 (the paper's accuracy metrics, Sec. 13.1: maximum absolute error
 // and RMSD against a reference implementation; plus the normwise relative
 // maximum and the L2 relative error).
 //

@@ -1,4 +1,4 @@
-// Kernels of the paper's numerical-accuracy suite (Sec. 11.1, Table 4): star
+// Kernels of the paper's numerical-accuracy suite (Sec. 13.1, Table 4): star
 // and box stencils of radius 1..4 in 2D and 3D, and the j* kernels (a star or
 // box of radius 1..2 divided by a constant):
 //     out(p) = ( sum_q w_q in(p + off_q) ) / divisor,

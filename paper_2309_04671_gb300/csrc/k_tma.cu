@@ -4,7 +4,7 @@
 //
 // Work decomposition.  A CTA owns a 64 x TY tile of the interior xy plane
 // and streams a chunk of z planes (the paper's 2.5D streaming templates,
-// Sec. 8, GPU backend table; streaming on the outermost axis, Sec. 3).
+// Sec. 9.3, GPU backend table; streaming on the outermost axis, Sec. 3).
 // Grid x = tiles (x fastest), grid y = z-chunks, so the CTAs resident at
 // any time work on neighbouring tiles at nearby z and the xy halos a tile
 // shares with its neighbours are served from L2.

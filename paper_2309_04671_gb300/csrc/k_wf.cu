@@ -32,7 +32,7 @@
 // moves u^t, u^{t-1}, vel (12 B) and u^{t+1}, u^{t+2} (8 B) per point: 20 B
 // per two updates instead of 32.
 //
-// Semi-stencil z sweep (the paper's `semi` template, Sec. 8).  A thread
+// Semi-stencil z sweep (the paper's `semi` template, Sec. 9.3).  A thread
 // uses each plane only when it lands: for its points it forms the new
 // accumulator c0 u(j) + sum_m c_m [x, y neighbours at distance m of plane j
 // + u(j - m)], and adds c_m u(j) to the pending accumulators of planes

@@ -1,5 +1,5 @@
 """GPU FP64 error norms (gbs_field_norms) against the oracle's err_norms
-(the accuracy metrics of Sec. 11.1) on the same fields."""
+(the accuracy metrics of Sec. 13.1) on the same fields."""
 import numpy as np
 import pytest
 

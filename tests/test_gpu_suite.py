@@ -1,4 +1,4 @@
-"""GPU parity of the numerical-accuracy suite kernels (Sec. 11.1, Table 4)
+"""GPU parity of the numerical-accuracy suite kernels (Sec. 13.1, Table 4)
 against the FP64 oracle.
 
 Bound: the GPU sums the footprint's n products in FP32 in the oracle's

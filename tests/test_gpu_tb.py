@@ -4,7 +4,7 @@ blocking) against the FP64 oracle and against the single-step path.
 Covers: the 64^3 constant-velocity Ricker problem with receivers, ragged
 and z-chunked grids with several sources (odd and even step counts, so
 pairs and trailing single steps both run), graph replay, restart at t0,
-the fallback for shapes the fused kernel does not take, workspace errors,
+host buffers, the fallback for shapes the fused kernel does not take, workspace errors,
 and the full 512^3 layered workload in the launch configuration the
 benchmark times.
 """
@@ -133,6 +133,22 @@ def test_unsupported_shape_runs_single_steps():
                                    src_amp=to_dev(amp))
     gbs.device_status()
     assert torch.equal(c0, c1) and torch.equal(p0, p1)
+
+
+def test_host_buffers_match_device_path():
+    need_gpu()
+    prob, _ = _ricker64(10, nrec=1)
+    z = np.zeros(W.padded_shape(prob.nx, prob.ny, prob.nz, prob.halo), np.float32)
+    hp = torch.from_numpy(z.copy()).pin_memory()
+    hu = torch.from_numpy(z.copy()).pin_memory()
+    hv = torch.from_numpy(prob.vel).pin_memory()
+    rp, ru = gbs.wave_propagate_tb(hp, hu, hv, prob.dt, prob.h, prob.halo, prob.nsteps,
+                                   src_idx=torch.from_numpy(prob.src_idx), src_amp=torch.from_numpy(prob.src_amp))
+    assert not ru.is_cuda
+    dp, du = gbs.wave_propagate_tb(to_dev(z), to_dev(z), to_dev(prob.vel), prob.dt, prob.h, prob.halo, prob.nsteps,
+                                   src_idx=to_dev(prob.src_idx), src_amp=to_dev(prob.src_amp))
+    gbs.device_status()
+    assert torch.equal(ru, du.cpu()) and torch.equal(rp, dp.cpu())
 
 
 def test_workspace_errors():

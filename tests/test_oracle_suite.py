@@ -1,5 +1,5 @@
 """Pins of the oracle's general stencil (the numerical-accuracy suite of
-Sec. 11.1, Table 4).
+Sec. 13.1, Table 4).
 
 * footprints: every kernel's shape, dimension and order reproduce the FLOP
   count Table 4 prints (one multiply per point, one add per extra point, one

@@ -7,7 +7,7 @@ source scaling), so that both the CUDA path and the FP64 oracle can be fed the
 same numbers without sharing any code that computes a result.
 
 Layout convention (the paper flattens each grid to 1D with halo padding,
-Sec. 10 "GPU Code Generation"): a padded field of interior ``nx*ny*nz`` and
+Sec. 11.3 "GPU Code Generation"): a padded field of interior ``nx*ny*nz`` and
 halo width ``halo`` is a C-contiguous array of shape
 ``(nz + 2*halo, ny + 2*halo, nx + 2*halo)`` -- x fastest, z slowest (the
 streamed axis).  Interior point ``(i, j, k)`` sits at padded index
