@@ -38,7 +38,8 @@
  *   - gbs_last_error() returns a message for the last failing call of the
  *     calling thread.
  *   - Nothing here allocates device memory, except batch plans
- *     (gbs_batch_plan_create), which own their buffers until destroyed.
+ *     (gbs_batch_plan_create), which own their buffers until destroyed, and
+ *     the self-test gbs_selftest_tb_timeout, which frees its own.
  */
 #ifndef GBSTENCIL_H
 #define GBSTENCIL_H
@@ -224,6 +225,18 @@ gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float *vel, floa
  * tile_y and ctas may be NULL.
  */
 int gbs_tb_supported(int64_t nx, int64_t ny, int64_t nz, int halo, int *tile_y, int *ctas);
+/*
+ * Self-test of the bounded waits (failure detection without a device fault).
+ * Launches one fused pair on a 64^3 zero grid in buffers it allocates,
+ * with an epoch its block counters never reach: stage B's copies wait on
+ * counters that nothing completes, every wait in the launch runs out after
+ * its bound (about 2 s), the kernel records GBS_ETIMEOUT and returns, and
+ * the CUDA context stays usable.  Synchronises `stream`, frees its buffers
+ * and returns the status the launch recorded: GBS_ETIMEOUT when the
+ * mechanism works (GBS_EINVAL if the launch recorded nothing,
+ * GBS_EUNSUPPORTED if the kernel cannot run here, GBS_ECUDA).
+ */
+gbs_status gbs_selftest_tb_timeout(void *stream);
 
 /*
  * The kernels of the paper's numerical-accuracy suite (Sec. 13.1, Table 4):

@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4
 # Entry points declared in include/gbstencil.h (checked by the tests).
 EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
            "gbs_wave_propagate_lp", "gbs_tb_workspace_bytes", "gbs_wave_propagate_tb", "gbs_tb_supported",
+           "gbs_selftest_tb_timeout",
            "gbs_norms_workspace_bytes", "gbs_field_norms", "gbs_field_norms_noalloc",
            "gbs_batch_plan_create", "gbs_batch_run", "gbs_batch_plan_info", "gbs_batch_plan_destroy",
            "gbs_adjoint_workspace_bytes", "gbs_adjoint_forward", "gbs_adjoint_backward", "gbs_fwi_gradient",
@@ -109,6 +110,8 @@ def load() -> ctypes.CDLL:
         lib.gbs_wave_propagate_tb.restype = c_int
         lib.gbs_tb_supported.argtypes = [i64, i64, i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
         lib.gbs_tb_supported.restype = c_int
+        lib.gbs_selftest_tb_timeout.argtypes = [vp]
+        lib.gbs_selftest_tb_timeout.restype = c_int
         lib.gbs_norms_workspace_bytes.argtypes = [i64, i64]
         lib.gbs_norms_workspace_bytes.restype = ctypes.c_size_t
         lib.gbs_field_norms.argtypes = [vp, vp, i64, i64, i64, c_int, vp, vp, ctypes.c_size_t, vp]
@@ -421,6 +424,13 @@ def wave_propagate_tb(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, 
                                         int(t0), _ptr(src), _ptr(rec), work.data_ptr(),
                                         work.numel() * work.element_size(), ctypes.byref(opts), _stream(stream)))
     return (u, u_prev) if nsteps % 2 else (u_prev, u)
+
+
+def selftest_tb_timeout(stream=None) -> int:
+    """Run the bounded-wait self-test (a fused pair whose counters never
+    complete) and return the device status it recorded (GBS_ETIMEOUT when
+    the waits run out and the kernel returns as designed)."""
+    return int(load().gbs_selftest_tb_timeout(_stream(stream)))
 
 
 def lp_workspace_bytes(nx: int, ny: int, nz: int) -> int:

@@ -747,6 +747,61 @@ extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float
     return gbs_wave_propagate(u_prev, u, vel, dt, h, nx, ny, nz, halo, rest, t0 + 2 * npairs, src, rec, opts, stream);
 }
 
+extern "C" gbs_status gbs_selftest_tb_timeout(void *stream)
+{
+    t_err[0] = 0;
+    const int64_t n = 64;
+    const int halo = 4;
+    const Grid g = dense_grid(n, n, n, halo);
+    WfShape sh{};
+    if (!wf_shape(g, &sh))
+        return fail(GBS_EUNSUPPORTED, "the fused-pair kernel cannot run on this device");
+    const TbLayout L = tb_layout(g);
+    const size_t fb = (size_t)field_elems(g) * 4;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, 3 * round256(fb) + L.total);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "self-test buffers");
+    float *up = reinterpret_cast<float *>(mem);
+    float *u = reinterpret_cast<float *>(mem + round256(fb));
+    float *vel = reinterpret_cast<float *>(mem + 2 * round256(fb));
+    char *work = mem + 3 * round256(fb);
+    unsigned *words = reinterpret_cast<unsigned *>(work + L.off_words);
+    gbs_status s = GBS_OK;
+    WfMaps m;
+    if ((s = make_map(&m.ua, u, g, 64 + 8, sh.tile_y + 8)) == GBS_OK &&
+        (s = make_map(&m.pa, up, g, 64, sh.tile_y)) == GBS_OK &&
+        (s = make_map(&m.ub, work + L.off_w1, g, 64 + 8, sh.tile_y + 8)) == GBS_OK &&
+        (s = make_map(&m.pb, u, g, 64, sh.tile_y)) == GBS_OK && (s = make_map(&m.vel, vel, g, 64, sh.tile_y)) == GBS_OK) {
+        WfParams p;
+        memset(&p, 0, sizeof(p));
+        p.g = g;
+        p.out[0] = reinterpret_cast<float *>(work + L.off_w1);
+        p.out[1] = reinterpret_cast<float *>(work + L.off_w2);
+        p.cf = wave_coeffs();
+        p.s = 1e-4f;
+        p.dt = 1e-3f;
+        p.inx = n;
+        p.iny = n;
+        p.words = words;
+        // counters start at zero and this launch adds one launch's worth, but
+        // stage B waits for two: its waits run out
+        p.epoch = 2;
+        p.t = 0;
+        if ((e = cudaMemsetAsync(mem, 0, 3 * round256(fb) + L.total, st)) != cudaSuccess ||
+            (e = wf_prepare(sh.tile_y)) != cudaSuccess || (e = launch_wf(sh, m, p, st)) != cudaSuccess)
+            s = cuda_fail(e, "self-test launch");
+    }
+    const unsigned v = wf_status_take(st);
+    cudaFree(mem);
+    if (s != GBS_OK)
+        return s;
+    if (v != 0)
+        return fail((gbs_status)v, "self-test: the stalled launch recorded device status %u", v);
+    return fail(GBS_EINVAL, "self-test: the stalled launch recorded no error");
+}
+
 extern "C" size_t gbs_lp_workspace_bytes(int64_t nx, int64_t ny, int64_t nz)
 {
     if (nx < 0 || ny < 0 || nz < 0)

@@ -4,10 +4,13 @@ blocking) against the FP64 oracle and against the single-step path.
 Covers: the 64^3 constant-velocity Ricker problem with receivers, ragged
 and z-chunked grids with several sources (odd and even step counts, so
 pairs and trailing single steps both run), graph replay, restart at t0,
-host buffers, the fallback for shapes the fused kernel does not take, workspace errors,
+host buffers, the fallback for shapes the fused kernel does not take, workspace errors, the
+bounded waits (a launch whose counters never complete returns GBS_ETIMEOUT),
 and the full 512^3 layered workload in the launch configuration the
 benchmark times.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -157,6 +160,27 @@ def test_workspace_errors():
     small = torch.empty(1024, dtype=torch.uint8, device=dev())
     with pytest.raises(gbs.GbsError):
         gbs.wave_propagate_tb(z.clone(), z.clone(), z + 1500.0, 1e-3, 10.0, 4, 4, work=small)
+
+
+def test_bounded_waits_run_out_and_the_context_survives():
+    """Failure detection without a device fault: a fused pair whose block
+    counters never complete times out in every wait, records GBS_ETIMEOUT and
+    returns; the next calls run normally."""
+    need_gpu()
+    t0 = time.time()
+    st = gbs.selftest_tb_timeout()
+    elapsed = time.time() - t0
+    assert st == gbs.GBS_ETIMEOUT, st
+    assert elapsed < 30, elapsed
+    gbs.device_status()   # the status word was read and cleared by the self-test
+    prob, _ = _ricker64(6, nrec=1)
+    z = np.zeros(W.padded_shape(prob.nx, prob.ny, prob.nz, prob.halo), np.float32)
+    _, cur = gbs.wave_propagate_tb(to_dev(z), to_dev(z), to_dev(prob.vel), prob.dt, prob.h, prob.halo, 6,
+                                   src_idx=to_dev(prob.src_idx), src_amp=to_dev(prob.src_amp))
+    gbs.device_status()
+    _, ru, _ = oracle.wave_propagate(z, z, prob.vel, prob.dt, prob.h, prob.halo, 6,
+                                     src_idx=prob.src_idx, src_amp=prob.src_amp)
+    assert oracle.err_norms(cur.cpu().numpy(), ru)["norm_max_rel"] <= tol_steps(6)
 
 
 def test_full_size_pairs(layered512):
