@@ -208,8 +208,10 @@ gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float *vel, floa
  *                 caller; contents on entry do not matter.
  * Pairs of steps run fused when gbs_tb_supported() says so for the sizes,
  * the fields are 16-byte aligned, there are at most 16 sources and
- * opts->kernel is not 2; they run in an even number, and the remaining steps
- * (all of them otherwise) run as gbs_wave_propagate.
+ * opts->kernel is not 2.  Pairs alternate between (u_prev, u) and the
+ * workspace fields; after an odd number of pairs the two newest fields are
+ * copied back (two device-to-device copies).  A remaining odd step (all
+ * steps, when pairs cannot run fused) runs as gbs_wave_propagate.
  * Errors: GBS_EINVAL (as gbs_wave_propagate, a small, misaligned or
  * overlapping workspace, an absorbing layer), GBS_EALIGN, GBS_ECUDA.
  */

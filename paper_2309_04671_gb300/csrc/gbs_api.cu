@@ -673,10 +673,9 @@ extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float
     WfShape sh{};
     const bool fused = tma_shape_ok(g) && aligned16(u_prev) && aligned16(u) && aligned16(vel) &&
                        (!src || src->n <= kMaxFusedSrc) && !(opts && opts->kernel == 2) && wf_shape(g, &sh);
-    // pairs run in an even number so the levels end in (u_prev, u); the rest are single steps
-    int64_t npairs = fused ? nsteps / 2 : 0;
-    if (npairs & 1)
-        --npairs;
+    // pairs alternate between (u_prev, u) and the workspace fields; after an
+    // odd number the two newest fields are copied back; an odd last step runs single
+    const int64_t npairs = fused ? nsteps / 2 : 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (npairs > 0) {
         float *w1 = reinterpret_cast<float *>(static_cast<char *>(work) + L.off_w1);
@@ -734,6 +733,12 @@ extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float
                 if ((r = launch_record(g, lv[q][2], rec, pi.t, st)) != cudaSuccess ||
                     (r = launch_record(g, lv[q][3], rec, pi.t + 1, st)) != cudaSuccess)
                     return cuda_fail(r, "receiver launch");
+            }
+            if (npairs & 1) {
+                const size_t fbytes = (size_t)field_elems(g) * 4;
+                if ((r = cudaMemcpyAsync(u_prev, w1, fbytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+                    (r = cudaMemcpyAsync(u, w2, fbytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+                    return cuda_fail(r, "copy of the newest fields");
             }
             return GBS_OK;
         };

@@ -7,7 +7,8 @@ pairs and trailing single steps both run), graph replay, restart at t0,
 host buffers, the fallback for shapes the fused kernel does not take, workspace errors, the
 bounded waits (a launch whose counters never complete returns GBS_ETIMEOUT),
 and the full 512^3 layered workload in the launch configuration the
-benchmark times.
+benchmark times (one pair at sampled points against the oracle, two pairs
+against single steps, time reversal).
 """
 import time
 
@@ -213,6 +214,46 @@ def test_full_size_pairs(layered512):
     gbs.device_status()
     err = max(float(torch.max(torch.abs(pb - to_dev(u)))), float(torch.max(torch.abs(cb - to_dev(up)))))
     assert err <= tol_steps(16), err
+
+
+def test_full_size_one_pair_sampled_vs_oracle(layered512):
+    """512^3 layered model, one fused pair in the benchmark's launch
+    configuration, against the oracle at sampled points (tile seams in x and
+    y, faces, random interior).  u^{t+1} comes from the oracle's step at the
+    points; u^{t+2} from its step at the points with u^{t+1} given exactly
+    on their stars (the oracle's first step there, stored as FP32 like the
+    kernel's)."""
+    prob = layered512
+    n, halo = prob.nx, prob.halo
+    up = W.uniform_field(n, n, n, halo, 611, halo_random=False)
+    u = W.uniform_field(n, n, n, halo, 612, halo_random=False)
+    q0, q1 = gbs.wave_propagate_tb(to_dev(up), to_dev(u), to_dev(prob.vel), prob.dt, prob.h, halo, 2)
+    gbs.device_status()
+    rng = np.random.default_rng(13)
+    idx = rng.integers(0, n ** 3, 12000).astype(np.int64)
+    ii = np.array([0, 1, 27, 28, 55, 56, 63, 64, 255, 256, n - 2, n - 1])
+    extra = W.linear_index(ii[:, None, None], ii[None, :, None], ii[None, None, :], n, n).reshape(-1)
+    idx = np.unique(np.concatenate([idx, extra]))
+    i, j, k = idx % n, (idx // n) % n, idx // (n * n)
+    # the stars of the samples (radius 4 on each axis), inside the interior
+    pts = [idx]
+    for m in range(1, 5):
+        for di, dj, dk in ((m, 0, 0), (-m, 0, 0), (0, m, 0), (0, -m, 0), (0, 0, m), (0, 0, -m)):
+            ok = (i + di >= 0) & (i + di < n) & (j + dj >= 0) & (j + dj < n) & (k + dk >= 0) & (k + dk < n)
+            pts.append(W.linear_index(i[ok] + di, j[ok] + dj, k[ok] + dk, n, n))
+    star = np.unique(np.concatenate(pts))
+    u1_star = oracle.wave_points(up, u, prob.vel, prob.dt, prob.h, halo, star)
+    u1 = np.zeros_like(u)
+    si, sj, sk = star % n, (star // n) % n, star // (n * n)
+    u1[sk + halo, sj + halo, si + halo] = u1_star.astype(np.float32)
+    ref1 = u1_star[np.searchsorted(star, idx)]
+    ref2 = oracle.wave_points(u, u1, prob.vel, prob.dt, prob.h, halo, idx)
+    got1 = W.interior(q0.cpu().numpy(), halo).reshape(-1)[idx]
+    got2 = W.interior(q1.cpu().numpy(), halo).reshape(-1)[idx]
+    e1 = oracle.err_norms(got1, ref1)
+    e2 = oracle.err_norms(got2, ref2)
+    assert e1["norm_max_rel"] <= tol_steps(1), e1
+    assert e2["norm_max_rel"] <= tol_steps(2), e2
 
 
 @pytest.fixture(scope="module")
