@@ -228,6 +228,35 @@ gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float *vel, floa
  */
 int gbs_tb_supported(int64_t nx, int64_t ny, int64_t nz, int halo, int *tile_y, int *ctas);
 /*
+ * Algorithm 1 on HOST fields: the same steps as gbs_wave_propagate
+ * (time_block = 0) or gbs_wave_propagate_tb (time_block = 2), with every
+ * host<->device copy inside the call.  Enqueued on `stream`: the fields,
+ * the source arrays and the receiver indices are copied to the device
+ * workspace, the steps run there, and the two newest fields and the trace
+ * rows the run wrote are copied back.  The host buffers hold the results
+ * once `stream` has been synchronised; pinned memory makes the copies
+ * asynchronous.
+ *   u_prev, u, vel  HOST float, padded layout; on entry (u^{t0-1}, u^{t0});
+ *                 on return u holds u^{t0+nsteps} and u_prev u^{t0+nsteps-1}
+ *                 whatever the parity of nsteps.
+ *   src, rec      optional; their idx, amp and trace pointers are HOST
+ *                 pointers.  Trace rows outside [t0, t0+nsteps) are left as
+ *                 they were.
+ *   work          DEVICE scratch of at least gbs_host_workspace_bytes(nx,
+ *                 ny, nz, halo, src->n, src->nt, rec->n, rec->nt,
+ *                 time_block) bytes, 16-byte aligned, owned by the caller.
+ * Other arguments as gbs_wave_propagate.  Errors: GBS_EINVAL (as the device
+ * calls, a bad time_block, a small or misaligned workspace), GBS_EALIGN,
+ * GBS_ECUDA.
+ */
+size_t gbs_host_workspace_bytes(int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsrc, int64_t src_nt,
+                                int64_t nrec, int64_t rec_nt, int time_block);
+gbs_status gbs_wave_propagate_host(float *u_prev, float *u, const float *vel, float dt, float h,
+                                   int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                                   int64_t t0, const gbs_src *src, const gbs_rec *rec, int time_block,
+                                   void *work, size_t work_bytes, const gbs_opts *opts, void *stream);
+
+/*
  * Self-test of the bounded waits (failure detection without a device fault).
  * Launches one fused pair on a 64^3 zero grid in buffers it allocates,
  * with an epoch its block counters never reach: stage B's copies wait on

@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4
 # Entry points declared in include/gbstencil.h (checked by the tests).
 EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
            "gbs_wave_propagate_lp", "gbs_tb_workspace_bytes", "gbs_wave_propagate_tb", "gbs_tb_supported",
-           "gbs_selftest_tb_timeout",
+           "gbs_selftest_tb_timeout", "gbs_host_workspace_bytes", "gbs_wave_propagate_host",
            "gbs_norms_workspace_bytes", "gbs_field_norms", "gbs_field_norms_noalloc",
            "gbs_batch_plan_create", "gbs_batch_run", "gbs_batch_plan_info", "gbs_batch_plan_destroy",
            "gbs_adjoint_workspace_bytes", "gbs_adjoint_forward", "gbs_adjoint_backward", "gbs_fwi_gradient",
@@ -110,6 +110,12 @@ def load() -> ctypes.CDLL:
         lib.gbs_wave_propagate_tb.restype = c_int
         lib.gbs_tb_supported.argtypes = [i64, i64, i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
         lib.gbs_tb_supported.restype = c_int
+        lib.gbs_host_workspace_bytes.argtypes = [i64, i64, i64, c_int, i64, i64, i64, i64, c_int]
+        lib.gbs_host_workspace_bytes.restype = ctypes.c_size_t
+        lib.gbs_wave_propagate_host.argtypes = [vp, vp, vp, c_float, c_float, i64, i64, i64, c_int, i64, i64,
+                                                ctypes.POINTER(_Src), ctypes.POINTER(_Rec), c_int, vp,
+                                                ctypes.c_size_t, ctypes.POINTER(_Opts), vp]
+        lib.gbs_wave_propagate_host.restype = c_int
         lib.gbs_selftest_tb_timeout.argtypes = [vp]
         lib.gbs_selftest_tb_timeout.restype = c_int
         lib.gbs_norms_workspace_bytes.argtypes = [i64, i64]
@@ -344,25 +350,41 @@ def wave_propagate(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, dt:
     return (u, u_prev) if nsteps % 2 else (u_prev, u)
 
 
+def _host_tensor(t: torch.Tensor, name: str, dtype) -> int:
+    if t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} CPU tensor")
+    return t.data_ptr()
+
+
 def _wave_propagate_host(u_prev, u, vel, dt, h, halo, nsteps, *, t0, src_idx, src_amp, rec_idx, rec_trace,
-                         kernel, tile_y, zchunk, use_graph, stream):
-    dev = torch.device("cuda", torch.cuda.current_device())
-    d_prev = u_prev.to(dev, non_blocking=True)
-    d_u = u.to(dev, non_blocking=True)
-    d_vel = vel.to(dev, non_blocking=True)
-    d_si = src_idx.to(dev, non_blocking=True) if src_idx is not None else None
-    d_sa = src_amp.to(dev, non_blocking=True) if src_amp is not None else None
-    d_ri = rec_idx.to(dev, non_blocking=True) if rec_idx is not None else None
-    d_tr = rec_trace.to(dev, non_blocking=True) if rec_trace is not None else None
-    a, b = wave_propagate(d_prev, d_u, d_vel, dt, h, halo, nsteps, t0=t0, src_idx=d_si, src_amp=d_sa,
-                          rec_idx=d_ri, rec_trace=d_tr, kernel=kernel, tile_y=tile_y, zchunk=zchunk,
-                          use_graph=use_graph, stream=stream)
-    # results land in the caller's host buffers: newest field into `u`, previous into `u_prev`
-    u.copy_(b, non_blocking=True)
-    u_prev.copy_(a, non_blocking=True)
-    if rec_trace is not None:
-        rec_trace.copy_(d_tr, non_blocking=True)
-    torch.cuda.current_stream().synchronize()
+                         kernel, tile_y, zchunk, use_graph, stream, time_block=0):
+    """Host tensors through gbs_wave_propagate_host: the copies to and from
+    the device happen inside the library call.  The newest field lands in
+    ``u``, the one before in ``u_prev``."""
+    p = [_host_tensor(t, n, torch.float32) for t, n in ((u_prev, "u_prev"), (u, "u"), (vel, "vel"))]
+    _same_shape(u, u_prev, vel)
+    nx, ny, nz = _dims(u, halo)
+    src = rec = None
+    nsrc = snt = nrec = rnt = 0
+    if src_idx is not None and src_idx.numel() > 0:
+        nsrc = src_idx.numel()
+        snt = src_amp.numel() // nsrc
+        src = _Src(nsrc, _host_tensor(src_idx, "src_idx", torch.int64), _host_tensor(src_amp, "src_amp", torch.float32),
+                   snt)
+    if rec_idx is not None and rec_idx.numel() > 0:
+        nrec = rec_idx.numel()
+        rnt = rec_trace.numel() // nrec
+        rec = _Rec(nrec, _host_tensor(rec_idx, "rec_idx", torch.int64),
+                   _host_tensor(rec_trace, "rec_trace", torch.float32), rnt)
+    lib = load()
+    nbytes = int(lib.gbs_host_workspace_bytes(nx, ny, nz, halo, nsrc, snt, nrec, rnt, int(time_block)))
+    work = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=torch.device("cuda", torch.cuda.current_device()))
+    opts = _opts(kernel, tile_y, zchunk, use_graph)
+    st = _stream(stream)
+    _check(lib.gbs_wave_propagate_host(p[0], p[1], p[2], float(dt), float(h), nx, ny, nz, halo, int(nsteps), int(t0),
+                                       _ptr(src), _ptr(rec), int(time_block), work.data_ptr(), nbytes,
+                                       ctypes.byref(opts), st))
+    (stream if stream is not None else torch.cuda.current_stream()).synchronize()
     return u_prev, u
 
 
@@ -398,18 +420,9 @@ def wave_propagate_tb(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, 
     runs, copies both fields (and the trace) back, and returns CPU tensors.
     """
     if not u.is_cuda:
-        dev = torch.device("cuda", torch.cuda.current_device())
-        d = [None if x is None else x.to(dev, non_blocking=True)
-             for x in (u_prev, u, vel, src_idx, src_amp, rec_idx, rec_trace)]
-        a, b = wave_propagate_tb(d[0], d[1], d[2], dt, h, halo, nsteps, t0=t0, src_idx=d[3], src_amp=d[4],
-                                 rec_idx=d[5], rec_trace=d[6], work=work, kernel=kernel, use_graph=use_graph,
-                                 stream=stream)
-        u.copy_(b, non_blocking=True)
-        u_prev.copy_(a, non_blocking=True)
-        if rec_trace is not None:
-            rec_trace.copy_(d[6], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        return u_prev, u
+        return _wave_propagate_host(u_prev, u, vel, dt, h, halo, nsteps, t0=t0, src_idx=src_idx, src_amp=src_amp,
+                                    rec_idx=rec_idx, rec_trace=rec_trace, kernel=kernel, tile_y=0, zchunk=0,
+                                    use_graph=use_graph, stream=stream, time_block=2)
     p = [_field(t, n) for t, n in ((u_prev, "u_prev"), (u, "u"), (vel, "vel"))]
     _same_shape(u, u_prev, vel)
     nx, ny, nz = _dims(u, halo)

@@ -1,5 +1,6 @@
 // C ABI of the gbstencil library (include/gbstencil.h): argument checks,
 // TMA descriptor set-up, kernel choice and the time loop of Algorithm 1.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -750,6 +751,127 @@ extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float
     if (rest == 0)
         return GBS_OK;
     return gbs_wave_propagate(u_prev, u, vel, dt, h, nx, ny, nz, halo, rest, t0 + 2 * npairs, src, rec, opts, stream);
+}
+
+namespace gbs {
+namespace {
+// Device workspace of the host-buffer entry: the three fields, the source
+// and receiver arrays, and (time-blocked) the pair workspace.
+struct HostLayout {
+    size_t off_up, off_u, off_vel, off_sidx, off_samp, off_ridx, off_tr, off_tb, total;
+};
+HostLayout host_layout(const Grid &g, int64_t nsrc, int64_t snt, int64_t nrec, int64_t rnt, int time_block)
+{
+    const size_t fb = round256((size_t)field_elems(g) * 4);
+    HostLayout L;
+    size_t off = 0;
+    L.off_up = off;
+    off += fb;
+    L.off_u = off;
+    off += fb;
+    L.off_vel = off;
+    off += fb;
+    L.off_sidx = off;
+    off += round256((size_t)std::max<int64_t>(nsrc, 0) * 8);
+    L.off_samp = off;
+    off += round256((size_t)std::max<int64_t>(nsrc, 0) * (size_t)std::max<int64_t>(snt, 0) * 4);
+    L.off_ridx = off;
+    off += round256((size_t)std::max<int64_t>(nrec, 0) * 8);
+    L.off_tr = off;
+    off += round256((size_t)std::max<int64_t>(nrec, 0) * (size_t)std::max<int64_t>(rnt, 0) * 4);
+    L.off_tb = off;
+    if (time_block == 2)
+        off += tb_layout(g).total;
+    L.total = off;
+    return L;
+}
+}  // namespace
+}  // namespace gbs
+
+extern "C" size_t gbs_host_workspace_bytes(int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsrc,
+                                           int64_t src_nt, int64_t nrec, int64_t rec_nt, int time_block)
+{
+    if (check_dims(nx, ny, nz, halo) != GBS_OK || nsrc < 0 || src_nt < 0 || nrec < 0 || rec_nt < 0 ||
+        (time_block != 0 && time_block != 2))
+        return 0;
+    return host_layout(dense_grid(nx, ny, nz, halo), nsrc, src_nt, nrec, rec_nt, time_block).total;
+}
+
+extern "C" gbs_status gbs_wave_propagate_host(float *u_prev, float *u, const float *vel, float dt, float h,
+                                              int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                                              int64_t t0, const gbs_src *src, const gbs_rec *rec, int time_block,
+                                              void *work, size_t work_bytes, const gbs_opts *opts, void *stream)
+{
+    t_err[0] = 0;
+    gbs_status s = check_dims(nx, ny, nz, halo);
+    if (s != GBS_OK)
+        return s;
+    if (time_block != 0 && time_block != 2)
+        return fail(GBS_EINVAL, "time_block must be 0 (one launch per step) or 2 (fused pairs)");
+    if (nsteps < 0 || t0 < 0)
+        return fail(GBS_EINVAL, "nsteps and t0 must be >= 0");
+    if ((s = check_src_rec(src, rec)) != GBS_OK)
+        return s;
+    if (!u_prev || !u || !vel)
+        return fail(GBS_EINVAL, "null field pointer");
+    if (u_prev == u)
+        return fail(GBS_EINVAL, "u_prev and u are the same buffer");
+    if (nx == 0 || ny == 0 || nz == 0 || nsteps == 0)
+        return GBS_OK;
+    const Grid g = dense_grid(nx, ny, nz, halo);
+    const int64_t nsrc = src ? src->n : 0, snt = src ? src->nt : 0;
+    const int64_t nrec = rec ? rec->n : 0, rnt = rec ? rec->nt : 0;
+    const HostLayout L = host_layout(g, nsrc, snt, nrec, rnt, time_block);
+    if (!work || work_bytes < L.total || !aligned16(work))
+        return fail(GBS_EINVAL, "workspace needs %zu bytes, 16-byte aligned (gbs_host_workspace_bytes)", L.total);
+    char *w = static_cast<char *>(work);
+    float *d_up = reinterpret_cast<float *>(w + L.off_up), *d_u = reinterpret_cast<float *>(w + L.off_u);
+    float *d_vel = reinterpret_cast<float *>(w + L.off_vel);
+    const size_t fb = (size_t)field_elems(g) * 4;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    auto h2d = [&](void *dst, const void *srcp, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, srcp, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+    };
+    auto d2h = [&](void *dst, const void *srcp, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, srcp, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
+    };
+    gbs_src dsrc{0, nullptr, nullptr, 0};
+    gbs_rec drec{0, nullptr, nullptr, 0};
+    if ((e = h2d(d_up, u_prev, fb)) != cudaSuccess || (e = h2d(d_u, u, fb)) != cudaSuccess ||
+        (e = h2d(d_vel, vel, fb)) != cudaSuccess)
+        return cuda_fail(e, "copy of the fields to the device");
+    if (nsrc > 0) {
+        dsrc = {nsrc, reinterpret_cast<const int64_t *>(w + L.off_sidx), reinterpret_cast<const float *>(w + L.off_samp),
+                snt};
+        if ((e = h2d(w + L.off_sidx, src->idx, (size_t)nsrc * 8)) != cudaSuccess ||
+            (e = h2d(w + L.off_samp, src->amp, (size_t)nsrc * snt * 4)) != cudaSuccess)
+            return cuda_fail(e, "copy of the sources to the device");
+    }
+    // receiver rows the run writes: [t0, t0 + nsteps) within [0, rnt)
+    const int64_t r0 = std::min(t0, rnt), r1 = std::min(t0 + nsteps, rnt);
+    if (nrec > 0) {
+        drec = {nrec, reinterpret_cast<const int64_t *>(w + L.off_ridx), reinterpret_cast<float *>(w + L.off_tr), rnt};
+        if ((e = h2d(w + L.off_ridx, rec->idx, (size_t)nrec * 8)) != cudaSuccess)
+            return cuda_fail(e, "copy of the receivers to the device");
+    }
+    s = time_block == 2
+            ? gbs_wave_propagate_tb(d_up, d_u, d_vel, dt, h, nx, ny, nz, halo, nsteps, t0, nsrc > 0 ? &dsrc : nullptr,
+                                    nrec > 0 ? &drec : nullptr, w + L.off_tb, L.total - L.off_tb, opts, stream)
+            : gbs_wave_propagate(d_up, d_u, d_vel, dt, h, nx, ny, nz, halo, nsteps, t0, nsrc > 0 ? &dsrc : nullptr,
+                                 nrec > 0 ? &drec : nullptr, opts, stream);
+    if (s != GBS_OK)
+        return s;
+    // the newest level into u, the one before into u_prev (on the device the
+    // buffers alternate: after an odd number of steps d_up holds the newest)
+    const float *newest = (nsteps & 1) ? d_up : d_u, *older = (nsteps & 1) ? d_u : d_up;
+    if ((e = d2h(u, newest, fb)) != cudaSuccess || (e = d2h(u_prev, older, fb)) != cudaSuccess)
+        return cuda_fail(e, "copy of the fields to the host");
+    if (nrec > 0 && r1 > r0 &&
+        (e = d2h(rec->trace + r0 * nrec, reinterpret_cast<float *>(w + L.off_tr) + r0 * nrec,
+                 (size_t)(r1 - r0) * nrec * 4)) != cudaSuccess)
+        return cuda_fail(e, "copy of the trace to the host");
+    return GBS_OK;
 }
 
 extern "C" gbs_status gbs_selftest_tb_timeout(void *stream)

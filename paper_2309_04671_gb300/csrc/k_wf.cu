@@ -68,10 +68,10 @@ struct WfCfg {
     static constexpr int PVU_BYTES = kTX * TY * 4;  // u_prev tile; the vel tile follows
     static constexpr int PV_BYTES = 2 * PVU_BYTES;
     static constexpr int PV_STRIDE = (PV_BYTES + 127) / 128 * 128;
-    // Ring depths.  A u stage holds a plane from its arrival until it has been
-    // the stencil centre (R planes later), so SL = R + 1 + planes in flight.
-    // Stage A streams from DRAM and keeps more planes in flight than stage B,
-    // whose loads are mostly served from L2.
+    // Ring depths.  The semi-stencil sweep reads a plane only when it lands,
+    // so a ring holds one stage in use and the rest in flight.  Stage A
+    // streams from DRAM and keeps more planes in flight than stage B, whose
+    // loads are mostly served from L2.  TY = 28: 218 KB of shared memory.
     static constexpr bool TALL = TY >= 24;
     static constexpr int SL_A = TALL ? 6 : 8;
     static constexpr int SP_A = TALL ? 5 : 6;
@@ -263,9 +263,9 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
     return __all_sync(0xffffffffu, ok);
 }
 
-// Compute warps of one stage (STAGE 0 writes u^{t+1}, STAGE 1 u^{t+2}), in
-// the semi-stencil form: each plane is used only when it
-// arrives.  At arrival j a thread forms, for its points, the new accumulator
+// Compute warps of one stage (STAGE 0 writes u^{t+1}, STAGE 1 u^{t+2}) in the
+// semi-stencil form: each plane is used only when it arrives.  At arrival j
+// a thread forms, for its points, the new accumulator
 //   acc(j) = c0 u(j) + sum_m c_m [x, y neighbours at distance m in plane j]
 //                    + sum_m c_m u(j - m)
 // and adds c_m u(j) to the pending accumulators of planes j - m; the

@@ -240,3 +240,30 @@ def test_tb_workspace_and_validation(lib):
     assert call(*args(fake[0], fake[1], work, big, opts=absorb)) == gbs.GBS_EINVAL
     assert call(*args(fake[0], fake[1], work, big, nsteps=0)) == gbs.GBS_OK
     assert call(*args(fake[0], fake[1], work, big, nsteps=-1)) == gbs.GBS_EINVAL
+
+
+def test_host_entry_workspace_and_validation(lib):
+    n = (8 + 8) ** 3 * 4
+    r = lambda v: (v + 255) // 256 * 256
+    base = 3 * r(n) + r(2 * 8) + r(2 * 10 * 4) + r(5 * 8) + r(5 * 7 * 4)
+    assert lib.gbs_host_workspace_bytes(8, 8, 8, 4, 2, 10, 5, 7, 0) == base
+    tb = lib.gbs_tb_workspace_bytes(8, 8, 8, 4)
+    assert lib.gbs_host_workspace_bytes(8, 8, 8, 4, 2, 10, 5, 7, 2) == base + tb
+    assert lib.gbs_host_workspace_bytes(8, 8, 8, 4, 0, 0, 0, 0, 1) == 0        # time_block must be 0 or 2
+    assert lib.gbs_host_workspace_bytes(-8, 8, 8, 4, 0, 0, 0, 0, 0) == 0
+    host = [np.zeros((16, 16, 16), np.float32) for _ in range(3)]
+    p = [ctypes.c_void_p(a.ctypes.data) for a in host]
+    work = ctypes.c_void_p(1 << 26)
+    big = ctypes.c_size_t(1 << 30)
+    call = lib.gbs_wave_propagate_host
+
+    def args(up, u, tblock=0, w=work, wb=big, nsteps=3):
+        return (up, u, p[2], ctypes.c_float(1e-3), ctypes.c_float(10.0), 8, 8, 8, 4, nsteps, 0, None, None, tblock,
+                w, wb, None, None)
+
+    assert call(*args(p[0], p[0])) == gbs.GBS_EINVAL                          # same buffer twice
+    assert call(*args(p[0], p[1], tblock=1)) == gbs.GBS_EINVAL                # bad time_block
+    assert call(*args(p[0], p[1], w=None)) == gbs.GBS_EINVAL                  # no workspace
+    assert call(*args(p[0], p[1], wb=ctypes.c_size_t(1024))) == gbs.GBS_EINVAL
+    assert call(*args(None, p[1])) == gbs.GBS_EINVAL
+    assert call(*args(p[0], p[1], nsteps=0)) == gbs.GBS_OK
