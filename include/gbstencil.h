@@ -96,7 +96,7 @@ typedef struct {
     int tile_y;     /* rows per CTA tile of the TMA kernel: 16 or 32 (x is always 64) */
     int zchunk;     /* planes streamed per CTA (>= 1) */
     int use_graph;  /* wave_propagate: 1 = capture the step loop in a CUDA graph and replay it */
-    /* gbs_wave_propagate (FP32, TMA kernel) only: an absorbing layer of
+    /* gbs_wave_propagate and gbs_wave_propagate_tb (FP32, TMA kernels) only: an absorbing layer of
      * absorb_width cells (<= 64) inside every face of the interior, the
      * damped wave equation u_tt + 2 eta u_t = V^2 lap u with a centred u_t:
      *   u^{n+1} = [2u^n - (1 - eta dt) u^{n-1} + dt^2 V^2 lap u^n] / (1 + eta dt)
@@ -200,8 +200,8 @@ gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float *vel, floa
  * Sec. 9.3), so the fields agree with gbs_wave_propagate to FP32 rounding, not
  * bit for bit.
  *   u_prev, u, vel, dt, h, sizes, halo, nsteps, t0, src, rec, opts
- *                 as gbs_wave_propagate, with the same parity rule on return
- *                 (no absorbing layer).
+ *                 as gbs_wave_propagate (absorbing layer included), with the
+ *                 same parity rule on return.
  *   work          DEVICE scratch of at least gbs_tb_workspace_bytes(nx, ny,
  *                 nz, halo) bytes (two fields and the block counters),
  *                 16-byte aligned, not overlapping the fields, owned by the
@@ -213,7 +213,7 @@ gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float *vel, floa
  * copied back (two device-to-device copies).  A remaining odd step (all
  * steps, when pairs cannot run fused) runs as gbs_wave_propagate.
  * Errors: GBS_EINVAL (as gbs_wave_propagate, a small, misaligned or
- * overlapping workspace, an absorbing layer), GBS_EALIGN, GBS_ECUDA.
+ * overlapping workspace), GBS_EALIGN, GBS_ECUDA.
  */
 size_t gbs_tb_workspace_bytes(int64_t nx, int64_t ny, int64_t nz, int halo);
 gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float *vel, float dt, float h,

@@ -409,7 +409,7 @@ def tb_supported(nx: int, ny: int, nz: int, halo: int) -> tuple[bool, int, int]:
 def wave_propagate_tb(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, dt: float, h: float,
                       halo: int, nsteps: int, *, t0: int = 0, src_idx=None, src_amp=None, rec_idx=None,
                       rec_trace=None, work: Optional[torch.Tensor] = None, kernel: int = 0,
-                      use_graph: bool = False, stream=None):
+                      use_graph: bool = False, absorb=None, stream=None):
     """Algorithm 1 with 2-step temporal blocking: the fields of wave_propagate
     (to FP32 rounding: the z sums run in the semi-stencil order), with pairs
     of steps fused into one launch.
@@ -420,6 +420,8 @@ def wave_propagate_tb(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, 
     runs, copies both fields (and the trace) back, and returns CPU tensors.
     """
     if not u.is_cuda:
+        if absorb:
+            raise ValueError("the absorbing layer takes device tensors")
         return _wave_propagate_host(u_prev, u, vel, dt, h, halo, nsteps, t0=t0, src_idx=src_idx, src_amp=src_amp,
                                     rec_idx=rec_idx, rec_trace=rec_trace, kernel=kernel, tile_y=0, zchunk=0,
                                     use_graph=use_graph, stream=stream, time_block=2)
@@ -432,7 +434,8 @@ def wave_propagate_tb(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, 
         raise ValueError("work must be a contiguous device tensor")
     src = _make_src(src_idx, src_amp)
     rec = _make_rec(rec_idx, rec_trace)
-    opts = _opts(kernel, 0, 0, use_graph)
+    ab = (absorb[0], absorb[1], absorb[2] if len(absorb) > 2 else False) if absorb else None
+    opts = _opts(kernel, 0, 0, use_graph, ab)
     _check(load().gbs_wave_propagate_tb(p[0], p[1], p[2], float(dt), float(h), nx, ny, nz, halo, int(nsteps),
                                         int(t0), _ptr(src), _ptr(rec), work.data_ptr(),
                                         work.numel() * work.element_size(), ctypes.byref(opts), _stream(stream)))

@@ -650,8 +650,6 @@ extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float
         return fail(GBS_EINVAL, "nsteps and t0 must be >= 0");
     if ((s = check_src_rec(src, rec)) != GBS_OK)
         return s;
-    if (absorb_requested(opts))
-        return fail(GBS_EINVAL, "the time-blocked propagation has no absorbing layer");
     if (nx == 0 || ny == 0 || nz == 0 || nsteps == 0)
         return GBS_OK;
     const Grid g = dense_grid(nx, ny, nz, halo);
@@ -710,6 +708,8 @@ extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float
         p.inx = nx;
         p.iny = ny;
         p.words = words;
+        if ((s = absorb_plan(opts, dt, 1, &p.ab)) != GBS_OK)
+            return s;
         cudaError_t e = wf_prepare(ty);
         if (e != cudaSuccess)
             return cuda_fail(e, "kernel attributes");

@@ -25,6 +25,7 @@ struct WfParams {
     int nblk;                    // blocks of kWfBlock stage-A planes per CTA
     unsigned epoch;              // launches on the same counters so far, this one included (>= 1)
     int64_t t;                   // time level of u (the launch writes u^{t+1} and u^{t+2})
+    Absorb ab;                   // absorbing layer (width 0 = none)
 };
 
 // Tensor maps of one launch: stage A reads u^t (box 72 x (TY+8)) and u^{t-1}

@@ -42,10 +42,16 @@
 // in another order than the single-step kernel, so the fields agree with it
 // to FP32 rounding.
 //
+// Absorbing layer (optional): both stages apply the damped update
+// u^{t+1} = A (2u^t - B u^{t-1} + (V dt)^2 lap u^t) at points within the
+// layer, A and B tabulated by the distance to the nearest absorbing face.
+//
 // z-chunks.  When the tiles alone do not fill the device, the z range is
 // split; stage A of a chunk then also computes the R planes either side of
 // it (stage B's z halo).  Neighbouring chunks compute those planes from the
 // same inputs with the same arithmetic and store the same bits.
+#include <algorithm>
+
 #include "gbs_wf.cuh"
 
 namespace gbs {
@@ -271,10 +277,10 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
 // and adds c_m u(j) to the pending accumulators of planes j - m; the
 // accumulator of plane j - R is then complete.  The queue holds u and the
 // accumulators of the last R planes; the u stage is free after the arrival.
-template <int TY, int STAGE>
+template <int TY, int STAGE, bool AB>
 __device__ __forceinline__ void wf_consumer(const WfParams &p, const Ring &rg, const int64_t tx0, const int64_t ty0,
                                             const int chunk, int *s_nsrc, int *s_src_x, int *s_src_y, int *s_src_z,
-                                            float *s_src_f)
+                                            float *s_src_f, const float2 *s_ab)
 {
     using C = WfCfg<TY>;
     constexpr int SL = STAGE == 0 ? C::SL_A : C::SL_B;
@@ -322,6 +328,12 @@ __device__ __forceinline__ void wf_consumer(const WfParams &p, const Ring &rg, c
     float *out_base = p.out[STAGE] + (H + gx) + g.px * (H + gy);
     const int64_t plane_stride = g.px * g.py;
     const uint64_t pol_out = STAGE == 0 ? policy_evict_last() : policy_evict_first();
+    // absorbing layer: sizes in 32 bits, and whether the tile lies inside the
+    // layer's inner boundary in x and y (then only z decides, uniformly)
+    const int aw = p.ab.width;
+    const int ab_nx = (int)g.nx, ab_ny = (int)g.ny, ab_nz = (int)g.nz;
+    const bool ab_tile_in = tx0 >= aw && tx0 + kTX <= g.nx - aw && ty0 >= aw && ty0 + TY <= g.ny - aw;
+    (void)ab_nx; (void)ab_ny; (void)ab_nz; (void)ab_tile_in;
 
     // V[a][r]: u of plane j - R + a; A*[a][r]: pending accumulator of plane j - R + a (a = 0..R-1)
     float4 V[kR][kVY];
@@ -401,10 +413,40 @@ __device__ __forceinline__ void wf_consumer(const WfParams &p, const Ring &rg, c
                 vel4[r] = ld4(pvv + (kVY * ty + r) * kTX + 4 * tx);
                 const f2 vs_l = mul2(lo(vel4[r]), S2), vs_h = mul2(hi(vel4[r]), S2);
                 const f2 c_l = mul2(vs_l, vs_l), c_h = mul2(vs_h, vs_h);
-                const f2 t_l = sub2(add2(lo(u0), lo(u0)), lo(up));
-                const f2 t_h = sub2(add2(hi(u0), hi(u0)), hi(up));
-                res_l[r] = fma2(c_l, AL[0][r], t_l);
-                res_h[r] = fma2(c_h, AH[0][r], t_h);
+                bool damp = false;
+                if constexpr (AB) {
+                    // absorbing layer: u_next = A (2u - B u_prev + c lap), A and B by the
+                    // distance d < width to the nearest absorbing face (a uniform test first)
+                    const int dzk = p.ab.free_top ? ab_nz - 1 - k : min(k, ab_nz - 1 - k);
+                    if (!(ab_tile_in && dzk >= aw)) {
+                        const int yy = (int)gy + r;
+                        const int dyz = min(min(yy, ab_ny - 1 - yy), dzk);
+                        const int gxi = (int)gx;
+                        if (dyz < aw || gxi < aw || gxi + 3 >= ab_nx - aw) {
+                            float4 A4, B4;
+                            float *pa = &A4.x, *pb = &B4.x;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                int d = min(dyz, min(gxi + e, ab_nx - 1 - gxi - e));
+                                d = d < 0 ? 0 : d;   // lanes past the interior are not stored
+                                const float2 ab = d < aw ? s_ab[d] : make_float2(1.f, 1.f);
+                                pa[e] = ab.x;
+                                pb[e] = ab.y;
+                            }
+                            const f2 td_l = sub2(add2(lo(u0), lo(u0)), mul2(lo(B4), lo(up)));
+                            const f2 td_h = sub2(add2(hi(u0), hi(u0)), mul2(hi(B4), hi(up)));
+                            res_l[r] = mul2(lo(A4), fma2(c_l, AL[0][r], td_l));
+                            res_h[r] = mul2(hi(A4), fma2(c_h, AH[0][r], td_h));
+                            damp = true;
+                        }
+                    }
+                }
+                if (!damp) {
+                    const f2 t_l = sub2(add2(lo(u0), lo(u0)), lo(up));
+                    const f2 t_h = sub2(add2(hi(u0), hi(u0)), hi(up));
+                    res_l[r] = fma2(c_l, AL[0][r], t_l);
+                    res_h[r] = fma2(c_h, AH[0][r], t_h);
+                }
             }
             __syncwarp();
             if (lane == 0)
@@ -561,7 +603,7 @@ __device__ __forceinline__ void wf_producer(const CUtensorMap *__restrict__ pm_u
 
 // CTA b: tile b % tiles, z-chunk b / tiles.  Warps: stage-A compute
 // [0, NT), stage-B compute [NT, 2 NT), then one copy-issuing warp per stage.
-template <int TY>
+template <int TY, bool AB>
 __global__ void __launch_bounds__(2 * WfCfg<TY>::NT + 64, 1)
     k_wf(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_pa,
          const __grid_constant__ CUtensorMap tm_ub, const __grid_constant__ CUtensorMap tm_pb,
@@ -574,6 +616,9 @@ __global__ void __launch_bounds__(2 * WfCfg<TY>::NT + 64, 1)
     __shared__ int s_src_x[2][kMaxFusedSrc], s_src_y[2][kMaxFusedSrc], s_src_z[2][kMaxFusedSrc];
     __shared__ float s_src_f[2][kMaxFusedSrc];
     __shared__ int s_bnext;   // stage B's next u^{t+1} plane to copy
+    // absorbing layer: A, B by distance (threads look up different distances;
+    // divergent constant-bank reads would serialise)
+    __shared__ float2 s_ab[kMaxAbsorb];
     const int ntiles = p.tiles_x * p.tiles_y;
     const int tile = (int)(blockIdx.x % (unsigned)ntiles);
     const int chunk = (int)(blockIdx.x / (unsigned)ntiles);
@@ -633,19 +678,22 @@ __global__ void __launch_bounds__(2 * WfCfg<TY>::NT + 64, 1)
         s_nsrc[1] = 0;
         s_bnext = stage_geo(p, chunk, 1).pfirst;
     }
+    if constexpr (AB)
+        for (int i = threadIdx.x; i < p.ab.width; i += blockDim.x)
+            s_ab[i] = make_float2(p.ab.A[i], p.ab.B[i]);
     __syncthreads();
     const int w = threadIdx.x / 32;
     if (w < NW)
-        wf_consumer<TY, 0>(p, ra, tx0, ty0, chunk, &s_nsrc[0], s_src_x[0], s_src_y[0], s_src_z[0], s_src_f[0]);
+        wf_consumer<TY, 0, AB>(p, ra, tx0, ty0, chunk, &s_nsrc[0], s_src_x[0], s_src_y[0], s_src_z[0], s_src_f[0], s_ab);
     else if (w < 2 * NW)
-        wf_consumer<TY, 1>(p, rb, tx0, ty0, chunk, &s_nsrc[1], s_src_x[1], s_src_y[1], s_src_z[1], s_src_f[1]);
+        wf_consumer<TY, 1, AB>(p, rb, tx0, ty0, chunk, &s_nsrc[1], s_src_x[1], s_src_y[1], s_src_z[1], s_src_f[1], s_ab);
     else if (w == 2 * NW && (threadIdx.x & 31) == 0)
         wf_producer<TY, 0>(&tm_ua, &tm_pa, &tm_vel, p, ra, tx0, ty0, tile, chunk, &s_bnext);
     else if (w == 2 * NW + 1 && (threadIdx.x & 31) == 0)
         wf_producer<TY, 1>(&tm_ub, &tm_pb, &tm_vel, p, rb, tx0, ty0, tile, chunk, &s_bnext);
 }
 
-template <int TY>
+template <int TY, bool AB>
 cudaError_t prepare_t()
 {
     static bool done[64] = {};
@@ -655,32 +703,38 @@ cudaError_t prepare_t()
         return e;
     if (dev >= 0 && dev < 64 && done[dev])
         return cudaSuccess;
-    e = cudaFuncSetAttribute(k_wf<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WfCfg<TY>::SMEM);
+    e = cudaFuncSetAttribute(k_wf<TY, AB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WfCfg<TY>::SMEM);
     if (e == cudaSuccess && dev >= 0 && dev < 64)
         done[dev] = true;
     return e;
 }
 
-// CTAs the device holds at once for tile height TY (0 on error).
-template <int TY>
-int slots_t()
+// CTAs the device holds at once for tile height TY, with and without the
+// absorbing layer (the smaller of the two; 0 on error).
+template <int TY, bool AB>
+int slots_ab()
 {
-    if (prepare_t<TY>() != cudaSuccess)
+    if (prepare_t<TY, AB>() != cudaSuccess)
         return 0;
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wf<TY>, 2 * WfCfg<TY>::NT + 64, WfCfg<TY>::SMEM) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wf<TY, AB>, 2 * WfCfg<TY>::NT + 64,
+                                                      WfCfg<TY>::SMEM) != cudaSuccess)
         return 0;
     return sms * per;
 }
-
 template <int TY>
+int slots_t()
+{
+    return std::min(slots_ab<TY, false>(), slots_ab<TY, true>());
+}
+
+template <int TY, bool AB>
 cudaError_t launch_t(const WfShape &s, const WfMaps &m, const WfParams &p, cudaStream_t st)
 {
-    cudaError_t e = prepare_t<TY>();
+    cudaError_t e = prepare_t<TY, AB>();
     if (e != cudaSuccess)
         return e;
     cudaLaunchConfig_t cfg = {};
@@ -693,7 +747,7 @@ cudaError_t launch_t(const WfShape &s, const WfMaps &m, const WfParams &p, cudaS
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_wf<TY>, m.ua, m.pa, m.ub, m.pb, m.vel, p);
+    return cudaLaunchKernelEx(&cfg, k_wf<TY, AB>, m.ua, m.pa, m.ub, m.pb, m.vel, p);
 }
 
 }  // namespace
@@ -741,7 +795,13 @@ bool wf_shape(const Grid &g, WfShape *s)
     return found;
 }
 
-cudaError_t wf_prepare(int tile_y) { return tile_y == 28 ? prepare_t<28>() : prepare_t<16>(); }
+cudaError_t wf_prepare(int tile_y)
+{
+    cudaError_t e = tile_y == 28 ? prepare_t<28, false>() : prepare_t<16, false>();
+    if (e == cudaSuccess)
+        e = tile_y == 28 ? prepare_t<28, true>() : prepare_t<16, true>();
+    return e;
+}
 
 cudaError_t launch_wf(const WfShape &s, const WfMaps &m, const WfParams &p, cudaStream_t st)
 {
@@ -754,9 +814,10 @@ cudaError_t launch_wf(const WfShape &s, const WfMaps &m, const WfParams &p, cuda
     q.zchunk = s.zchunk;
     q.nchunks = s.nchunks;
     q.nblk = s.nblk;
+    const bool ab = q.ab.width > 0;
     switch (s.tile_y) {
-    case 28: return launch_t<28>(s, m, q, st);
-    case 16: return launch_t<16>(s, m, q, st);
+    case 28: return ab ? launch_t<28, true>(s, m, q, st) : launch_t<28, false>(s, m, q, st);
+    case 16: return ab ? launch_t<16, true>(s, m, q, st) : launch_t<16, false>(s, m, q, st);
     default: return cudaErrorInvalidValue;
     }
 }

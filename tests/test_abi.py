@@ -236,7 +236,7 @@ def test_tb_workspace_and_validation(lib):
     assert call(*args(fake[0], fake[1], None, big)) == gbs.GBS_EINVAL            # no workspace
     assert call(*args(fake[0], fake[1], ctypes.c_void_p((1 << 26) + 4), big)) == gbs.GBS_EINVAL   # misaligned
     assert call(*args(fake[0], fake[1], fake[1], big)) == gbs.GBS_EINVAL         # workspace over a field
-    absorb = ctypes.byref(gbs._Opts(0, 0, 0, 0, 4, 10.0, 0))
+    absorb = ctypes.byref(gbs._Opts(0, 0, 0, 0, 65, 10.0, 0))   # absorbing layer wider than 64 cells
     assert call(*args(fake[0], fake[1], work, big, opts=absorb)) == gbs.GBS_EINVAL
     assert call(*args(fake[0], fake[1], work, big, nsteps=0)) == gbs.GBS_OK
     assert call(*args(fake[0], fake[1], work, big, nsteps=-1)) == gbs.GBS_EINVAL

@@ -3,7 +3,9 @@ against the FP64 oracle's damped step.
 
 * layered model, Ricker source, all six faces absorbing and with a free
   top face, against oracle.wave_propagate_damped (per-step FP32 bound);
-* width 0 is the plain leapfrog bit for bit;
+* the same through fused pairs of steps (wave_propagate_tb), and at 512^3
+  against single steps;
+* width 0 is the plain leapfrog bit for bit (single steps and pairs);
 * a pulse loses most of its energy in the layer (as in the oracle pin);
 * the layer is rejected where it is not available (16-bit storage, the
   plain-load kernel, shapes the TMA kernel cannot take).
@@ -26,8 +28,9 @@ def _eta_max(width, vmax):
     return 3 * vmax * np.log(1e3) / (2 * width * h)
 
 
+@pytest.mark.parametrize("path", ["single", "pairs"])
 @pytest.mark.parametrize("free_top", [False, True])
-def test_absorbing_layer_against_oracle(free_top):
+def test_absorbing_layer_against_oracle(free_top, path):
     need_gpu()
     nx, ny, nz, nsteps, width = 48, 40, 36, 40, 8
     vel = W.layered_velocity(nx, ny, nz, H, 31)
@@ -38,8 +41,11 @@ def test_absorbing_layer_against_oracle(free_top):
     amp = np.stack([W.ricker(nsteps, dt, 15.0, t0=0.01), W.ricker(nsteps, dt, 20.0, t0=0.012)],
                    axis=1).astype(np.float32)
     z = np.zeros(W.padded_shape(nx, ny, nz, H), np.float32)
-    _, cur = gbs.wave_propagate(to_dev(z), to_dev(z), to_dev(vel), dt, h, H, nsteps, src_idx=to_dev(src),
-                                src_amp=to_dev(amp), absorb=(width, eta_max, free_top))
+    fn = gbs.wave_propagate if path == "single" else gbs.wave_propagate_tb
+    if path == "pairs":
+        assert gbs.tb_supported(nx, ny, nz, H)[0]
+    _, cur = fn(to_dev(z), to_dev(z), to_dev(vel), dt, h, H, nsteps, src_idx=to_dev(src),
+                src_amp=to_dev(amp), absorb=(width, eta_max, free_top))
     gbs.device_status()
     eta = oracle.absorbing_eta(nx, ny, nz, H, width, eta_max, free_surface=free_top)
     _, ref = oracle.wave_propagate_damped(z, z, vel, eta, dt, h, H, nsteps, src_idx=src, src_amp=amp)
@@ -57,6 +63,39 @@ def test_width_zero_is_the_plain_step():
     _, b = gbs.wave_propagate(to_dev(z), to_dev(z), *args, absorb=(0, 100.0), **kw)
     gbs.device_status()
     assert torch.equal(a, b)
+
+
+def test_pairs_width_zero_is_the_plain_pair():
+    need_gpu()
+    prob = W.small_constant_problem(n=48, nsteps=12)
+    z = np.zeros(W.padded_shape(48, 48, 48, H), np.float32)
+    args = (to_dev(prob.vel), prob.dt, prob.h, H, 12)
+    kw = dict(src_idx=to_dev(prob.src_idx), src_amp=to_dev(prob.src_amp))
+    _, a = gbs.wave_propagate_tb(to_dev(z), to_dev(z), *args, **kw)
+    _, b = gbs.wave_propagate_tb(to_dev(z), to_dev(z), *args, absorb=(0, 100.0), **kw)
+    gbs.device_status()
+    assert torch.equal(a, b)
+
+
+def test_pairs_full_size_against_single_steps():
+    """512^3 layered model with a 20-cell layer: fused pairs (the benchmark's
+    launch configuration) against single steps (the single-step layer is
+    checked against the oracle above), 10 steps."""
+    need_gpu()
+    prob = W.layered_problem(n=512, nsteps=10)
+    n, width = 512, 20
+    eta_max = _eta_max(width, float(W.interior(prob.vel, H).max()))
+    vel, si, sa = to_dev(prob.vel), to_dev(prob.src_idx), to_dev(prob.src_amp)
+    up = W.uniform_field(n, n, n, H, 701, halo_random=False)
+    u = W.uniform_field(n, n, n, H, 702, halo_random=False)
+    p0, c0 = gbs.wave_propagate(to_dev(up), to_dev(u), vel, prob.dt, prob.h, H, 10, src_idx=si, src_amp=sa,
+                                absorb=(width, eta_max))
+    p1, c1 = gbs.wave_propagate_tb(to_dev(up), to_dev(u), vel, prob.dt, prob.h, H, 10, src_idx=si, src_amp=sa,
+                                   absorb=(width, eta_max))
+    gbs.device_status()
+    scale = float(torch.max(torch.abs(c0)))
+    err = max(float(torch.max(torch.abs(c1 - c0))), float(torch.max(torch.abs(p1 - p0))))
+    assert err <= tol_steps(10) * scale, (err, scale)
 
 
 def test_pulse_is_absorbed():
