@@ -95,6 +95,30 @@ def test_vs_oracle_and_single_step(shape, nsteps):
     assert np.all(tc[halo_mask(tc.shape, halo)] == 0)
 
 
+def test_sixteen_sources_on_seams_and_chunk_boundaries():
+    """The most sources the kernel fuses (16), on z-chunk boundaries, tile
+    seams in y and x, and the corners of the grid, with receivers on the same
+    cells; a grid the fused kernel splits into z-chunks."""
+    need_gpu()
+    nx, ny, nz, nsteps = 128, 64, 256, 12
+    ok, tile_y, ctas = gbs.tb_supported(nx, ny, nz, 4)
+    assert ok and ctas > (nx // 64) * ((ny + tile_y - 1) // tile_y), (ok, tile_y, ctas)   # z-chunks in use
+    up, u, vel, dt, h, halo, _, _, _ = _case((nx, ny, nz), nsteps, 91)
+    cells = [(0, 0, 0), (127, 63, 255), (63, 15, 16), (64, 16, 15), (63, 16, 17), (64, 15, 31), (1, 31, 32),
+             (126, 32, 33), (65, 47, 48), (62, 48, 63), (5, 16, 64), (100, 15, 127), (33, 31, 128), (96, 32, 129),
+             (70, 47, 191), (20, 48, 240)]
+    src = np.array([W.linear_index(i, j, k, nx, ny) for i, j, k in cells], np.int64)
+    amp = np.random.default_rng(5).standard_normal((nsteps, len(cells))).astype(np.float32)
+    trace = torch.zeros((nsteps, src.size), device=dev())
+    p, c = gbs.wave_propagate_tb(to_dev(up), to_dev(u), to_dev(vel), dt, h, halo, nsteps, src_idx=to_dev(src),
+                                 src_amp=to_dev(amp), rec_idx=to_dev(src), rec_trace=trace)
+    gbs.device_status()
+    rp, ru, rtr = oracle.wave_propagate(up, u, vel, dt, h, halo, nsteps, src_idx=src, src_amp=amp, rec_idx=src)
+    for got, ref in ((c, ru), (p, rp), (trace, rtr)):
+        e = oracle.err_norms(got.cpu().numpy(), ref)
+        assert e["finite"] and e["norm_max_rel"] <= tol_steps(nsteps), e
+
+
 def test_graph_replay_and_restart():
     """Graph replay gives the same bits; 8 + 6 steps (t0 = 8) agrees with
     14 steps and with the oracle."""
