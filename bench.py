@@ -45,6 +45,7 @@ UNIT = "Gpoint-updates/s"
 BYTES_PER_POINT = 16          # read u, u_prev, vel; write u_next (FP32)
 BYTES_PER_POINT_PAIR = 20     # two fused steps: read u^t, u^{t-1}, vel; write u^{t+1}, u^{t+2}
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0      # GB300 HBM3e nominal bandwidth (context; the measured copy peak is the basis)
 CSRC = os.path.join(ROOT, "paper_2309_04671_gb300", "csrc")
 # committed ncu DRAM counts per launch, valid while the kernel sources hash the same
 TRAFFIC = {
@@ -953,7 +954,9 @@ def run_ours(args):
                        "graph": args.graph},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-                         "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                         "peak_kind": peak_kind,
+                         "frac_of_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
+                         "nominal_peak": NOMINAL_HBM_GBS, "alg_bytes_per_launch": alg_bytes,
                          "alg_bytes_per_point_per_launch": bytes_per_point,
                          "point_updates_per_launch": prob.npoints * (2 if tb else 1),
                          "kernel_ms_per_launch": per_launch_ms, "kernel_launches": kernel_launches,
