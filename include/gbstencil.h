@@ -57,7 +57,7 @@ typedef enum {
     GBS_EALIGN = 2,       /* alignment demanded by an explicit kernel choice not met */
     GBS_ECUDA = 3,        /* a CUDA runtime/driver call failed */
     GBS_ETIMEOUT = 4,     /* device: a bounded pipeline wait ran out */
-    GBS_EUNSTABLE = 5,    /* reserved: CFL limit exceeded */
+    GBS_EUNSTABLE = 5,    /* CFL limit exceeded (gbs_check_cfl) */
     GBS_ENOMEM = 6,       /* reserved */
     GBS_ENAN = 7,         /* reserved */
     GBS_EUNSUPPORTED = 8  /* no kernel for this combination */
@@ -255,6 +255,22 @@ gbs_status gbs_wave_propagate_host(float *u_prev, float *u, const float *vel, fl
                                    int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
                                    int64_t t0, const gbs_src *src, const gbs_rec *rec, int time_block,
                                    void *work, size_t work_bytes, const gbs_opts *opts, void *stream);
+
+/*
+ * Stability check of the radius-4 leapfrog (optional, synchronous): computes
+ * max |vel| over the interior on the device, waits for `stream`, and
+ * compares the CFL number max|vel| dt / h with the stability limit
+ * 2 / sqrt(3 (|c0| + 2 sum_m |c_m|)) = 0.4529 of Eq. 2 with the 8th-order
+ * weights in 3D.
+ *   vel           DEVICE float, padded layout.
+ *   cfl, limit    HOST, optional: the CFL number and the limit.
+ * Returns GBS_OK when the steps are stable, GBS_EUNSTABLE when the CFL
+ * number exceeds the limit (or the velocity holds a NaN), GBS_EINVAL,
+ * GBS_ECUDA.  Calls on different streams share one device word: they must
+ * not overlap.
+ */
+gbs_status gbs_check_cfl(const float *vel, int64_t nx, int64_t ny, int64_t nz, int halo, float dt, float h,
+                         double *cfl, double *limit, void *stream);
 
 /*
  * Self-test of the bounded waits (failure detection without a device fault).

@@ -22,14 +22,14 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgbstencil.so")
 
-GBS_OK, GBS_EINVAL, GBS_EALIGN, GBS_ECUDA, GBS_ETIMEOUT = 0, 1, 2, 3, 4
+GBS_OK, GBS_EINVAL, GBS_EALIGN, GBS_ECUDA, GBS_ETIMEOUT, GBS_EUNSTABLE = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4: "GBS_ETIMEOUT",
                 5: "GBS_EUNSTABLE", 6: "GBS_ENOMEM", 7: "GBS_ENAN", 8: "GBS_EUNSUPPORTED"}
 
 # Entry points declared in include/gbstencil.h (checked by the tests).
 EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
            "gbs_wave_propagate_lp", "gbs_tb_workspace_bytes", "gbs_wave_propagate_tb", "gbs_tb_supported",
-           "gbs_selftest_tb_timeout", "gbs_host_workspace_bytes", "gbs_wave_propagate_host",
+           "gbs_selftest_tb_timeout", "gbs_host_workspace_bytes", "gbs_wave_propagate_host", "gbs_check_cfl",
            "gbs_norms_workspace_bytes", "gbs_field_norms", "gbs_field_norms_noalloc",
            "gbs_batch_plan_create", "gbs_batch_run", "gbs_batch_plan_info", "gbs_batch_plan_destroy",
            "gbs_adjoint_workspace_bytes", "gbs_adjoint_forward", "gbs_adjoint_backward", "gbs_fwi_gradient",
@@ -116,6 +116,9 @@ def load() -> ctypes.CDLL:
                                                 ctypes.POINTER(_Src), ctypes.POINTER(_Rec), c_int, vp,
                                                 ctypes.c_size_t, ctypes.POINTER(_Opts), vp]
         lib.gbs_wave_propagate_host.restype = c_int
+        lib.gbs_check_cfl.argtypes = [vp, i64, i64, i64, c_int, c_float, c_float, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), vp]
+        lib.gbs_check_cfl.restype = c_int
         lib.gbs_selftest_tb_timeout.argtypes = [vp]
         lib.gbs_selftest_tb_timeout.restype = c_int
         lib.gbs_norms_workspace_bytes.argtypes = [i64, i64]
@@ -440,6 +443,17 @@ def wave_propagate_tb(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, 
                                         int(t0), _ptr(src), _ptr(rec), work.data_ptr(),
                                         work.numel() * work.element_size(), ctypes.byref(opts), _stream(stream)))
     return (u, u_prev) if nsteps % 2 else (u_prev, u)
+
+
+def check_cfl(vel: torch.Tensor, dt: float, h: float, halo: int, stream=None) -> tuple[float, float]:
+    """(cfl, limit) of the radius-4 leapfrog on this velocity; raises
+    GbsError with status GBS_EUNSTABLE when cfl exceeds the limit."""
+    pv = _field(vel, "vel")
+    nx, ny, nz = _dims(vel, halo)
+    c, lim = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().gbs_check_cfl(pv, nx, ny, nz, halo, float(dt), float(h), ctypes.byref(c), ctypes.byref(lim),
+                                _stream(stream)))
+    return c.value, lim.value
 
 
 def selftest_tb_timeout(stream=None) -> int:

@@ -1091,6 +1091,100 @@ extern "C" gbs_status gbs_field_norms_noalloc(const float *x, const float *ref, 
     return GBS_OK;
 }
 
+namespace gbs {
+namespace {
+// max |x| over the interior as the bits of a non-negative float (the bit
+// patterns of non-negative floats order like their values; a NaN orders above
+// every number, so it reads as unstable)
+__device__ unsigned g_absmax_bits;
+
+__global__ void __launch_bounds__(256) k_absmax(Grid g, const float *x, unsigned *out)
+{
+    __shared__ float sh[8];
+    float m = 0.f;
+    const int64_t rows = g.ny * g.nz;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int64_t j = row % g.ny, k = row / g.ny;
+        const float *r = x + g.halo + g.px * ((j + g.halo) + g.py * (k + g.halo));
+        for (int64_t i = threadIdx.x; i < g.nx; i += blockDim.x) {
+            const float a = fabsf(r[i]);
+            m = (a != a || a > m) ? a : m;   // a NaN stays once seen
+        }
+    }
+    unsigned b = __float_as_uint(m);
+    for (int o = 16; o > 0; o >>= 1)
+        b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    if ((threadIdx.x & 31) == 0)
+        sh[threadIdx.x >> 5] = __uint_as_float(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned v = 0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w)
+            v = max(v, __float_as_uint(sh[w]));
+        atomicMax(out, v);
+    }
+}
+
+// The largest CFL number v dt / h at which the 3D leapfrog with the radius-4
+// weights is stable: the step is stable while (v dt/h)^2 times the largest
+// eigenvalue of -L (h = 1), 3 (|c0| + 2 sum |c_m|), stays at or below 4.
+double cfl_limit_r4()
+{
+    double s = std::fabs(kFd2[3][0]);
+    for (int m = 1; m <= 4; ++m)
+        s += 2.0 * std::fabs(kFd2[3][m]);
+    return 2.0 / std::sqrt(3.0 * s);
+}
+}  // namespace
+}  // namespace gbs
+
+extern "C" gbs_status gbs_check_cfl(const float *vel, int64_t nx, int64_t ny, int64_t nz, int halo, float dt, float h,
+                                    double *cfl, double *limit, void *stream)
+{
+    t_err[0] = 0;
+    gbs_status s = check_dims(nx, ny, nz, halo);
+    if (s != GBS_OK)
+        return s;
+    if (!vel)
+        return fail(GBS_EINVAL, "null velocity");
+    if (!(dt > 0.f) || !(h > 0.f))
+        return fail(GBS_EINVAL, "dt and h must be positive");
+    const double lim = cfl_limit_r4();
+    if (limit)
+        *limit = lim;
+    if (cfl)
+        *cfl = 0.0;
+    if (nx == 0 || ny == 0 || nz == 0)
+        return GBS_OK;
+    const Grid g = dense_grid(nx, ny, nz, halo);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned *dbits = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&dbits), g_absmax_bits);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(dbits, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) {
+        const int64_t rows = g.ny * g.nz;
+        const unsigned blocks = (unsigned)std::min<int64_t>(rows, 152 * 8);
+        k_absmax<<<blocks, 256, 0, st>>>(g, vel, dbits);
+        e = cudaGetLastError();
+    }
+    unsigned bits = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&bits, dbits, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "velocity maximum");
+    float vmax;
+    memcpy(&vmax, &bits, sizeof(vmax));
+    const double c = (double)vmax * (double)dt / (double)h;
+    if (cfl)
+        *cfl = c;
+    if (!(c <= lim))
+        return fail(GBS_EUNSTABLE, "CFL number %.6g = max|v| dt / h exceeds the stability limit %.6g", c, lim);
+    return GBS_OK;
+}
+
 extern "C" gbs_status gbs_fd2_coeffs(int radius, float *out)
 {
     t_err[0] = 0;

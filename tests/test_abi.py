@@ -267,3 +267,19 @@ def test_host_entry_workspace_and_validation(lib):
     assert call(*args(p[0], p[1], wb=ctypes.c_size_t(1024))) == gbs.GBS_EINVAL
     assert call(*args(None, p[1])) == gbs.GBS_EINVAL
     assert call(*args(p[0], p[1], nsteps=0)) == gbs.GBS_OK
+
+
+def test_cfl_check_validation_and_limit(lib):
+    lim = ctypes.c_double(0.0)
+    cfl = ctypes.c_double(0.0)
+    fake = ctypes.c_void_p(1 << 20)
+    # an empty grid needs no device and reports the limit of the radius-4 3D leapfrog
+    assert lib.gbs_check_cfl(fake, 0, 8, 8, 4, ctypes.c_float(1e-3), ctypes.c_float(10.0), ctypes.byref(cfl),
+                             ctypes.byref(lim), None) == gbs.GBS_OK
+    c = oracle.fd2_coeffs(4)
+    assert abs(lim.value - 2.0 / np.sqrt(3.0 * (abs(c[0]) + 2 * np.sum(np.abs(c[1:]))))) < 1e-12
+    assert abs(lim.value - 0.4529) < 1e-4
+    assert lib.gbs_check_cfl(None, 8, 8, 8, 4, ctypes.c_float(1e-3), ctypes.c_float(10.0), None, None,
+                             None) == gbs.GBS_EINVAL
+    assert lib.gbs_check_cfl(fake, 8, 8, 8, 4, ctypes.c_float(0.0), ctypes.c_float(10.0), None, None,
+                             None) == gbs.GBS_EINVAL

@@ -203,3 +203,44 @@ def test_precision_size_1024_one_step_sampled():
     got = c[k + halo, j + halo, i + halo].astype(np.float64)
     e = oracle.err_norms(got, ref)
     assert e["norm_max_rel"] <= TOL_ONE, e
+
+
+def test_cfl_check_matches_the_steps():
+    """gbs_check_cfl: the reported CFL number, rejection above the limit (and
+    of a NaN velocity), and the limit itself against the kernel: random
+    fields stay bounded just below it and grow explosively just above it."""
+    need_gpu()
+    n, halo, h = 40, 4, 10.0
+    vel = W.layered_velocity(n, n, n, halo, 77)
+    vmax = float(W.interior(vel, halo).max())
+    d_vel = to_dev(vel)
+    dt = W.dt_for_cfl(0.4, h, vmax)
+    c, lim = gbs.check_cfl(d_vel, dt, h, halo)
+    assert abs(c - 0.4) < 1e-5 and abs(lim - 0.4529) < 1e-4, (c, lim)
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.check_cfl(d_vel, dt * 1.2, h, halo)
+    assert e.value.status == gbs.GBS_EUNSTABLE
+    bad = d_vel.clone()
+    bad[halo + 3, halo + 5, halo + 7] = float("nan")
+    with pytest.raises(gbs.GbsError) as e:
+        gbs.check_cfl(bad, dt, h, halo)
+    assert e.value.status == gbs.GBS_EUNSTABLE
+    # the limit against the kernel, on a constant velocity (in the layered
+    # model the fastest layer is too thin for the mode that sets the limit)
+    v0 = 3000.0
+    d_const = to_dev(W.constant_velocity(n, n, n, halo, v0))
+    up = W.uniform_field(n, n, n, halo, 81, halo_random=False)
+    u = W.uniform_field(n, n, n, halo, 82, halo_random=False)
+    peak = {}
+    for cfl in (0.44, 0.47):
+        dtc = W.dt_for_cfl(cfl, h, v0)
+        if cfl > lim:
+            with pytest.raises(gbs.GbsError):
+                gbs.check_cfl(d_const, dtc, h, halo)
+        else:
+            gbs.check_cfl(d_const, dtc, h, halo)
+        _, cur = gbs.wave_propagate(to_dev(up), to_dev(u), d_const, dtc, h, halo, 60)
+        gbs.device_status()
+        peak[cfl] = float(torch.nan_to_num(cur.abs(), nan=float("inf")).max())
+    assert peak[0.44] < 100.0, peak
+    assert peak[0.47] > 1e6, peak
