@@ -28,9 +28,19 @@
 #include <cmath>
 #include <cstring>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gbs_internal.cuh"
 
 namespace gbs {
+// Named range around a library call for profilers (NVTX; a no-op
+// unless a tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 namespace {
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
@@ -364,6 +374,7 @@ extern "C" gbs_status gbs_adjoint_forward(const float *vel, float dt, float h, i
                                           int64_t ckpt_every, void *work, size_t work_bytes, const gbs_opts *opts,
                                           void *stream)
 {
+    const TraceRange trace_range("gbs_adjoint_forward");
     clear_error();
     gbs_status s = check_common(vel, dt, h, nx, ny, nz, halo, nsteps, src, ckpt_every, work);
     if (s != GBS_OK)
@@ -386,6 +397,7 @@ extern "C" gbs_status gbs_adjoint_backward(const float *vel, float dt, float h, 
                                            int64_t nrec, const float *adj_src, int64_t ckpt_every, void *work,
                                            size_t work_bytes, double *grad, const gbs_opts *opts, void *stream)
 {
+    const TraceRange trace_range("gbs_adjoint_backward");
     clear_error();
     gbs_status s = check_common(vel, dt, h, nx, ny, nz, halo, nsteps, src, ckpt_every, work);
     if (s != GBS_OK)
@@ -417,6 +429,7 @@ extern "C" gbs_status gbs_fwi_gradient(const float *vel, float dt, float h, int6
                                        int64_t ckpt_every, void *work, size_t work_bytes, double *grad,
                                        double *misfit, const gbs_opts *opts, void *stream)
 {
+    const TraceRange trace_range("gbs_fwi_gradient");
     clear_error();
     gbs_status s = check_common(vel, dt, h, nx, ny, nz, halo, nsteps, src, ckpt_every, work);
     if (s != GBS_OK)

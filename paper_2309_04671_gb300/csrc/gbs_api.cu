@@ -9,10 +9,20 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gbs_internal.cuh"
 #include "gbs_wf.cuh"
 
 namespace gbs {
+// Named range around a library call for profilers (NVTX; a no-op
+// unless a tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 namespace {
 
 thread_local char t_err[512] = "";
@@ -456,6 +466,7 @@ extern "C" gbs_status gbs_stencil_apply(const float *in, float *out, int64_t nx,
                                         int radius, const float *coeffs_x, const float *coeffs_y,
                                         const float *coeffs_z, int halo, void *stream)
 {
+    const TraceRange trace_range("gbs_stencil_apply");
     t_err[0] = 0;
     gbs_status s = check_dims(nx, ny, nz, halo);
     if (s != GBS_OK)
@@ -512,6 +523,7 @@ extern "C" gbs_status gbs_wave_step(const float *u_prev, const float *u, float *
                                     float dt, float h, int64_t nx, int64_t ny, int64_t nz, int halo,
                                     const gbs_src *src, const gbs_rec *rec, int64_t step, void *stream)
 {
+    const TraceRange trace_range("gbs_wave_step");
     t_err[0] = 0;
     gbs_status s = check_dims(nx, ny, nz, halo);
     if (s != GBS_OK)
@@ -535,6 +547,7 @@ extern "C" gbs_status gbs_wave_propagate(float *u_prev, float *u, const float *v
                                          int64_t t0, const gbs_src *src, const gbs_rec *rec,
                                          const gbs_opts *opts, void *stream)
 {
+    const TraceRange trace_range("gbs_wave_propagate");
     t_err[0] = 0;
     gbs_status s = check_dims(nx, ny, nz, halo);
     if (s != GBS_OK)
@@ -642,6 +655,7 @@ extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float
                                             int64_t t0, const gbs_src *src, const gbs_rec *rec, void *work,
                                             size_t work_bytes, const gbs_opts *opts, void *stream)
 {
+    const TraceRange trace_range("gbs_wave_propagate_tb");
     t_err[0] = 0;
     gbs_status s = check_dims(nx, ny, nz, halo);
     if (s != GBS_OK)
@@ -802,6 +816,7 @@ extern "C" gbs_status gbs_wave_propagate_host(float *u_prev, float *u, const flo
                                               int64_t t0, const gbs_src *src, const gbs_rec *rec, int time_block,
                                               void *work, size_t work_bytes, const gbs_opts *opts, void *stream)
 {
+    const TraceRange trace_range("gbs_wave_propagate_host");
     t_err[0] = 0;
     gbs_status s = check_dims(nx, ny, nz, halo);
     if (s != GBS_OK)
@@ -943,6 +958,7 @@ extern "C" gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float
                                             gbs_dtype storage, void *work, size_t work_bytes,
                                             const gbs_opts *opts, void *stream)
 {
+    const TraceRange trace_range("gbs_wave_propagate_lp");
     t_err[0] = 0;
     gbs_status s = check_dims(nx, ny, nz, halo);
     if (s != GBS_OK)
@@ -1036,6 +1052,7 @@ extern "C" size_t gbs_norms_workspace_bytes(int64_t ny, int64_t nz)
 extern "C" gbs_status gbs_field_norms(const float *x, const float *ref, int64_t nx, int64_t ny, int64_t nz,
                                       int halo, double *out, void *work, size_t work_bytes, void *stream)
 {
+    const TraceRange trace_range("gbs_field_norms");
     t_err[0] = 0;
     gbs_status s = check_dims(nx, ny, nz, halo);
     if (s != GBS_OK)

@@ -15,6 +15,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gbs_internal.cuh"
 
 struct gbs_batch_plan {
@@ -38,6 +40,14 @@ struct gbs_batch_plan {
 };
 
 namespace gbs {
+// Named range around a library call for profilers (NVTX; a no-op
+// unless a tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 namespace {
 
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
@@ -350,6 +360,7 @@ extern "C" gbs_status gbs_batch_plan_create(gbs_batch_plan **plan, const gbs_sho
 
 extern "C" gbs_status gbs_batch_run(gbs_batch_plan *plan, int64_t nsteps, int64_t t0, int use_graph, void *stream)
 {
+    const TraceRange trace_range("gbs_batch_run");
     clear_error();
     if (!plan)
         return set_error(GBS_EINVAL, "null plan");

@@ -5,9 +5,19 @@
 #include <cstdint>
 #include <cstring>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gbs_internal.cuh"
 
 namespace gbs {
+// Named range around a library call for profilers (NVTX; a no-op
+// unless a tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 namespace {
 
 // Footprint offsets in the order the caller's weights follow: lexicographic
@@ -43,6 +53,7 @@ extern "C" gbs_status gbs_stencil_suite(const float *in, float *out, int64_t nx,
                                         int dims, int shape, int radius, const float *weights, float divisor,
                                         void *stream)
 {
+    const TraceRange trace_range("gbs_stencil_suite");
     clear_error();
     if (dims != 2 && dims != 3)
         return set_error(GBS_EINVAL, "dims must be 2 or 3");
