@@ -23,13 +23,20 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// max that keeps a NaN (fmax would drop it): a NaN anywhere in a field makes
+// its maximum norms NaN, as in the oracle
+__device__ __forceinline__ double nanmax(double a, double b)
+{
+    return (a != a || b != b) ? a + b : fmax(a, b);
+}
+
 __device__ __forceinline__ void reduce4(double v[4], double *sh)
 {
     // v[0], v[1]: max; v[2], v[3]: sum -- warp shuffles, then across warps
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        v[0] = fmax(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
-        v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+        v[0] = nanmax(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+        v[1] = nanmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
         v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
         v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
     }
@@ -40,8 +47,8 @@ __device__ __forceinline__ void reduce4(double v[4], double *sh)
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int ww = 1; ww < kThreads / 32; ++ww) {
-            v[0] = fmax(v[0], sh[ww * 4 + 0]);
-            v[1] = fmax(v[1], sh[ww * 4 + 1]);
+            v[0] = nanmax(v[0], sh[ww * 4 + 0]);
+            v[1] = nanmax(v[1], sh[ww * 4 + 1]);
             v[2] += sh[ww * 4 + 2];
             v[3] += sh[ww * 4 + 3];
         }
@@ -62,8 +69,8 @@ __global__ void __launch_bounds__(kThreads) k_norms_partial(Grid g, const float 
             const double a = (double)x[base + i];
             const double b = ref ? (double)ref[base + i] : 0.0;
             const double d = a - b;
-            v[0] = fmax(v[0], fabs(d));
-            v[1] = fmax(v[1], fabs(b));
+            v[0] = nanmax(v[0], fabs(d));
+            v[1] = nanmax(v[1], fabs(b));
             v[2] += d * d;
             v[3] += b * b;
         }
@@ -80,8 +87,8 @@ __global__ void __launch_bounds__(kThreads) k_norms_final(const double *part, in
     __shared__ double sh[kThreads / 32 * 4];
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t b = threadIdx.x; b < nparts; b += kThreads) {
-        v[0] = fmax(v[0], part[b * 4 + 0]);
-        v[1] = fmax(v[1], part[b * 4 + 1]);
+        v[0] = nanmax(v[0], part[b * 4 + 0]);
+        v[1] = nanmax(v[1], part[b * 4 + 1]);
         v[2] += part[b * 4 + 2];
         v[3] += part[b * 4 + 3];
     }

@@ -48,3 +48,23 @@ def test_norms_deterministic_full_size():
     assert torch.equal(r1, r2)
     # uniform[-1,1] minus an independent uniform[-1,1]: E[d^2] = 2/3
     assert float(r1[7]) == pytest.approx(np.sqrt(2.0 / 3.0), rel=1e-3)
+
+
+def test_a_nan_shows_in_the_norms():
+    """NaN in the field (or the reference) makes the maximum norms NaN, as in
+    the oracle: a broken run cannot pass a max-error check."""
+    need_gpu()
+    halo = 4
+    x = W.uniform_field(40, 33, 17, halo, 21)
+    ref = W.uniform_field(40, 33, 17, halo, 22)
+    x[halo + 9, halo + 20, halo + 31] = np.nan
+    got = gbs.norms_dict(gbs.field_norms(to_dev(x), to_dev(ref), halo=halo))
+    e = oracle.err_norms(W.interior(x, halo), W.interior(ref, halo))
+    assert np.isnan(e["max_abs"]) and np.isnan(got["max_abs"]), got
+    assert np.isnan(got["norm_max_rel"]) and np.isnan(e["norm_max_rel"])
+    assert np.isnan(got["rmsd"]) and np.isnan(e["rmsd"])
+    # a NaN in the halo is outside the interior and does not count
+    y = W.uniform_field(40, 33, 17, halo, 23)
+    y[1, 1, 1] = np.nan
+    got = gbs.norms_dict(gbs.field_norms(to_dev(y), to_dev(ref), halo=halo))
+    assert np.isfinite(got["max_abs"]), got
