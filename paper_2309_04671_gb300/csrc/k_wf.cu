@@ -27,8 +27,9 @@
 // The grid is launched cooperatively, so every CTA is resident and every
 // wait ends once the stage-A warps it waits for have run; all waits are
 // bounded.  Stage B reads u^{t+1} soon after stage A stored it and u^t, vel
-// soon after stage A read them; those copies carry an L2 evict_last policy
-// and the last reads evict_first, so stage B is served from L2 and DRAM
+// soon after stage A read them: stage A's issuing thread stays within kLead
+// planes of stage B's, those copies carry an L2 evict_last policy and the
+// last reads evict_first, so stage B is served from L2 and DRAM
 // moves u^t, u^{t-1}, vel (12 B) and u^{t+1}, u^{t+2} (8 B) per point: 20 B
 // per two updates instead of 32.
 //
