@@ -565,6 +565,19 @@ def batched_forms(args, stream, hbm, nshots=64, nsteps=200):
         out[fmt]["sequential_single_shot"] = {"value": pts * nsteps / (ms_seq * 1e-3) / 1e9, "unit": UNIT,
                                               "ms_per_step": ms_seq}
         out[fmt]["speedup_vs_sequential"] = ms_seq / ms
+    # the FP64 oracle on the host cores: 4 of the shots, a bounded number of steps
+    import oracle
+    oracle.build()
+    sample, ost = shots[:4], 50
+    hostv = [(sh.vel.cpu().numpy(), sh.src_idx.cpu().numpy(), sh.src_amp.cpu().numpy()) for sh in sample]
+    t0 = time.perf_counter()
+    for (v, si, sa), sh in zip(hostv, sample):
+        z = np.zeros_like(v)
+        oracle.wave_propagate(z, z, v, sh.dt, sh.h, 4, ost, src_idx=si, src_amp=sa)
+    t_o = time.perf_counter() - t0
+    ipts = sum((v.shape[0] - 8) * (v.shape[1] - 8) * (v.shape[2] - 8) for v, _, _ in hostv)
+    out["oracle_4_shots"] = {"value": ipts * ost / t_o / 1e9, "unit": UNIT, "cores": os.cpu_count(),
+                             "sample": f"{ost} FP64 leapfrog steps of the first 4 shots ({t_o:.1f} s)"}
     del shots
     torch.cuda.empty_cache()
     return out
@@ -723,7 +736,50 @@ def adjoint_form(args, stream, hbm, n=256, nsteps=1000, nshots=8):
                                         "speedup_fused": ms_p / (ms_g / nshots), "grad_norm_max_rel_diff": diff}
     del res, d_obs
     torch.cuda.empty_cache()
+    out["oracle_64"] = _adjoint_oracle_64(nsteps, stream)
     return out
+
+
+def _adjoint_oracle_64(nsteps, stream, m=64):
+    """The gradient recipe on an m^3 copy (one shot, every step): the FP64
+    oracle on the host cores against the GPU path (time and error)."""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    import workloads as W
+    import oracle
+    oracle.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    halo, h = 4, 10.0
+    vel = W.layered_velocity(m, m, m, halo, W.SEED_BASE + 5)
+    c = np.arange(m + 2 * halo, dtype=np.float64) - halo - m / 2
+    zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")
+    vtrue = (vel * (1.0 + 0.05 * np.exp(-(xx * xx + yy * yy + zz * zz) / (2 * (m / 8) ** 2)))).astype(np.float32)
+    vtrue = W.zero_halo(vtrue, halo)
+    dt = W.dt_for_cfl(0.4, h, float(vtrue.max()))
+    src = np.array([W.linear_index(m // 3, m // 2, 2, m, m)], np.int64)
+    rec = np.array([W.linear_index(i, j, 8, m, m) for j in range(m) for i in range(m)], np.int64)
+    amp = W.ricker(nsteps, dt, 15.0).astype(np.float32).reshape(nsteps, 1)
+    _, d_obs = oracle.forward_states(vtrue, dt, h, halo, nsteps, src_idx=src, src_amp=amp, rec_idx=rec)
+    d_obs = d_obs.astype(np.float32)
+    t0 = time.perf_counter()
+    j_o, g_o = oracle.fwi_gradient(vel, dt, h, halo, nsteps, d_obs, src_idx=src, src_amp=amp, rec_idx=rec)
+    t_o = time.perf_counter() - t0
+    args = (torch.from_numpy(vel).to(dev), dt, h, halo, nsteps, torch.from_numpy(d_obs).to(dev))
+    kw = dict(src_idx=torch.from_numpy(src).to(dev), src_amp=torch.from_numpy(amp).to(dev),
+              rec_idx=torch.from_numpy(rec).to(dev))
+    res = {}
+
+    def run():
+        res["r"] = gbs.fwi_gradient(*args, **kw)
+    run()
+    ms, _, _ = time_calls(run, 1, stream)
+    gbs.device_status()
+    misfit, grad = res["r"][0], res["r"][1]
+    e = oracle.err_norms(grad.cpu().numpy(), g_o)
+    return {"grid": [m, m, m], "steps": nsteps, "oracle_seconds": t_o, "oracle_cores": os.cpu_count(),
+            "gpu_ms": ms, "gpu_vs_oracle": t_o * 1e3 / ms,
+            "grad_norm_max_rel_err": e["norm_max_rel"], "grad_l2_rel_err": e["l2_rel"],
+            "misfit_rel_err": abs(float(misfit.cpu()[0]) - j_o) / j_o}
 
 
 def W_padded(prob):
