@@ -23,7 +23,7 @@ struct WfParams {
     int zchunk, nchunks;         // z range of a CTA
     unsigned *words;             // block counters: [chunk][tile][nblk], zero before the first launch
     int nblk;                    // blocks of kWfBlock stage-A planes per CTA
-    unsigned epoch;              // launches on the same counters so far, this one included (>= 1)
+    unsigned epoch;              // launches on the same counters so far, this one included (mod 2^32)
     int64_t t;                   // time level of u (the launch writes u^{t+1} and u^{t+2})
     Absorb ab;                   // absorbing layer (width 0 = none)
 };
@@ -47,7 +47,7 @@ struct WfShape {
 // Stage A publishes its output in blocks of this many planes: a block
 // counter of a tile rises by one for each tile (itself and its x, y
 // neighbours) that has stored the block, so it reaches (those tiles) x
-// (launches so far) when stage B of the tile may read the block.
+// (launches so far), modulo 2^32, when stage B of the tile may read the block.
 constexpr int kWfBlock = 4;
 // Most block counters a launch uses (the workspace holds this many).
 constexpr int kWfMaxWords = 1 << 18;

@@ -521,7 +521,10 @@ __device__ __forceinline__ void wf_producer(const CUtensorMap *__restrict__ pm_u
     unsigned *words = p.words + (int64_t)chunk * ntiles * p.nblk;
     int deps[5];
     const int ndeps = tile_deps(p, tile, deps);
-    const unsigned need = (unsigned)ndeps * p.epoch;    // stage B: count of a published block
+    // stage B: count of a published block, modulo 2^32 like the counters
+    // (during a launch a counter lies within ndeps below it, so the signed
+    // difference decides even after the product wraps)
+    const unsigned need = (unsigned)ndeps * p.epoch;
     const int nblk_a = (sg.a1 - sg.a0 + kPB - 1) / kPB; // stage A's blocks
     int n_u = 0, n_pv = 0, n_pub = 0, ok_blk = -1;
     // stage A: u^t and vel are read again by stage B, u^{t-1} is not; stage B's reads are the last
@@ -543,7 +546,7 @@ __device__ __forceinline__ void wf_producer(const CUtensorMap *__restrict__ pm_u
                 if (b >= sg.a0 && b < sg.a1) {
                     const int blk = (b - sg.a0) / kPB;
                     if (blk > ok_blk) {
-                        if (ld_acquire(words + (int64_t)tile * p.nblk + blk) >= need) {
+                        if ((int)(ld_acquire(words + (int64_t)tile * p.nblk + blk) - need) >= 0) {
                             ok_blk = blk;
                             fence_proxy_async_global();
                         } else {
