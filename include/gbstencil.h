@@ -38,8 +38,9 @@
  *   - gbs_last_error() returns a message for the last failing call of the
  *     calling thread.
  *   - Nothing here allocates device memory, except batch plans
- *     (gbs_batch_plan_create), which own their buffers until destroyed, and
- *     the self-test gbs_selftest_tb_timeout, which frees its own.
+ *     (gbs_batch_plan_create) and pipelines (gbs_pipeline_create), which own
+ *     their buffers until destroyed, and the self-test
+ *     gbs_selftest_tb_timeout, which frees its own.
  */
 #ifndef GBSTENCIL_H
 #define GBSTENCIL_H
@@ -58,7 +59,7 @@ typedef enum {
     GBS_ECUDA = 3,        /* a CUDA runtime/driver call failed */
     GBS_ETIMEOUT = 4,     /* device: a bounded pipeline wait ran out */
     GBS_EUNSTABLE = 5,    /* CFL limit exceeded (gbs_check_cfl) */
-    GBS_ENOMEM = 6,       /* reserved */
+    GBS_ENOMEM = 6,       /* device memory for a pipeline could not be allocated */
     GBS_ENAN = 7,         /* reserved */
     GBS_EUNSUPPORTED = 8  /* no kernel for this combination */
 } gbs_status;
@@ -255,6 +256,52 @@ gbs_status gbs_wave_propagate_host(float *u_prev, float *u, const float *vel, fl
                                    int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
                                    int64_t t0, const gbs_src *src, const gbs_rec *rec, int time_block,
                                    void *work, size_t work_bytes, const gbs_opts *opts, void *stream);
+
+/*
+ * Pipelined propagation of independent problems held in HOST memory (the
+ * steps of gbs_wave_propagate_host, Algorithm 1, for each problem).  The
+ * host<->device copies of one problem overlap the steps of another: a
+ * pipeline owns `depth` device workspaces (one per problem in flight) and
+ * three streams, for uploads, steps and downloads.  Problem k uses
+ * workspace k % depth.  Its steps follow its upload and the steps of
+ * problem k-1 (steps run in submission order on one stream, so fused pairs,
+ * one cooperative launch each, never run concurrently).  Its download
+ * follows its steps.  Its upload waits for the previous download from the
+ * same workspace, and for every download still in flight that writes host
+ * memory this problem reads (so a problem may continue from the results of
+ * an earlier submission, passed as the same host buffers).
+ *   gbs_pipeline_create   nx, ny, nz, halo: the grid of every problem;
+ *                 nsrc_max x src_nt_max, nrec_max x rec_nt_max: the largest
+ *                 source and receiver arrays a submission may pass;
+ *                 time_block 0 (one launch per step) or 2 (fused pairs);
+ *                 depth in [1, 8] problems in flight (2 overlaps the copies
+ *                 of one problem with the steps of the next); opts as
+ *                 gbs_wave_propagate (copied).  Allocates depth workspaces of
+ *                 gbs_host_workspace_bytes(...) bytes on the current device.
+ *                 Errors: GBS_EINVAL, GBS_ENOMEM, GBS_ECUDA.
+ *   gbs_pipeline_submit   enqueues one problem and returns without waiting:
+ *                 u_prev, u, vel, src (idx, amp), rec (idx, trace) are HOST
+ *                 pointers with the meaning of gbs_wave_propagate_host; on
+ *                 completion u holds u^{t0+nsteps} and u_prev u^{t0+nsteps-1}.
+ *                 The buffers must stay valid and unmodified by the caller
+ *                 until gbs_pipeline_wait returns; pinned memory lets the
+ *                 copies run asynchronously.  Call on the creating device.
+ *                 Errors: GBS_EINVAL (as gbs_wave_propagate_host, arrays
+ *                 above the pipeline's sizes, another device), GBS_ECUDA.
+ *   gbs_pipeline_wait     blocks the calling thread until every submitted
+ *                 problem's results are in host memory.  Errors: GBS_ECUDA.
+ *   gbs_pipeline_workspace_bytes  device bytes the pipeline holds.
+ *   gbs_pipeline_destroy  waits for outstanding work and frees everything.
+ */
+typedef struct gbs_pipeline gbs_pipeline;
+gbs_status gbs_pipeline_create(gbs_pipeline **pipeline, int64_t nx, int64_t ny, int64_t nz, int halo,
+                               int64_t nsrc_max, int64_t src_nt_max, int64_t nrec_max, int64_t rec_nt_max,
+                               int time_block, int depth, const gbs_opts *opts);
+gbs_status gbs_pipeline_submit(gbs_pipeline *pipeline, float *u_prev, float *u, const float *vel, float dt, float h,
+                               int64_t nsteps, int64_t t0, const gbs_src *src, const gbs_rec *rec);
+gbs_status gbs_pipeline_wait(gbs_pipeline *pipeline);
+size_t gbs_pipeline_workspace_bytes(gbs_pipeline *pipeline);
+void gbs_pipeline_destroy(gbs_pipeline *pipeline);
 
 /*
  * Stability check of the radius-4 leapfrog (optional, synchronous): computes

@@ -30,6 +30,8 @@ STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4
 EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
            "gbs_wave_propagate_lp", "gbs_tb_workspace_bytes", "gbs_wave_propagate_tb", "gbs_tb_supported",
            "gbs_selftest_tb_timeout", "gbs_host_workspace_bytes", "gbs_wave_propagate_host", "gbs_check_cfl",
+           "gbs_pipeline_create", "gbs_pipeline_submit", "gbs_pipeline_wait", "gbs_pipeline_workspace_bytes",
+           "gbs_pipeline_destroy",
            "gbs_norms_workspace_bytes", "gbs_field_norms", "gbs_field_norms_noalloc",
            "gbs_batch_plan_create", "gbs_batch_run", "gbs_batch_plan_info", "gbs_batch_plan_destroy",
            "gbs_adjoint_workspace_bytes", "gbs_adjoint_forward", "gbs_adjoint_backward", "gbs_fwi_gradient",
@@ -116,6 +118,18 @@ def load() -> ctypes.CDLL:
                                                 ctypes.POINTER(_Src), ctypes.POINTER(_Rec), c_int, vp,
                                                 ctypes.c_size_t, ctypes.POINTER(_Opts), vp]
         lib.gbs_wave_propagate_host.restype = c_int
+        lib.gbs_pipeline_create.argtypes = [ctypes.POINTER(vp), i64, i64, i64, c_int, i64, i64, i64, i64, c_int, c_int,
+                                            ctypes.POINTER(_Opts)]
+        lib.gbs_pipeline_create.restype = c_int
+        lib.gbs_pipeline_submit.argtypes = [vp, vp, vp, vp, c_float, c_float, i64, i64, ctypes.POINTER(_Src),
+                                            ctypes.POINTER(_Rec)]
+        lib.gbs_pipeline_submit.restype = c_int
+        lib.gbs_pipeline_wait.argtypes = [vp]
+        lib.gbs_pipeline_wait.restype = c_int
+        lib.gbs_pipeline_workspace_bytes.argtypes = [vp]
+        lib.gbs_pipeline_workspace_bytes.restype = ctypes.c_size_t
+        lib.gbs_pipeline_destroy.argtypes = [vp]
+        lib.gbs_pipeline_destroy.restype = None
         lib.gbs_check_cfl.argtypes = [vp, i64, i64, i64, c_int, c_float, c_float, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), vp]
         lib.gbs_check_cfl.restype = c_int
@@ -389,6 +403,73 @@ def _wave_propagate_host(u_prev, u, vel, dt, h, halo, nsteps, *, t0, src_idx, sr
                                        ctypes.byref(opts), st))
     (stream if stream is not None else torch.cuda.current_stream()).synchronize()
     return u_prev, u
+
+
+def _host_src_rec(src_idx, src_amp, rec_idx, rec_trace):
+    src = rec = None
+    if src_idx is not None and src_idx.numel() > 0:
+        nsrc = src_idx.numel()
+        src = _Src(nsrc, _host_tensor(src_idx, "src_idx", torch.int64), _host_tensor(src_amp, "src_amp", torch.float32),
+                   src_amp.numel() // nsrc)
+    if rec_idx is not None and rec_idx.numel() > 0:
+        nrec = rec_idx.numel()
+        rec = _Rec(nrec, _host_tensor(rec_idx, "rec_idx", torch.int64),
+                   _host_tensor(rec_trace, "rec_trace", torch.float32), rec_trace.numel() // nrec)
+    return src, rec
+
+
+class Pipeline:
+    """Independent problems held in host memory (CPU tensors, ideally
+    pinned), propagated with the copies of one problem overlapping the steps
+    of another (gbs_pipeline_*).  ``submit`` enqueues one problem and returns
+    at once; after ``wait`` each submitted problem's ``u`` holds
+    u^{t0+nsteps} and ``u_prev`` u^{t0+nsteps-1}.  Submitting the same
+    tensors again continues that problem from its results.  ``depth``
+    problems are in flight; ``time_block=2`` fuses pairs of steps."""
+
+    def __init__(self, nx: int, ny: int, nz: int, halo: int, *, depth: int = 2, time_block: int = 2,
+                 nsrc_max: int = 0, src_nt_max: int = 0, nrec_max: int = 0, rec_nt_max: int = 0,
+                 kernel: int = 0, tile_y: int = 0, zchunk: int = 0, use_graph: bool = False):
+        lib = load()
+        self._p = ctypes.c_void_p()
+        self._shape = (nz + 2 * halo, ny + 2 * halo, nx + 2 * halo)
+        self._keep = []
+        opts = _opts(kernel, tile_y, zchunk, use_graph)
+        _check(lib.gbs_pipeline_create(ctypes.byref(self._p), int(nx), int(ny), int(nz), int(halo), int(nsrc_max),
+                                       int(src_nt_max), int(nrec_max), int(rec_nt_max), int(time_block), int(depth),
+                                       ctypes.byref(opts)))
+
+    def submit(self, u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, dt: float, h: float, nsteps: int, *,
+               t0: int = 0, src_idx=None, src_amp=None, rec_idx=None, rec_trace=None) -> None:
+        if not self._p:
+            raise RuntimeError("pipeline is closed")
+        p = [_host_tensor(t, n, torch.float32) for t, n in ((u_prev, "u_prev"), (u, "u"), (vel, "vel"))]
+        _same_shape(u, u_prev, vel)
+        if tuple(u.shape) != self._shape:
+            raise ValueError(f"fields must have the pipeline's padded shape {self._shape}")
+        src, rec = _host_src_rec(src_idx, src_amp, rec_idx, rec_trace)
+        self._keep.append((u_prev, u, vel, src_idx, src_amp, rec_idx, rec_trace, src, rec))
+        _check(load().gbs_pipeline_submit(self._p, p[0], p[1], p[2], float(dt), float(h), int(nsteps), int(t0),
+                                          _ptr(src), _ptr(rec)))
+
+    def wait(self) -> None:
+        _check(load().gbs_pipeline_wait(self._p))
+        self._keep.clear()
+
+    def workspace_bytes(self) -> int:
+        return int(load().gbs_pipeline_workspace_bytes(self._p))
+
+    def close(self) -> None:
+        if getattr(self, "_p", None):
+            load().gbs_pipeline_destroy(self._p)
+            self._p = ctypes.c_void_p()
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tb_workspace_bytes(nx: int, ny: int, nz: int, halo: int) -> int:

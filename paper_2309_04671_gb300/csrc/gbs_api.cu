@@ -496,8 +496,7 @@ extern "C" gbs_status gbs_stencil_apply(const float *in, float *out, int64_t nx,
     cudaError_t e;
     cudaEvent_t e0 = prof_begin(st);
     if (tma_ok) {
-        TmaPlan plan;
-        memset(&plan, 0, sizeof(plan));
+        TmaPlan plan{};
         if ((s = make_map(&plan.u, in, g, 64 + 8, 16 + 2 * radius)) != GBS_OK)
             return s;
         plan.prev = plan.u;
@@ -811,13 +810,94 @@ extern "C" size_t gbs_host_workspace_bytes(int64_t nx, int64_t ny, int64_t nz, i
     return host_layout(dense_grid(nx, ny, nz, halo), nsrc, src_nt, nrec, rec_nt, time_block).total;
 }
 
-extern "C" gbs_status gbs_wave_propagate_host(float *u_prev, float *u, const float *vel, float dt, float h,
-                                              int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
-                                              int64_t t0, const gbs_src *src, const gbs_rec *rec, int time_block,
-                                              void *work, size_t work_bytes, const gbs_opts *opts, void *stream)
+namespace gbs {
+namespace {
+// One problem of the host-buffer entry, split into its three phases so that
+// a pipeline can put them on different streams.
+struct HostJob {
+    Grid g;
+    HostLayout L;
+    char *w;                    // device workspace
+    float *u_prev, *u;          // host fields
+    const float *vel;
+    float dt, h;
+    int64_t nsteps, t0;
+    const gbs_src *src;         // host arrays
+    const gbs_rec *rec;
+    int time_block;
+    const gbs_opts *opts;
+    int64_t nsrc() const { return src ? src->n : 0; }
+    int64_t nrec() const { return rec ? rec->n : 0; }
+    size_t field_bytes() const { return (size_t)field_elems(g) * 4; }
+    float *d_up() const { return reinterpret_cast<float *>(w + L.off_up); }
+    float *d_u() const { return reinterpret_cast<float *>(w + L.off_u); }
+    // receiver rows the run writes: [t0, t0 + nsteps) within [0, rec->nt)
+    int64_t r0() const { return rec ? std::min(t0, rec->nt) : 0; }
+    int64_t r1() const { return rec ? std::min(t0 + nsteps, rec->nt) : 0; }
+};
+
+cudaError_t host_upload(const HostJob &j, cudaStream_t st)
 {
-    const TraceRange trace_range("gbs_wave_propagate_host");
-    t_err[0] = 0;
+    auto h2d = [&](void *dst, const void *srcp, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, srcp, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+    };
+    const size_t fb = j.field_bytes();
+    cudaError_t e;
+    if ((e = h2d(j.d_up(), j.u_prev, fb)) != cudaSuccess || (e = h2d(j.d_u(), j.u, fb)) != cudaSuccess ||
+        (e = h2d(j.w + j.L.off_vel, j.vel, fb)) != cudaSuccess)
+        return e;
+    if (j.nsrc() > 0 && ((e = h2d(j.w + j.L.off_sidx, j.src->idx, (size_t)j.nsrc() * 8)) != cudaSuccess ||
+                         (e = h2d(j.w + j.L.off_samp, j.src->amp, (size_t)j.nsrc() * j.src->nt * 4)) != cudaSuccess))
+        return e;
+    if (j.nrec() > 0 && (e = h2d(j.w + j.L.off_ridx, j.rec->idx, (size_t)j.nrec() * 8)) != cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
+gbs_status host_steps(const HostJob &j, cudaStream_t st)
+{
+    const int64_t nsrc = j.nsrc(), nrec = j.nrec();
+    gbs_src dsrc{0, nullptr, nullptr, 0};
+    gbs_rec drec{0, nullptr, nullptr, 0};
+    if (nsrc > 0)
+        dsrc = {nsrc, reinterpret_cast<const int64_t *>(j.w + j.L.off_sidx),
+                reinterpret_cast<const float *>(j.w + j.L.off_samp), j.src->nt};
+    if (nrec > 0)
+        drec = {nrec, reinterpret_cast<const int64_t *>(j.w + j.L.off_ridx), reinterpret_cast<float *>(j.w + j.L.off_tr),
+                j.rec->nt};
+    const Grid &g = j.g;
+    float *d_vel = reinterpret_cast<float *>(j.w + j.L.off_vel);
+    return j.time_block == 2
+               ? gbs_wave_propagate_tb(j.d_up(), j.d_u(), d_vel, j.dt, j.h, g.nx, g.ny, g.nz, g.halo, j.nsteps, j.t0,
+                                       nsrc > 0 ? &dsrc : nullptr, nrec > 0 ? &drec : nullptr, j.w + j.L.off_tb,
+                                       j.L.total - j.L.off_tb, j.opts, st)
+               : gbs_wave_propagate(j.d_up(), j.d_u(), d_vel, j.dt, j.h, g.nx, g.ny, g.nz, g.halo, j.nsteps, j.t0,
+                                    nsrc > 0 ? &dsrc : nullptr, nrec > 0 ? &drec : nullptr, j.opts, st);
+}
+
+cudaError_t host_download(const HostJob &j, cudaStream_t st)
+{
+    auto d2h = [&](void *dst, const void *srcp, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, srcp, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
+    };
+    // the newest level into u, the one before into u_prev (on the device the
+    // buffers alternate: after an odd number of steps d_up holds the newest)
+    const size_t fb = j.field_bytes();
+    const float *newest = (j.nsteps & 1) ? j.d_up() : j.d_u(), *older = (j.nsteps & 1) ? j.d_u() : j.d_up();
+    cudaError_t e;
+    if ((e = d2h(j.u, newest, fb)) != cudaSuccess || (e = d2h(j.u_prev, older, fb)) != cudaSuccess)
+        return e;
+    const int64_t nrec = j.nrec(), r0 = j.r0(), r1 = j.r1();
+    if (nrec > 0 && r1 > r0)
+        return d2h(j.rec->trace + r0 * nrec, reinterpret_cast<float *>(j.w + j.L.off_tr) + r0 * nrec,
+                   (size_t)(r1 - r0) * nrec * 4);
+    return cudaSuccess;
+}
+
+// Argument checks shared by the host entry and pipeline submissions.
+gbs_status check_host_job(int64_t nx, int64_t ny, int64_t nz, int halo, int time_block, int64_t nsteps, int64_t t0,
+                          const gbs_src *src, const gbs_rec *rec, const float *u_prev, const float *u, const float *vel)
+{
     gbs_status s = check_dims(nx, ny, nz, halo);
     if (s != GBS_OK)
         return s;
@@ -831,62 +911,243 @@ extern "C" gbs_status gbs_wave_propagate_host(float *u_prev, float *u, const flo
         return fail(GBS_EINVAL, "null field pointer");
     if (u_prev == u)
         return fail(GBS_EINVAL, "u_prev and u are the same buffer");
+    return GBS_OK;
+}
+}  // namespace
+}  // namespace gbs
+
+extern "C" gbs_status gbs_wave_propagate_host(float *u_prev, float *u, const float *vel, float dt, float h,
+                                              int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                                              int64_t t0, const gbs_src *src, const gbs_rec *rec, int time_block,
+                                              void *work, size_t work_bytes, const gbs_opts *opts, void *stream)
+{
+    const TraceRange trace_range("gbs_wave_propagate_host");
+    t_err[0] = 0;
+    gbs_status s = check_host_job(nx, ny, nz, halo, time_block, nsteps, t0, src, rec, u_prev, u, vel);
+    if (s != GBS_OK)
+        return s;
     if (nx == 0 || ny == 0 || nz == 0 || nsteps == 0)
         return GBS_OK;
     const Grid g = dense_grid(nx, ny, nz, halo);
-    const int64_t nsrc = src ? src->n : 0, snt = src ? src->nt : 0;
-    const int64_t nrec = rec ? rec->n : 0, rnt = rec ? rec->nt : 0;
-    const HostLayout L = host_layout(g, nsrc, snt, nrec, rnt, time_block);
+    const HostLayout L = host_layout(g, src ? src->n : 0, src ? src->nt : 0, rec ? rec->n : 0, rec ? rec->nt : 0,
+                                     time_block);
     if (!work || work_bytes < L.total || !aligned16(work))
         return fail(GBS_EINVAL, "workspace needs %zu bytes, 16-byte aligned (gbs_host_workspace_bytes)", L.total);
-    char *w = static_cast<char *>(work);
-    float *d_up = reinterpret_cast<float *>(w + L.off_up), *d_u = reinterpret_cast<float *>(w + L.off_u);
-    float *d_vel = reinterpret_cast<float *>(w + L.off_vel);
-    const size_t fb = (size_t)field_elems(g) * 4;
+    const HostJob j{g, L, static_cast<char *>(work), u_prev, u, vel, dt, h, nsteps, t0, src, rec, time_block, opts};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    auto h2d = [&](void *dst, const void *srcp, size_t bytes) {
-        return bytes ? cudaMemcpyAsync(dst, srcp, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
-    };
-    auto d2h = [&](void *dst, const void *srcp, size_t bytes) {
-        return bytes ? cudaMemcpyAsync(dst, srcp, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
-    };
-    gbs_src dsrc{0, nullptr, nullptr, 0};
-    gbs_rec drec{0, nullptr, nullptr, 0};
-    if ((e = h2d(d_up, u_prev, fb)) != cudaSuccess || (e = h2d(d_u, u, fb)) != cudaSuccess ||
-        (e = h2d(d_vel, vel, fb)) != cudaSuccess)
-        return cuda_fail(e, "copy of the fields to the device");
-    if (nsrc > 0) {
-        dsrc = {nsrc, reinterpret_cast<const int64_t *>(w + L.off_sidx), reinterpret_cast<const float *>(w + L.off_samp),
-                snt};
-        if ((e = h2d(w + L.off_sidx, src->idx, (size_t)nsrc * 8)) != cudaSuccess ||
-            (e = h2d(w + L.off_samp, src->amp, (size_t)nsrc * snt * 4)) != cudaSuccess)
-            return cuda_fail(e, "copy of the sources to the device");
-    }
-    // receiver rows the run writes: [t0, t0 + nsteps) within [0, rnt)
-    const int64_t r0 = std::min(t0, rnt), r1 = std::min(t0 + nsteps, rnt);
-    if (nrec > 0) {
-        drec = {nrec, reinterpret_cast<const int64_t *>(w + L.off_ridx), reinterpret_cast<float *>(w + L.off_tr), rnt};
-        if ((e = h2d(w + L.off_ridx, rec->idx, (size_t)nrec * 8)) != cudaSuccess)
-            return cuda_fail(e, "copy of the receivers to the device");
-    }
-    s = time_block == 2
-            ? gbs_wave_propagate_tb(d_up, d_u, d_vel, dt, h, nx, ny, nz, halo, nsteps, t0, nsrc > 0 ? &dsrc : nullptr,
-                                    nrec > 0 ? &drec : nullptr, w + L.off_tb, L.total - L.off_tb, opts, stream)
-            : gbs_wave_propagate(d_up, d_u, d_vel, dt, h, nx, ny, nz, halo, nsteps, t0, nsrc > 0 ? &dsrc : nullptr,
-                                 nrec > 0 ? &drec : nullptr, opts, stream);
+    cudaError_t e = host_upload(j, st);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "copy of the inputs to the device");
+    if ((s = host_steps(j, st)) != GBS_OK)
+        return s;
+    if ((e = host_download(j, st)) != cudaSuccess)
+        return cuda_fail(e, "copy of the results to the host");
+    return GBS_OK;
+}
+
+// Pipelined host-buffer propagation of independent problems: uploads on
+// one stream, steps on a second, downloads on a third.  Problem k uses
+// workspace k % depth; its steps follow its upload and the previous
+// problem's steps (one stream), so cooperative launches never overlap; its
+// upload waits until the workspace's previous download is done and until
+// every download still in flight into host memory that it reads is done.
+struct gbs_pipeline {
+    gbs::Grid g;
+    int64_t nx, ny, nz;
+    int halo, time_block, depth, device;
+    int64_t nsrc_max, snt_max, nrec_max, rnt_max;
+    gbs::HostLayout L;
+    gbs_opts opts;
+    bool has_opts;
+    std::vector<char *> work;
+    cudaStream_t s_in, s_run, s_out;
+    std::vector<cudaEvent_t> ev_in, ev_run, ev_out;
+    // host bytes each workspace's last download writes: [lo, hi) ranges
+    std::vector<std::vector<std::pair<const char *, const char *>>> writes;
+    int64_t submitted;
+};
+
+namespace gbs {
+namespace {
+void pipeline_free(gbs_pipeline *p)
+{
+    if (!p)
+        return;
+    for (cudaStream_t st : {p->s_in, p->s_run, p->s_out})
+        if (st)
+            cudaStreamSynchronize(st);
+    for (char *w : p->work)
+        if (w)
+            cudaFree(w);
+    for (auto *v : {&p->ev_in, &p->ev_run, &p->ev_out})
+        for (cudaEvent_t e : *v)
+            if (e)
+                cudaEventDestroy(e);
+    for (cudaStream_t st : {p->s_in, p->s_run, p->s_out})
+        if (st)
+            cudaStreamDestroy(st);
+    delete p;
+}
+bool ranges_meet(const char *a0, const char *a1, const char *b0, const char *b1) { return a0 < b1 && b0 < a1; }
+}  // namespace
+}  // namespace gbs
+
+extern "C" gbs_status gbs_pipeline_create(gbs_pipeline **out, int64_t nx, int64_t ny, int64_t nz, int halo,
+                                          int64_t nsrc_max, int64_t src_nt_max, int64_t nrec_max, int64_t rec_nt_max,
+                                          int time_block, int depth, const gbs_opts *opts)
+{
+    const TraceRange trace_range("gbs_pipeline_create");
+    t_err[0] = 0;
+    if (!out)
+        return fail(GBS_EINVAL, "null pipeline pointer");
+    *out = nullptr;
+    gbs_status s = check_dims(nx, ny, nz, halo);
     if (s != GBS_OK)
         return s;
-    // the newest level into u, the one before into u_prev (on the device the
-    // buffers alternate: after an odd number of steps d_up holds the newest)
-    const float *newest = (nsteps & 1) ? d_up : d_u, *older = (nsteps & 1) ? d_u : d_up;
-    if ((e = d2h(u, newest, fb)) != cudaSuccess || (e = d2h(u_prev, older, fb)) != cudaSuccess)
-        return cuda_fail(e, "copy of the fields to the host");
-    if (nrec > 0 && r1 > r0 &&
-        (e = d2h(rec->trace + r0 * nrec, reinterpret_cast<float *>(w + L.off_tr) + r0 * nrec,
-                 (size_t)(r1 - r0) * nrec * 4)) != cudaSuccess)
-        return cuda_fail(e, "copy of the trace to the host");
+    if (time_block != 0 && time_block != 2)
+        return fail(GBS_EINVAL, "time_block must be 0 (one launch per step) or 2 (fused pairs)");
+    if (depth < 1 || depth > 8)
+        return fail(GBS_EINVAL, "depth must be in [1, 8] (got %d)", depth);
+    if (nsrc_max < 0 || src_nt_max < 0 || nrec_max < 0 || rec_nt_max < 0)
+        return fail(GBS_EINVAL, "source and receiver sizes must be >= 0");
+    if (nx == 0 || ny == 0 || nz == 0)
+        return fail(GBS_EINVAL, "a pipeline needs a non-empty interior");
+    gbs_pipeline *p = new gbs_pipeline();
+    p->g = dense_grid(nx, ny, nz, halo);
+    p->nx = nx;
+    p->ny = ny;
+    p->nz = nz;
+    p->halo = halo;
+    p->time_block = time_block;
+    p->depth = depth;
+    p->nsrc_max = nsrc_max;
+    p->snt_max = src_nt_max;
+    p->nrec_max = nrec_max;
+    p->rnt_max = rec_nt_max;
+    p->L = host_layout(p->g, nsrc_max, src_nt_max, nrec_max, rec_nt_max, time_block);
+    p->has_opts = opts != nullptr;
+    if (opts)
+        p->opts = *opts;
+    p->submitted = 0;
+    cudaError_t e = cudaGetDevice(&p->device);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+        e = cudaStreamCreateWithFlags(i == 0 ? &p->s_in : i == 1 ? &p->s_run : &p->s_out, cudaStreamNonBlocking);
+    p->work.assign(depth, nullptr);
+    p->ev_in.assign(depth, nullptr);
+    p->ev_run.assign(depth, nullptr);
+    p->ev_out.assign(depth, nullptr);
+    p->writes.assign(depth, {});
+    for (int i = 0; i < depth && e == cudaSuccess; ++i) {
+        e = cudaMalloc(reinterpret_cast<void **>(&p->work[i]), p->L.total);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            gbs::pipeline_free(p);
+            return fail(GBS_ENOMEM, "pipeline workspaces: %d x %zu bytes", depth, p->L.total);
+        }
+        for (auto *v : {&p->ev_in, &p->ev_run, &p->ev_out})
+            if (e == cudaSuccess)
+                e = cudaEventCreateWithFlags(&(*v)[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        gbs::pipeline_free(p);
+        return cuda_fail(e, "pipeline streams, events or workspaces");
+    }
+    *out = p;
     return GBS_OK;
+}
+
+extern "C" gbs_status gbs_pipeline_submit(gbs_pipeline *p, float *u_prev, float *u, const float *vel, float dt,
+                                          float h, int64_t nsteps, int64_t t0, const gbs_src *src, const gbs_rec *rec)
+{
+    const TraceRange trace_range("gbs_pipeline_submit");
+    t_err[0] = 0;
+    if (!p)
+        return fail(GBS_EINVAL, "null pipeline");
+    gbs_status s = check_host_job(p->nx, p->ny, p->nz, p->halo, p->time_block, nsteps, t0, src, rec, u_prev, u, vel);
+    if (s != GBS_OK)
+        return s;
+    if (src && (src->n > p->nsrc_max || (src->n > 0 && src->nt > p->snt_max)))
+        return fail(GBS_EINVAL, "at most %lld sources x %lld steps (the pipeline's sizes)", (long long)p->nsrc_max,
+                    (long long)p->snt_max);
+    if (rec && (rec->n > p->nrec_max || (rec->n > 0 && rec->nt > p->rnt_max)))
+        return fail(GBS_EINVAL, "at most %lld receivers x %lld steps (the pipeline's sizes)", (long long)p->nrec_max,
+                    (long long)p->rnt_max);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device)
+        return fail(GBS_EINVAL, "submit on the device the pipeline was created on");
+    if (nsteps == 0)
+        return GBS_OK;
+    const int slot = (int)(p->submitted % p->depth);
+    const HostJob j{p->g, p->L, p->work[slot], u_prev, u, vel, dt, h, nsteps, t0, src, rec, p->time_block,
+                    p->has_opts ? &p->opts : nullptr};
+    const size_t fb = j.field_bytes();
+    // host bytes this problem reads
+    std::vector<std::pair<const char *, const char *>> reads;
+    auto add = [](std::vector<std::pair<const char *, const char *>> &v, const void *a, size_t n) {
+        if (a && n)
+            v.emplace_back(static_cast<const char *>(a), static_cast<const char *>(a) + n);
+    };
+    add(reads, u_prev, fb);
+    add(reads, u, fb);
+    add(reads, vel, fb);
+    if (j.nsrc() > 0) {
+        add(reads, src->idx, (size_t)j.nsrc() * 8);
+        add(reads, src->amp, (size_t)j.nsrc() * src->nt * 4);
+    }
+    if (j.nrec() > 0)
+        add(reads, rec->idx, (size_t)j.nrec() * 8);
+    cudaError_t e = cudaSuccess;
+    const int64_t first = std::max<int64_t>(0, p->submitted - p->depth);
+    for (int64_t k = first; k < p->submitted && e == cudaSuccess; ++k) {
+        const int q = (int)(k % p->depth);
+        bool wait = q == slot;   // the workspace is free once its last download is done
+        for (const auto &w : p->writes[q])
+            for (const auto &r : reads)
+                wait = wait || gbs::ranges_meet(w.first, w.second, r.first, r.second);
+        if (wait)
+            e = cudaStreamWaitEvent(p->s_in, p->ev_out[q], 0);
+    }
+    if (e == cudaSuccess && (e = host_upload(j, p->s_in)) == cudaSuccess &&
+        (e = cudaEventRecord(p->ev_in[slot], p->s_in)) == cudaSuccess)
+        e = cudaStreamWaitEvent(p->s_run, p->ev_in[slot], 0);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "pipeline upload");
+    if ((s = host_steps(j, p->s_run)) != GBS_OK)
+        return s;
+    if ((e = cudaEventRecord(p->ev_run[slot], p->s_run)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p->s_out, p->ev_run[slot], 0)) != cudaSuccess ||
+        (e = host_download(j, p->s_out)) != cudaSuccess || (e = cudaEventRecord(p->ev_out[slot], p->s_out)) != cudaSuccess)
+        return cuda_fail(e, "pipeline download");
+    std::vector<std::pair<const char *, const char *>> writes;
+    add(writes, u_prev, fb);
+    add(writes, u, fb);
+    if (j.nrec() > 0 && j.r1() > j.r0())
+        add(writes, rec->trace + j.r0() * j.nrec(), (size_t)(j.r1() - j.r0()) * j.nrec() * 4);
+    p->writes[slot] = std::move(writes);
+    ++p->submitted;
+    return GBS_OK;
+}
+
+extern "C" gbs_status gbs_pipeline_wait(gbs_pipeline *p)
+{
+    const TraceRange trace_range("gbs_pipeline_wait");
+    t_err[0] = 0;
+    if (!p)
+        return fail(GBS_EINVAL, "null pipeline");
+    for (cudaStream_t st : {p->s_in, p->s_run, p->s_out}) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "pipeline wait");
+    }
+    return GBS_OK;
+}
+
+extern "C" size_t gbs_pipeline_workspace_bytes(gbs_pipeline *p) { return p ? p->L.total * (size_t)p->depth : 0; }
+
+extern "C" void gbs_pipeline_destroy(gbs_pipeline *p)
+{
+    const TraceRange trace_range("gbs_pipeline_destroy");
+    gbs::pipeline_free(p);
 }
 
 extern "C" gbs_status gbs_selftest_tb_timeout(void *stream)

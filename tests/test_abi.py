@@ -220,8 +220,9 @@ def test_tb_workspace_and_validation(lib):
     r256 = (n + 255) // 256 * 256
     assert gbs.tb_workspace_bytes(8, 8, 8, 4) == 2 * r256 + (1 << 18) * 4
     assert gbs.tb_workspace_bytes(-1, 8, 8, 4) == 0
-    # no device here: the fused path is never reported as available
-    assert gbs.tb_supported(64, 64, 64, 4) == (False, 0, 0)
+    # without a device the fused path is never reported as available
+    if not gbs.torch.cuda.is_available():
+        assert gbs.tb_supported(64, 64, 64, 4) == (False, 0, 0)
     fake = [ctypes.c_void_p(1 << 20), ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20)]
     work = ctypes.c_void_p(1 << 26)
     big = ctypes.c_size_t(1 << 30)
@@ -283,3 +284,23 @@ def test_cfl_check_validation_and_limit(lib):
                              None) == gbs.GBS_EINVAL
     assert lib.gbs_check_cfl(fake, 8, 8, 8, 4, ctypes.c_float(0.0), ctypes.c_float(10.0), None, None,
                              None) == gbs.GBS_EINVAL
+
+
+def test_pipeline_validation_before_device(lib):
+    pp = ctypes.c_void_p()
+    create = lib.gbs_pipeline_create
+    assert create(None, 8, 8, 8, 4, 0, 0, 0, 0, 2, 2, None) == gbs.GBS_EINVAL            # nowhere to put it
+    assert create(ctypes.byref(pp), 8, 8, 8, 4, 0, 0, 0, 0, 1, 2, None) == gbs.GBS_EINVAL   # time_block 0 or 2
+    assert create(ctypes.byref(pp), 8, 8, 8, 4, 0, 0, 0, 0, 2, 0, None) == gbs.GBS_EINVAL   # depth in [1, 8]
+    assert create(ctypes.byref(pp), 8, 8, 8, 4, 0, 0, 0, 0, 2, 9, None) == gbs.GBS_EINVAL
+    assert create(ctypes.byref(pp), 8, 8, 8, 4, -1, 0, 0, 0, 2, 2, None) == gbs.GBS_EINVAL  # negative sizes
+    assert create(ctypes.byref(pp), 0, 8, 8, 4, 0, 0, 0, 0, 2, 2, None) == gbs.GBS_EINVAL   # empty interior
+    assert create(ctypes.byref(pp), 8, 8, 8, -4, 0, 0, 0, 0, 2, 2, None) == gbs.GBS_EINVAL  # bad halo
+    assert not pp.value
+    host = [np.zeros((16, 16, 16), np.float32) for _ in range(3)]
+    p = [ctypes.c_void_p(a.ctypes.data) for a in host]
+    assert lib.gbs_pipeline_submit(None, p[0], p[1], p[2], ctypes.c_float(1e-3), ctypes.c_float(10.0), 2, 0, None,
+                                   None) == gbs.GBS_EINVAL
+    assert lib.gbs_pipeline_wait(None) == gbs.GBS_EINVAL
+    assert lib.gbs_pipeline_workspace_bytes(None) == 0
+    lib.gbs_pipeline_destroy(None)                                                         # no-op
