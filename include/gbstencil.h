@@ -292,6 +292,7 @@ gbs_status gbs_wave_propagate_host(float *u_prev, float *u, const float *vel, fl
  *                 problem's results are in host memory.  Errors: GBS_ECUDA.
  *   gbs_pipeline_workspace_bytes  device bytes the pipeline holds.
  *   gbs_pipeline_destroy  waits for outstanding work and frees everything.
+ * A pipeline is used by one host thread at a time.
  */
 typedef struct gbs_pipeline gbs_pipeline;
 gbs_status gbs_pipeline_create(gbs_pipeline **pipeline, int64_t nx, int64_t ny, int64_t nz, int halo,
