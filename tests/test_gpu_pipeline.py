@@ -6,7 +6,8 @@ problem overlapping the steps of another.  The same kernels run in the same
 order for each problem, so every result must equal, bit for bit, the same
 problem run alone through the host-buffer entry: fields, traces, and
 problems continued from an earlier submission's results (the same host
-tensors submitted again, which makes the upload wait for that download).
+tensors submitted again, which makes the upload wait for that download),
+with and without the steps captured into CUDA graphs.
 """
 import numpy as np
 import pytest
@@ -37,13 +38,14 @@ def _problem(nx, ny, nz, seed, nt, nrec):
     return dict(up=up, u=u, vel=vel, dt=dt, si=si, sa=sa, ri=ri)
 
 
-@pytest.mark.parametrize("time_block,depth", [(2, 2), (0, 3), (2, 1)])
-def test_pipeline_matches_problems_run_alone(time_block, depth):
+@pytest.mark.parametrize("time_block,depth,graph", [(2, 2, False), (0, 3, False), (2, 1, False), (2, 2, True),
+                                                   (0, 2, True)])
+def test_pipeline_matches_problems_run_alone(time_block, depth, graph):
     need_gpu()
     nx, ny, nz, halo, nt = 64, 48, 40, 4, 24
     probs = [_problem(nx, ny, nz, 700 + 10 * k, nt, 40) for k in range(3)]
     pipe = gbs.Pipeline(nx, ny, nz, halo, depth=depth, time_block=time_block, nsrc_max=8, src_nt_max=nt,
-                        nrec_max=64, rec_nt_max=nt)
+                        nrec_max=64, rec_nt_max=nt, use_graph=graph)
     assert pipe.workspace_bytes() >= depth * 3 * W.padded_shape(nx, ny, nz, halo)[0] * 4
     # pipeline: A, B, C for 9 steps, then A and B continued for 7 more (t0 = 9)
     host = []
