@@ -8,6 +8,8 @@ What is checked, and what it would catch in the oracle:
   of the leapfrog scheme is constant without sources (any wrong weight of the
   Laplacian term, a transposed velocity index or a wrong h scaling breaks it);
 * time reversal: the scheme run backwards returns the initial pair;
+* one step of a plane wave (halo holding the same wave) follows the discrete
+  dispersion closed form ((2 + (V dt)^2 lam) A - B) sin(k.x + phi);
 * linearity in the sources, restart at t0, and receiver traces.
 """
 import numpy as np
@@ -193,3 +195,28 @@ def test_source_time_index():
     assert u4[k + halo, j + halo, i + halo] == (v * dt) ** 2
     assert np.count_nonzero(u4) == 1
     assert tr[:3].tolist() == [[0.0]] * 3 and tr[3, 0] == (v * dt) ** 2
+
+
+def test_plane_wave_step_dispersion():
+    """One step of a plane wave whose halo holds the same wave (the stencil
+    sees exact values everywhere): the interior of u^{n+1} is
+    ((2 + (V dt)^2 lam) A - B) sin(k.x + phi), with lam the discrete symbol
+    sum_a (c0 + 2 sum_m c_m cos(m k_a h)) / h^2 of the radius-4 Laplacian.
+    Pins the factor 2, the sign of u^{n-1}, the (V dt)^2 scaling and the h^2
+    normalisation of Eq. 2 together."""
+    nx, ny, nz, halo, h, v = 10, 9, 8, 4, 10.0, 2500.0
+    dt = W.dt_for_cfl(0.4, h, v)
+    k = (0.11, -0.23, 0.17)          # radians per metre
+    phi, A, B = 0.3, 1.3, -0.6
+    shape = W.padded_shape(nx, ny, nz, halo)
+    z, y, x = np.meshgrid(*(h * (np.arange(s) - halo) for s in shape), indexing="ij")
+    wave = np.sin(k[0] * x + k[1] * y + k[2] * z + phi)
+    c = oracle.fd2_coeffs(4)
+    lam = sum((c[0] + 2 * sum(c[m] * np.cos(m * ka * h) for m in range(1, 5))) / h ** 2 for ka in k)
+    vel = np.full(shape, v)
+    nxt, _ = oracle.wave_step(B * wave, A * wave, vel, dt, h, halo)
+    want = ((2 + (v * dt) ** 2 * lam) * A - B) * W.interior(wave, halo)
+    np.testing.assert_allclose(W.interior(nxt, halo), want, rtol=0, atol=1e-12)
+    # and the same wave advanced with the continuous symbol -|k|^2 differs (the pin sees the discretisation)
+    lam_c = -sum(ka * ka for ka in k)
+    assert abs(lam - lam_c) > 1e-9 * abs(lam_c)
