@@ -244,3 +244,31 @@ def test_cfl_check_matches_the_steps():
         peak[cfl] = float(torch.nan_to_num(cur.abs(), nan=float("inf")).max())
     assert peak[0.44] < 100.0, peak
     assert peak[0.47] > 1e6, peak
+
+
+@pytest.mark.parametrize("shape", [(64, 48, 40), (37, 21, 13)])
+def test_plane_wave_step_against_dispersion_closed_form(shape):
+    """One GPU step of a plane wave whose halo holds the same wave equals the
+    discrete dispersion closed form ((2 + (V dt)^2 lam) A - B) sin(k.x + phi)
+    (lam: the radius-4 symbol), on the TMA path (64 x 48 x 40) and the
+    plain-load path (ragged 37 x 21 x 13).  Tolerance: the one-step FP32
+    bound, normwise."""
+    need_gpu()
+    nx, ny, nz = shape
+    halo, h, v = 4, 10.0, 2500.0
+    dt = W.dt_for_cfl(0.4, h, v)
+    k = (0.11, -0.23, 0.17)
+    phi, A, B = 0.3, 1.3, -0.6
+    pshape = W.padded_shape(nx, ny, nz, halo)
+    z, y, x = np.meshgrid(*(h * (np.arange(s) - halo) for s in pshape), indexing="ij")
+    wave = np.sin(k[0] * x + k[1] * y + k[2] * z + phi)
+    c = oracle.fd2_coeffs(4)
+    lam = sum((c[0] + 2 * sum(c[m] * np.cos(m * ka * h) for m in range(1, 5))) / h ** 2 for ka in k)
+    up = (B * wave).astype(np.float32)
+    u = (A * wave).astype(np.float32)
+    nxt = to_dev(np.zeros(pshape, np.float32))
+    gbs.wave_step(to_dev(up), to_dev(u), nxt, to_dev(np.full(pshape, v, np.float32)), dt, h, halo)
+    gbs.device_status()
+    want = ((2 + (float(np.float32(v)) * dt) ** 2 * lam) * A - B) * W.interior(wave, halo)
+    e = oracle.err_norms(W.interior(nxt.cpu().numpy(), halo), want)
+    assert e["norm_max_rel"] <= TOL_ONE, e
