@@ -101,3 +101,35 @@ def test_kernels_agree():
     b = gbs.stencil_apply(t, o, radius=4, cx=c, cy=c, cz=c, halo=halo).cpu().numpy()
     e = oracle.err_norms(W.interior(b, halo), W.interior(a, halo))
     assert e["norm_max_rel"] <= TOL_ONE, e
+
+
+@pytest.mark.parametrize("R", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [(64, 48, 40, 4), (37, 21, 13, 4)])
+def test_plane_wave_symbol_closed_form(shape, R):
+    """A plane wave whose halo holds the same wave: Eq. 3 with the order-2R
+    weights over spacings (hx, hy, hz) gives sym * sin(k.x + phi), with
+    sym = sum_a (c0 + 2 sum_m c_m cos(m k_a h_a)) / h_a^2 (closed form, no
+    oracle).  Every point must lie within the a-priori FP32 bound: inputs,
+    weights and the sum of 6R + 1 terms each rounded once,
+    (6R + 4) u sum_q |w_q| max|in| + u |exact|, u = 2^-24."""
+    need_gpu()
+    nx, ny, nz, halo = shape
+    hs = (0.7, 1.1, 0.9)
+    k = (0.9, -1.7, 2.3)
+    phi = 0.4
+    pshape = W.padded_shape(nx, ny, nz, halo)
+    z, y, x = np.meshgrid(*((np.arange(s) - halo) * hh for s, hh in zip(pshape, hs[::-1])), indexing="ij")
+    wave = np.sin(k[0] * x + k[1] * y + k[2] * z + phi)
+    c = oracle.fd2_coeffs(R)
+    sym = sum((c[0] + 2 * sum(c[m] * np.cos(m * ka * ha) for m in range(1, R + 1))) / ha ** 2
+              for ka, ha in zip(k, hs))
+    cx, cy, cz = ((c / (ha * ha)).astype(np.float32) for ha in hs)
+    out = gbs.stencil_apply(to_dev(wave.astype(np.float32)), radius=R, cx=cx, cy=cy, cz=cz, halo=halo)
+    gbs.device_status()
+    exact = sym * W.interior(wave, halo)
+    u = 2.0 ** -24
+    wsum = sum(abs(c[0]) / ha ** 2 + 2 * sum(abs(c[m]) for m in range(1, R + 1)) / ha ** 2 for ha in hs)
+    bound = (6 * R + 4) * u * wsum * 1.0 + u * np.abs(exact)
+    err = np.abs(W.interior(out.cpu().numpy(), halo).astype(np.float64) - exact)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    assert np.max(np.abs(exact)) > 0.5 * abs(sym)
