@@ -272,3 +272,32 @@ def test_plane_wave_step_against_dispersion_closed_form(shape):
     want = ((2 + (float(np.float32(v)) * dt) ** 2 * lam) * A - B) * W.interior(wave, halo)
     e = oracle.err_norms(W.interior(nxt.cpu().numpy(), halo), want)
     assert e["norm_max_rel"] <= TOL_ONE, e
+
+
+@pytest.mark.parametrize("shape", [(64, 48, 40), (37, 21, 13)])
+def test_degenerate_steps_are_exact(shape):
+    """Degenerate cases of Eq. 2 with exact FP32 answers, on every step path
+    (TMA or plain loads for the shape, and fused pairs): with V = 0 each step
+    is u^{n+1} = 2u^n - u^{n-1} (one rounding, as numpy computes it in FP32);
+    with u^0 = u^{-1} = 0 and no source the field stays exactly zero."""
+    need_gpu()
+    nx, ny, nz = shape
+    halo, h, dt, n = 4, 10.0, 1e-3, 6
+    up = W.uniform_field(nx, ny, nz, halo, 21, halo_random=False)
+    u = W.uniform_field(nx, ny, nz, halo, 22, halo_random=False)
+    vel0 = np.zeros_like(u)
+    a, b = up.copy(), u.copy()
+    for _ in range(n):
+        a, b = b, (np.float32(2) * b - a).astype(np.float32)
+    runs = [gbs.wave_propagate]
+    if gbs.tb_supported(nx, ny, nz, halo)[0]:
+        runs.append(gbs.wave_propagate_tb)
+    for run in runs:
+        p, c = run(to_dev(up), to_dev(u), to_dev(vel0), dt, h, halo, n)
+        gbs.device_status()
+        assert np.array_equal(c.cpu().numpy(), b) and np.array_equal(p.cpu().numpy(), a), run.__name__
+        z = np.zeros_like(u)
+        vel = W.layered_velocity(nx, ny, nz, halo, 23)
+        p, c = run(to_dev(z), to_dev(z), to_dev(vel), W.dt_for_cfl(0.4, h, float(vel.max())), h, halo, n)
+        gbs.device_status()
+        assert not bool(c.any()) and not bool(p.any()), run.__name__
