@@ -304,3 +304,13 @@ def test_pipeline_validation_before_device(lib):
     assert lib.gbs_pipeline_wait(None) == gbs.GBS_EINVAL
     assert lib.gbs_pipeline_workspace_bytes(None) == 0
     lib.gbs_pipeline_destroy(None)                                                         # no-op
+
+
+def test_pipeline_binding_raises_on_bad_arguments(lib):
+    with pytest.raises(gbs.GbsError):
+        gbs.Pipeline(8, 8, 8, 4, depth=0)
+    with pytest.raises(gbs.GbsError):
+        gbs.Pipeline(8, 8, 8, 4, time_block=3)
+    if not gbs.torch.cuda.is_available():
+        with pytest.raises(gbs.GbsError):            # no device: streams and workspaces cannot be made
+            gbs.Pipeline(8, 8, 8, 4)
