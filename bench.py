@@ -493,10 +493,14 @@ def precision_errors(stream, n=256, nsteps=500):
                                       src_amp=prob.src_amp)
     t_oracle = time.perf_counter() - t0
     out = {"grid": [n, n, n], "steps": nsteps, "oracle_seconds": t_oracle}
-    for fmt in ("f32", "bf16", "f16"):
+    for fmt in ("f32", "f32_tb", "bf16", "f16"):
         a, b = torch.zeros_like(vel), torch.zeros_like(vel)
         if fmt == "f32":
             _, cur = gbs.wave_propagate(a, b, vel, prob.dt, prob.h, prob.halo, nsteps, src_idx=si, src_amp=sa)
+        elif fmt == "f32_tb":
+            # the headline path: fused pairs of steps (falls back to single steps where no fused shape fits)
+            out["f32_tb_fused"] = bool(gbs.tb_supported(n, n, n, prob.halo)[0])
+            _, cur = gbs.wave_propagate_tb(a, b, vel, prob.dt, prob.h, prob.halo, nsteps, src_idx=si, src_amp=sa)
         else:
             _, cur = gbs.wave_propagate_lp(a, b, vel, prob.dt, prob.h, prob.halo, nsteps, storage=fmt, src_idx=si,
                                            src_amp=sa)

@@ -329,7 +329,9 @@ gbs_status gbs_check_cfl(const float *vel, int64_t nx, int64_t ny, int64_t nz, i
  * the CUDA context stays usable.  Synchronises `stream`, frees its buffers
  * and returns the status the launch recorded: GBS_ETIMEOUT when the
  * mechanism works (GBS_EINVAL if the launch recorded nothing,
- * GBS_EUNSUPPORTED if the kernel cannot run here, GBS_ECUDA).
+ * GBS_EUNSUPPORTED if the kernel cannot run here, GBS_ECUDA).  If an
+ * earlier fused-pair launch left a device status, the self-test does not
+ * run: it returns GBS_EINVAL and leaves that status for gbs_device_status.
  */
 gbs_status gbs_selftest_tb_timeout(void *stream);
 
@@ -494,7 +496,10 @@ gbs_status gbs_field_norms(const float *x, const float *ref, int64_t nx, int64_t
  * be serialised by the caller.  Nothing in it needs clearing between calls.
  * The first call on a device looks up the array's device address (and may
  * load the library's GPU code on that device); make that first call outside
- * any stream capture.  No device memory is allocated or freed.
+ * any stream capture.  The address is kept for the life of the process, so
+ * do not call this entry point after a cudaDeviceReset of a device it has
+ * already run on (the array then lives at a new address).  No device memory
+ * is allocated or freed.
  * Errors: GBS_EINVAL, GBS_ECUDA.
  */
 gbs_status gbs_field_norms_noalloc(const float *x, const float *ref, int64_t nx, int64_t ny, int64_t nz,

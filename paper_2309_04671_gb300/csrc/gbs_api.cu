@@ -1162,6 +1162,12 @@ extern "C" gbs_status gbs_selftest_tb_timeout(void *stream)
     const TbLayout L = tb_layout(g);
     const size_t fb = (size_t)field_elems(g) * 4;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // a status recorded by an earlier launch belongs to its caller: leave it
+    // for gbs_device_status and run no test that would mix it with this one's
+    const unsigned before = wf_status_peek(st);
+    if (before != 0)
+        return fail(GBS_EINVAL, "self-test not run: an earlier fused-pair launch recorded device status %u "
+                                "(read it with gbs_device_status first)", before);
     char *mem = nullptr;
     cudaError_t e = cudaMalloc(&mem, 3 * round256(fb) + L.total);
     if (e != cudaSuccess)

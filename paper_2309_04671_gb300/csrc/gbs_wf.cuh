@@ -59,5 +59,7 @@ bool wf_shape(const Grid &g, WfShape *s);
 cudaError_t wf_prepare(int tile_y);
 cudaError_t launch_wf(const WfShape &s, const WfMaps &m, const WfParams &p, cudaStream_t st);
 unsigned wf_status_take(cudaStream_t st);
+// The fused kernel's device status word after synchronising `st`, left in place.
+unsigned wf_status_peek(cudaStream_t st);
 
 }  // namespace gbs

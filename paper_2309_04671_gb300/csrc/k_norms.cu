@@ -109,9 +109,10 @@ __global__ void __launch_bounds__(kThreads) k_norms_final(const double *part, in
 
 // Device address of g_norm_scratch on the current device.  Host code cannot
 // use the array's name as a device pointer, so the address is looked up once
-// per device (with that device current) and cached.  The first lookup on a
-// device may load the module there, so it must not happen inside a stream
-// capture.
+// per device (with that device current) and cached for the life of the
+// process (a cudaDeviceReset would move the array; the entry point's
+// documentation rules that out).  The first lookup on a device may load the
+// module there, so it must not happen inside a stream capture.
 cudaError_t norms_static_scratch(double **ptr)
 {
     static std::mutex mu;

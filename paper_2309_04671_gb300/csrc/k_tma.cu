@@ -333,20 +333,32 @@ __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, c
     const float *amp_row = (C::WAVE && p.src_amp != nullptr && t >= 0 && t < p.src_nt)
                                ? p.src_amp + t * p.nsrc
                                : nullptr;
-    if (amp_row != nullptr && tid < p.nsrc) {
-        const int64_t lin = p.src_idx[tid];
-        if (lin < 0 || lin >= p.inx * p.iny * g.nz) {
-            atomicCAS(&g_status_tma, 0u, (unsigned)GBS_EINVAL);
-        } else {
-            const int64_t i = lin % p.inx, j = (lin / p.inx) % p.iny, k = lin / (p.inx * p.iny);
-            if (i >= tx0 && i < tx0 + kTX && j >= ty0 && j < ty0 + TY && k >= z0 && k < z1) {
-                const int slot = atomicAdd(&s_nsrc, 1);
-                s_src_x[slot] = (int)(i - tx0);
-                s_src_y[slot] = (int)(j - ty0);
-                s_src_z[slot] = (int)k;
-                s_src_f[slot] = amp_row[tid];
+    // Slots in source-index order (a ballot over warp 0, nsrc <= 32), so
+    // that sources sharing a cell are added in the same order on every run.
+    if (tid < 32) {
+        bool in = false;
+        int64_t i = 0, j = 0, k = 0;
+        if (amp_row != nullptr && tid < p.nsrc) {
+            const int64_t lin = p.src_idx[tid];
+            if (lin < 0 || lin >= p.inx * p.iny * g.nz) {
+                atomicCAS(&g_status_tma, 0u, (unsigned)GBS_EINVAL);
+            } else {
+                i = lin % p.inx;
+                j = (lin / p.inx) % p.iny;
+                k = lin / (p.inx * p.iny);
+                in = i >= tx0 && i < tx0 + kTX && j >= ty0 && j < ty0 + TY && k >= z0 && k < z1;
             }
         }
+        const unsigned inb = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            const int slot = __popc(inb & ((1u << tid) - 1u));
+            s_src_x[slot] = (int)(i - tx0);
+            s_src_y[slot] = (int)(j - ty0);
+            s_src_z[slot] = (int)k;
+            s_src_f[slot] = amp_row[tid];
+        }
+        if (tid == 0)
+            s_nsrc = __popc(inb);
     }
 
     // epilogue constants (identity scales for FP32); 16-bit state slot of level t is t % 3

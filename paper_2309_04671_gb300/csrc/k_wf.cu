@@ -296,20 +296,33 @@ __device__ __forceinline__ void wf_consumer(const WfParams &p, const Ring &rg, c
     const int64_t t = p.t + STAGE;
 
     const float *amp_row = (p.src_amp != nullptr && t >= 0 && t < p.src_nt) ? p.src_amp + t * p.nsrc : nullptr;
-    if (amp_row != nullptr && tid < p.nsrc) {
-        const int64_t lin = p.src_idx[tid];
-        if (lin < 0 || lin >= p.inx * p.iny * g.nz) {
-            atomicCAS(&g_status_wf, 0u, (unsigned)GBS_EINVAL);
-        } else {
-            const int64_t i = lin % p.inx, j = (lin / p.inx) % p.iny, k = lin / (p.inx * p.iny);
-            if (i >= tx0 && i < tx0 + kTX && j >= ty0 && j < ty0 + TY && k >= o0 && k < o0 + nzc) {
-                const int slot = atomicAdd(s_nsrc, 1);
-                s_src_x[slot] = (int)(i - tx0);
-                s_src_y[slot] = (int)(j - ty0);
-                s_src_z[slot] = (int)k;
-                s_src_f[slot] = amp_row[tid];
+    // Slots in source-index order (a ballot over the stage's first warp,
+    // nsrc <= 32), so that sources sharing a cell are added in the same order
+    // on every run and by both z-chunks that compute a halo plane.
+    if (tid < 32) {
+        bool in = false;
+        int64_t i = 0, j = 0, k = 0;
+        if (amp_row != nullptr && tid < p.nsrc) {
+            const int64_t lin = p.src_idx[tid];
+            if (lin < 0 || lin >= p.inx * p.iny * g.nz) {
+                atomicCAS(&g_status_wf, 0u, (unsigned)GBS_EINVAL);
+            } else {
+                i = lin % p.inx;
+                j = (lin / p.inx) % p.iny;
+                k = lin / (p.inx * p.iny);
+                in = i >= tx0 && i < tx0 + kTX && j >= ty0 && j < ty0 + TY && k >= o0 && k < o0 + nzc;
             }
         }
+        const unsigned inb = __ballot_sync(0xffffffffu, in);
+        if (in) {
+            const int slot = __popc(inb & ((1u << tid) - 1u));
+            s_src_x[slot] = (int)(i - tx0);
+            s_src_y[slot] = (int)(j - ty0);
+            s_src_z[slot] = (int)k;
+            s_src_f[slot] = amp_row[tid];
+        }
+        if (tid == 0)
+            *s_nsrc = __popc(inb);
     }
     stage_sync(1 + STAGE, C::NT);
 
@@ -824,6 +837,16 @@ cudaError_t launch_wf(const WfShape &s, const WfMaps &m, const WfParams &p, cuda
     case 16: return ab ? launch_t<16, true>(s, m, q, st) : launch_t<16, false>(s, m, q, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+unsigned wf_status_peek(cudaStream_t st)
+{
+    unsigned v = 0;
+    if (cudaStreamSynchronize(st) != cudaSuccess)
+        return GBS_ECUDA;
+    if (cudaMemcpyFromSymbol(&v, g_status_wf, sizeof(v)) != cudaSuccess)
+        return GBS_ECUDA;
+    return v;
 }
 
 unsigned wf_status_take(cudaStream_t st)

@@ -116,3 +116,47 @@ def test_batch_plan_repeat_bit_identical():
             for k, ((p, c), (p0, c0)) in enumerate(zip(got, first)):
                 assert torch.equal(p, p0) and torch.equal(c, c0), (storage, rep, k)
         plan.close()
+
+
+def test_shared_source_cells_on_chunk_seams_repeat_bit_identical():
+    """Pairs of sources in one cell, on planes next to the z-chunk seams of a
+    tall grid (planes that the stage A of both neighbouring chunks computes
+    and stores).  Each pair is added in source-index order, so every repeat
+    and both chunks give the same bits; the result also matches the oracle."""
+    import oracle
+    from gpu_util import tol_steps
+
+    need_gpu()
+    nx, ny, nz, halo, nsteps = 128, 56, 512, 4, 8
+    ok, tile_y, ctas = gbs.tb_supported(nx, ny, nz, halo)
+    tiles = ((nx + 63) // 64) * ((ny + tile_y - 1) // tile_y)
+    assert ok and ctas % tiles == 0 and ctas // tiles >= 4, (ok, tile_y, ctas)
+    zc = -(-nz // (ctas // tiles))                     # planes per chunk
+    rng = np.random.default_rng(941)
+    cells = []
+    for s, d in zip(range(1, 9), (-2, -1, 0, 1, -2, -1, 0, 1)):
+        k = s * zc + d
+        cells.append(W.linear_index(int(rng.integers(0, nx)), int(rng.integers(0, ny)), min(k, nz - 1), nx, ny))
+    src = np.repeat(np.array(cells, np.int64), 2)     # every cell twice
+    amp = rng.uniform(-1, 1, (nsteps, src.size)).astype(np.float32)
+    vel = W.layered_velocity(nx, ny, nz, halo, 942)
+    dt = W.dt_for_cfl(0.4, 10.0, float(W.interior(vel, halo).max()))
+    z = np.zeros(W.padded_shape(nx, ny, nz, halo), np.float32)
+    d_vel, si, sa = to_dev(vel), to_dev(src), to_dev(amp)
+    side = torch.cuda.Stream()
+    big = torch.empty(1 << 29, device=dev())
+    first = None
+    for rep in range(REPEATS):
+        torch.cuda.synchronize()
+        if rep % 2:
+            _perturb(side, big)
+        p, c = gbs.wave_propagate_tb(to_dev(z), to_dev(z), d_vel, dt, 10.0, halo, nsteps, src_idx=si, src_amp=sa)
+        torch.cuda.synchronize()
+        gbs.device_status()
+        if first is None:
+            first = (p.clone(), c.clone())
+            continue
+        assert torch.equal(p, first[0]) and torch.equal(c, first[1]), rep
+    _, ru, _ = oracle.wave_propagate(z, z, vel, dt, 10.0, halo, nsteps, src_idx=src, src_amp=amp)
+    e = oracle.err_norms(first[1].cpu().numpy(), ru)
+    assert e["finite"] and e["norm_max_rel"] <= tol_steps(nsteps), e

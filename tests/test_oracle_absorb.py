@@ -120,3 +120,54 @@ def test_profile():
     mask = np.ones(eta.shape, bool)
     mask[H:-H, H:-H, H:-H] = False
     assert np.all(eta[mask] == 0)
+
+
+def _damped_problem(n=10, nt_src=5):
+    vel = W.layered_velocity(n, n, n, H, 21).astype(np.float64)
+    dt = W.dt_for_cfl(0.4, h, float(W.interior(vel, H).max()))
+    eta = oracle.absorbing_eta(n, n, n, H, 3, 80.0)
+    rng = np.random.default_rng(22)
+    up = W.zero_halo(rng.uniform(-1, 1, vel.shape), H)
+    u = W.zero_halo(rng.uniform(-1, 1, vel.shape), H)
+    si = np.array([W.linear_index(2, 3, 4, n, n), W.linear_index(7, 1, 8, n, n)], np.int64)
+    amp = rng.uniform(-1, 1, (nt_src, 2))
+    return up, u, vel, eta, dt, si, amp
+
+
+def test_propagate_damped_is_the_loop_of_steps_with_restart():
+    """wave_propagate_damped over 8 steps from t0 = 3 equals an explicit loop of
+    wave_step_damped that injects source row n at step n only while n < src_nt
+    (rows 3, 4 here; steps 5..10 have no source), and a split run (3 + 5
+    steps, the second from t0 = 6) equals the unsplit one bit for bit."""
+    up, u, vel, eta, dt, si, amp = _damped_problem()
+    t0, ns = 3, 8
+    a, b = up.copy(), u.copy()
+    for n in range(t0, t0 + ns):
+        if n < amp.shape[0]:
+            nxt = oracle.wave_step_damped(a, b, vel, eta, dt, h, H, src_idx=si, src_f=amp[n])
+        else:
+            nxt = oracle.wave_step_damped(a, b, vel, eta, dt, h, H)
+        a, b = b, nxt
+    p, q = oracle.wave_propagate_damped(up, u, vel, eta, dt, h, H, ns, t0=t0, src_idx=si, src_amp=amp)
+    np.testing.assert_array_equal(p, a)
+    np.testing.assert_array_equal(q, b)
+    p1, q1 = oracle.wave_propagate_damped(up, u, vel, eta, dt, h, H, 3, t0=t0, src_idx=si, src_amp=amp)
+    p2, q2 = oracle.wave_propagate_damped(p1, q1, vel, eta, dt, h, H, ns - 3, t0=t0 + 3, src_idx=si, src_amp=amp)
+    np.testing.assert_array_equal(p2, a)
+    np.testing.assert_array_equal(q2, b)
+    # the source rows matter: without them the result differs at the source cells
+    _, q0 = oracle.wave_propagate_damped(up, u, vel, eta, dt, h, H, ns, t0=t0)
+    assert not np.array_equal(q0, q)
+
+
+def test_propagate_damped_without_layer_is_algorithm_1():
+    """eta = 0: the damped time loop equals the oracle's Algorithm 1 (the C
+    time loop, pinned by energy, time reversal and the dispersion closed form)
+    with the same sources, including rows past the source function's end."""
+    up, u, vel, _, dt, si, amp = _damped_problem()
+    eta = np.zeros_like(vel)
+    ns, t0 = 9, 1
+    p, q = oracle.wave_propagate_damped(up, u, vel, eta, dt, h, H, ns, t0=t0, src_idx=si, src_amp=amp)
+    p_ref, q_ref, _ = oracle.wave_propagate(up, u, vel, dt, h, H, ns, t0=t0, src_idx=si, src_amp=amp)
+    np.testing.assert_allclose(p, p_ref, rtol=0, atol=1e-13 * np.abs(p_ref).max())
+    np.testing.assert_allclose(q, q_ref, rtol=0, atol=1e-13 * np.abs(q_ref).max())

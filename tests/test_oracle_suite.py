@@ -109,3 +109,57 @@ def test_divisor_and_orientation():
     assert got[0, 1, 2] == 0.25                          # x=1 sees in(x+1) = in(2)
     assert got[0, 1, 3] == 0.5                           # x=2 sees 2 in(2)
     assert got[0, 1, 1] == 0.0                           # nothing mirrored to x=0
+
+
+def _ragged_cases():
+    # (kernel, interior (nz, ny, nx), halo (hx, hy, hz)): per-axis halos differ so
+    # that an hx/hy (or nx/ny) swap in the index decoding reads other cells
+    return [("star3d3r", (5, 7, 11), (3, 5, 4)), ("box3d2r", (4, 9, 6), (2, 4, 3)),
+            ("j3d27pt", (3, 5, 8), (1, 2, 1)), ("star2d4r", (3, 6, 13), (5, 4, 0)),
+            ("box2d3r", (2, 11, 5), (3, 6, 0)), ("j2d9pt-gol", (1, 4, 9), (2, 1, 0))]
+
+
+@pytest.mark.parametrize("name,dims,halo", _ragged_cases(), ids=[c[0] for c in _ragged_cases()])
+def test_points_equal_the_full_evaluation(name, dims, halo):
+    """stencil_general_points at every interior linear index (x fastest, then
+    y, then z) equals stencil_general at that point, on FP32 inputs."""
+    shape, dim, r, div = oracle.SUITE[name]
+    fp = oracle.footprint(shape, dim, r)
+    rng = np.random.default_rng(len(fp) + 100)
+    w = rng.uniform(-2, 2, len(fp))
+    x = _field(dims, halo, 17).astype(np.float32)
+    divisor = 3.0 if div else 1.0
+    full = oracle.stencil_general(x.astype(np.float64), fp, w, halo, divisor)
+    nz, ny, nx = dims
+    hx, hy, hz = halo
+    idx = np.arange(nx * ny * nz, dtype=np.int64)
+    got = oracle.stencil_general_points(x, fp, w, halo, idx, divisor)
+    want = full[hz:hz + nz, hy:hy + ny, hx:hx + nx].reshape(-1)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-13)
+    # a subset in shuffled order gives the same values at the same indices
+    sub = rng.permutation(idx)[: max(1, idx.size // 3)]
+    np.testing.assert_array_equal(oracle.stencil_general_points(x, fp, w, halo, sub, divisor), got[sub])
+
+
+def test_points_of_a_delta_field_read_the_mirrored_weights():
+    """A single 1 at interior (i0, j0, k0): the output at p holds w_q for the
+    offset q = (i0, j0, k0) - p, zero where no offset reaches it -- checked
+    by hand at the points whose offsets differ on each axis."""
+    fp = np.array([[1, 0, 0], [0, 2, 0], [0, 0, -1], [-2, -1, 1]], np.int32)
+    w = np.array([3.0, 5.0, 7.0, 11.0])
+    hx, hy, hz = 2, 3, 1
+    nz, ny, nx = 4, 6, 7
+    x = np.zeros((nz + 2 * hz, ny + 2 * hy, nx + 2 * hx), np.float32)
+    i0, j0, k0 = 3, 2, 1
+    x[hz + k0, hy + j0, hx + i0] = 1.0
+
+    def lin(i, j, k):
+        return (k * ny + j) * nx + i
+
+    pts = {lin(i0 - 1, j0, k0): 3.0, lin(i0, j0 - 2, k0): 5.0, lin(i0, j0, k0 + 1): 7.0,
+           lin(i0 + 2, j0 + 1, k0 - 1): 11.0, lin(i0, j0, k0): 0.0, lin(i0 + 1, j0, k0): 0.0}
+    idx = np.array(list(pts), np.int64)
+    got = oracle.stencil_general_points(x, fp, w, (hx, hy, hz), idx)
+    np.testing.assert_array_equal(got, np.array(list(pts.values())))
+    got_div = oracle.stencil_general_points(x, fp, w, (hx, hy, hz), idx, divisor=2.0)
+    np.testing.assert_array_equal(got_div, np.array(list(pts.values())) / 2.0)

@@ -57,10 +57,18 @@ def test_noalloc_matches_workspace_version_twice():
 
 
 def test_noalloc_rejects_interiors_beyond_its_scratch():
-    _need_gpu()
+    """ny*nz = 2048*1024 rows > 16384 records x 64 rows: rejected on the host.
+    The field and the output are real device buffers of the declared sizes
+    (76 MB), so that even a launch past a broken check would stay in bounds;
+    the output must come back untouched."""
+    torch = _need_gpu()
     lib = gbs.load()
-    fake = ctypes.c_void_p(1 << 20)
-    # ny*nz = 2048*1024 rows > 16384 records x 64 rows: rejected on the host, nothing launched
-    rc = lib.gbs_field_norms_noalloc(fake, None, 1, 2048, 1024, 4, fake, None)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nx, ny, nz, halo = 1, 2048, 1024, 4
+    x = torch.zeros((nz + 2 * halo, ny + 2 * halo, nx + 2 * halo), dtype=torch.float32, device=dev)
+    out = torch.full((8,), float("nan"), dtype=torch.float64, device=dev)
+    rc = _noalloc(lib, x, None, out, halo)
     assert rc == gbs.GBS_EINVAL
     assert b"rows" in lib.gbs_last_error()
+    torch.cuda.synchronize()
+    assert torch.isnan(out).all()
