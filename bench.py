@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
                     help="wave-field storage of the main timed path (arithmetic is FP32 in all)")
-    ap.add_argument("--forms", default="single,storage,radius,errors,precision,absorb,batched,adjoint,suite",
+    ap.add_argument("--forms", default="single,storage,radius,errors,precision,absorb,batched,adjoint,suite,tblock",
                     help="comma list of extra forms to measure after the main line, or 'none'")
     ap.add_argument("--no-forms", action="store_true", help="same as --forms none")
     ap.add_argument("--adj-n", type=int, default=256, help="adjoint form: interior side")
@@ -867,6 +867,72 @@ def single_step_form(prob, args, stream, hbm, vel, si, sa):
             "traffic": traffic_per_launch(prob.nx, "single"), "alg_bytes_per_point": BYTES_PER_POINT}
 
 
+def tblock_form(args, stream, hbm, sizes=(256, 384, 512), nsteps=96):
+    """Temporal blocking against the number of steps fused per launch (1, 2,
+    3) on the layered workload at several sizes: whole-call throughput, the
+    fused kernel's time per launch, and DRAM bytes per update at the
+    algorithmic minimum (16, 10, 8).  Nothing is recomputed across tiles; a
+    z-chunked shape adds (steps-1) R planes either side of a chunk to the
+    earlier stages (reported as the fraction of extra plane updates)."""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    import workloads as W
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {"leapfrog_steps_per_call": nsteps,
+           "alg_bytes_per_update": {"1": 16, "2": 10, "3": 8}}
+    for n in sizes:
+        halo = 4
+        vel = W.layered_velocity_torch(n, n, n, halo, W.SEED_BASE + 2, dev)
+        dt = W.dt_for_cfl(0.4, 10.0, float(vel.max()))
+        src = torch.tensor([W.linear_index(n // 2, n // 2, 20, n, n)], dtype=torch.int64, device=dev)
+        amp = torch.from_numpy(W.ricker(nsteps, dt, 15.0).astype(np.float32).reshape(nsteps, 1)).to(dev)
+        pts = n * n * n
+        row = {}
+        for tb in (1, 2, 3):
+            if tb > 1:
+                ok, ty, ctas = gbs.tbn_supported(n, n, n, halo, tb)
+                if not ok:
+                    row[str(tb)] = {"fused": False}
+                    continue
+                work = gbs.tbn_workspace(vel, halo, tb)
+            a, b = torch.zeros_like(vel), torch.zeros_like(vel)
+            st = {"a": a, "b": b}
+
+            def run():
+                if tb == 1:
+                    st["a"], st["b"] = gbs.wave_propagate(st["a"], st["b"], vel, dt, 10.0, halo, nsteps, src_idx=src,
+                                                          src_amp=amp)
+                else:
+                    st["a"], st["b"] = gbs.wave_propagate_tbn(st["a"], st["b"], vel, dt, 10.0, halo, nsteps, tb,
+                                                              src_idx=src, src_amp=amp, work=work)
+            for _ in range(2):
+                run()
+            gbs.device_status()
+            ms, kms, kl = time_calls(run, 4, stream)
+            gbs.device_status()
+            alg = {1: 16, 2: 20, 3: 24}[tb]
+            ach = alg * pts / (kms * 1e-3) / 1e9 if kms else None
+            r = {"value": pts * nsteps / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_call": ms,
+                 "kernel_us_per_launch": kms * 1e3 if kms else None, "launches_per_call": kl / 4 if kl else None,
+                 "kernel_us_per_step": kms * 1e3 / tb if kms else None,
+                 "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                              "frac": ach / hbm if ach else None, "alg_bytes_per_point_per_launch": alg}}
+            if tb > 1:
+                nt = ((n + 63) // 64) * ((n + ty - 1) // ty)
+                chunks = ctas // nt
+                zc = -(-n // chunks)
+                extra = sum(min(n, zc * (c + 1) + (tb - 1 - s) * 4) - max(0, zc * c - (tb - 1 - s) * 4)
+                            for c in range(chunks) for s in range(tb)) / (tb * n) - 1.0
+                r.update({"fused": True, "tile_y": ty, "ctas": ctas, "zchunks": chunks,
+                          "extra_plane_updates": extra})
+            row[str(tb)] = r
+            del a, b, st
+        out[f"{n}^3"] = row
+        del vel
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -1022,6 +1088,8 @@ def run_ours(args):
             forms["absorbing_layer"] = absorb_form(prob, args, stream, hbm)
         if "suite" in wanted:
             forms["suite"] = suite_form(args, stream, hbm)
+        if "tblock" in wanted:
+            forms["temporal_blocking"] = tblock_form(args, stream, hbm)
         if "adjoint" in wanted:
             forms["adjoint"] = adjoint_form(args, stream, hbm, n=args.adj_n, nsteps=args.adj_steps,
                                             nshots=args.adj_shots)

@@ -228,6 +228,34 @@ gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float *vel, floa
  * tile_y and ctas may be NULL.
  */
 int gbs_tb_supported(int64_t nx, int64_t ny, int64_t nz, int halo, int *tile_y, int *ctas);
+
+/*
+ * Algorithm 1 with temporal blocking of time_block = 2 or 3 steps per launch
+ * (the paper's 3.5D blocking, Sec. 3; Table 2 lists the number of time steps
+ * blocked as a tuning choice).  time_block = 2 is gbs_wave_propagate_tb.
+ * With 3, every CTA streams its tile three times in one launch: stage s
+ * computes u^{t+1+s} from u^{t+s} once the tile and its four neighbours have
+ * stored the planes it needs, so three steps move 24 bytes per point
+ * through DRAM instead of 48, on 64 x 16 tiles (three pipelines share the
+ * SM's shared memory).  Nothing is recomputed, except that z-chunked grids
+ * compute the R (stage 1) or 2R (stage 0) planes either side of a chunk in
+ * both neighbouring chunks.  Launches rotate over (u_prev, u) and time_block
+ * workspace fields; the two newest fields are copied back at the end; steps
+ * left over run as a fused pair and/or a single step.  Fields, sources,
+ * receivers, options and the parity rule are those of gbs_wave_propagate_tb.
+ *   work          DEVICE scratch of at least gbs_tbn_workspace_bytes(...,
+ *                 time_block) bytes (time_block fields and the counters),
+ *                 16-byte aligned, not overlapping the fields.
+ * gbs_tbn_supported: 1 when launches of time_block steps run fused on this
+ * grid on the current device (tile height and CTA count returned), else 0.
+ * Errors: as gbs_wave_propagate_tb; GBS_EINVAL for time_block not 2 or 3.
+ */
+size_t gbs_tbn_workspace_bytes(int64_t nx, int64_t ny, int64_t nz, int halo, int time_block);
+int gbs_tbn_supported(int64_t nx, int64_t ny, int64_t nz, int halo, int time_block, int *tile_y, int *ctas);
+gbs_status gbs_wave_propagate_tbn(float *u_prev, float *u, const float *vel, float dt, float h,
+                                  int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                                  int64_t t0, const gbs_src *src, const gbs_rec *rec, int time_block, void *work,
+                                  size_t work_bytes, const gbs_opts *opts, void *stream);
 /*
  * Algorithm 1 on HOST fields: the same steps as gbs_wave_propagate
  * (time_block = 0) or gbs_wave_propagate_tb (time_block = 2), with every

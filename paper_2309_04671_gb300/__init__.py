@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4
 # Entry points declared in include/gbstencil.h (checked by the tests).
 EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
            "gbs_wave_propagate_lp", "gbs_tb_workspace_bytes", "gbs_wave_propagate_tb", "gbs_tb_supported",
+           "gbs_tbn_workspace_bytes", "gbs_wave_propagate_tbn", "gbs_tbn_supported",
            "gbs_selftest_tb_timeout", "gbs_host_workspace_bytes", "gbs_wave_propagate_host", "gbs_check_cfl",
            "gbs_pipeline_create", "gbs_pipeline_submit", "gbs_pipeline_wait", "gbs_pipeline_workspace_bytes",
            "gbs_pipeline_destroy",
@@ -112,6 +113,14 @@ def load() -> ctypes.CDLL:
         lib.gbs_wave_propagate_tb.restype = c_int
         lib.gbs_tb_supported.argtypes = [i64, i64, i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
         lib.gbs_tb_supported.restype = c_int
+        lib.gbs_tbn_workspace_bytes.argtypes = [i64, i64, i64, c_int, c_int]
+        lib.gbs_tbn_workspace_bytes.restype = ctypes.c_size_t
+        lib.gbs_wave_propagate_tbn.argtypes = [vp, vp, vp, c_float, c_float, i64, i64, i64, c_int, i64, i64,
+                                               ctypes.POINTER(_Src), ctypes.POINTER(_Rec), c_int, vp,
+                                               ctypes.c_size_t, ctypes.POINTER(_Opts), vp]
+        lib.gbs_wave_propagate_tbn.restype = c_int
+        lib.gbs_tbn_supported.argtypes = [i64, i64, i64, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+        lib.gbs_tbn_supported.restype = c_int
         lib.gbs_host_workspace_bytes.argtypes = [i64, i64, i64, c_int, i64, i64, i64, i64, c_int]
         lib.gbs_host_workspace_bytes.restype = ctypes.c_size_t
         lib.gbs_wave_propagate_host.argtypes = [vp, vp, vp, c_float, c_float, i64, i64, i64, c_int, i64, i64,
@@ -523,6 +532,50 @@ def wave_propagate_tb(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, 
     _check(load().gbs_wave_propagate_tb(p[0], p[1], p[2], float(dt), float(h), nx, ny, nz, halo, int(nsteps),
                                         int(t0), _ptr(src), _ptr(rec), work.data_ptr(),
                                         work.numel() * work.element_size(), ctypes.byref(opts), _stream(stream)))
+    return (u, u_prev) if nsteps % 2 else (u_prev, u)
+
+
+def tbn_workspace_bytes(nx: int, ny: int, nz: int, halo: int, time_block: int) -> int:
+    """Bytes of device scratch gbs_wave_propagate_tbn needs for time_block (2 or 3) steps per launch."""
+    return int(load().gbs_tbn_workspace_bytes(int(nx), int(ny), int(nz), int(halo), int(time_block)))
+
+
+def tbn_workspace(u: torch.Tensor, halo: int, time_block: int) -> torch.Tensor:
+    """A device byte tensor large enough for wave_propagate_tbn on fields shaped like u."""
+    nx, ny, nz = _dims(u, halo)
+    return torch.empty(tbn_workspace_bytes(nx, ny, nz, halo, time_block), dtype=torch.uint8, device=u.device)
+
+
+def tbn_supported(nx: int, ny: int, nz: int, halo: int, time_block: int) -> tuple[bool, int, int]:
+    """(fused, tile_y, ctas): whether launches of time_block steps run fused on this grid on the current device."""
+    ty, ctas = ctypes.c_int(0), ctypes.c_int(0)
+    ok = load().gbs_tbn_supported(int(nx), int(ny), int(nz), int(halo), int(time_block), ctypes.byref(ty),
+                                  ctypes.byref(ctas))
+    return bool(ok), int(ty.value), int(ctas.value)
+
+
+def wave_propagate_tbn(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, dt: float, h: float,
+                       halo: int, nsteps: int, time_block: int, *, t0: int = 0, src_idx=None, src_amp=None,
+                       rec_idx=None, rec_trace=None, work: Optional[torch.Tensor] = None, kernel: int = 0,
+                       use_graph: bool = False, absorb=None, stream=None):
+    """Algorithm 1 with temporal blocking of time_block (2 or 3) steps per
+    launch (device tensors): the fields of wave_propagate to FP32 rounding.
+    Returns (prev, cur) as wave_propagate.  ``work`` is device scratch of at
+    least tbn_workspace_bytes(..., time_block) bytes (allocated per call if None)."""
+    p = [_field(t, n) for t, n in ((u_prev, "u_prev"), (u, "u"), (vel, "vel"))]
+    _same_shape(u, u_prev, vel)
+    nx, ny, nz = _dims(u, halo)
+    if work is None:
+        work = tbn_workspace(u, halo, time_block)
+    if not (work.is_cuda and work.is_contiguous()):
+        raise ValueError("work must be a contiguous device tensor")
+    src = _make_src(src_idx, src_amp)
+    rec = _make_rec(rec_idx, rec_trace)
+    ab = (absorb[0], absorb[1], absorb[2] if len(absorb) > 2 else False) if absorb else None
+    opts = _opts(kernel, 0, 0, use_graph, ab)
+    _check(load().gbs_wave_propagate_tbn(p[0], p[1], p[2], float(dt), float(h), nx, ny, nz, halo, int(nsteps),
+                                         int(t0), _ptr(src), _ptr(rec), int(time_block), work.data_ptr(),
+                                         work.numel() * work.element_size(), ctypes.byref(opts), _stream(stream)))
     return (u, u_prev) if nsteps % 2 else (u_prev, u)
 
 

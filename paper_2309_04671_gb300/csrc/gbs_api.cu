@@ -608,103 +608,69 @@ extern "C" gbs_status gbs_wave_propagate(float *u_prev, float *u, const float *v
 
 namespace gbs {
 namespace {
-// Workspace of the time-blocked propagation: two fields in the caller's
-// layout (u^{t+1}, u^{t+2} of every other pair) and the block counters.
+// Workspace of the time-blocked propagation with `steps` steps per launch:
+// `steps` fields in the caller's layout (the outputs of a launch) and the
+// block counters.
 struct TbLayout {
-    size_t off_w1, off_w2, off_words, total;
+    size_t off_w1, field_stride, off_words, total;
 };
-TbLayout tb_layout(const Grid &g)
+TbLayout tb_layout(const Grid &g, int steps)
 {
     const size_t n = (size_t)field_elems(g) * 4;
     TbLayout L;
     L.off_w1 = 0;
-    L.off_w2 = round256(n);
-    L.off_words = L.off_w2 + round256(n);
+    L.field_stride = round256(n);
+    L.off_words = (size_t)steps * L.field_stride;
     L.total = L.off_words + (size_t)kWfMaxWords * 4;
     return L;
 }
-}  // namespace
-}  // namespace gbs
 
-extern "C" size_t gbs_tb_workspace_bytes(int64_t nx, int64_t ny, int64_t nz, int halo)
-{
-    if (check_dims(nx, ny, nz, halo) != GBS_OK)
-        return 0;
-    return tb_layout(dense_grid(nx, ny, nz, halo)).total;
-}
+bool tb_steps_ok(int time_block) { return time_block == 2 || time_block == 3; }
 
-extern "C" int gbs_tb_supported(int64_t nx, int64_t ny, int64_t nz, int halo, int *tile_y, int *ctas)
+// gbs_wave_propagate_tbn after argument checks: `steps` steps per launch
+// while at least `steps` remain, then a pair (three-step launches) or a
+// single step for the rest.
+gbs_status propagate_tb(int steps, float *u_prev, float *u, const float *vel, float dt, float h, const Grid &g,
+                        int64_t nsteps, int64_t t0, const gbs_src *src, const gbs_rec *rec, void *work,
+                        const gbs_opts *opts, cudaStream_t st)
 {
-    t_err[0] = 0;
-    if (check_dims(nx, ny, nz, halo) != GBS_OK || halo < 4 || nx == 0 || ny == 0 || nz == 0)
-        return 0;
-    const Grid g = dense_grid(nx, ny, nz, halo);
-    WfShape sh;
-    if (!tma_shape_ok(g) || !wf_shape(g, &sh))
-        return 0;
-    if (tile_y)
-        *tile_y = sh.tile_y;
-    if (ctas)
-        *ctas = sh.ctas;
-    return 1;
-}
-
-extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float *vel, float dt, float h,
-                                            int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
-                                            int64_t t0, const gbs_src *src, const gbs_rec *rec, void *work,
-                                            size_t work_bytes, const gbs_opts *opts, void *stream)
-{
-    const TraceRange trace_range("gbs_wave_propagate_tb");
-    t_err[0] = 0;
-    gbs_status s = check_dims(nx, ny, nz, halo);
-    if (s != GBS_OK)
-        return s;
-    if (nsteps < 0 || t0 < 0)
-        return fail(GBS_EINVAL, "nsteps and t0 must be >= 0");
-    if ((s = check_src_rec(src, rec)) != GBS_OK)
-        return s;
-    if (nx == 0 || ny == 0 || nz == 0 || nsteps == 0)
-        return GBS_OK;
-    const Grid g = dense_grid(nx, ny, nz, halo);
-    if (u_prev == u)
-        return fail(GBS_EINVAL, "u_prev and u are the same buffer");
-    if ((s = check_wave_fields(g, u_prev, u, u_prev, vel, dt, h)) != GBS_OK)
-        return s;
-    if (overlap(u_prev, u, field_elems(g)))
-        return fail(GBS_EINVAL, "u_prev and u overlap");
-    const TbLayout L = tb_layout(g);
-    if (!work || work_bytes < L.total || !aligned16(work))
-        return fail(GBS_EINVAL, "workspace needs %zu bytes, 16-byte aligned (gbs_tb_workspace_bytes)", L.total);
-    const char *wb = static_cast<const char *>(work);
-    const int64_t fe = field_elems(g);
-    for (const float *f : {static_cast<const float *>(u_prev), static_cast<const float *>(u), vel}) {
-        const char *fb = reinterpret_cast<const char *>(f);
-        if (fb < wb + L.total && wb < fb + fe * 4)
-            return fail(GBS_EINVAL, "workspace overlaps a field");
-    }
+    const TbLayout L = tb_layout(g, steps);
     WfShape sh{};
     const bool fused = tma_shape_ok(g) && aligned16(u_prev) && aligned16(u) && aligned16(vel) &&
-                       (!src || src->n <= kMaxFusedSrc) && !(opts && opts->kernel == 2) && wf_shape(g, &sh);
-    // pairs alternate between (u_prev, u) and the workspace fields; after an
-    // odd number the two newest fields are copied back; an odd last step runs single
-    const int64_t npairs = fused ? nsteps / 2 : 0;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (npairs > 0) {
-        float *w1 = reinterpret_cast<float *>(static_cast<char *>(work) + L.off_w1);
-        float *w2 = reinterpret_cast<float *>(static_cast<char *>(work) + L.off_w2);
+                       (!src || src->n <= kMaxFusedSrc) && !(opts && opts->kernel == 2) && wf_shape(g, steps, &sh);
+    int64_t nl = fused ? nsteps / steps : 0;   // fused launches
+    // an odd number of launches of an odd step count would leave the newest
+    // field in u where the parity rule wants it in u_prev: the last launch's
+    // steps then run as pairs and a single step, which follow the rule
+    if ((steps & 1) && (nl & 1))
+        --nl;
+    gbs_status s = GBS_OK;
+    if (nl > 0) {
+        // buffer slots: 0 = u_prev, 1 = u, 2.. = the workspace fields.  Launch
+        // i reads slots (a, a+1), a = i*steps mod (steps+2), and writes the
+        // `steps` slots after them; the newest two are copied back at the end
+        const int nslots = steps + 2;
+        float *slot[kWfMaxSteps + 2];
+        slot[0] = u_prev;
+        slot[1] = u;
+        for (int k = 0; k < steps; ++k)
+            slot[2 + k] = reinterpret_cast<float *>(static_cast<char *>(work) + L.off_w1 + k * L.field_stride);
         unsigned *words = reinterpret_cast<unsigned *>(static_cast<char *>(work) + L.off_words);
         const int ty = sh.tile_y;
-        // parity 0 reads (u_prev, u) and writes (w1, w2); parity 1 the reverse
-        float *lv[2][4] = {{u_prev, u, w1, w2}, {w1, w2, u_prev, u}};
-        WfMaps maps[2];
-        for (int q = 0; q < 2; ++q) {
-            float *pr = lv[q][0], *cu = lv[q][1], *c1 = lv[q][2];
-            if ((s = make_map(&maps[q].ua, cu, g, 64 + 8, ty + 8)) != GBS_OK ||
-                (s = make_map(&maps[q].pa, pr, g, 64, ty)) != GBS_OK ||
-                (s = make_map(&maps[q].ub, c1, g, 64 + 8, ty + 8)) != GBS_OK ||
-                (s = make_map(&maps[q].pb, cu, g, 64, ty)) != GBS_OK ||
-                (s = make_map(&maps[q].vel, vel, g, 64, ty)) != GBS_OK)
+        WfMaps maps[kWfMaxSteps + 2];
+        for (int a = 0; a < nslots; ++a) {
+            float *pr = slot[a], *cu = slot[(a + 1) % nslots];
+            WfMaps &m = maps[a];
+            if ((s = make_map(&m.ua, cu, g, 64 + 8, ty + 8)) != GBS_OK || (s = make_map(&m.pa, pr, g, 64, ty)) != GBS_OK ||
+                (s = make_map(&m.vel, vel, g, 64, ty)) != GBS_OK)
                 return s;
+            for (int k = 0; k + 1 < kWfMaxSteps; ++k) {
+                // stage k+1 reads u^{t+1+k} (output slot a+2+k) and u^{t+k} (slot a+1+k)
+                const int ko = k + 1 < steps ? k : 0;
+                if ((s = make_map(&m.ub[k], slot[(a + 2 + ko) % nslots], g, 64 + 8, ty + 8)) != GBS_OK ||
+                    (s = make_map(&m.pb[k], slot[(a + 1 + ko) % nslots], g, 64, ty)) != GBS_OK)
+                    return s;
+            }
         }
         WfParams p;
         memset(&p, 0, sizeof(p));
@@ -718,41 +684,50 @@ extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float
             p.src_nt = src->nt;
             p.nsrc = (int)src->n;
         }
-        p.inx = nx;
-        p.iny = ny;
+        p.inx = g.nx;
+        p.iny = g.ny;
         p.words = words;
         if ((s = absorb_plan(opts, dt, 1, &p.ab)) != GBS_OK)
             return s;
-        cudaError_t e = wf_prepare(ty);
+        cudaError_t e = wf_prepare(steps, ty);
         if (e != cudaSuccess)
             return cuda_fail(e, "kernel attributes");
         auto enqueue = [&]() -> gbs_status {
-            cudaError_t r = cudaMemsetAsync(words, 0, (size_t)sh.ctas * sh.nblk * 4, st);
+            cudaError_t r = cudaMemsetAsync(words, 0, (size_t)(steps - 1) * sh.ctas * sh.nblk * 4, st);
             if (r != cudaSuccess)
                 return cuda_fail(r, "block counters");
-            if ((r = launch_zero_shell(w1, (int64_t)((L.off_w2 - L.off_w1) / 4), 2, g, st)) != cudaSuccess)
+            if ((r = launch_zero_shell(slot[2], (int64_t)(L.field_stride / 4), steps, g, st)) != cudaSuccess)
                 return cuda_fail(r, "workspace halo");
-            for (int64_t i = 0; i < npairs; ++i) {
-                const int q = (int)(i & 1);
+            for (int64_t i = 0; i < nl; ++i) {
+                const int a = (int)((i * steps) % nslots);
                 WfParams pi = p;
-                pi.out[0] = lv[q][2];
-                pi.out[1] = lv[q][3];
+                for (int k = 0; k < steps; ++k)
+                    pi.out[k] = slot[(a + 2 + k) % nslots];
                 pi.epoch = (unsigned)(i + 1);
-                pi.t = t0 + 2 * i;
+                pi.t = t0 + steps * i;
                 cudaEvent_t e0 = prof_begin(st);
-                r = launch_wf(sh, maps[q], pi, st);
+                r = launch_wf(sh, maps[a], pi, st);
                 prof_end(e0, st);
                 if (r != cudaSuccess)
                     return cuda_fail(r, "time-blocked launch");
-                if ((r = launch_record(g, lv[q][2], rec, pi.t, st)) != cudaSuccess ||
-                    (r = launch_record(g, lv[q][3], rec, pi.t + 1, st)) != cudaSuccess)
-                    return cuda_fail(r, "receiver launch");
+                for (int k = 0; k < steps; ++k)
+                    if ((r = launch_record(g, pi.out[k], rec, pi.t + k, st)) != cudaSuccess)
+                        return cuda_fail(r, "receiver launch");
             }
-            if (npairs & 1) {
+            const int a = (int)((nl * steps) % nslots);
+            if (a != 0) {
                 const size_t fbytes = (size_t)field_elems(g) * 4;
-                if ((r = cudaMemcpyAsync(u_prev, w1, fbytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
-                    (r = cudaMemcpyAsync(u, w2, fbytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
-                    return cuda_fail(r, "copy of the newest fields");
+                const int older = a, newer = (a + 1) % nslots;
+                // copy the newest two back to (u_prev, u) without overwriting either first
+                if (newer == 0) {
+                    if ((r = cudaMemcpyAsync(u, slot[newer], fbytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+                        (r = cudaMemcpyAsync(u_prev, slot[older], fbytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+                        return cuda_fail(r, "copy of the newest fields");
+                } else {
+                    if ((r = cudaMemcpyAsync(u_prev, slot[older], fbytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+                        (r = cudaMemcpyAsync(u, slot[newer], fbytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+                        return cuda_fail(r, "copy of the newest fields");
+                }
             }
             return GBS_OK;
         };
@@ -760,10 +735,97 @@ extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float
         if ((s = graph ? run_captured(st, enqueue) : enqueue()) != GBS_OK)
             return s;
     }
-    const int64_t rest = nsteps - 2 * npairs;
+    const int64_t done = steps * nl;
+    const int64_t rest = nsteps - done;
     if (rest == 0)
         return GBS_OK;
-    return gbs_wave_propagate(u_prev, u, vel, dt, h, nx, ny, nz, halo, rest, t0 + 2 * npairs, src, rec, opts, stream);
+    if (fused && rest >= 2)
+        return propagate_tb(2, u_prev, u, vel, dt, h, g, rest, t0 + done, src, rec, work, opts, st);
+    return gbs_wave_propagate(u_prev, u, vel, dt, h, g.nx, g.ny, g.nz, g.halo, rest, t0 + done, src, rec, opts, st);
+}
+}  // namespace
+}  // namespace gbs
+
+extern "C" size_t gbs_tbn_workspace_bytes(int64_t nx, int64_t ny, int64_t nz, int halo, int time_block)
+{
+    if (check_dims(nx, ny, nz, halo) != GBS_OK || !tb_steps_ok(time_block))
+        return 0;
+    return tb_layout(dense_grid(nx, ny, nz, halo), time_block).total;
+}
+
+extern "C" size_t gbs_tb_workspace_bytes(int64_t nx, int64_t ny, int64_t nz, int halo)
+{
+    return gbs_tbn_workspace_bytes(nx, ny, nz, halo, 2);
+}
+
+extern "C" int gbs_tbn_supported(int64_t nx, int64_t ny, int64_t nz, int halo, int time_block, int *tile_y, int *ctas)
+{
+    t_err[0] = 0;
+    if (check_dims(nx, ny, nz, halo) != GBS_OK || halo < 4 || nx == 0 || ny == 0 || nz == 0 ||
+        !tb_steps_ok(time_block))
+        return 0;
+    const Grid g = dense_grid(nx, ny, nz, halo);
+    WfShape sh;
+    if (!tma_shape_ok(g) || !wf_shape(g, time_block, &sh))
+        return 0;
+    if (tile_y)
+        *tile_y = sh.tile_y;
+    if (ctas)
+        *ctas = sh.ctas;
+    return 1;
+}
+
+extern "C" int gbs_tb_supported(int64_t nx, int64_t ny, int64_t nz, int halo, int *tile_y, int *ctas)
+{
+    return gbs_tbn_supported(nx, ny, nz, halo, 2, tile_y, ctas);
+}
+
+extern "C" gbs_status gbs_wave_propagate_tbn(float *u_prev, float *u, const float *vel, float dt, float h,
+                                             int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                                             int64_t t0, const gbs_src *src, const gbs_rec *rec, int time_block,
+                                             void *work, size_t work_bytes, const gbs_opts *opts, void *stream)
+{
+    const TraceRange trace_range("gbs_wave_propagate_tbn");
+    t_err[0] = 0;
+    gbs_status s = check_dims(nx, ny, nz, halo);
+    if (s != GBS_OK)
+        return s;
+    if (!tb_steps_ok(time_block))
+        return fail(GBS_EINVAL, "time_block must be 2 or 3 (got %d)", time_block);
+    if (nsteps < 0 || t0 < 0)
+        return fail(GBS_EINVAL, "nsteps and t0 must be >= 0");
+    if ((s = check_src_rec(src, rec)) != GBS_OK)
+        return s;
+    if (nx == 0 || ny == 0 || nz == 0 || nsteps == 0)
+        return GBS_OK;
+    const Grid g = dense_grid(nx, ny, nz, halo);
+    if (u_prev == u)
+        return fail(GBS_EINVAL, "u_prev and u are the same buffer");
+    if ((s = check_wave_fields(g, u_prev, u, u_prev, vel, dt, h)) != GBS_OK)
+        return s;
+    if (overlap(u_prev, u, field_elems(g)))
+        return fail(GBS_EINVAL, "u_prev and u overlap");
+    const TbLayout L = tb_layout(g, time_block);
+    if (!work || work_bytes < L.total || !aligned16(work))
+        return fail(GBS_EINVAL, "workspace needs %zu bytes, 16-byte aligned (gbs_tbn_workspace_bytes)", L.total);
+    const char *wb = static_cast<const char *>(work);
+    const int64_t fe = field_elems(g);
+    for (const float *f : {static_cast<const float *>(u_prev), static_cast<const float *>(u), vel}) {
+        const char *fb = reinterpret_cast<const char *>(f);
+        if (fb < wb + L.total && wb < fb + fe * 4)
+            return fail(GBS_EINVAL, "workspace overlaps a field");
+    }
+    return propagate_tb(time_block, u_prev, u, vel, dt, h, g, nsteps, t0, src, rec, work, opts,
+                        static_cast<cudaStream_t>(stream));
+}
+
+extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float *vel, float dt, float h,
+                                            int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                                            int64_t t0, const gbs_src *src, const gbs_rec *rec, void *work,
+                                            size_t work_bytes, const gbs_opts *opts, void *stream)
+{
+    return gbs_wave_propagate_tbn(u_prev, u, vel, dt, h, nx, ny, nz, halo, nsteps, t0, src, rec, 2, work, work_bytes,
+                                  opts, stream);
 }
 
 namespace gbs {
@@ -794,7 +856,7 @@ HostLayout host_layout(const Grid &g, int64_t nsrc, int64_t snt, int64_t nrec, i
     off += round256((size_t)std::max<int64_t>(nrec, 0) * (size_t)std::max<int64_t>(rnt, 0) * 4);
     L.off_tb = off;
     if (time_block == 2)
-        off += tb_layout(g).total;
+        off += tb_layout(g, 2).total;
     L.total = off;
     return L;
 }
@@ -1157,9 +1219,9 @@ extern "C" gbs_status gbs_selftest_tb_timeout(void *stream)
     const int halo = 4;
     const Grid g = dense_grid(n, n, n, halo);
     WfShape sh{};
-    if (!wf_shape(g, &sh))
+    if (!wf_shape(g, 2, &sh))
         return fail(GBS_EUNSUPPORTED, "the fused-pair kernel cannot run on this device");
-    const TbLayout L = tb_layout(g);
+    const TbLayout L = tb_layout(g, 2);
     const size_t fb = (size_t)field_elems(g) * 4;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // a status recorded by an earlier launch belongs to its caller: leave it
@@ -1176,18 +1238,22 @@ extern "C" gbs_status gbs_selftest_tb_timeout(void *stream)
     float *u = reinterpret_cast<float *>(mem + round256(fb));
     float *vel = reinterpret_cast<float *>(mem + 2 * round256(fb));
     char *work = mem + 3 * round256(fb);
+    float *w1 = reinterpret_cast<float *>(work + L.off_w1);
+    float *w2 = reinterpret_cast<float *>(work + L.off_w1 + L.field_stride);
     unsigned *words = reinterpret_cast<unsigned *>(work + L.off_words);
     gbs_status s = GBS_OK;
     WfMaps m;
     if ((s = make_map(&m.ua, u, g, 64 + 8, sh.tile_y + 8)) == GBS_OK &&
         (s = make_map(&m.pa, up, g, 64, sh.tile_y)) == GBS_OK &&
-        (s = make_map(&m.ub, work + L.off_w1, g, 64 + 8, sh.tile_y + 8)) == GBS_OK &&
-        (s = make_map(&m.pb, u, g, 64, sh.tile_y)) == GBS_OK && (s = make_map(&m.vel, vel, g, 64, sh.tile_y)) == GBS_OK) {
+        (s = make_map(&m.ub[0], w1, g, 64 + 8, sh.tile_y + 8)) == GBS_OK &&
+        (s = make_map(&m.pb[0], u, g, 64, sh.tile_y)) == GBS_OK &&
+        (s = make_map(&m.ub[1], w1, g, 64 + 8, sh.tile_y + 8)) == GBS_OK &&
+        (s = make_map(&m.pb[1], u, g, 64, sh.tile_y)) == GBS_OK && (s = make_map(&m.vel, vel, g, 64, sh.tile_y)) == GBS_OK) {
         WfParams p;
         memset(&p, 0, sizeof(p));
         p.g = g;
-        p.out[0] = reinterpret_cast<float *>(work + L.off_w1);
-        p.out[1] = reinterpret_cast<float *>(work + L.off_w2);
+        p.out[0] = w1;
+        p.out[1] = w2;
         p.cf = wave_coeffs();
         p.s = 1e-4f;
         p.dt = 1e-3f;
@@ -1199,7 +1265,7 @@ extern "C" gbs_status gbs_selftest_tb_timeout(void *stream)
         p.epoch = 2;
         p.t = 0;
         if ((e = cudaMemsetAsync(mem, 0, 3 * round256(fb) + L.total, st)) != cudaSuccess ||
-            (e = wf_prepare(sh.tile_y)) != cudaSuccess || (e = launch_wf(sh, m, p, st)) != cudaSuccess)
+            (e = wf_prepare(2, sh.tile_y)) != cudaSuccess || (e = launch_wf(sh, m, p, st)) != cudaSuccess)
             s = cuda_fail(e, "self-test launch");
     }
     const unsigned v = wf_status_take(st);

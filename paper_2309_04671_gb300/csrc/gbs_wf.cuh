@@ -1,4 +1,4 @@
-// Two leapfrog steps in one launch (2-step temporal blocking without
+// Several leapfrog steps in one launch (temporal blocking without
 // recomputation): parameters and launcher of k_wf.cu.
 #pragma once
 
@@ -6,11 +6,14 @@
 
 namespace gbs {
 
-// Arguments of one fused pair of steps on a dense FP32 field: reads u^t,
-// u^{t-1} and vel, writes u^{t+1} to out[0] and u^{t+2} to out[1].
+// Most steps fused in one launch.
+constexpr int kWfMaxSteps = 3;
+
+// Arguments of one launch of `steps` fused steps on a dense FP32 field:
+// reads u^t, u^{t-1} and vel, writes u^{t+1+s} to out[s], s < steps.
 struct WfParams {
     Grid g;
-    float *out[2];
+    float *out[kWfMaxSteps];
     Coeffs cf;                   // the wave weights (axis 0 is used, as in the single step)
     float s;                     // dt / h
     float dt;
@@ -21,42 +24,47 @@ struct WfParams {
     int64_t inx, iny;            // interior sizes the source indices refer to
     int tiles_x, tiles_y;        // 64 x tile_y tiles of the xy plane
     int zchunk, nchunks;         // z range of a CTA
-    unsigned *words;             // block counters: [chunk][tile][nblk], zero before the first launch
-    int nblk;                    // blocks of kWfBlock stage-A planes per CTA
+    unsigned *words;             // block counters: [stage][chunk][tile][nblk], zero before the first launch
+    int nblk;                    // blocks of kWfBlock planes per stage and CTA
     unsigned epoch;              // launches on the same counters so far, this one included (mod 2^32)
-    int64_t t;                   // time level of u (the launch writes u^{t+1} and u^{t+2})
+    int64_t t;                   // time level of u (the launch writes u^{t+1} .. u^{t+steps})
     Absorb ab;                   // absorbing layer (width 0 = none)
 };
 
-// Tensor maps of one launch: stage A reads u^t (box 72 x (TY+8)) and u^{t-1}
-// (64 x TY); stage B reads u^{t+1} (72 x (TY+8)) and u^t (64 x TY); both read
-// vel (64 x TY).
+// Tensor maps of one launch.  Stage 0 reads u^t (box 72 x (TY+8)) and
+// u^{t-1} (64 x TY); stage s >= 1 reads u^{t+s} = out[s-1] (ub[s-1], box
+// 72 x (TY+8)) and u^{t+s-1} (pb[s-1], 64 x TY); every stage reads vel
+// (64 x TY).
 struct WfMaps {
-    CUtensorMap ua, pa, ub, pb, vel;
+    CUtensorMap ua, pa;
+    CUtensorMap ub[kWfMaxSteps - 1], pb[kWfMaxSteps - 1];
+    CUtensorMap vel;
 };
 
 // Launch shape: every CTA of the grid must be resident at once.
 struct WfShape {
+    int steps;      // fused steps per launch (2 or 3)
     int tile_y;
     int tiles_x, tiles_y;
     int zchunk, nchunks;
     int ctas;
-    int nblk;       // counters per CTA
+    int nblk;       // counters per stage and CTA
 };
 
-// Stage A publishes its output in blocks of this many planes: a block
+// A stage publishes its output in blocks of this many planes: a block
 // counter of a tile rises by one for each tile (itself and its x, y
 // neighbours) that has stored the block, so it reaches (those tiles) x
-// (launches so far), modulo 2^32, when stage B of the tile may read the block.
+// (launches so far), modulo 2^32, when the next stage of the tile may read
+// the block.
 constexpr int kWfBlock = 4;
 // Most block counters a launch uses (the workspace holds this many).
 constexpr int kWfMaxWords = 1 << 18;
 
-// Picks the tile height and the number of z-chunks for grid g so that all
-// CTAs fit on the device at once; false when no shape fits (or the device
-// cannot be queried).
-bool wf_shape(const Grid &g, WfShape *s);
-cudaError_t wf_prepare(int tile_y);
+// Picks the tile height and the number of z-chunks for `steps` fused steps
+// on grid g so that all CTAs fit on the device at once; false when no shape
+// fits (or the device cannot be queried).
+bool wf_shape(const Grid &g, int steps, WfShape *s);
+cudaError_t wf_prepare(int steps, int tile_y);
 cudaError_t launch_wf(const WfShape &s, const WfMaps &m, const WfParams &p, cudaStream_t st);
 unsigned wf_status_take(cudaStream_t st);
 // The fused kernel's device status word after synchronising `st`, left in place.

@@ -1,37 +1,41 @@
-// Two leapfrog steps (Eq. 2, Algorithm 1) fused in one launch on sm_103a:
-// 2-step temporal blocking (the paper's temporal blocking, Sec. 3) without
-// recomputing a halo.
+// Several leapfrog steps (Eq. 2, Algorithm 1) fused in one launch on sm_103a:
+// temporal blocking (the paper's 3.5D blocking, Sec. 3: 2.5D streaming plus
+// blocking in time; Table 2's "number of time steps") without recomputing
+// a halo.
 //
 // Each CTA owns a 64 x TY tile of the interior xy plane and a z range, and
-// runs two TMA-fed 2.5D streaming pipelines over it:
-//   stage A computes u^{t+1} = 2u^t - u^{t-1} + (V dt)^2 lap u^t (+ sources)
+// runs one TMA-fed 2.5D streaming pipeline per fused step over it:
+//   stage 0 computes u^{t+1} = 2u^t - u^{t-1} + (V dt)^2 lap u^t (+ sources)
 //           from u^t, u^{t-1} and vel and stores it;
-//   stage B computes u^{t+2} from u^{t+1}, u^t and vel.  A u^{t+1} box
-//           reaches 4 points into the four neighbouring tiles (its corners
-//           belong to diagonal tiles, which the star never reads), so stage
-//           B copies a block of planes only once this tile and those
-//           neighbours have stored it.
+//   stage s computes u^{t+1+s} from u^{t+s} (stored by stage s-1), u^{t+s-1}
+//           and vel.  A u^{t+s} box reaches 4 points into the four
+//           neighbouring tiles (its corners belong to diagonal tiles, which
+//           the star never reads), so stage s copies a block of planes only
+//           once this tile and those neighbours have stored it.
 // Each stage has compute warps and one copy-issuing warp (warp
 // specialisation).  The issuing thread keeps the rings full: it waits
-// (non-blocking tests) for a free stage, issues the TMA copy, and for stage
-// A publishes stored blocks; the compute warps wait only on "full"
-// mbarriers and release stages on "empty" mbarriers.
+// (non-blocking tests) for a free stage, issues the TMA copy, and for every
+// stage but the last publishes stored blocks; the compute warps wait only on
+// "full" mbarriers and release stages on "empty" mbarriers.
 //
-// Publication.  Stage-A compute threads fence their u^{t+1} stores for the
-// async proxy (fence.proxy.async.global) and arrive on a "block stored"
-// barrier; the issuing thread then executes one GPU-scope fence and adds 1
-// to the block's counter of every tile that reads it.  Stage B's issuing
+// Publication.  A stage's compute threads fence their stores for the async
+// proxy (fence.proxy.async.global) and arrive on a "block stored" barrier;
+// the issuing thread then executes one GPU-scope fence and adds 1 to the
+// block's counter of every tile that reads it.  The next stage's issuing
 // thread copies a block once its counter equals (tiles it covers) x
-// (launches so far) (acquire, then fence.proxy.async.global).
+// (launches so far) (acquire, then fence.proxy.async.global).  Stage s >= 2
+// also reads u^{t+s-1} (a stage output) at its own points; it issues that
+// copy of a plane only after the u^{t+s} copy R planes further on, whose
+// block, by the stages' order, was published after the plane it needs.
 //
 // The grid is launched cooperatively, so every CTA is resident and every
-// wait ends once the stage-A warps it waits for have run; all waits are
-// bounded.  Stage B reads u^{t+1} soon after stage A stored it and u^t, vel
-// soon after stage A read them: stage A's issuing thread stays within kLead
-// planes of stage B's, those copies carry an L2 evict_last policy and the
-// last reads evict_first, so stage B is served from L2 and DRAM
-// moves u^t, u^{t-1}, vel (12 B) and u^{t+1}, u^{t+2} (8 B) per point: 20 B
-// per two updates instead of 32.
+// wait ends once the warps it waits for have run; all waits are bounded.
+// A later stage reads what the earlier stage stored and read shortly before:
+// an issuing thread stays within kLead planes of the next stage's, those
+// copies carry an L2 evict_last policy and the last reads evict_first, so
+// the later stages are served from L2.  DRAM moves u^t, u^{t-1}, vel (12 B)
+// and every stage's output (4 B each) per point: 20 B per two updates
+// instead of 32, 24 B per three instead of 48.
 //
 // Semi-stencil z sweep (the paper's `semi` template, Sec. 9.3).  A thread
 // uses each plane only when it lands: for its points it forms the new
@@ -39,18 +43,18 @@
 // + u(j - m)], and adds c_m u(j) to the pending accumulators of planes
 // j - m, so the accumulator of plane j - R is complete.  A u stage is free
 // right after its plane lands (no R-plane residency), which leaves room for
-// deep rings of both stages in shared memory.  The sums are those of Eq. 3
-// in another order than the single-step kernel, so the fields agree with it
-// to FP32 rounding.
+// deep rings in shared memory.  The sums are those of Eq. 3 in another order
+// than the single-step kernel, so the fields agree with it to FP32 rounding.
 //
-// Absorbing layer (optional): both stages apply the damped update
+// Absorbing layer (optional): every stage applies the damped update
 // u^{t+1} = A (2u^t - B u^{t-1} + (V dt)^2 lap u^t) at points within the
 // layer, A and B tabulated by the distance to the nearest absorbing face.
 //
 // z-chunks.  When the tiles alone do not fill the device, the z range is
-// split; stage A of a chunk then also computes the R planes either side of
-// it (stage B's z halo).  Neighbouring chunks compute those planes from the
-// same inputs with the same arithmetic and store the same bits.
+// split; stage s of a chunk then also computes the (steps-1-s) R planes
+// either side of it (the z halo of the later stages).  Neighbouring chunks
+// compute those planes from the same inputs with the same arithmetic (sources
+// in index order) and store the same bits.
 #include <algorithm>
 
 #include "gbs_wf.cuh"
@@ -64,10 +68,27 @@ constexpr int kR = 4;       // radius of the wave operator
 constexpr int kTX = 64;     // tile width (16 threads x 4 points)
 constexpr int kVY = 2;      // rows per thread
 
-template <int TY>
+// Ring depths (u boxes, u_prev + vel tiles) of stage S of an NS-step launch
+// with tile height TY.  The semi-stencil sweep reads a plane only when it
+// lands, so a ring holds one stage in use and the rest in flight.  Stage 0
+// streams from DRAM and keeps more planes in flight than the later stages,
+// whose loads are mostly served from L2.
+template <int TY, int NS>
+struct WfRings {
+    static constexpr int SL0 = NS == 3 ? 7 : (TY >= 24 ? 6 : 8);
+    static constexpr int SP0 = NS == 3 ? 5 : (TY >= 24 ? 5 : 6);
+    static constexpr int SLn = NS == 3 ? 5 : (TY >= 24 ? 4 : 6);
+    static constexpr int SPn = NS == 3 ? 4 : (TY >= 24 ? 3 : 4);
+    static constexpr int sl(int s) { return s == 0 ? SL0 : SLn; }
+    static constexpr int sp(int s) { return s == 0 ? SP0 : SPn; }
+};
+
+template <int TY, int NS>
 struct WfCfg {
+    using RG = WfRings<TY, NS>;
     static constexpr int NTX = kTX / 4;
-    static constexpr int NT = NTX * (TY / kVY);     // threads per stage
+    static constexpr int NT = NTX * (TY / kVY);     // compute threads per stage
+    static constexpr int NTHREADS = NS * NT + NS * 32;
     static constexpr int BW = kTX + 8;              // u box: 4-wide x halo each side
     static constexpr int BH = TY + 2 * kR;
     static constexpr int L_BYTES = BW * BH * 4;
@@ -75,23 +96,16 @@ struct WfCfg {
     static constexpr int PVU_BYTES = kTX * TY * 4;  // u_prev tile; the vel tile follows
     static constexpr int PV_BYTES = 2 * PVU_BYTES;
     static constexpr int PV_STRIDE = (PV_BYTES + 127) / 128 * 128;
-    // Ring depths.  The semi-stencil sweep reads a plane only when it lands,
-    // so a ring holds one stage in use and the rest in flight.  Stage A
-    // streams from DRAM and keeps more planes in flight than stage B, whose
-    // loads are mostly served from L2.  TY = 28: 218 KB of shared memory.
-    static constexpr bool TALL = TY >= 24;
-    static constexpr int SL_A = TALL ? 6 : 8;
-    static constexpr int SP_A = TALL ? 5 : 6;
-    static constexpr int SL_B = TALL ? 4 : 6;
-    static constexpr int SP_B = TALL ? 3 : 4;
-    static constexpr size_t OFF_LA = 0;
-    static constexpr size_t OFF_PA = OFF_LA + (size_t)SL_A * L_STRIDE;
-    static constexpr size_t OFF_LB = OFF_PA + (size_t)SP_A * PV_STRIDE;
-    static constexpr size_t OFF_PB = OFF_LB + (size_t)SL_B * L_STRIDE;
-    static constexpr size_t OFF_BAR = OFF_PB + (size_t)SP_B * PV_STRIDE;
-    static constexpr size_t SMEM = OFF_BAR + (size_t)(2 * (SL_A + SP_A + SL_B + SP_B) + 8) * 8;
+    static constexpr size_t stage_bytes(int s) { return (size_t)RG::sl(s) * L_STRIDE + (size_t)RG::sp(s) * PV_STRIDE; }
+    static constexpr size_t off_land(int s) { return s == 0 ? 0 : off_land(s - 1) + stage_bytes(s - 1); }
+    static constexpr size_t off_pv(int s) { return off_land(s) + (size_t)RG::sl(s) * L_STRIDE; }
+    static constexpr int bars(int s) { return s < 0 ? 0 : bars(s - 1) + 2 * (RG::sl(s) + RG::sp(s)); }
+    static constexpr size_t OFF_BAR = off_land(NS - 1) + stage_bytes(NS - 1);
+    static constexpr int kNSB = 8;                  // "block stored" barriers per publishing stage
+    static constexpr size_t SMEM = OFF_BAR + (size_t)(bars(NS - 1) + (NS - 1) * kNSB) * 8;
     static_assert(NT % 32 == 0, "a stage is whole warps");
-    static_assert(SL_A >= 2 && SL_B >= 2 && SP_A >= 2 && SP_B >= 2, "one stage in use, one in flight");
+    static_assert(RG::SL0 >= 2 && RG::SLn >= 2 && RG::SP0 >= 2 && RG::SPn >= 2, "one stage in use, one in flight");
+    static_assert(SMEM <= 224 * 1024, "shared memory of one CTA per SM");
 };
 
 // ---- packed FP32 pairs (f32x2) ----
@@ -210,31 +224,29 @@ __device__ __forceinline__ void fence_proxy_async_global()
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// stage A issues u planes at most this far ahead of stage B's next plane
-// (more than a block plus R planes, so stage A can always publish what
-// stage B waits for)
+// a stage's issuing thread copies u planes at most this far ahead of the
+// next stage's next plane (more than a block plus R planes, so it can always
+// publish what the next stage waits for)
 constexpr int kLead = 14;
 constexpr unsigned kPollSleepNs = 32;   // pause of an issuing thread that found nothing to do
-constexpr int kPB = kWfBlock;   // stage-A output planes per published block
-constexpr int kNS = 8;   // ring of "block stored" barriers
-static_assert(kLead > kWfBlock + 4 + 1, "stage A must be able to publish the block stage B waits for");
+constexpr int kPB = kWfBlock;   // output planes per published block
+static_assert(kLead > kWfBlock + 4 + 1, "a stage must be able to publish the block the next one waits for");
 
-// Planes of one stage of a CTA.  Stage A covers the chunk and R planes
-// either side of it (stage B's z halo), clamped to the interior.
+// Planes of one stage of a CTA.  Stage s covers the chunk and (NS-1-s) R
+// planes either side of it (the z halo of the later stages), clamped to the
+// interior.
 struct StageGeo {
-    int a0, a1;          // stage A's output planes
     int o0, nzc;         // this stage's first output plane, count
     int pfirst, nplanes; // first u plane streamed, count
 };
-__device__ __forceinline__ StageGeo stage_geo(const WfParams &p, int chunk, int stage)
+__device__ __forceinline__ StageGeo stage_geo(const WfParams &p, int chunk, int stage, int ns)
 {
     StageGeo s;
     const int nz = (int)p.g.nz;
     const int z0c = chunk * p.zchunk, z1c = min(nz, z0c + p.zchunk);
-    s.a0 = max(0, z0c - kR);
-    s.a1 = min(nz, z1c + kR);
-    s.o0 = stage == 0 ? s.a0 : z0c;
-    s.nzc = (stage == 0 ? s.a1 : z1c) - s.o0;
+    const int ext = (ns - 1 - stage) * kR;
+    s.o0 = max(0, z0c - ext);
+    s.nzc = min(nz, z1c + ext) - s.o0;
     s.pfirst = s.o0 - kR;
     s.nplanes = s.nzc + 2 * kR;
     return s;
@@ -242,15 +254,15 @@ __device__ __forceinline__ StageGeo stage_geo(const WfParams &p, int chunk, int 
 
 // Shared-memory rings and barriers of one stage.  full_*: the copy landed
 // (expect_tx).  empty_*: every consumer warp is done with the stage.
-// stored: every stage-A consumer thread has stored (and fenced) a block.
+// stored: every consumer thread of the stage has stored (and fenced) a block.
 struct Ring {
     unsigned char *land, *pv;
     uint64_t *full_u, *empty_u, *full_pv, *empty_pv, *stored;
 };
 
-// The tiles whose u^{t+1} a stage-B box of `tile` covers: itself and its x, y
-// neighbours (the relation is symmetric: they are also the tiles whose
-// stage B reads this tile's u^{t+1}).
+// The tiles whose output a box of `tile` covers: itself and its x, y
+// neighbours (the relation is symmetric: they are also the tiles that read
+// this tile's output).
 __device__ __forceinline__ int tile_deps(const WfParams &p, int tile, int *d)
 {
     const int ix = tile % p.tiles_x, iy = tile / p.tiles_x;
@@ -263,6 +275,13 @@ __device__ __forceinline__ int tile_deps(const WfParams &p, int tile, int *d)
     return n;
 }
 
+// Counters of stage `stage`'s blocks for one chunk and tile.
+__device__ __forceinline__ unsigned *stage_words(const WfParams &p, int stage, int chunk, int tile)
+{
+    const int64_t ntiles = (int64_t)p.tiles_x * p.tiles_y;
+    return p.words + (((int64_t)stage * p.nchunks + chunk) * ntiles + tile) * p.nblk;
+}
+
 // Warp-uniform bounded wait on a full barrier.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
 {
@@ -270,35 +289,36 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
     return __all_sync(0xffffffffu, ok);
 }
 
-// Compute warps of one stage (STAGE 0 writes u^{t+1}, STAGE 1 u^{t+2}) in the
-// semi-stencil form: each plane is used only when it arrives.  At arrival j
-// a thread forms, for its points, the new accumulator
+// Compute warps of stage STAGE (writes u^{t+1+STAGE}) in the semi-stencil
+// form: each plane is used only when it arrives.  At arrival j a thread
+// forms, for its points, the new accumulator
 //   acc(j) = c0 u(j) + sum_m c_m [x, y neighbours at distance m in plane j]
 //                    + sum_m c_m u(j - m)
 // and adds c_m u(j) to the pending accumulators of planes j - m; the
 // accumulator of plane j - R is then complete.  The queue holds u and the
 // accumulators of the last R planes; the u stage is free after the arrival.
-template <int TY, int STAGE, bool AB>
+template <int TY, int NS, int STAGE, bool AB>
 __device__ __forceinline__ void wf_consumer(const WfParams &p, const Ring &rg, const int64_t tx0, const int64_t ty0,
                                             const int chunk, int *s_nsrc, int *s_src_x, int *s_src_y, int *s_src_z,
                                             float *s_src_f, const float2 *s_ab)
 {
-    using C = WfCfg<TY>;
-    constexpr int SL = STAGE == 0 ? C::SL_A : C::SL_B;
-    constexpr int SP = STAGE == 0 ? C::SP_A : C::SP_B;
+    using C = WfCfg<TY, NS>;
+    constexpr int SL = C::RG::sl(STAGE);
+    constexpr int SP = C::RG::sp(STAGE);
+    constexpr bool PUB = STAGE < NS - 1;
     const Grid &g = p.g;
     const int tid = threadIdx.x - STAGE * C::NT;
     const int lane = threadIdx.x & 31;
     const int tx = tid % C::NTX, ty = tid / C::NTX;
     const int H = g.halo;
-    const StageGeo sg = stage_geo(p, chunk, STAGE);
+    const StageGeo sg = stage_geo(p, chunk, STAGE, NS);
     const int o0 = sg.o0, nzc = sg.nzc, nplanes = sg.nplanes;
     const int64_t t = p.t + STAGE;
 
-    const float *amp_row = (p.src_amp != nullptr && t >= 0 && t < p.src_nt) ? p.src_amp + t * p.nsrc : nullptr;
     // Slots in source-index order (a ballot over the stage's first warp,
     // nsrc <= 32), so that sources sharing a cell are added in the same order
     // on every run and by both z-chunks that compute a halo plane.
+    const float *amp_row = (p.src_amp != nullptr && t >= 0 && t < p.src_nt) ? p.src_amp + t * p.nsrc : nullptr;
     if (tid < 32) {
         bool in = false;
         int64_t i = 0, j = 0, k = 0;
@@ -338,16 +358,20 @@ __device__ __forceinline__ void wf_consumer(const WfParams &p, const Ring &rg, c
     const int ly = kR + kVY * ty;
     const int64_t gx = tx0 + 4 * tx;
     const int64_t gy = ty0 + kVY * ty;
-    const bool xin = gx < g.nx;
-    float *out_base = p.out[STAGE] + (H + gx) + g.px * (H + gy);
+    const bool st0 = gx < g.nx && gy < g.ny;         // rows this thread stores
+    const bool st1 = gx < g.nx && gy + 1 < g.ny;
     const int64_t plane_stride = g.px * g.py;
-    const uint64_t pol_out = STAGE == 0 ? policy_evict_last() : policy_evict_first();
+    float *dst = p.out[STAGE] + (H + gx) + g.px * (H + gy) + plane_stride * (int64_t)(H + o0);
+    const uint64_t pol_out = PUB ? policy_evict_last() : policy_evict_first();
     // absorbing layer: sizes in 32 bits, and whether the tile lies inside the
     // layer's inner boundary in x and y (then only z decides, uniformly)
     const int aw = p.ab.width;
     const int ab_nx = (int)g.nx, ab_ny = (int)g.ny, ab_nz = (int)g.nz;
     const bool ab_tile_in = tx0 >= aw && tx0 + kTX <= g.nx - aw && ty0 >= aw && ty0 + TY <= g.ny - aw;
     (void)ab_nx; (void)ab_ny; (void)ab_nz; (void)ab_tile_in;
+    // shared-memory offsets of the thread's points in a u box and a tile
+    const int su_off = (ly * C::BW + lx) * 4;
+    const int pv_off = ((kVY * ty) * kTX + 4 * tx) * 4;
 
     // V[a][r]: u of plane j - R + a; A*[a][r]: pending accumulator of plane j - R + a (a = 0..R-1)
     float4 V[kR][kVY];
@@ -361,27 +385,31 @@ __device__ __forceinline__ void wf_consumer(const WfParams &p, const Ring &rg, c
             AH[a][r] = 0ull;
         }
 
+    int st = 0, sph = 0;       // u ring slot and phase of plane j
+    int sp = 0, pph = 0;       // pv ring slot and phase of output plane j - 2R
+    int blk_left = kPB;        // output planes left in the current block
+    int blk_id = 0;
     for (int j = 0; j < nplanes; ++j) {
-        const int st = j % SL;
-        if (!warp_wait(&rg.full_u[st], (uint32_t)((j / SL) & 1)))
+        if (!warp_wait(&rg.full_u[st], (uint32_t)sph))
             return;
-        const float *su = reinterpret_cast<const float *>(rg.land + st * C::L_STRIDE);
+        const unsigned char *su = rg.land + st * C::L_STRIDE + su_off;
         float4 cu[kVY];
 #pragma unroll
         for (int r = 0; r < kVY; ++r)
-            cu[r] = ld4(su + (ly + r) * C::BW + lx);
+            cu[r] = ld4(reinterpret_cast<const float *>(su + r * C::BW * 4));
         f2 NL[kVY], NH[kVY];
 #pragma unroll
         for (int r = 0; r < kVY; ++r) {
-            const float4 lf = ld4(su + (ly + r) * C::BW + lx - 4);
-            const float4 rt = ld4(su + (ly + r) * C::BW + lx + 4);
+            const float *row = reinterpret_cast<const float *>(su + r * C::BW * 4);
+            const float4 lf = ld4(row - 4);
+            const float4 rt = ld4(row + 4);
             const float4 cen = cu[r];
             f2 acc_l = mul2(C0, lo(cen)), acc_h = mul2(C0, hi(cen));
             f2 acc2_l = 0ull, acc2_h = 0ull;
 #pragma unroll
             for (int m = 1; m <= kR; ++m) {
-                const float4 yp = (r + m < kVY) ? cu[r + m] : ld4(su + (ly + r + m) * C::BW + lx);
-                const float4 ym = (r - m >= 0) ? cu[r - m] : ld4(su + (ly + r - m) * C::BW + lx);
+                const float4 yp = (r + m < kVY) ? cu[r + m] : ld4(row + m * C::BW);
+                const float4 ym = (r - m >= 0) ? cu[r - m] : ld4(row - m * C::BW);
                 f2 xs_l, xs_h;
                 if (m & 1) {
                     const float w[12] = {lf.x, lf.y, lf.z, lf.w, cen.x, cen.y, cen.z, cen.w, rt.x, rt.y, rt.z, rt.w};
@@ -408,23 +436,25 @@ __device__ __forceinline__ void wf_consumer(const WfParams &p, const Ring &rg, c
         __syncwarp();
         if (lane == 0)
             mbar_arrive(&rg.empty_u[st]);
+        if (++st == SL) {
+            st = 0;
+            sph ^= 1;
+        }
 
         if (j >= 2 * kR) {
             // plane j - R is complete: output plane o0 + cj
             const int cj = j - 2 * kR;
             const int k = o0 + cj;
-            const int sp = cj % SP;
-            if (!warp_wait(&rg.full_pv[sp], (uint32_t)((cj / SP) & 1)))
+            if (!warp_wait(&rg.full_pv[sp], (uint32_t)pph))
                 return;
-            const float *pvu = reinterpret_cast<const float *>(rg.pv + sp * C::PV_STRIDE);
-            const float *pvv = reinterpret_cast<const float *>(rg.pv + sp * C::PV_STRIDE + C::PVU_BYTES);
+            const unsigned char *pvs = rg.pv + sp * C::PV_STRIDE + pv_off;
             f2 res_l[kVY], res_h[kVY];
             float4 vel4[kVY];
 #pragma unroll
             for (int r = 0; r < kVY; ++r) {
                 const float4 u0 = V[0][r];
-                const float4 up = ld4(pvu + (kVY * ty + r) * kTX + 4 * tx);
-                vel4[r] = ld4(pvv + (kVY * ty + r) * kTX + 4 * tx);
+                const float4 up = ld4(reinterpret_cast<const float *>(pvs + r * kTX * 4));
+                vel4[r] = ld4(reinterpret_cast<const float *>(pvs + C::PVU_BYTES + r * kTX * 4));
                 const f2 vs_l = mul2(lo(vel4[r]), S2), vs_h = mul2(hi(vel4[r]), S2);
                 const f2 c_l = mul2(vs_l, vs_l), c_h = mul2(vs_h, vs_h);
                 bool damp = false;
@@ -465,6 +495,10 @@ __device__ __forceinline__ void wf_consumer(const WfParams &p, const Ring &rg, c
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(&rg.empty_pv[sp]);
+            if (++sp == SP) {
+                sp = 0;
+                pph ^= 1;
+            }
             if (nsrc_cta > 0) {
                 for (int i = 0; i < nsrc_cta; ++i) {
                     if (s_src_z[i] != k || (s_src_x[i] >> 2) != tx)
@@ -484,14 +518,18 @@ __device__ __forceinline__ void wf_consumer(const WfParams &p, const Ring &rg, c
                     }
                 }
             }
-            float *dst = out_base + plane_stride * (int64_t)(H + k);
-#pragma unroll
-            for (int r = 0; r < kVY; ++r)
-                if (xin && gy + r < g.ny)
-                    st_pairs_pol(dst + r * g.px, res_l[r], res_h[r], pol_out);
-            if (STAGE == 0 && (cj % kPB == kPB - 1 || cj == nzc - 1)) {
-                fence_proxy_async_global();
-                mbar_arrive(&rg.stored[(cj / kPB) % kNS]);
+            if (st0)
+                st_pairs_pol(dst, res_l[0], res_h[0], pol_out);
+            if (st1)
+                st_pairs_pol(dst + g.px, res_l[1], res_h[1], pol_out);
+            dst += plane_stride;
+            if constexpr (PUB) {
+                if (--blk_left == 0 || cj == nzc - 1) {
+                    fence_proxy_async_global();
+                    mbar_arrive(&rg.stored[blk_id % C::kNSB]);
+                    ++blk_id;
+                    blk_left = kPB;
+                }
             }
         }
         // shift: plane j becomes the newest entry
@@ -512,54 +550,62 @@ __device__ __forceinline__ void wf_consumer(const WfParams &p, const Ring &rg, c
     }
 }
 
-// Copy-issuing thread of one stage (lane 0 of the stage's producer warp).
-// Stage A also publishes its stored blocks: for each, one GPU-scope fence,
-// then +1 on the block's counter of every tile that reads it.  Stage B
-// issues a u^{t+1} copy once its block's counter reaches (tiles it covers)
-// x epoch.  Every wait is bounded; on a timeout the thread records
-// GBS_ETIMEOUT and waits (bounded) for the copies it issued before leaving.
-template <int TY, int STAGE>
+// Copy-issuing thread of stage STAGE (lane 0 of the stage's producer warp).
+// Every stage but the last also publishes its stored blocks: for each, one
+// GPU-scope fence, then +1 on the block's counter of every tile that reads
+// it.  A later stage issues a u^{t+STAGE} copy once the block's counter of
+// the stage before reaches (tiles it covers) x epoch.  Every wait is
+// bounded; on a timeout the thread records GBS_ETIMEOUT and waits (bounded)
+// for the copies it issued before leaving.
+template <int TY, int NS, int STAGE>
 __device__ __forceinline__ void wf_producer(const CUtensorMap *__restrict__ pm_u,
                                             const CUtensorMap *__restrict__ pm_prev,
                                             const CUtensorMap *__restrict__ pm_vel, const WfParams &p,
                                             const Ring &rg, const int64_t tx0, const int64_t ty0, const int tile,
-                                            const int chunk, volatile int *b_next)
+                                            const int chunk, volatile int *s_next)
 {
-    using C = WfCfg<TY>;
-    constexpr int SL = STAGE == 0 ? C::SL_A : C::SL_B;
-    constexpr int SP = STAGE == 0 ? C::SP_A : C::SP_B;
+    using C = WfCfg<TY, NS>;
+    constexpr int SL = C::RG::sl(STAGE);
+    constexpr int SP = C::RG::sp(STAGE);
+    constexpr bool PUB = STAGE < NS - 1;
+    constexpr bool LAST = STAGE == NS - 1;
     const int H = p.g.halo;
-    const StageGeo sg = stage_geo(p, chunk, STAGE);
-    const int ntiles = p.tiles_x * p.tiles_y;
-    unsigned *words = p.words + (int64_t)chunk * ntiles * p.nblk;
+    const StageGeo sg = stage_geo(p, chunk, STAGE, NS);
     int deps[5];
     const int ndeps = tile_deps(p, tile, deps);
-    // stage B: count of a published block, modulo 2^32 like the counters
+    // counters of a published block reach this, modulo 2^32 like the counters
     // (during a launch a counter lies within ndeps below it, so the signed
     // difference decides even after the product wraps)
     const unsigned need = (unsigned)ndeps * p.epoch;
-    const int nblk_a = (sg.a1 - sg.a0 + kPB - 1) / kPB; // stage A's blocks
+    const int nblk_out = (sg.nzc + kPB - 1) / kPB;   // this stage's published blocks
+    // the stage before: its output planes and counters (this stage's u box)
+    const StageGeo sb = stage_geo(p, chunk, STAGE > 0 ? STAGE - 1 : 0, NS);
+    const unsigned *wait_words = STAGE > 0 ? stage_words(p, STAGE - 1, chunk, tile) : nullptr;
+    unsigned *pub_words[5];
+    if constexpr (PUB)
+        for (int i = 0; i < ndeps; ++i)
+            pub_words[i] = stage_words(p, STAGE, chunk, deps[i]);
     int n_u = 0, n_pv = 0, n_pub = 0, ok_blk = -1;
-    // stage A: u^t and vel are read again by stage B, u^{t-1} is not; stage B's reads are the last
-    const uint64_t pol_keep = STAGE == 0 ? policy_evict_last() : policy_evict_first();
+    // data a later stage reads again stays in L2 (evict_last); last reads go first
+    const uint64_t pol_keep = LAST ? policy_evict_first() : policy_evict_last();
     const uint64_t pol_drop = policy_evict_first();
     uint64_t t_idle = global_timer_ns();
     bool fail = false;
-    while (n_u < sg.nplanes || n_pv < sg.nzc || (STAGE == 0 && n_pub < nblk_a)) {
+    while (n_u < sg.nplanes || n_pv < sg.nzc || (PUB && n_pub < nblk_out)) {
         bool prog = false;
         if (n_u < sg.nplanes) {
             const int st = n_u % SL;
             bool ready = n_u < SL || mbar_test(&rg.empty_u[st], (uint32_t)((n_u / SL - 1) & 1));
-            // stage A stays within kLead planes of stage B, so the data stage B
-            // reads again is still in L2 (stage B publishes its next plane)
-            if (STAGE == 0 && sg.pfirst + n_u > *b_next + kLead)
+            // stay within kLead planes of the next stage, so the data it reads
+            // again is still in L2 (it publishes its next plane)
+            if (PUB && sg.pfirst + n_u > s_next[STAGE + 1] + kLead)
                 ready = false;
-            if (ready && STAGE == 1) {
-                const int b = sg.pfirst + n_u;   // plane of u^{t+1}
-                if (b >= sg.a0 && b < sg.a1) {
-                    const int blk = (b - sg.a0) / kPB;
+            if (ready && STAGE > 0) {
+                const int b = sg.pfirst + n_u;   // plane of the previous stage's output
+                if (b >= sb.o0 && b < sb.o0 + sb.nzc) {
+                    const int blk = (b - sb.o0) / kPB;
                     if (blk > ok_blk) {
-                        if ((int)(ld_acquire(words + (int64_t)tile * p.nblk + blk) - need) >= 0) {
+                        if ((int)(ld_acquire(wait_words + blk) - need) >= 0) {
                             ok_blk = blk;
                             fence_proxy_async_global();
                         } else {
@@ -573,14 +619,20 @@ __device__ __forceinline__ void wf_producer(const CUtensorMap *__restrict__ pm_u
                 tma_load_3d_pol(rg.land + st * C::L_STRIDE, pm_u, (int)(H + tx0 - 4), (int)(H + ty0 - kR),
                                 H + sg.pfirst + n_u, &rg.full_u[st], pol_keep);
                 ++n_u;
-                if (STAGE == 1)
-                    *b_next = n_u < sg.nplanes ? sg.pfirst + n_u : 1 << 30;
+                if (STAGE > 0)
+                    s_next[STAGE] = n_u < sg.nplanes ? sg.pfirst + n_u : 1 << 30;
                 prog = true;
             }
         }
         if (n_pv < sg.nzc) {
             const int st = n_pv % SP;
-            if (n_pv < SP || mbar_test(&rg.empty_pv[st], (uint32_t)((n_pv / SP - 1) & 1))) {
+            bool ready = n_pv < SP || mbar_test(&rg.empty_pv[st], (uint32_t)((n_pv / SP - 1) & 1));
+            // stage >= 2 reads u^{t+STAGE-1}, the output of stage STAGE-2: a
+            // plane only after the u box R planes further on was copied (its
+            // block was published after this plane's)
+            if (STAGE >= 2 && sg.o0 + n_pv + kR >= sg.pfirst + n_u)
+                ready = false;
+            if (ready) {
                 unsigned char *dst = rg.pv + st * C::PV_STRIDE;
                 mbar_arrive_expect_tx(&rg.full_pv[st], C::PV_BYTES);
                 tma_load_3d_pol(dst, pm_prev, (int)(H + tx0), (int)(H + ty0), H + sg.o0 + n_pv, &rg.full_pv[st],
@@ -591,11 +643,11 @@ __device__ __forceinline__ void wf_producer(const CUtensorMap *__restrict__ pm_u
                 prog = true;
             }
         }
-        if (STAGE == 0 && n_pub < nblk_a &&
-            mbar_test(&rg.stored[n_pub % kNS], (uint32_t)((n_pub / kNS) & 1))) {
+        if (PUB && n_pub < nblk_out &&
+            mbar_test(&rg.stored[n_pub % C::kNSB], (uint32_t)((n_pub / C::kNSB) & 1))) {
             fence_acq_rel_gpu();
             for (int i = 0; i < ndeps; ++i)
-                red_add_relaxed(words + (int64_t)deps[i] * p.nblk + n_pub, 1u);
+                red_add_relaxed(pub_words[i] + n_pub, 1u);
             ++n_pub;
             prog = true;
         }
@@ -618,24 +670,50 @@ __device__ __forceinline__ void wf_producer(const CUtensorMap *__restrict__ pm_u
     }
 }
 
-// CTA b: tile b % tiles, z-chunk b / tiles.  Warps: stage-A compute
-// [0, NT), stage-B compute [NT, 2 NT), then one copy-issuing warp per stage.
-template <int TY, bool AB>
-__global__ void __launch_bounds__(2 * WfCfg<TY>::NT + 64, 1)
-    k_wf(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_pa,
-         const __grid_constant__ CUtensorMap tm_ub, const __grid_constant__ CUtensorMap tm_pb,
-         const __grid_constant__ CUtensorMap tm_vel, const __grid_constant__ WfParams p)
+// Sources of one stage, kept in shared memory.
+struct SrcSlots {
+    int n;
+    int x[kMaxFusedSrc], y[kMaxFusedSrc], z[kMaxFusedSrc];
+    float f[kMaxFusedSrc];
+};
+
+// Runs stage S (compute warp or issuing thread) if S is this warp's stage.
+template <int TY, int NS, int S, bool AB>
+__device__ __forceinline__ void wf_dispatch(int w, const WfMaps &m, const WfParams &p, const Ring *rings,
+                                            int64_t tx0, int64_t ty0, int tile, int chunk, SrcSlots *src,
+                                            volatile int *s_next, const float2 *s_ab)
 {
-    using C = WfCfg<TY>;
+    using C = WfCfg<TY, NS>;
+    constexpr int NW = C::NT / 32;
+    if constexpr (S < NS) {
+        if (w >= S * NW && w < (S + 1) * NW) {
+            wf_consumer<TY, NS, S, AB>(p, rings[S], tx0, ty0, chunk, &src[S].n, src[S].x, src[S].y, src[S].z,
+                                       src[S].f, s_ab);
+        } else if (w == NS * NW + S) {
+            if ((threadIdx.x & 31) == 0)
+                wf_producer<TY, NS, S>(S == 0 ? &m.ua : &m.ub[S > 0 ? S - 1 : 0],
+                                       S == 0 ? &m.pa : &m.pb[S > 0 ? S - 1 : 0], &m.vel, p, rings[S], tx0, ty0,
+                                       tile, chunk, s_next);
+        } else {
+            wf_dispatch<TY, NS, S + 1, AB>(w, m, p, rings, tx0, ty0, tile, chunk, src, s_next, s_ab);
+        }
+    }
+}
+
+// CTA b: tile b % tiles, z-chunk b / tiles.  Warps: the compute warps of
+// stage 0, 1, ..., then one copy-issuing warp per stage.
+template <int TY, int NS, bool AB>
+__global__ void __launch_bounds__(WfCfg<TY, NS>::NTHREADS, 1)
+    k_wf(const __grid_constant__ WfMaps m, const __grid_constant__ WfParams p)
+{
+    using C = WfCfg<TY, NS>;
     constexpr int NW = C::NT / 32;   // compute warps per stage
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ int s_nsrc[2];
-    __shared__ int s_src_x[2][kMaxFusedSrc], s_src_y[2][kMaxFusedSrc], s_src_z[2][kMaxFusedSrc];
-    __shared__ float s_src_f[2][kMaxFusedSrc];
-    __shared__ int s_bnext;   // stage B's next u^{t+1} plane to copy
+    __shared__ SrcSlots s_src[NS];
+    __shared__ int s_next[NS];   // stage s's next u plane to copy (s >= 1)
     // absorbing layer: A, B by distance (threads look up different distances;
     // divergent constant-bank reads would serialise)
-    __shared__ float2 s_ab[kMaxAbsorb];
+    __shared__ float2 s_ab[AB ? kMaxAbsorb : 1];
     const int ntiles = p.tiles_x * p.tiles_y;
     const int tile = (int)(blockIdx.x % (unsigned)ntiles);
     const int chunk = (int)(blockIdx.x / (unsigned)ntiles);
@@ -651,66 +729,58 @@ __global__ void __launch_bounds__(2 * WfCfg<TY>::NT + 64, 1)
         return;
     }
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
-    Ring ra, rb;
-    ra.land = smem + C::OFF_LA;
-    ra.pv = smem + C::OFF_PA;
-    ra.full_u = bars;
-    ra.empty_u = ra.full_u + C::SL_A;
-    ra.full_pv = ra.empty_u + C::SL_A;
-    ra.empty_pv = ra.full_pv + C::SP_A;
-    ra.stored = ra.empty_pv + C::SP_A;
-    rb.land = smem + C::OFF_LB;
-    rb.pv = smem + C::OFF_PB;
-    rb.full_u = ra.stored + kNS;
-    rb.empty_u = rb.full_u + C::SL_B;
-    rb.full_pv = rb.empty_u + C::SL_B;
-    rb.empty_pv = rb.full_pv + C::SP_B;
-    rb.stored = nullptr;
+    Ring rings[NS];
+    {
+        uint64_t *b = bars;
+        uint64_t *stored = bars + C::bars(NS - 1);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            rings[s].land = smem + C::off_land(s);
+            rings[s].pv = smem + C::off_pv(s);
+            rings[s].full_u = b;
+            b += C::RG::sl(s);
+            rings[s].empty_u = b;
+            b += C::RG::sl(s);
+            rings[s].full_pv = b;
+            b += C::RG::sp(s);
+            rings[s].empty_pv = b;
+            b += C::RG::sp(s);
+            rings[s].stored = s < NS - 1 ? stored + s * C::kNSB : nullptr;
+        }
+    }
     if (threadIdx.x == 0) {
-        prefetch_tmap(&tm_ua);
-        prefetch_tmap(&tm_pa);
-        prefetch_tmap(&tm_ub);
-        prefetch_tmap(&tm_pb);
-        prefetch_tmap(&tm_vel);
-        for (int i = 0; i < C::SL_A; ++i) {
-            mbar_init(&ra.full_u[i], 1);
-            mbar_init(&ra.empty_u[i], NW);
+        prefetch_tmap(&m.ua);
+        prefetch_tmap(&m.pa);
+        for (int s = 0; s + 1 < NS; ++s) {
+            prefetch_tmap(&m.ub[s]);
+            prefetch_tmap(&m.pb[s]);
         }
-        for (int i = 0; i < C::SP_A; ++i) {
-            mbar_init(&ra.full_pv[i], 1);
-            mbar_init(&ra.empty_pv[i], NW);
-        }
-        for (int i = 0; i < kNS; ++i)
-            mbar_init(&ra.stored[i], C::NT);
-        for (int i = 0; i < C::SL_B; ++i) {
-            mbar_init(&rb.full_u[i], 1);
-            mbar_init(&rb.empty_u[i], NW);
-        }
-        for (int i = 0; i < C::SP_B; ++i) {
-            mbar_init(&rb.full_pv[i], 1);
-            mbar_init(&rb.empty_pv[i], NW);
+        prefetch_tmap(&m.vel);
+        for (int s = 0; s < NS; ++s) {
+            for (int i = 0; i < C::RG::sl(s); ++i) {
+                mbar_init(&rings[s].full_u[i], 1);
+                mbar_init(&rings[s].empty_u[i], NW);
+            }
+            for (int i = 0; i < C::RG::sp(s); ++i) {
+                mbar_init(&rings[s].full_pv[i], 1);
+                mbar_init(&rings[s].empty_pv[i], NW);
+            }
+            if (s < NS - 1)
+                for (int i = 0; i < C::kNSB; ++i)
+                    mbar_init(&rings[s].stored[i], C::NT);
+            s_src[s].n = 0;
+            s_next[s] = stage_geo(p, chunk, s, NS).pfirst;
         }
         fence_mbar_init();
-        s_nsrc[0] = 0;
-        s_nsrc[1] = 0;
-        s_bnext = stage_geo(p, chunk, 1).pfirst;
     }
     if constexpr (AB)
         for (int i = threadIdx.x; i < p.ab.width; i += blockDim.x)
             s_ab[i] = make_float2(p.ab.A[i], p.ab.B[i]);
     __syncthreads();
-    const int w = threadIdx.x / 32;
-    if (w < NW)
-        wf_consumer<TY, 0, AB>(p, ra, tx0, ty0, chunk, &s_nsrc[0], s_src_x[0], s_src_y[0], s_src_z[0], s_src_f[0], s_ab);
-    else if (w < 2 * NW)
-        wf_consumer<TY, 1, AB>(p, rb, tx0, ty0, chunk, &s_nsrc[1], s_src_x[1], s_src_y[1], s_src_z[1], s_src_f[1], s_ab);
-    else if (w == 2 * NW && (threadIdx.x & 31) == 0)
-        wf_producer<TY, 0>(&tm_ua, &tm_pa, &tm_vel, p, ra, tx0, ty0, tile, chunk, &s_bnext);
-    else if (w == 2 * NW + 1 && (threadIdx.x & 31) == 0)
-        wf_producer<TY, 1>(&tm_ub, &tm_pb, &tm_vel, p, rb, tx0, ty0, tile, chunk, &s_bnext);
+    wf_dispatch<TY, NS, 0, AB>(threadIdx.x / 32, m, p, rings, tx0, ty0, tile, chunk, s_src, s_next, s_ab);
 }
 
-template <int TY, bool AB>
+template <int TY, int NS, bool AB>
 cudaError_t prepare_t()
 {
     static bool done[64] = {};
@@ -720,51 +790,58 @@ cudaError_t prepare_t()
         return e;
     if (dev >= 0 && dev < 64 && done[dev])
         return cudaSuccess;
-    e = cudaFuncSetAttribute(k_wf<TY, AB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WfCfg<TY>::SMEM);
+    e = cudaFuncSetAttribute(k_wf<TY, NS, AB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WfCfg<TY, NS>::SMEM);
     if (e == cudaSuccess && dev >= 0 && dev < 64)
         done[dev] = true;
     return e;
 }
 
-// CTAs the device holds at once for tile height TY, with and without the
-// absorbing layer (the smaller of the two; 0 on error).
-template <int TY, bool AB>
+// CTAs the device holds at once for NS steps at tile height TY, with and
+// without the absorbing layer (the smaller of the two; 0 on error).
+template <int TY, int NS, bool AB>
 int slots_ab()
 {
-    if (prepare_t<TY, AB>() != cudaSuccess)
+    if (prepare_t<TY, NS, AB>() != cudaSuccess)
         return 0;
     int dev = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wf<TY, AB>, 2 * WfCfg<TY>::NT + 64,
-                                                      WfCfg<TY>::SMEM) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_wf<TY, NS, AB>, WfCfg<TY, NS>::NTHREADS,
+                                                      WfCfg<TY, NS>::SMEM) != cudaSuccess)
         return 0;
     return sms * per;
 }
-template <int TY>
+template <int TY, int NS>
 int slots_t()
 {
-    return std::min(slots_ab<TY, false>(), slots_ab<TY, true>());
+    return std::min(slots_ab<TY, NS, false>(), slots_ab<TY, NS, true>());
 }
 
-template <int TY, bool AB>
+template <int TY, int NS, bool AB>
 cudaError_t launch_t(const WfShape &s, const WfMaps &m, const WfParams &p, cudaStream_t st)
 {
-    cudaError_t e = prepare_t<TY, AB>();
+    cudaError_t e = prepare_t<TY, NS, AB>();
     if (e != cudaSuccess)
         return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)s.ctas);
-    cfg.blockDim = dim3(2 * WfCfg<TY>::NT + 64);
-    cfg.dynamicSmemBytes = WfCfg<TY>::SMEM;
+    cfg.blockDim = dim3(WfCfg<TY, NS>::NTHREADS);
+    cfg.dynamicSmemBytes = WfCfg<TY, NS>::SMEM;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_wf<TY, AB>, m.ua, m.pa, m.ub, m.pb, m.vel, p);
+    return cudaLaunchKernelEx(&cfg, k_wf<TY, NS, AB>, m, p);
+}
+
+int slots_for(int steps, int h)
+{
+    if (steps == 2)
+        return h == 28 ? slots_t<28, 2>() : slots_t<16, 2>();
+    return steps == 3 && h == 16 ? slots_t<16, 3>() : 0;
 }
 
 }  // namespace
@@ -772,15 +849,21 @@ cudaError_t launch_t(const WfShape &s, const WfMaps &m, const WfParams &p, cudaS
 // Shape choice.  A CTA streams its whole z range, and all CTAs run at once,
 // so the launch lasts as long as one CTA: about (planes + overhead) x tile
 // rows.  Among the tile heights and chunk counts whose CTAs all fit, take
-// the one with the least such work per CTA (a chunk adds stage A's 2R extra
-// planes; a tile row adds its 2R-row halo to the u boxes).
-bool wf_shape(const Grid &g, WfShape *s)
+// the one with the least such work per CTA (a chunk adds the earlier stages'
+// extra planes; a tile row adds its 2R-row halo to the u boxes).
+bool wf_shape(const Grid &g, int steps, WfShape *s)
 {
-    const int heights[2] = {28, 16};
+    if (steps != 2 && steps != 3)
+        return false;
+    const int heights2[2] = {28, 16};
+    const int heights3[1] = {16};
+    const int *heights = steps == 2 ? heights2 : heights3;
+    const int nh = steps == 2 ? 2 : 1;
     double best = 1e300;
     bool found = false;
-    for (int h : heights) {
-        const int slots = h == 28 ? slots_t<28>() : slots_t<16>();
+    for (int hi = 0; hi < nh; ++hi) {
+        const int h = heights[hi];
+        const int slots = slots_for(steps, h);
         if (slots <= 0)
             continue;
         const int64_t tx = (g.nx + kTX - 1) / kTX, ty = (g.ny + h - 1) / h;
@@ -791,14 +874,16 @@ bool wf_shape(const Grid &g, WfShape *s)
             const int64_t zc = (g.nz + c - 1) / c;
             if (c > 1 && zc < 16)
                 break;
-            const int64_t nblk = (zc + 2 * kR + kPB - 1) / kPB;
-            if (tiles * c * nblk > kWfMaxWords)
+            const int64_t nblk = (zc + 2 * (steps - 1) * kR + kPB - 1) / kPB;
+            if ((int64_t)(steps - 1) * tiles * c * nblk > kWfMaxWords)
                 continue;
-            const double extra = c > 1 ? 2.0 * kR * 0.5 : 0.0;   // stage A's extra planes: one stage of two
+            // the earlier stages' extra planes, averaged over the stages
+            const double extra = c > 1 ? 2.0 * kR * (steps - 1) * 0.5 : 0.0;
             const double cost = ((double)zc + extra) * (double)(h + kR);
             if (cost < best * 0.999) {
                 best = cost;
                 found = true;
+                s->steps = steps;
                 s->tile_y = h;
                 s->tiles_x = (int)tx;
                 s->tiles_y = (int)ty;
@@ -812,18 +897,25 @@ bool wf_shape(const Grid &g, WfShape *s)
     return found;
 }
 
-cudaError_t wf_prepare(int tile_y)
+cudaError_t wf_prepare(int steps, int tile_y)
 {
-    cudaError_t e = tile_y == 28 ? prepare_t<28, false>() : prepare_t<16, false>();
+    if (steps == 3 && tile_y == 16) {
+        cudaError_t e = prepare_t<16, 3, false>();
+        return e == cudaSuccess ? prepare_t<16, 3, true>() : e;
+    }
+    if (steps != 2 || (tile_y != 28 && tile_y != 16))
+        return cudaErrorInvalidValue;
+    cudaError_t e = tile_y == 28 ? prepare_t<28, 2, false>() : prepare_t<16, 2, false>();
     if (e == cudaSuccess)
-        e = tile_y == 28 ? prepare_t<28, true>() : prepare_t<16, true>();
+        e = tile_y == 28 ? prepare_t<28, 2, true>() : prepare_t<16, 2, true>();
     return e;
 }
 
 cudaError_t launch_wf(const WfShape &s, const WfMaps &m, const WfParams &p, cudaStream_t st)
 {
     if (s.ctas <= 0 || (int64_t)s.tiles_x * s.tiles_y * s.nchunks != s.ctas ||
-        (int64_t)s.ctas * s.nblk > kWfMaxWords || s.nblk * kPB < s.zchunk + 2 * kR)
+        (int64_t)(s.steps - 1) * s.ctas * s.nblk > kWfMaxWords ||
+        s.nblk * kPB < s.zchunk + 2 * (s.steps - 1) * kR)
         return cudaErrorInvalidConfiguration;
     WfParams q = p;
     q.tiles_x = s.tiles_x;
@@ -832,9 +924,13 @@ cudaError_t launch_wf(const WfShape &s, const WfMaps &m, const WfParams &p, cuda
     q.nchunks = s.nchunks;
     q.nblk = s.nblk;
     const bool ab = q.ab.width > 0;
+    if (s.steps == 3 && s.tile_y == 16)
+        return ab ? launch_t<16, 3, true>(s, m, q, st) : launch_t<16, 3, false>(s, m, q, st);
+    if (s.steps != 2)
+        return cudaErrorInvalidValue;
     switch (s.tile_y) {
-    case 28: return ab ? launch_t<28, true>(s, m, q, st) : launch_t<28, false>(s, m, q, st);
-    case 16: return ab ? launch_t<16, true>(s, m, q, st) : launch_t<16, false>(s, m, q, st);
+    case 28: return ab ? launch_t<28, 2, true>(s, m, q, st) : launch_t<28, 2, false>(s, m, q, st);
+    case 16: return ab ? launch_t<16, 2, true>(s, m, q, st) : launch_t<16, 2, false>(s, m, q, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -1,4 +1,6 @@
 """Helpers shared by the GPU parity tests (no arithmetic of the method)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -6,12 +8,29 @@ torch = pytest.importorskip("torch")
 
 # Tolerances (normwise: max|gpu - oracle| / max|oracle| over the interior).
 # One FP32 application of the star stencil or the leapfrog step: the
-# requirement is 2e-6.  After N steps: 2e-6 * N.
+# requirement is 2e-6.  After N steps the bound is 2e-6 + 6.5e-8 N: fitted to
+# the errors first observed on a GB300 (normwise, every multi-step parity
+# test): at most 6.4e-7 over 8-22 steps of ragged random fields, 8.3e-6
+# after 500 steps of the layered Ricker workload (256^3 and a z-chunked
+# 128 x 56 x 512 grid, fused pairs and single steps alike).  The bound is 4-7x
+# those values, so a systematic error of a few 1e-6 fails.
 TOL_ONE = 2e-6
+TOL_PER_STEP = 6.5e-8
 
 
 def tol_steps(n: int) -> float:
-    return TOL_ONE * max(1, n)
+    return TOL_ONE + TOL_PER_STEP * max(1, n)
+
+
+def log_error(err: float, what: str) -> None:
+    """With GBS_ERRLOG set, appends an error that a test checks without
+    oracle.err_norms (the record the multi-step bound is fitted from)."""
+    path = os.environ.get("GBS_ERRLOG")
+    if path:
+        import json
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", ""), "what": what,
+                                "norm_max_rel": float(err)}) + "\n")
 
 
 def need_gpu():

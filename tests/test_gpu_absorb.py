@@ -16,7 +16,7 @@ import pytest
 import oracle
 import paper_2309_04671_gb300 as gbs
 import workloads as W
-from gpu_util import dev, need_gpu, to_dev, tol_steps, torch
+from gpu_util import dev, log_error, need_gpu, to_dev, tol_steps, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -95,6 +95,7 @@ def test_pairs_full_size_against_single_steps():
     gbs.device_status()
     scale = float(torch.max(torch.abs(c0)))
     err = max(float(torch.max(torch.abs(c1 - c0))), float(torch.max(torch.abs(p1 - p0))))
+    log_error(err / scale, "absorb single vs pairs, 10 steps")
     assert err <= tol_steps(10) * scale, (err, scale)
 
 

@@ -55,3 +55,24 @@ def test_500_steps_vs_oracle(shape, chunked):
             e = oracle.err_norms(got.cpu().numpy(), ref)
             assert e["finite"] and e["norm_max_rel"] <= tol, (fn.__name__, e)
         assert np.all(c.cpu().numpy()[halo_mask(z.shape, prob.halo)] == 0)
+
+
+@pytest.mark.parametrize("shape", [(256, 256, 256), (128, 56, 512)], ids=["256cube", "tall_zchunked"])
+def test_500_steps_three_per_launch_vs_oracle(shape):
+    """The same workloads with three steps fused per launch."""
+    need_gpu()
+    nx, ny, nz = shape
+    prob = W.layered_problem(n=nx, ny=ny, nz=nz, nsteps=NSTEPS, seed_offset=3)
+    assert gbs.tbn_supported(nx, ny, nz, prob.halo, 3)[0]
+    rec = _receivers(nx, ny, 8, 4)
+    z = np.zeros(W.padded_shape(nx, ny, nz, prob.halo), np.float32)
+    rp, ru, rtr = oracle.wave_propagate(z, z, prob.vel, prob.dt, prob.h, prob.halo, NSTEPS, src_idx=prob.src_idx,
+                                        src_amp=prob.src_amp, rec_idx=rec)
+    trace = torch.zeros((NSTEPS, rec.size), device=dev())
+    p, c = gbs.wave_propagate_tbn(to_dev(z), to_dev(z), to_dev(prob.vel), prob.dt, prob.h, prob.halo, NSTEPS, 3,
+                                  src_idx=to_dev(prob.src_idx), src_amp=to_dev(prob.src_amp), rec_idx=to_dev(rec),
+                                  rec_trace=trace)
+    gbs.device_status()
+    for got, ref in ((c, ru), (p, rp), (trace, rtr)):
+        e = oracle.err_norms(got.cpu().numpy(), ref)
+        assert e["finite"] and e["norm_max_rel"] <= tol_steps(NSTEPS), e

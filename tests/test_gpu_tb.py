@@ -18,7 +18,7 @@ import pytest
 import oracle
 import paper_2309_04671_gb300 as gbs
 import workloads as W
-from gpu_util import dev, halo_mask, need_gpu, to_dev, tol_steps, torch
+from gpu_util import dev, halo_mask, log_error, need_gpu, to_dev, tol_steps, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -230,6 +230,7 @@ def test_full_size_pairs(layered512):
     scale = float(torch.max(torch.abs(c0)))
     err = max(float(torch.max(torch.abs(c1 - c0))), float(torch.max(torch.abs(p1 - p0))))
     del p0, c0
+    log_error(err / scale, "512^3 pairs vs single, 4 steps")
     assert err <= tol_steps(4) * scale, (err, scale)
     # 8 steps forward, swap the pair, 8 steps back: the start returns
     a, b = to_dev(up), to_dev(u)
@@ -237,6 +238,7 @@ def test_full_size_pairs(layered512):
     pb, cb = gbs.wave_propagate_tb(cf, pf, vel, prob.dt, prob.h, halo, 8, work=work)
     gbs.device_status()
     err = max(float(torch.max(torch.abs(pb - to_dev(u)))), float(torch.max(torch.abs(cb - to_dev(up)))))
+    log_error(err, "512^3 pairs, 8 + 8 reversed steps (absolute, fields of max 1)")
     assert err <= tol_steps(16), err
 
 

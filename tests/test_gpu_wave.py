@@ -13,7 +13,7 @@ import pytest
 import oracle
 import paper_2309_04671_gb300 as gbs
 import workloads as W
-from gpu_util import TOL_ONE, dev, halo_mask, need_gpu, to_dev, tol_steps, torch
+from gpu_util import TOL_ONE, dev, halo_mask, log_error, need_gpu, to_dev, tol_steps, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -173,6 +173,7 @@ def test_full_size_time_reversal(layered512):
     gbs.device_status()
     scale = float(torch.max(torch.abs(c0c)))
     err = max(float(torch.max(torch.abs(p2 - c0c))), float(torch.max(torch.abs(c2 - p0c))))
+    log_error(err / scale, "512^3 single steps, 50 + 50 reversed")
     assert err <= tol_steps(100) * scale, (err, scale)
 
 
