@@ -22,6 +22,11 @@ What each function follows (arXiv 2309.04671):
   equation u_tt + 2 eta u_t = V^2 lap u with a centred u_t and a quadratic
   damping profile near the faces (the paper surrounds its domain with an
   absorbing boundary, Sec. 2.2, but gives no equations for it).
+* :func:`pml_zeta`, :func:`pml_state`, :func:`pml_step`, :func:`pml_propagate`
+  -- the perfectly matched layer the paper puts around its domain (Sec. 2.2:
+  an extra 7-point star stencil on a second array in the PML region) with
+  the equations of Grote & Sim (2010) for the second-order wave equation:
+  one scalar and one vector auxiliary field; full-grid arrays here.
 * :func:`round_to_format`, :func:`lp_scale_exponent`, :func:`lp_encode`,
   :func:`lp_wave_step` -- wave fields stored in BF16/FP16 with a per-field
   power-of-two scale (IEEE round-to-nearest-even from the format's
@@ -558,6 +563,132 @@ def fwi_gradient(vel, dt: float, h: float, halo: int, nsteps: int, d_obs, *, src
     g = adjoint_gradient(vel, dt, h, halo, nsteps, r, src_idx=src_idx, src_amp=src_amp, rec_idx=rec_idx,
                          states=states)
     return 0.5 * float(np.sum(r * r)), g
+
+
+# ---------------------------------------------------------------------------
+# PML around the domain (Sec. 2.2 names a PML; its equations come from
+# Grote & Sim, "Efficient PML for the wave equation", 2010)
+# ---------------------------------------------------------------------------
+def pml_zeta(n: int, width: int, zeta_max: float, low: bool = True, high: bool = True) -> np.ndarray:
+    """Damping along one axis at interior indices 0..n-1 (FP64).
+
+    d = distance (cells) to the nearest absorbing face of this axis; the
+    profile is zeta_max ((W-1-d)/(W-1))^2 for d < W-1 and zero from d = W-1
+    on, so the innermost of the W stored layers carries no damping and the
+    region inside them sees no auxiliary term.  ``low``/``high``: whether the
+    faces at index 0 / n-1 absorb."""
+    i = np.arange(n, dtype=np.float64)
+    big = np.full(n, np.inf)
+    d = np.minimum(i if low else big, (n - 1 - i) if high else big)
+    w1 = width - 1
+    z = np.where(d < w1, zeta_max * ((w1 - d) / max(w1, 1)) ** 2, 0.0)
+    return z
+
+
+def pml_state(shape) -> dict:
+    """Zero auxiliary state for fields of the padded ``shape``: phi (three
+    components, the vector field at half steps) and psi (the time integral
+    of u), full-grid FP64 arrays with a zero halo."""
+    return {"phi": [np.zeros(shape) for _ in range(3)], "psi": np.zeros(shape)}
+
+
+def pml_step(u_prev, u, vel, state, dt: float, h: float, halo: int, width: int, zeta_max: float, *,
+             free_top: bool = False, src_idx=None, src_f=None):
+    """One leapfrog step with the PML; returns u^{n+1} and updates ``state``
+    (phi^{n-1/2} -> phi^{n+1/2}, psi^n -> psi^{n+1}) in place.
+
+    Continuous equations (Grote & Sim 2010, 3D, for u_tt = V^2 lap u with
+    V^2 outside the divergence), zeta_j = zeta_j(x_j):
+        u_tt + S1 u_t + S2 u + S3 psi = V^2 (lap u + div phi)
+        psi_t = u
+        phi_j,t = -zeta_j phi_j + a_j d_j u + b_j d_j psi
+    with S1 = sum zeta, S2 = zx zy + zy zz + zz zx, S3 = zx zy zz,
+    a_j = (sum of the other two zeta) - zeta_j, b_j = (product of the other two).
+    Discretisation (this library's): lap = the 25-point operator of Eq. 3
+    (weights c_m / h^2); d_j and div = second-order central differences
+    (a 7-point star); u_t centred over the two leapfrog levels:
+        u^{n+1} = [2u^n - (1 - dt S1/2) u^{n-1}
+                   + dt^2 (V^2 (lap u^n + div phi^{n-1/2}) - S2 u^n - S3 psi^n)] / (1 + dt S1/2)
+        phi_j^{n+1/2} = [(1 - dt zeta_j/2) phi_j^{n-1/2} + dt (a_j d_j u^n + b_j d_j psi^n)] / (1 + dt zeta_j/2)
+        psi^{n+1} = psi^n + dt u^{n+1}
+    then sources f^n are added as (V dt)^2 f^n (Algorithm 1 adds them after
+    the update).  The halo stays zero."""
+    up, uc, v = _f64(u_prev), _f64(u), _f64(vel)
+    nx, ny, nz = _dims(uc, halo)
+    H = halo
+    I = (slice(H, H + nz), slice(H, H + ny), slice(H, H + nx))
+    zx = pml_zeta(nx, width, zeta_max)[None, None, :]
+    zy = pml_zeta(ny, width, zeta_max)[None, :, None]
+    zz = pml_zeta(nz, width, zeta_max, low=not free_top)[:, None, None]
+    S1 = zx + zy + zz
+    S2 = zx * zy + zy * zz + zz * zx
+    S3 = zx * zy * zz
+    a = (zy + zz - zx, zz + zx - zy, zx + zy - zz)
+    b = (zy * zz, zz * zx, zx * zy)
+    zeta = (zx, zy, zz)
+    c = axis_coeffs(4, h)
+    lap = stencil_apply(uc, 4, c, c, c, H)[I]
+
+    def d(f, axis):
+        # central difference along x (axis 0), y (1) or z (2) at the interior
+        lo = [H, H, H]
+        lo[axis] -= 1
+        hi = [H, H, H]
+        hi[axis] += 1
+        m = (slice(hi[2], hi[2] + nz), slice(hi[1], hi[1] + ny), slice(hi[0], hi[0] + nx))
+        p_ = (slice(lo[2], lo[2] + nz), slice(lo[1], lo[1] + ny), slice(lo[0], lo[0] + nx))
+        return (f[m] - f[p_]) / (2.0 * h)
+
+    phi, psi = state["phi"], state["psi"]
+    div = d(phi[0], 0) + d(phi[1], 1) + d(phi[2], 2)
+    V2 = v[I] * v[I]
+    nxt = np.zeros_like(uc)
+    nxt[I] = (2.0 * uc[I] - (1.0 - dt * S1 / 2.0) * up[I]
+              + dt * dt * (V2 * (lap + div) - S2 * uc[I] - S3 * psi[I])) / (1.0 + dt * S1 / 2.0)
+    new_phi = []
+    for j in range(3):
+        f = np.zeros_like(uc)
+        f[I] = ((1.0 - dt * zeta[j] / 2.0) * phi[j][I]
+                + dt * (a[j] * d(uc, j) + b[j] * d(psi, j))) / (1.0 + dt * zeta[j] / 2.0)
+        new_phi.append(f)
+    new_psi = psi.copy()
+    new_psi[I] = psi[I] + dt * nxt[I]
+    state["phi"], state["psi"] = new_phi, new_psi
+    if src_idx is not None and src_f is not None:
+        si = np.asarray(src_idx, np.int64).reshape(-1)
+        sf = np.asarray(src_f, np.float64).reshape(-1)
+        for idx, f in zip(si, sf):
+            i, j, k = int(idx % nx), int((idx // nx) % ny), int(idx // (nx * ny))
+            vv = v[k + H, j + H, i + H]
+            nxt[k + H, j + H, i + H] += (vv * dt) ** 2 * f
+    return nxt
+
+
+def pml_propagate(u_prev, u, vel, dt: float, h: float, halo: int, nsteps: int, width: int, zeta_max: float, *,
+                  free_top: bool = False, t0: int = 0, state=None, src_idx=None, src_amp=None, rec_idx=None,
+                  rec_nt: int | None = None):
+    """Algorithm 1 with the PML: steps t0 .. t0+nsteps-1 (row n of ``src_amp``
+    is f^n, injected while n < its rows).  Returns (u_prev, u, trace, state)
+    with (u_prev, u) = (u^{t0+nsteps-1}, u^{t0+nsteps}) and trace row n =
+    u^{n+1} at the receivers; ``state`` (from :func:`pml_state`, zero if None)
+    carries phi and psi across calls."""
+    a, b = _f64(u_prev).copy(), _f64(u).copy()
+    st = pml_state(a.shape) if state is None else state
+    nx, ny, nz = _dims(b, halo)
+    si = None if src_idx is None else np.asarray(src_idx, np.int64).reshape(-1)
+    sa = None if src_amp is None else _f64(np.asarray(src_amp).reshape(-1, si.size))
+    ri = np.zeros(0, np.int64) if rec_idx is None else np.asarray(rec_idx, np.int64).reshape(-1)
+    rnt = (t0 + nsteps) if rec_nt is None else rec_nt
+    tr = np.zeros((rnt, ri.size))
+    for n in range(t0, t0 + nsteps):
+        f = None if (si is None or n >= sa.shape[0]) else sa[n]
+        nxt = pml_step(a, b, vel, st, dt, h, halo, width, zeta_max, free_top=free_top,
+                       src_idx=si if f is not None else None, src_f=f)
+        a, b = b, nxt
+        if ri.size and n < rnt:
+            flat = b[halo:halo + nz, halo:halo + ny, halo:halo + nx].reshape(-1)
+            tr[n] = flat[ri]
+    return a, b, tr, st
 
 
 # ---------------------------------------------------------------------------
