@@ -18,7 +18,7 @@ import pytest
 import oracle
 import paper_2309_04671_gb300 as gbs
 import workloads as W
-from gpu_util import dev, halo_mask, log_error, need_gpu, to_dev, tol_steps, torch
+from gpu_util import dev, halo_mask, log_error, need_gpu, to_dev, tol_reversal, tol_steps, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -239,7 +239,7 @@ def test_full_size_pairs(layered512):
     gbs.device_status()
     err = max(float(torch.max(torch.abs(pb - to_dev(u)))), float(torch.max(torch.abs(cb - to_dev(up)))))
     log_error(err, "512^3 pairs, 8 + 8 reversed steps (absolute, fields of max 1)")
-    assert err <= tol_steps(16), err
+    assert err <= tol_reversal(16), err
 
 
 def test_full_size_one_pair_sampled_vs_oracle(layered512):

@@ -71,9 +71,10 @@ def test_three_steps_vs_oracle_and_single_step(shape, nsteps):
 
 def test_sources_on_chunk_seams_restart_graph_and_repeat():
     """Sixteen sources (pairs sharing cells) next to the z-chunk seams of a
-    tall grid, receivers on the same cells: 7 + 8 steps (restart at t0 = 7)
-    equal 15 steps bit for bit; a graph replay and repeated runs give the
-    same bits; the result matches the oracle."""
+    tall grid, receivers on the same cells: 6 + 9 steps (restart at t0 = 6)
+    equal 15 steps bit for bit (both run steps 1-12 as four launches, 13-14
+    as a fused pair and 15 as a single step); a graph replay and repeated
+    runs give the same bits; the result matches the oracle."""
     need_gpu()
     nx, ny, nz, nsteps = 128, 48, 512, 15
     ok, tile_y, ctas = gbs.tbn_supported(nx, ny, nz, 4, 3)
@@ -96,8 +97,8 @@ def test_sources_on_chunk_seams_restart_graph_and_repeat():
     tr_full = torch.zeros((nsteps, src.size), device=dev())
     p_full, c_full = run(nsteps, 0, to_dev(up), to_dev(u), tr_full)
     tr_split = torch.zeros((nsteps, src.size), device=dev())
-    p1, c1 = run(7, 0, to_dev(up), to_dev(u), tr_split)
-    p2, c2 = run(8, 7, p1, c1, tr_split)
+    p1, c1 = run(6, 0, to_dev(up), to_dev(u), tr_split)
+    p2, c2 = run(9, 6, p1, c1, tr_split)
     gbs.device_status()
     assert torch.equal(p2, p_full) and torch.equal(c2, c_full) and torch.equal(tr_split, tr_full)
     s = torch.cuda.Stream()
