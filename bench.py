@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32",
                     help="wave-field storage of the main timed path (arithmetic is FP32 in all)")
-    ap.add_argument("--forms", default="single,storage,radius,errors,precision,absorb,batched,adjoint,suite,tblock",
+    ap.add_argument("--forms", default="single,storage,radius,errors,precision,absorb,pml,batched,adjoint,suite,tblock",
                     help="comma list of extra forms to measure after the main line, or 'none'")
     ap.add_argument("--no-forms", action="store_true", help="same as --forms none")
     ap.add_argument("--adj-n", type=int, default=256, help="adjoint form: interior side")
@@ -933,6 +933,52 @@ def tblock_form(args, stream, hbm, sizes=(256, 384, 512), nsteps=96):
     return out
 
 
+def pml_form(prob, args, stream, hbm, width=20):
+    """The headline workload inside a PML of `width` cells (Grote & Sim
+    equations; the inner box on the TMA kernel, six slabs on the slab kernel
+    with their auxiliary fields), against the plain loop and the damping
+    layer of the same width.  Algorithmic bytes per step: 16 per inner point,
+    48 per slab point (u, u_prev, vel, u_next; phi x3 and psi read and
+    written)."""
+    import torch
+    import paper_2309_04671_gb300 as gbs
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n, halo, ns = prob.nx, prob.halo, prob.nsteps
+    vel = torch.from_numpy(prob.vel).to(dev)
+    si, sa = torch.from_numpy(prob.src_idx).to(dev), torch.from_numpy(prob.src_amp).to(dev)
+    vmax = float(prob.meta["vmax"])
+    zmax = 3 * vmax * np.log(1e3) / (2 * (width - 1) * prob.h)
+    state = gbs.pml_state(vel, halo, width)
+    a, b = torch.zeros_like(vel), torch.zeros_like(vel)
+    st = {"a": a, "b": b}
+
+    def run():
+        st["a"], st["b"] = gbs.wave_propagate_pml(st["a"], st["b"], vel, prob.dt, prob.h, halo, ns, width, zmax,
+                                                  state=state, state_init=True, src_idx=si, src_amp=sa)
+    for _ in range(2):
+        run()
+    gbs.device_status()
+    k = 3
+    ms, kms, kl = time_calls(run, k, stream)
+    gbs.device_status()
+    inner = (n - 2 * width) ** 3
+    slab = n ** 3 - inner
+    kernel_ms_per_step = kms * kl / (k * ns) if kms else None
+    alg = 16 * inner + 48 * slab
+    ach = alg / (kernel_ms_per_step * 1e-3) / 1e9 if kernel_ms_per_step else None
+    out = {"workload": f"{n}^3 layered workload, PML of {width} cells on every face, zeta_max "
+                       f"{zmax:.1f} 1/s (3 v_max ln(1e3) / (2 (W-1) h)), {ns} steps per call",
+           "value": prob.npoints * ns / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_call": ms, "calls": k,
+           "slab_points": slab, "inner_points": inner,
+           "state_bytes": int(state.numel()),
+           "kernel_ms_per_step": kernel_ms_per_step,
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                        "frac": ach / hbm if ach else None, "alg_bytes_per_step": alg}}
+    del a, b, st, state
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -1088,6 +1134,8 @@ def run_ours(args):
             forms["absorbing_layer"] = absorb_form(prob, args, stream, hbm)
         if "suite" in wanted:
             forms["suite"] = suite_form(args, stream, hbm)
+        if "pml" in wanted:
+            forms["pml"] = pml_form(prob, args, stream, hbm)
         if "tblock" in wanted:
             forms["temporal_blocking"] = tblock_form(args, stream, hbm)
         if "adjoint" in wanted:

@@ -257,6 +257,47 @@ gbs_status gbs_wave_propagate_tbn(float *u_prev, float *u, const float *vel, flo
                                   int64_t t0, const gbs_src *src, const gbs_rec *rec, int time_block, void *work,
                                   size_t work_bytes, const gbs_opts *opts, void *stream);
 /*
+ * Algorithm 1 with a perfectly matched layer (PML) around the domain.  The
+ * paper runs its operator inside a PML (Sec. 2.2: the PML region applies the
+ * 25-point stencil and a 7-point star stencil to a second array) and gives
+ * no equations for it; these are the equations of Grote & Sim (2010) for the
+ * second-order wave equation, with zeta_j = zeta_j(x_j):
+ *   u_tt + S1 u_t + S2 u + S3 psi = V^2 (lap u + div phi),  psi_t = u,
+ *   phi_j,t = -zeta_j phi_j + a_j d_j u + b_j d_j psi,
+ * S1 = zx+zy+zz, S2 = zx zy+zy zz+zz zx, S3 = zx zy zz, a_j = (the other two
+ * summed) - zeta_j, b_j = the other two multiplied.  Discretised with the
+ * 25-point lap of gbs_wave_step, central differences (a 7-point star) for
+ * d_j and div, u_t centred over the leapfrog levels:
+ *   u^{n+1} = [2u^n - (1 - dt S1/2) u^{n-1} + dt^2 (V^2 (lap u^n + div phi^{n-1/2})
+ *             - S2 u^n - S3 psi^n)] / (1 + dt S1/2)
+ *   phi_j^{n+1/2} = [(1 - dt zeta_j/2) phi_j^{n-1/2} + dt (a_j d_j u^n + b_j d_j psi^n)] / (1 + dt zeta_j/2)
+ *   psi^{n+1} = psi^n + dt u^{n+1}
+ * then the sources, (V dt)^2 f^n, and the receivers.  zeta_j = zeta_max
+ * ((W-1-d)/(W-1))^2 at distance d < W-1 cells from an absorbing face of axis
+ * j, zero elsewhere (free_top = 1: the face z = 0 does not absorb).
+ * Seven regions: the inner box (W cells from every absorbing face) runs the
+ * plain step on the TMA kernel; the six slabs run the PML step above, with
+ * phi and psi stored only on the slabs.
+ *   u_prev, u, vel, dt, h, sizes, halo, nsteps, t0, src, rec
+ *                 as gbs_wave_propagate (parity rule included); halo % 4 ==
+ *                 0, nx % 4 == 0, 16-byte aligned fields.
+ *   width         W, a multiple of 4 in 4..64, with nx, ny >= 2W + 4 and an
+ *                 inner box of at least one plane.
+ *   zeta_max      [1/s], >= 0 (e.g. 3 v_max ln(1/R) / (2 (W-1) h), R = 1e-3).
+ *   state         DEVICE scratch of gbs_pml_state_bytes(nx, ny, nz, width,
+ *                 free_top) bytes, 16-byte aligned, owned by the caller: two
+ *                 copies of phi and psi on the slabs; it carries them from one
+ *                 call to the next (restart at t0 with the same state).
+ *   state_init    1: zero the state first (phi^{-1/2} = 0, psi^{t0} = 0).
+ * Errors: GBS_EINVAL (sizes, width, state), GBS_EALIGN, GBS_ECUDA.
+ */
+size_t gbs_pml_state_bytes(int64_t nx, int64_t ny, int64_t nz, int width, int free_top);
+gbs_status gbs_wave_propagate_pml(float *u_prev, float *u, const float *vel, float dt, float h,
+                                  int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps, int64_t t0,
+                                  const gbs_src *src, const gbs_rec *rec, int width, float zeta_max, int free_top,
+                                  void *state, size_t state_bytes, int state_init, void *stream);
+
+/*
  * Algorithm 1 on HOST fields: the same steps as gbs_wave_propagate
  * (time_block = 0) or gbs_wave_propagate_tb (time_block = 2), with every
  * host<->device copy inside the call.  Enqueued on `stream`: the fields,

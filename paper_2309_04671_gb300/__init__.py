@@ -30,6 +30,7 @@ STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4
 EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
            "gbs_wave_propagate_lp", "gbs_tb_workspace_bytes", "gbs_wave_propagate_tb", "gbs_tb_supported",
            "gbs_tbn_workspace_bytes", "gbs_wave_propagate_tbn", "gbs_tbn_supported",
+           "gbs_pml_state_bytes", "gbs_wave_propagate_pml",
            "gbs_selftest_tb_timeout", "gbs_host_workspace_bytes", "gbs_wave_propagate_host", "gbs_check_cfl",
            "gbs_pipeline_create", "gbs_pipeline_submit", "gbs_pipeline_wait", "gbs_pipeline_workspace_bytes",
            "gbs_pipeline_destroy",
@@ -113,6 +114,12 @@ def load() -> ctypes.CDLL:
         lib.gbs_wave_propagate_tb.restype = c_int
         lib.gbs_tb_supported.argtypes = [i64, i64, i64, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
         lib.gbs_tb_supported.restype = c_int
+        lib.gbs_pml_state_bytes.argtypes = [i64, i64, i64, c_int, c_int]
+        lib.gbs_pml_state_bytes.restype = ctypes.c_size_t
+        lib.gbs_wave_propagate_pml.argtypes = [vp, vp, vp, c_float, c_float, i64, i64, i64, c_int, i64, i64,
+                                               ctypes.POINTER(_Src), ctypes.POINTER(_Rec), c_int, c_float, c_int,
+                                               vp, ctypes.c_size_t, c_int, vp]
+        lib.gbs_wave_propagate_pml.restype = c_int
         lib.gbs_tbn_workspace_bytes.argtypes = [i64, i64, i64, c_int, c_int]
         lib.gbs_tbn_workspace_bytes.restype = ctypes.c_size_t
         lib.gbs_wave_propagate_tbn.argtypes = [vp, vp, vp, c_float, c_float, i64, i64, i64, c_int, i64, i64,
@@ -576,6 +583,46 @@ def wave_propagate_tbn(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor,
     _check(load().gbs_wave_propagate_tbn(p[0], p[1], p[2], float(dt), float(h), nx, ny, nz, halo, int(nsteps),
                                          int(t0), _ptr(src), _ptr(rec), int(time_block), work.data_ptr(),
                                          work.numel() * work.element_size(), ctypes.byref(opts), _stream(stream)))
+    return (u, u_prev) if nsteps % 2 else (u_prev, u)
+
+
+def pml_state_bytes(nx: int, ny: int, nz: int, width: int, free_top: bool = False) -> int:
+    """Bytes of the PML state (two copies of phi and psi on the six slabs); 0 for unusable sizes."""
+    return int(load().gbs_pml_state_bytes(int(nx), int(ny), int(nz), int(width), int(bool(free_top))))
+
+
+def pml_state(u: torch.Tensor, halo: int, width: int, free_top: bool = False) -> torch.Tensor:
+    """A device byte tensor for the PML state of fields shaped like u (contents set by state_init)."""
+    nx, ny, nz = _dims(u, halo)
+    nb = pml_state_bytes(nx, ny, nz, width, free_top)
+    if nb == 0:
+        raise GbsError(GBS_EINVAL, "no PML of this width fits these sizes")
+    return torch.empty(nb, dtype=torch.uint8, device=u.device)
+
+
+def wave_propagate_pml(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, dt: float, h: float, halo: int,
+                       nsteps: int, width: int, zeta_max: float, *, free_top: bool = False, t0: int = 0,
+                       state: Optional[torch.Tensor] = None, state_init: Optional[bool] = None, src_idx=None,
+                       src_amp=None, rec_idx=None, rec_trace=None, stream=None):
+    """Algorithm 1 with the PML (device tensors): the inner box on the TMA
+    kernel, the six slabs with their auxiliary fields on the slab kernel.
+    ``state`` (from pml_state) carries phi and psi between calls; it is zeroed
+    when ``state_init`` (default: when a new state is allocated).  Returns
+    (prev, cur) as wave_propagate."""
+    p = [_field(t, n) for t, n in ((u_prev, "u_prev"), (u, "u"), (vel, "vel"))]
+    _same_shape(u, u_prev, vel)
+    nx, ny, nz = _dims(u, halo)
+    if state is None:
+        state = pml_state(u, halo, width, free_top)
+        state_init = True if state_init is None else state_init
+    if not (state.is_cuda and state.is_contiguous()):
+        raise ValueError("state must be a contiguous device tensor")
+    src = _make_src(src_idx, src_amp)
+    rec = _make_rec(rec_idx, rec_trace)
+    _check(load().gbs_wave_propagate_pml(p[0], p[1], p[2], float(dt), float(h), nx, ny, nz, halo, int(nsteps),
+                                         int(t0), _ptr(src), _ptr(rec), int(width), float(zeta_max),
+                                         int(bool(free_top)), state.data_ptr(), state.numel() * state.element_size(),
+                                         int(bool(state_init)), _stream(stream)))
     return (u, u_prev) if nsteps % 2 else (u_prev, u)
 
 

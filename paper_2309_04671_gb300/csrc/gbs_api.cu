@@ -95,6 +95,27 @@ gbs_status make_map(CUtensorMap *m, const void *base, const Grid &g, int bw, int
     return GBS_OK;
 }
 
+// FP32 tensor map over a box of dims (dx, dy, dz) elements inside a larger
+// padded array of row pitch px and py rows per plane (a view of a sub-box),
+// box bw x bh x 1.
+gbs_status make_map_view(CUtensorMap *m, const void *base, int64_t dx, int64_t dy, int64_t dz, int64_t px,
+                         int64_t py, int bw, int bh)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc)
+        return fail(GBS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[3] = {(cuuint64_t)dx, (cuuint64_t)dy, (cuuint64_t)dz};
+    const cuuint64_t strides[2] = {(cuuint64_t)px * 4, (cuuint64_t)(px * py) * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(GBS_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return GBS_OK;
+}
+
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int64_t field_elems(const Grid &g) { return g.px * g.py * (g.nz + 2 * g.halo); }
@@ -826,6 +847,133 @@ extern "C" gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float
 {
     return gbs_wave_propagate_tbn(u_prev, u, vel, dt, h, nx, ny, nz, halo, nsteps, t0, src, rec, 2, work, work_bytes,
                                   opts, stream);
+}
+
+namespace gbs {
+namespace {
+// PML sizes: width a multiple of 4 in 4..64 (the inner box must start on a
+// 16-byte boundary for its TMA kernel), an inner box of at least 4 x 1 x 1.
+gbs_status pml_check(int64_t nx, int64_t ny, int64_t nz, int w, int free_top)
+{
+    if (w < 4 || w > 64 || w % 4 != 0)
+        return fail(GBS_EINVAL, "PML width must be a multiple of 4 in 4..64 (got %d)", w);
+    const int64_t zl = free_top ? 0 : w;
+    if (nx - 2 * w < 4 || ny - 2 * w < 1 || nz - w - zl < 1)
+        return fail(GBS_EINVAL, "the interior (%lld, %lld, %lld) leaves no inner box inside a PML of width %d",
+                    (long long)nx, (long long)ny, (long long)nz, w);
+    return GBS_OK;
+}
+}  // namespace
+}  // namespace gbs
+
+extern "C" size_t gbs_pml_state_bytes(int64_t nx, int64_t ny, int64_t nz, int width, int free_top)
+{
+    if (check_dims(nx, ny, nz, 4) != GBS_OK || pml_check(nx, ny, nz, width, free_top) != GBS_OK) {
+        t_err[0] = 0;
+        return 0;
+    }
+    return (size_t)2 * 4 * (size_t)pml_slab_points(nx, ny, nz, width, free_top != 0) * 4;
+}
+
+extern "C" gbs_status gbs_wave_propagate_pml(float *u_prev, float *u, const float *vel, float dt, float h,
+                                             int64_t nx, int64_t ny, int64_t nz, int halo, int64_t nsteps,
+                                             int64_t t0, const gbs_src *src, const gbs_rec *rec, int width,
+                                             float zeta_max, int free_top, void *state, size_t state_bytes,
+                                             int state_init, void *stream)
+{
+    const TraceRange trace_range("gbs_wave_propagate_pml");
+    t_err[0] = 0;
+    gbs_status s = check_dims(nx, ny, nz, halo);
+    if (s != GBS_OK)
+        return s;
+    if (nsteps < 0 || t0 < 0)
+        return fail(GBS_EINVAL, "nsteps and t0 must be >= 0");
+    if ((s = pml_check(nx, ny, nz, width, free_top)) != GBS_OK)
+        return s;
+    if (!(zeta_max >= 0.f) || !std::isfinite(zeta_max))
+        return fail(GBS_EINVAL, "zeta_max must be finite and >= 0");
+    if ((s = check_src_rec(src, rec)) != GBS_OK)
+        return s;
+    const Grid g = dense_grid(nx, ny, nz, halo);
+    if (!tma_shape_ok(g) || halo < 4)
+        return fail(GBS_EALIGN, "the PML path needs halo %% 4 == 0 (>= 4) and nx %% 4 == 0");
+    if (u_prev == u)
+        return fail(GBS_EINVAL, "u_prev and u are the same buffer");
+    if ((s = check_wave_fields(g, u_prev, u, u_prev, vel, dt, h)) != GBS_OK)
+        return s;
+    if (overlap(u_prev, u, field_elems(g)))
+        return fail(GBS_EINVAL, "u_prev and u overlap");
+    if (!aligned16(u_prev) || !aligned16(u) || !aligned16(vel))
+        return fail(GBS_EALIGN, "the PML path needs 16-byte aligned fields");
+    const int64_t npts = pml_slab_points(nx, ny, nz, width, free_top != 0);
+    const size_t need = (size_t)2 * 4 * (size_t)npts * 4;
+    if (!state || state_bytes < need || !aligned16(state))
+        return fail(GBS_EINVAL, "PML state needs %zu bytes, 16-byte aligned (gbs_pml_state_bytes)", need);
+    {
+        const char *sb = static_cast<const char *>(state);
+        for (const float *f : {static_cast<const float *>(u_prev), static_cast<const float *>(u), vel}) {
+            const char *fb = reinterpret_cast<const char *>(f);
+            if (fb < sb + need && sb < fb + field_elems(g) * 4)
+                return fail(GBS_EINVAL, "the PML state overlaps a field");
+        }
+    }
+    if (nsteps == 0 && !state_init)
+        return GBS_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float *aux = static_cast<float *>(state);
+    cudaError_t e;
+    if (state_init && (e = cudaMemsetAsync(state, 0, need, st)) != cudaSuccess)
+        return cuda_fail(e, "PML state");
+    if (nsteps == 0)
+        return GBS_OK;
+    // the inner box as a view of the padded fields: interior origin shifted by
+    // (w, w, zl), the same halo (its halo cells are the slabs' current values)
+    const int64_t w = width, zl = free_top ? 0 : width;
+    Grid gv = g;
+    gv.nx = nx - 2 * w;
+    gv.ny = ny - 2 * w;
+    gv.nz = nz - w - zl;
+    const int64_t off = w + g.px * (w + g.py * zl);
+    const int ty = 16;
+    StepPlan sp[2];
+    float *fld[2] = {u_prev, u};
+    for (int q = 0; q < 2; ++q) {
+        // parity q reads (u_prev, u) = (fld[q], fld[1-q]) and writes fld[q]
+        sp[q].kernel = 1;
+        sp[q].tile_y = ty;
+        sp[q].zchunk = 0;
+        sp[q].storage = GBS_F32;
+        const int64_t dx = gv.nx + 2 * halo, dy = gv.ny + 2 * halo, dz = gv.nz + 2 * halo;
+        if ((s = make_map_view(&sp[q].tma.u, fld[1 - q] + off, dx, dy, dz, g.px, g.py, 64 + 8, ty + 8)) != GBS_OK ||
+            (s = make_map_view(&sp[q].tma.prev, fld[q] + off, dx, dy, dz, g.px, g.py, 64, ty)) != GBS_OK ||
+            (s = make_map_view(&sp[q].tma.vel, vel + off, dx, dy, dz, g.px, g.py, 64, ty)) != GBS_OK)
+            return s;
+    }
+    if ((e = tma_prepare_wave(GBS_F32, ty)) != cudaSuccess)
+        return cuda_fail(e, "kernel attributes");
+    float c5[5];
+    for (int m = 0; m < 5; ++m)
+        c5[m] = (float)kFd2[3][m];
+    for (int64_t i = 0; i < nsteps; ++i) {
+        const int q = (int)(i & 1);
+        float *prev = fld[q], *cur = fld[1 - q];
+        const int64_t t = t0 + i;
+        if ((s = run_step(sp[q], gv, prev + off, cur + off, prev + off, vel + off, dt, h, nullptr, nullptr, t,
+                          nullptr, st)) != GBS_OK)
+            return s;
+        const float *sin = aux + (size_t)(t & 1) * 4 * npts;
+        float *sout = aux + (size_t)((t + 1) & 1) * 4 * npts;
+        cudaEvent_t e0 = prof_begin(st);
+        e = launch_pml(g, prev, cur, prev, vel, dt, h, width, zeta_max, free_top != 0, c5, sin, sout, st);
+        prof_end(e0, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "PML slab launch");
+        if ((e = launch_inject(g, prev, vel, dt, src, t, st)) != cudaSuccess)
+            return cuda_fail(e, "source injection launch");
+        if ((e = launch_record(g, prev, rec, t, st)) != cudaSuccess)
+            return cuda_fail(e, "receiver launch");
+    }
+    return GBS_OK;
 }
 
 namespace gbs {

@@ -238,6 +238,16 @@ cudaError_t launch_fold(float *gp, double *g, int64_t n, cudaStream_t st);
 // zero all of nfields fields (stride elements apart, layout g) outside the box a step writes
 cudaError_t launch_zero_shell(float *base, int64_t stride, int nfields, const Grid &g, cudaStream_t st);
 
+// PML slabs (k_pml.cu): compact points of the six boundary slabs of width w
+// (the z-low slab left out with a reflecting top), and one step of the
+// slabs: u_next at slab points, the auxiliary fields (phi x3, psi; each
+// pml_slab_points floats) from state_in to state_out.  c5: unit-spacing
+// weights of the 25-point operator.
+int64_t pml_slab_points(int64_t nx, int64_t ny, int64_t nz, int w, bool free_top);
+cudaError_t launch_pml(const Grid &g, const float *u_prev, const float *u, float *u_next, const float *vel,
+                       float dt, float h, int w, float zeta_max, bool free_top, const float *c5,
+                       const float *state_in, float *state_out, cudaStream_t st);
+
 // Error norms (k_norms.cu): one FP64 partial record of 4 doubles per block
 // of kNormRowsPerBlock rows; `out` receives kNormOut doubles.
 constexpr int kNormRowsPerBlock = 64;

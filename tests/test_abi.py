@@ -329,3 +329,28 @@ def test_pipeline_binding_raises_on_bad_arguments(lib):
     if not gbs.torch.cuda.is_available():
         with pytest.raises(gbs.GbsError):            # no device: streams and workspaces cannot be made
             gbs.Pipeline(8, 8, 8, 4)
+
+
+def test_pml_state_size_and_validation(lib, no_device):
+    # two copies of (phi x3, psi) on the slabs: z slabs of full planes, then
+    # y slabs over the middle planes, then x slabs over the middle rows
+    nx, ny, nz, w = 48, 44, 40, 8
+    pts = nx * ny * 2 * w + 2 * nx * w * (nz - 2 * w) + 2 * w * (ny - 2 * w) * (nz - 2 * w)
+    assert lib.gbs_pml_state_bytes(nx, ny, nz, w, 0) == 2 * 4 * pts * 4
+    pts_top = nx * ny * w + 2 * nx * w * (nz - w) + 2 * w * (ny - 2 * w) * (nz - w)
+    assert lib.gbs_pml_state_bytes(nx, ny, nz, w, 1) == 2 * 4 * pts_top * 4
+    for bad in (0, 6, 68):
+        assert lib.gbs_pml_state_bytes(nx, ny, nz, bad, 0) == 0
+    assert lib.gbs_pml_state_bytes(19, ny, nz, w, 0) == 0
+    fake = [ctypes.c_void_p(1 << 20), ctypes.c_void_p(2 << 20), ctypes.c_void_p(3 << 20), ctypes.c_void_p(4 << 20)]
+
+    def call(width=w, zmax=10.0, state=fake[3], nbytes=1 << 30, nx_=nx):
+        return lib.gbs_wave_propagate_pml(fake[0], fake[1], fake[2], ctypes.c_float(1e-3), ctypes.c_float(10.0),
+                                          nx_, ny, nz, 4, 3, 0, None, None, width, ctypes.c_float(zmax), 0, state,
+                                          nbytes, 1, None)
+    assert call(width=6) == gbs.GBS_EINVAL
+    assert call(zmax=-1.0) == gbs.GBS_EINVAL
+    assert call(state=None) == gbs.GBS_EINVAL
+    assert call(nbytes=1024) == gbs.GBS_EINVAL
+    assert call(state=ctypes.c_void_p((4 << 20) + 4)) == gbs.GBS_EINVAL
+    assert call(state=fake[1]) == gbs.GBS_EINVAL          # over a field
