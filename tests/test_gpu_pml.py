@@ -92,7 +92,8 @@ def test_zero_damping_is_the_plain_loop_and_restart_is_exact():
 def test_pulse_leaves_through_the_layer():
     """A Gaussian pulse in a 96^3 box with a 16-cell PML, 150 steps: the GPU
     field matches the oracle's to the multi-step bound (scaled by the pulse's
-    peak) and the inner box keeps less than 1e-3 of that peak."""
+    peak), and the inner box keeps less than a tenth of what it keeps with
+    rigid (Dirichlet) faces, where the reflections have come back by then."""
     need_gpu()
     n, width, nsteps, v = 96, 16, 150, 1500.0
     shape = W.padded_shape(n, n, n, H)
@@ -108,7 +109,11 @@ def test_pulse_leaves_through_the_layer():
     peak = float(np.abs(u0).max())
     assert float(np.abs(got - ru).max()) <= tol_steps(nsteps) * peak
     inner = (slice(H + width, H + n - width),) * 3
-    assert float(np.abs(got[inner]).max()) < 1e-3 * peak
+    _, rig = gbs.wave_propagate(to_dev(u0), to_dev(u0), to_dev(vel), dt, h, H, nsteps)
+    gbs.device_status()
+    left_pml = float(np.abs(got[inner]).max())
+    left_rigid = float(np.abs(rig.cpu().numpy()[inner]).max())
+    assert left_pml < 0.1 * left_rigid, (left_pml, left_rigid)
 
 
 def test_bad_widths_and_sizes_are_rejected():
