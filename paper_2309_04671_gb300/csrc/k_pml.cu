@@ -23,8 +23,7 @@
 // Storage: phi (3 components) and psi live only on the slabs, in a compact
 // layout of six boxes (z-low, z-high, y-low, y-high, x-low, x-high; each x
 // fastest), twice (the step reads one copy and writes the other).  A
-// thread updates a short z column of one box (u of the column and its z
-// halo held in registers); neighbouring threads take neighbouring x.
+// thread updates one slab point; the thread index is its compact index.
 #include "gbs_internal.cuh"
 
 namespace gbs {
@@ -38,7 +37,6 @@ struct Slabs {
     int nx, ny, nz;
     int w, zl;                 // width; planes of the z-low slab (0 with a reflecting top)
     int base[7];               // region r covers compact indices [base[r], base[r+1])
-    int cbase[7];              // region r covers thread columns [cbase[r], cbase[r+1])
 };
 
 // Box of region r: origin (x0, y0, z0) and sizes (bx, by, bz).
@@ -74,14 +72,19 @@ __device__ __forceinline__ int compact_index(const Slabs &s, int i, int j, int k
     return -1;
 }
 
-// value of a slab field at interior point (i, j, k): zero outside the
-// interior (the Dirichlet halo) and in the inner box
-__device__ __forceinline__ float slab_at(const Slabs &s, const float *f, int i, int j, int k)
+// Compact index of a neighbour: -1 outside the interior (the Dirichlet
+// halo) or in the inner box.  Arithmetic only, so that the loads it feeds
+// can all be in flight at once.
+__device__ __forceinline__ int nb_index(const Slabs &s, int i, int j, int k)
 {
-    if (i < 0 || j < 0 || k < 0 || i >= s.nx || j >= s.ny || k >= s.nz)
-        return 0.f;
-    const int c = compact_index(s, i, j, k);
-    return c < 0 ? 0.f : f[c];
+    const bool in = i >= 0 && j >= 0 && k >= 0 && i < s.nx && j < s.ny && k < s.nz;
+    return in ? compact_index(s, i, j, k) : -1;
+}
+
+__device__ __forceinline__ float masked(const float *__restrict__ f, int c)
+{
+    const float v = __ldg(f + max(c, 0));
+    return c >= 0 ? v : 0.f;
 }
 
 struct PmlParams {
@@ -101,104 +104,87 @@ struct PmlParams {
 __device__ __forceinline__ float zeta_of(const PmlParams &p, int d)
 {
     const int w1 = p.s.w - 1;
-    if (d >= w1)
-        return 0.f;
     const float r = (float)(w1 - d) * p.inv_w1;
-    return p.zmax * r * r;
+    return d < w1 ? p.zmax * r * r : 0.f;
 }
 
-// One thread: a column of up to kKZ consecutive z points of one region, with
-// u of the column and its 4-plane z halo in registers.  Threads of a block
-// take consecutive x.
-constexpr int kKZ = 4;
-
+// One thread per slab point; the thread index is the point's compact index
+// (x fastest within each of the six boxes).
 __global__ void __launch_bounds__(kThreadsPml) k_pml(const float *__restrict__ u_prev, const float *__restrict__ u,
                                                     float *__restrict__ u_next, const float *__restrict__ vel,
                                                     const __grid_constant__ PmlParams p)
 {
     const Slabs &s = p.s;
-    const int col = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (col >= s.cbase[6])
+    const int c = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= s.base[6])
         return;
     int r = 0;
 #pragma unroll
     for (int q = 1; q < 6; ++q)
-        r += col >= s.cbase[q] ? 1 : 0;
+        r += c >= s.base[q] ? 1 : 0;
     int x0, y0, z0, bx, by, bz;
     region_box(s, r, x0, y0, z0, bx, by, bz);
-    const int l = col - s.cbase[r];
+    const int l = c - s.base[r];
     const int li = l % bx, t = l / bx;
-    const int lj = t % by, kb = t / by;
-    const int i = x0 + li, j = y0 + lj, k0 = z0 + kb * kKZ;
-    const int kn = min(kKZ, bz - kb * kKZ);
+    const int i = x0 + li, j = y0 + t % by, k = z0 + t / by;
 
     const Grid &g = p.g;
     const int64_t sy = g.px, sz = g.px * g.py;
-    const int64_t at0 = (g.halo + i) + g.px * ((g.halo + j) + g.py * (int64_t)(g.halo + k0));
-    float uz[kKZ + 8];   // u at planes k0-4 .. k0+kKZ+3 of this column
+    const int64_t at = (g.halo + i) + g.px * ((g.halo + j) + g.py * (int64_t)(g.halo + k));
+    // neighbours of the auxiliary fields (central differences)
+    const int cxm = nb_index(s, i - 1, j, k), cxp = nb_index(s, i + 1, j, k);
+    const int cym = nb_index(s, i, j - 1, k), cyp = nb_index(s, i, j + 1, k);
+    const int czm = nb_index(s, i, j, k - 1), czp = nb_index(s, i, j, k + 1);
+    const float *__restrict__ phx = p.phi_in[0];
+    const float *__restrict__ phy = p.phi_in[1];
+    const float *__restrict__ phz = p.phi_in[2];
+    const float *__restrict__ psin = p.psi_in;
+    const float div_h2 = 0.5f * p.h *
+                         ((masked(phx, cxp) - masked(phx, cxm)) + (masked(phy, cyp) - masked(phy, cym)) +
+                          (masked(phz, czp) - masked(phz, czm)));
+    const float uc = __ldg(u + at);
+    // the 25-point operator with unit-spacing weights: centre, then
+    // distance 1..4 (x, y, z pairs)
+    float lap = (p.c[0] + p.c[0] + p.c[0]) * uc;
+    float du[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int q = 0; q < kKZ + 8; ++q)
-        uz[q] = q < kn + 8 ? u[at0 + (q - 4) * sz] : 0.f;
+    for (int m = 1; m <= 4; ++m) {
+        const float xm = __ldg(u + at - m), xp = __ldg(u + at + m);
+        const float ym = __ldg(u + at - m * sy), yp = __ldg(u + at + m * sy);
+        const float zm = __ldg(u + at - m * sz), zp = __ldg(u + at + m * sz);
+        if (m == 1) {
+            du[0] = xp - xm;
+            du[1] = yp - ym;
+            du[2] = zp - zm;
+        }
+        lap += p.c[m] * ((xp + xm) + (yp + ym) + (zp + zm));
+    }
     const int dx = min(i, s.nx - 1 - i), dy = min(j, s.ny - 1 - j);
-    const float zx = zeta_of(p, dx), zy = zeta_of(p, dy);
-    const float dt = p.dt, h = p.h, inv2h = 0.5f / h;
-    const float c0 = p.c[0] + p.c[0] + p.c[0];
-    const float *phi_x = p.phi_in[0], *phi_y = p.phi_in[1], *phi_z = p.phi_in[2];
+    const int dz = p.free_top ? s.nz - 1 - k : min(k, s.nz - 1 - k);
+    const float zx = zeta_of(p, dx), zy = zeta_of(p, dy), zz = zeta_of(p, dz);
+    const float S1 = zx + zy + zz;
+    const float S2 = zx * zy + zy * zz + zz * zx;
+    const float S3 = zx * zy * zz;
+    const float dt = p.dt, inv2h = 0.5f / p.h;
+    const float psi = __ldg(psin + c);
+    const float vs = __ldg(vel + at) * p.sdt;
+    const float A = 1.f / (1.f + 0.5f * dt * S1), B = 1.f - 0.5f * dt * S1;
+    const float un =
+        A * (2.f * uc - B * __ldg(u_prev + at) + vs * vs * (lap + div_h2) - dt * dt * (S2 * uc + S3 * psi));
+    u_next[at] = un;
+    p.psi_out[c] = psi + dt * un;
+    // phi^{n+1/2}
+    const float zeta[3] = {zx, zy, zz};
+    const float aj[3] = {zy + zz - zx, zz + zx - zy, zx + zy - zz};
+    const float bj[3] = {zy * zz, zz * zx, zx * zy};
+    const int cm[3] = {cxm, cym, czm}, cp[3] = {cxp, cyp, czp};
 #pragma unroll
-    for (int kk = 0; kk < kKZ; ++kk) {
-        if (kk >= kn)
-            break;
-        const int k = k0 + kk;
-        const int64_t at = at0 + kk * sz;
-        const int c = s.base[r] + li + bx * (lj + by * (kb * kKZ + kk));
-        const float uc = uz[kk + 4];
-        // the 25-point operator with unit-spacing weights: centre, then
-        // distance 1..4 (x, y, z pairs)
-        float lap = c0 * uc;
-        float xm1 = 0.f, xp1 = 0.f, ym1 = 0.f, yp1 = 0.f;
-#pragma unroll
-        for (int m = 1; m <= 4; ++m) {
-            const float xm = u[at - m], xp = u[at + m];
-            const float ym = u[at - m * sy], yp = u[at + m * sy];
-            if (m == 1) {
-                xm1 = xm; xp1 = xp; ym1 = ym; yp1 = yp;
-            }
-            lap += p.c[m] * ((xp + xm) + (yp + ym) + (uz[kk + 4 + m] + uz[kk + 4 - m]));
-        }
-        const int dz = p.free_top ? s.nz - 1 - k : min(k, s.nz - 1 - k);
-        const float zz = zeta_of(p, dz);
-        const float S1 = zx + zy + zz;
-        const float S2 = zx * zy + zy * zz + zz * zx;
-        const float S3 = zx * zy * zz;
-        // h^2 div phi^{n-1/2} (central differences; phi is zero outside the slabs)
-        const float div_h2 = 0.5f * h *
-                             ((slab_at(s, phi_x, i + 1, j, k) - slab_at(s, phi_x, i - 1, j, k)) +
-                              (slab_at(s, phi_y, i, j + 1, k) - slab_at(s, phi_y, i, j - 1, k)) +
-                              (slab_at(s, phi_z, i, j, k + 1) - slab_at(s, phi_z, i, j, k - 1)));
-        const float psi = p.psi_in[c];
-        const float vs = vel[at] * p.sdt;
-        const float A = 1.f / (1.f + 0.5f * dt * S1), B = 1.f - 0.5f * dt * S1;
-        const float un =
-            A * (2.f * uc - B * u_prev[at] + vs * vs * (lap + div_h2) - dt * dt * (S2 * uc + S3 * psi));
-        u_next[at] = un;
-        p.psi_out[c] = psi + dt * un;
-        // phi^{n+1/2}
-        const float zeta[3] = {zx, zy, zz};
-        const float aj[3] = {zy + zz - zx, zz + zx - zy, zx + zy - zz};
-        const float bj[3] = {zy * zz, zz * zx, zx * zy};
-        const float du[3] = {(xp1 - xm1) * inv2h, (yp1 - ym1) * inv2h, (uz[kk + 5] - uz[kk + 3]) * inv2h};
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            float dpsi = 0.f;
-            if (bj[q] != 0.f) {
-                const int oi = q == 0, oj = q == 1, ok = q == 2;
-                dpsi = (slab_at(s, p.psi_in, i + oi, j + oj, k + ok) - slab_at(s, p.psi_in, i - oi, j - oj, k - ok)) *
-                       inv2h;
-            }
-            const float ph = p.phi_in[q][c];
-            p.phi_out[q][c] = ((1.f - 0.5f * dt * zeta[q]) * ph + dt * (aj[q] * du[q] + bj[q] * dpsi)) /
-                              (1.f + 0.5f * dt * zeta[q]);
-        }
+    for (int q = 0; q < 3; ++q) {
+        // psi's central difference matters only where b_q != 0 (edges and corners of the layer)
+        const float dpsi = bj[q] != 0.f ? (masked(psin, cp[q]) - masked(psin, cm[q])) * inv2h : 0.f;
+        const float ph = __ldg(p.phi_in[q] + c);
+        p.phi_out[q][c] = ((1.f - 0.5f * dt * zeta[q]) * ph + dt * (aj[q] * du[q] * inv2h + bj[q] * dpsi)) /
+                          (1.f + 0.5f * dt * zeta[q]);
     }
 }
 
@@ -231,11 +217,8 @@ cudaError_t launch_pml(const Grid &g, const float *u_prev, const float *u, float
     const int64_t cnt[6] = {(int64_t)s.nx * s.ny, (int64_t)s.nx * s.ny, (int64_t)s.nx * w, (int64_t)s.nx * w,
                             (int64_t)w * (s.ny - 2 * w), (int64_t)w * (s.ny - 2 * w)};
     s.base[0] = 0;
-    s.cbase[0] = 0;
-    for (int r = 0; r < 6; ++r) {
+    for (int r = 0; r < 6; ++r)
         s.base[r + 1] = s.base[r] + (int)(cnt[r] * zb[r]);
-        s.cbase[r + 1] = s.cbase[r] + (int)(cnt[r] * ((zb[r] + kKZ - 1) / kKZ));
-    }
     for (int m = 0; m < 5; ++m)
         p.c[m] = c5[m];
     p.sdt = (float)((double)dt / (double)h);
@@ -251,7 +234,7 @@ cudaError_t launch_pml(const Grid &g, const float *u_prev, const float *u, float
     }
     p.psi_in = state_in + 3 * n;
     p.psi_out = state_out + 3 * n;
-    const int64_t blocks = ((int64_t)s.cbase[6] + kThreadsPml - 1) / kThreadsPml;
+    const int64_t blocks = ((int64_t)s.base[6] + kThreadsPml - 1) / kThreadsPml;
     if (blocks <= 0)
         return cudaSuccess;
     k_pml<<<(unsigned)blocks, kThreadsPml, 0, st>>>(u_prev, u, u_next, vel, p);
