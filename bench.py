@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--kernel", type=int, default=0)
     ap.add_argument("--path", choices=["tb", "single"], default="tb",
                     help="FP32 propagation: fused pairs of steps (tb) or one launch per step (single)")
+    ap.add_argument("--time-block", type=int, choices=[2, 3], default=2,
+                    help="tb path: steps fused per launch (3 needs 64 x 16 tiles to fit the SMs)")
     ap.add_argument("--graph", action="store_true", help="replay the step loop as a CUDA graph")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1000,9 +1002,13 @@ def run_ours(args):
     sa = torch.from_numpy(prob.src_amp).to(dev)
     stream = torch.cuda.current_stream()
     tb = args.storage == "f32" and args.path == "tb"
+    tblk = args.time_block
     if tb:
-        kw = dict(src_idx=si, src_amp=sa, kernel=args.kernel, use_graph=args.graph, work=gbs.tb_workspace(a, halo))
-        propagate = gbs.wave_propagate_tb
+        kw = dict(src_idx=si, src_amp=sa, kernel=args.kernel, use_graph=args.graph,
+                  work=gbs.tbn_workspace(a, halo, tblk))
+
+        def propagate(u_prev, u, vel_, dt_, h_, halo_, n_, **k):
+            return gbs.wave_propagate_tbn(u_prev, u, vel_, dt_, h_, halo_, n_, tblk, **k)
     elif args.storage == "f32":
         kw = dict(src_idx=si, src_amp=sa, kernel=args.kernel, tile_y=args.tile_y, zchunk=args.zchunk,
                   use_graph=args.graph)
@@ -1012,8 +1018,9 @@ def run_ours(args):
                   storage=args.storage, work=gbs.lp_workspace(a, halo))
         propagate = gbs.wave_propagate_lp
     # algorithmic bytes per point of one launch of the dominant kernel
-    bytes_per_point = BYTES_PER_POINT_PAIR if tb else (BYTES_PER_POINT if args.storage == "f32" else 10)
-    tb_shape = gbs.tb_supported(prob.nx, prob.ny, prob.nz, halo) if tb else None
+    bytes_per_point = (BYTES_PER_POINT_PAIR if tblk == 2 else 24) if tb else \
+        (BYTES_PER_POINT if args.storage == "f32" else 10)
+    tb_shape = gbs.tbn_supported(prob.nx, prob.ny, prob.nz, halo, tblk) if tb else None
 
     # warm-up (also builds the wavefield)
     for _ in range(max(3, args.warmup)):
@@ -1048,8 +1055,8 @@ def run_ours(args):
     per_launch_ms = kernel_ms / max(1, kernel_launches)
     alg_bytes = bytes_per_point * prob.npoints
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9 if kernel_launches else None
-    traffic = (traffic_per_launch(n, "tb" if tb else "single") if args.storage == "f32" and prob.nz == n
-               else None)
+    traffic = (traffic_per_launch(n, "tb" if tb else "single")
+               if args.storage == "f32" and prob.nz == n and not (tb and tblk != 2) else None)
     # sources are added inside the step kernels (at most 16); the fused path
     # also zeroes its workspace halo with one kernel per call
     inject_launches = args.steps if tb else 0
@@ -1152,11 +1159,12 @@ def run_ours(args):
                        "l2": f"no flush: each of the 3 fields ({4 * int(np.prod(shape)) / 1e6:.0f} MB) exceeds "
                              "the 129 MB L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "kernel": (f"k_wf<TY={tb_shape[1]}>: two fused leapfrog steps per launch "
-                                  f"(2-step temporal blocking, {tb_shape[2]} cooperative CTAs)" if tb else
+                       "kernel": (f"k_wf<TY={tb_shape[1]}>: {tblk} fused leapfrog steps per launch "
+                                  f"({tblk}-step temporal blocking, {tb_shape[2]} cooperative CTAs)" if tb else
                                   ("k_tma<R=4,wave>" if args.kernel != 2 else "k_generic<R=4,wave>"))
                        if args.storage == "f32" else f"k_tma<R=4,wave,{args.storage} storage>",
-                       "path": "fused pairs of steps" if tb else "one launch per step",
+                       "path": ("fused pairs of steps" if tblk == 2 else "three fused steps per launch") if tb
+                       else "one launch per step",
                        "storage": args.storage,
                        "tile_y": (tb_shape[1] if tb else args.tile_y or 16), "zchunk": args.zchunk or "auto",
                        "graph": args.graph},
@@ -1166,7 +1174,7 @@ def run_ours(args):
                          "frac_of_nominal": (achieved / NOMINAL_HBM_GBS) if achieved else None,
                          "nominal_peak": NOMINAL_HBM_GBS, "alg_bytes_per_launch": alg_bytes,
                          "alg_bytes_per_point_per_launch": bytes_per_point,
-                         "point_updates_per_launch": prob.npoints * (2 if tb else 1),
+                         "point_updates_per_launch": prob.npoints * (tblk if tb else 1),
                          "kernel_ms_per_launch": per_launch_ms, "kernel_launches": kernel_launches,
                          # the throughput against the single-step minimum of 16 B per update (can exceed 1)
                          "single_step_basis_frac": (value * BYTES_PER_POINT / hbm) if args.storage == "f32"
