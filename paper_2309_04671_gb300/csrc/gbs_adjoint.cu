@@ -14,10 +14,13 @@
 // With K = 1 every state is kept once instead (N+1 fields: 74 GB for 1000
 // steps at 256^3, which HBM holds) and nothing is recomputed.
 //
-// The adjoint step is the forward wave-step kernel; the imaging condition is
-// the same TMA kernel in its kImage mode (stencil of u^m times nu^{m+1},
+// A backward step is one launch of the fused adjoint-imaging kernel
+// (k_adjimg.cu: the adjoint step, and the stencil of u^m times nu^{m+1}
 // summed in FP32 over at most 32 steps, then folded into the FP64
-// gradient); the source cells get their term from a small kernel.  The forward pass stores (u^{sK-1}, u^{sK}) every K steps;
+// gradient); receivers beyond the fused ones and the source cells get their
+// terms from small kernels.  opts->kernel = 1 selects the two-kernel form
+// instead (the forward wave-step kernel, then the same TMA kernel in its
+// kImage mode), kept for comparison.  The forward pass stores (u^{sK-1}, u^{sK}) every K steps;
 // the backward pass walks the segments last to first, recomputes the K
 // states of a segment from its checkpoint into a segment buffer, and runs
 // the adjoint steps of the segment against them.  All fields live in the
@@ -114,7 +117,9 @@ struct Ctx {
     unsigned char *w;
     float *vel, *wt, *gp;   // velocity, imaging weight 2/(h^2 v), FP32 partial gradient
     CUtensorMap vel_map, w_map, gp_map;
+    CUtensorMap vel_map16, gp_map16;   // 64 x 16 tiles of the fused adjoint-imaging kernel
     int tile_y, zchunk;
+    bool fused_image;                  // the adjoint step and the imaging condition in one launch
     float dt, h;
     cudaStream_t st;
 
@@ -193,6 +198,34 @@ gbs_status image(const Ctx &c, const float *u_m, const float *nu, const gbs_src 
     return GBS_OK;
 }
 
+// One backward step in one launch: nu^{m+1} into nu_a (which holds
+// nu^{m+3}) from nu_b = nu^{m+2}, and the imaging condition of step m
+// against u^m; then receivers beyond the fused ones and the source cells.
+gbs_status step_image(const Ctx &c, float *nu_a, const float *nu_b, const float *u_m, const gbs_src *adj,
+                      const gbs_src *src, int64_t m)
+{
+    CUtensorMap nu2, nu3, um;
+    gbs_status s = make_tensor_map(&nu2, nu_b, c.gi, 64 + 8, 16 + 8, GBS_F32);
+    if (s == GBS_OK)
+        s = make_tensor_map(&nu3, nu_a, c.gi, 64, 16, GBS_F32);
+    if (s == GBS_OK)
+        s = make_tensor_map(&um, u_m, c.gi, 64 + 8, 16 + 8, GBS_F32);
+    if (s != GBS_OK)
+        return s;
+    const Coeffs cf = wave_weights();
+    cudaEvent_t e0 = profile_begin(c.st);
+    cudaError_t e = launch_adjimg(c.gi, nu2, nu3, c.vel_map16, um, c.gp_map16, nu_a, c.gp, c.dt, c.h, cf, adj, c.gc,
+                                  m, 0, c.st);
+    profile_end(e0, c.st);
+    if (e != cudaSuccess)
+        return set_cuda_error(e, "adjoint-imaging launch");
+    if ((e = launch_inject_image(c.gc, c.gi, nu_a, c.gp, u_m, c.vel, c.dt, c.h, cf, adj, m, c.st)) != cudaSuccess)
+        return set_cuda_error(e, "receiver injection launch");
+    if ((e = launch_image_src(c.gc, c.gi, c.grad(), nu_a, c.vel, src, m, c.st)) != cudaSuccess)
+        return set_cuda_error(e, "imaging source launch");
+    return GBS_OK;
+}
+
 gbs_status check_common(const float *vel, float dt, float h, int64_t nx, int64_t ny, int64_t nz, int halo,
                         int64_t nsteps, const gbs_src *src, int64_t ckpt_every, const void *work)
 {
@@ -229,6 +262,9 @@ Ctx make_ctx(const AdjLayout &L, int64_t nx, int64_t ny, int64_t nz, int halo, v
     c.wt = c.fld(L.off_w);
     c.gp = c.fld(L.off_gp);
     c.tile_y = (opts && opts->tile_y == 32) ? 32 : 16;
+    // kernel = 1 keeps the two-kernel form (the step, then the imaging
+    // kernel) for comparison; otherwise one fused launch per backward step
+    c.fused_image = !(opts && opts->kernel == 1);
     c.zchunk = (opts && opts->zchunk > 0) ? opts->zchunk : tma_default_zchunk(4, kWave, c.tile_y, GBS_F32, c.gi);
     c.dt = dt;
     c.h = h;
@@ -253,6 +289,10 @@ gbs_status load_velocity(Ctx &c, const float *vel)
         s = make_tensor_map(&c.w_map, c.wt, c.gi, 64, c.tile_y, GBS_F32);
     if (s == GBS_OK)
         s = make_tensor_map(&c.gp_map, c.gp, c.gi, 64, c.tile_y, GBS_F32);
+    if (s == GBS_OK)
+        s = make_tensor_map(&c.vel_map16, c.vel, c.gi, 64, 16, GBS_F32);
+    if (s == GBS_OK)
+        s = make_tensor_map(&c.gp_map16, c.gp, c.gi, 64, 16, GBS_F32);
     return s;
 }
 
@@ -303,7 +343,10 @@ gbs_status backward(Ctx &c, int64_t nsteps, const gbs_src *src, const gbs_src *a
 {
     const AdjLayout &L = *c.L;
     float *a = c.fld(L.off_n[0]), *b = c.fld(L.off_n[1]);   // nu^{m+3}, nu^{m+2}
-    cudaError_t e = cudaMemsetAsync(a, 0, 2 * L.field, c.st);
+    cudaError_t e = c.fused_image ? adjimg_prepare() : cudaSuccess;
+    if (e != cudaSuccess)
+        return set_cuda_error(e, "kernel attributes");
+    e = cudaMemsetAsync(a, 0, 2 * L.field, c.st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(c.grad(), 0, (size_t)grid_elems(c.gi) * sizeof(double), c.st);
     if (e == cudaSuccess)
@@ -317,8 +360,9 @@ gbs_status backward(Ctx &c, int64_t nsteps, const gbs_src *src, const gbs_src *a
         return set_cuda_error(e, "adjoint init");
     if (L.store_all) {
         for (int64_t m = nsteps - 1; m >= 0; --m) {
-            gbs_status r = step(c, a, b, a, adj, m);   // a <- nu^{m+1}
-            if (r == GBS_OK)
+            gbs_status r = c.fused_image ? step_image(c, a, b, c.state(m), adj, src, m)   // a <- nu^{m+1}
+                                         : step(c, a, b, a, adj, m);
+            if (r == GBS_OK && !c.fused_image)
                 r = image(c, c.state(m), a, src, m);
             if (r != GBS_OK)
                 return r;
@@ -343,8 +387,9 @@ gbs_status backward(Ctx &c, int64_t nsteps, const gbs_src *src, const gbs_src *a
                 return r;
         }
         for (int64_t m = m1 - 1; m >= m0; --m) {
-            gbs_status r = step(c, a, b, a, adj, m);   // a <- nu^{m+1}
-            if (r == GBS_OK)
+            gbs_status r = c.fused_image ? step_image(c, a, b, u_at(m), adj, src, m)   // a <- nu^{m+1}
+                                         : step(c, a, b, a, adj, m);
+            if (r == GBS_OK && !c.fused_image)
                 r = image(c, u_at(m), a, src, m);
             if (r != GBS_OK)
                 return r;

@@ -1701,7 +1701,8 @@ extern "C" gbs_status gbs_device_status(void *stream)
     const unsigned b = misc_status_take(st);
     const unsigned c = suite_status_take(st);
     const unsigned d = wf_status_take(st);
-    const unsigned v = a ? a : (b ? b : (c ? c : d));
+    const unsigned e = adjimg_status_take(st);
+    const unsigned v = a ? a : (b ? b : (c ? c : (d ? d : e)));
     if (v != 0)
         return fail((gbs_status)v, "device status %u", v);
     return GBS_OK;

@@ -248,6 +248,23 @@ cudaError_t launch_pml(const Grid &g, const float *u_prev, const float *u, float
                        float dt, float h, int w, float zeta_max, bool free_top, const float *c5,
                        const float *state_in, float *state_out, cudaStream_t st);
 
+// The adjoint step and the imaging condition in one launch (k_adjimg.cu):
+// nu^{m+1} (into nu_out, which may hold nu^{m+3}: nu3 maps it) from the
+// nu^{m+2} box (nu2) and vel, and gp += (L u^m) nu^{m+1} 2/(h^2 v) from the
+// u^m box (um) and the gp tile (gmap).  Maps: boxes 72 x 24, tiles 64 x 16,
+// all in the internal layout g.  Receivers as sources are added in the
+// kernel when there are at most kMaxFusedSrc; launch_inject_image adds more
+// (to nu and, with their imaging term, to gp).
+cudaError_t adjimg_prepare();
+cudaError_t launch_adjimg(const Grid &g, const CUtensorMap &nu2, const CUtensorMap &nu3, const CUtensorMap &vel,
+                          const CUtensorMap &um, const CUtensorMap &gmap, float *nu_out, float *gp, float dt, float h,
+                          const Coeffs &cf, const gbs_src *rec_src, const Grid &gc, int64_t m, int zchunk,
+                          cudaStream_t st);
+cudaError_t launch_inject_image(const Grid &gc, const Grid &g, float *nu, float *gp, const float *um,
+                                const float *vel, float dt, float h, const Coeffs &cf, const gbs_src *rec_src,
+                                int64_t m, cudaStream_t st);
+unsigned adjimg_status_take(cudaStream_t st);
+
 // Error norms (k_norms.cu): one FP64 partial record of 4 doubles per block
 // of kNormRowsPerBlock rows; `out` receives kNormOut doubles.
 constexpr int kNormRowsPerBlock = 64;
