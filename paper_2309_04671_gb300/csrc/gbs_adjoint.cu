@@ -117,8 +117,9 @@ struct Ctx {
     unsigned char *w;
     float *vel, *wt, *gp;   // velocity, imaging weight 2/(h^2 v), FP32 partial gradient
     CUtensorMap vel_map, w_map, gp_map;
-    CUtensorMap vel_map16, gp_map16;   // 64 x 16 tiles of the fused adjoint-imaging kernel
+    CUtensorMap vel_map_ai, gp_map_ai; // 64 x ai_ty tiles of the fused adjoint-imaging kernel
     int tile_y, zchunk;
+    int ai_ty, ai_zc;                  // its tile height and z-chunk
     bool fused_image;                  // the adjoint step and the imaging condition in one launch
     float dt, h;
     cudaStream_t st;
@@ -205,17 +206,18 @@ gbs_status step_image(const Ctx &c, float *nu_a, const float *nu_b, const float 
                       const gbs_src *src, int64_t m)
 {
     CUtensorMap nu2, nu3, um;
-    gbs_status s = make_tensor_map(&nu2, nu_b, c.gi, 64 + 8, 16 + 8, GBS_F32);
+    const int ty = c.ai_ty;
+    gbs_status s = make_tensor_map(&nu2, nu_b, c.gi, 64 + 8, ty + 8, GBS_F32);
     if (s == GBS_OK)
-        s = make_tensor_map(&nu3, nu_a, c.gi, 64, 16, GBS_F32);
+        s = make_tensor_map(&nu3, nu_a, c.gi, 64, ty, GBS_F32);
     if (s == GBS_OK)
-        s = make_tensor_map(&um, u_m, c.gi, 64 + 8, 16 + 8, GBS_F32);
+        s = make_tensor_map(&um, u_m, c.gi, 64 + 8, ty + 8, GBS_F32);
     if (s != GBS_OK)
         return s;
     const Coeffs cf = wave_weights();
     cudaEvent_t e0 = profile_begin(c.st);
-    cudaError_t e = launch_adjimg(c.gi, nu2, nu3, c.vel_map16, um, c.gp_map16, nu_a, c.gp, c.dt, c.h, cf, adj, c.gc,
-                                  m, 0, c.st);
+    cudaError_t e = launch_adjimg(c.gi, nu2, nu3, c.vel_map_ai, um, c.gp_map_ai, nu_a, c.gp, c.dt, c.h, cf, adj, c.gc,
+                                  m, ty, c.ai_zc, c.st);
     profile_end(e0, c.st);
     if (e != cudaSuccess)
         return set_cuda_error(e, "adjoint-imaging launch");
@@ -265,6 +267,12 @@ Ctx make_ctx(const AdjLayout &L, int64_t nx, int64_t ny, int64_t nz, int halo, v
     // kernel = 1 keeps the two-kernel form (the step, then the imaging
     // kernel) for comparison; otherwise one fused launch per backward step
     c.fused_image = !(opts && opts->kernel == 1);
+    // tile_y 16 or 28 also chooses the fused kernel's tile height (28 leaves the forward kernels at 16)
+    adjimg_shape(c.gi, &c.ai_ty, &c.ai_zc);
+    if (opts && (opts->tile_y == 16 || opts->tile_y == 28) && opts->tile_y != c.ai_ty) {
+        c.ai_ty = opts->tile_y;
+        c.ai_zc = 0;
+    }
     c.zchunk = (opts && opts->zchunk > 0) ? opts->zchunk : tma_default_zchunk(4, kWave, c.tile_y, GBS_F32, c.gi);
     c.dt = dt;
     c.h = h;
@@ -290,9 +298,9 @@ gbs_status load_velocity(Ctx &c, const float *vel)
     if (s == GBS_OK)
         s = make_tensor_map(&c.gp_map, c.gp, c.gi, 64, c.tile_y, GBS_F32);
     if (s == GBS_OK)
-        s = make_tensor_map(&c.vel_map16, c.vel, c.gi, 64, 16, GBS_F32);
+        s = make_tensor_map(&c.vel_map_ai, c.vel, c.gi, 64, c.ai_ty, GBS_F32);
     if (s == GBS_OK)
-        s = make_tensor_map(&c.gp_map16, c.gp, c.gi, 64, 16, GBS_F32);
+        s = make_tensor_map(&c.gp_map_ai, c.gp, c.gi, 64, c.ai_ty, GBS_F32);
     return s;
 }
 

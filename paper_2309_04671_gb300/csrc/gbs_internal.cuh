@@ -251,14 +251,15 @@ cudaError_t launch_pml(const Grid &g, const float *u_prev, const float *u, float
 // The adjoint step and the imaging condition in one launch (k_adjimg.cu):
 // nu^{m+1} (into nu_out, which may hold nu^{m+3}: nu3 maps it) from the
 // nu^{m+2} box (nu2) and vel, and gp += (L u^m) nu^{m+1} 2/(h^2 v) from the
-// u^m box (um) and the gp tile (gmap).  Maps: boxes 72 x 24, tiles 64 x 16,
-// all in the internal layout g.  Receivers as sources are added in the
+// u^m box (um) and the gp tile (gmap).  Maps: boxes 72 x (TY+8), tiles 64 x
+// TY, all in the internal layout g, with TY from adjimg_shape (or tile_y).  Receivers as sources are added in the
 // kernel when there are at most kMaxFusedSrc; launch_inject_image adds more
 // (to nu and, with their imaging term, to gp).
 cudaError_t adjimg_prepare();
+void adjimg_shape(const Grid &g, int *tile_y, int *zchunk);
 cudaError_t launch_adjimg(const Grid &g, const CUtensorMap &nu2, const CUtensorMap &nu3, const CUtensorMap &vel,
                           const CUtensorMap &um, const CUtensorMap &gmap, float *nu_out, float *gp, float dt, float h,
-                          const Coeffs &cf, const gbs_src *rec_src, const Grid &gc, int64_t m, int zchunk,
+                          const Coeffs &cf, const gbs_src *rec_src, const Grid &gc, int64_t m, int tile_y, int zchunk,
                           cudaStream_t st);
 cudaError_t launch_inject_image(const Grid &gc, const Grid &g, float *nu, float *gp, const float *um,
                                 const float *vel, float dt, float h, const Coeffs &cf, const gbs_src *rec_src,

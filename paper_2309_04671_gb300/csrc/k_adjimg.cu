@@ -4,7 +4,7 @@
 //   stage A:  nu^{m+1} = 2 nu^{m+2} - nu^{m+3} + (v dt)^2 (L nu^{m+2} + R^T a_m)
 //   stage B:  g += (L u^m) nu^{m+1} w,   w = 2 / (h^2 v)  (0 where v = 0)
 // g is the FP32 partial gradient (folded into FP64 every few steps by the
-// caller).  Each CTA owns a 64 x 16 tile and a z-chunk and runs two TMA-fed
+// caller).  Each CTA owns a 64 x TY tile (TY 16 or 28) and a z-chunk and runs two TMA-fed
 // 2.5D streaming pipelines over it, like the fused-step kernel: stage A
 // streams nu^{m+2} boxes (with nu^{m+3} and vel tiles), stage B streams u^m
 // boxes (with g and vel tiles).  Stage B reads nu^{m+1} at its own points
@@ -37,9 +37,12 @@ __device__ unsigned g_status_ai = 0;
 constexpr int kR = 4;
 constexpr int kTX = 64;
 constexpr int kVY = 2;
-constexpr int kTY = 16;
 
+// Tile height TY 16 (4 + 4 compute warps) or 28 (7 + 7, as the fused-step
+// kernel); ring depths keep one CTA per SM within 224 KB of shared memory.
+template <int TY>
 struct AiCfg {
+    static constexpr int kTY = TY;
     static constexpr int NTX = kTX / 4;
     static constexpr int NT = NTX * (kTY / kVY);     // compute threads per stage
     static constexpr int NW = NT / 32;
@@ -51,8 +54,8 @@ struct AiCfg {
     static constexpr int PVU_BYTES = kTX * kTY * 4;  // first tile (nu^{m+3} | g); vel follows
     static constexpr int PV_BYTES = 2 * PVU_BYTES;
     static constexpr int PV_STRIDE = (PV_BYTES + 127) / 128 * 128;
-    static constexpr int SL = 7;                     // per stage: u boxes in flight
-    static constexpr int SP = 5;                     // per stage: tile pairs in flight
+    static constexpr int SL = TY >= 24 ? 5 : 7;      // per stage: u boxes in flight
+    static constexpr int SP = TY >= 24 ? 4 : 5;      // per stage: tile pairs in flight
     static constexpr int ND = 16;                    // nu^{m+1} hand-over barriers
     static constexpr size_t STAGE_BYTES = (size_t)SL * L_STRIDE + (size_t)SP * PV_STRIDE;
     static constexpr size_t OFF_BAR = 2 * STAGE_BYTES;
@@ -198,12 +201,13 @@ struct Ring {
 
 // Compute warps of one stage (A: adjoint step, B: imaging) in the
 // semi-stencil form of the fused-step kernel.
-template <int STAGE>
+template <int TY, int STAGE>
 __device__ __forceinline__ void ai_consumer(const AiParams &p, const Ring &rg, uint64_t *nu_full, uint64_t *nu_free,
                                             const int64_t tx0, const int64_t ty0, const int z0, const int nzc,
                                             int *s_nsrc, int *s_src_x, int *s_src_y, int *s_src_z, float *s_src_f)
 {
-    using C = AiCfg;
+    using C = AiCfg<TY>;
+    constexpr int kTY = TY;
     const Grid &g = p.g;
     const int tid = threadIdx.x - STAGE * C::NT;
     const int lane = threadIdx.x & 31;
@@ -436,12 +440,12 @@ __device__ __forceinline__ void ai_consumer(const AiParams &p, const Ring &rg, u
 // Copy-issuing thread of one stage: the u boxes (nu^{m+2} or u^m) and the
 // tile pairs ((nu^{m+3}, vel) or (g, vel)).  Stage A stays within kLead
 // planes of stage B, so B's second reads of vel and nu^{m+1} hit L2.
-template <int STAGE>
+template <int TY, int STAGE>
 __device__ __forceinline__ void ai_producer(const CUtensorMap *pm_u, const CUtensorMap *pm_a,
                                             const CUtensorMap *pm_vel, const Ring &rg, const int H, const int64_t tx0,
                                             const int64_t ty0, const int z0, const int nzc, volatile int *b_next)
 {
-    using C = AiCfg;
+    using C = AiCfg<TY>;
     const int pfirst = z0 - kR, nplanes = nzc + 2 * kR;
     int n_u = 0, n_pv = 0;
     const uint64_t pol_u = policy_evict_first();
@@ -498,10 +502,12 @@ __device__ __forceinline__ void ai_producer(const CUtensorMap *pm_u, const CUten
 
 // CTA b: tile b % tiles, z-chunk b / tiles.  Warps: stage A's compute warps,
 // stage B's, then one issuing warp per stage.
-__global__ void __launch_bounds__(AiCfg::NTHREADS, 1)
+template <int TY>
+__global__ void __launch_bounds__(AiCfg<TY>::NTHREADS, 1)
     k_adjimg(const __grid_constant__ AiMaps m, const __grid_constant__ AiParams p)
 {
-    using C = AiCfg;
+    using C = AiCfg<TY>;
+    constexpr int kTY = TY;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ int s_nsrc;
     __shared__ int s_src_x[kMaxFusedSrc], s_src_y[kMaxFusedSrc], s_src_z[kMaxFusedSrc];
@@ -559,13 +565,13 @@ __global__ void __launch_bounds__(AiCfg::NTHREADS, 1)
     __syncthreads();
     const int w = threadIdx.x / 32;
     if (w < C::NW)
-        ai_consumer<0>(p, rg[0], nu_full, nu_free, tx0, ty0, z0, nzc, &s_nsrc, s_src_x, s_src_y, s_src_z, s_src_f);
+        ai_consumer<TY, 0>(p, rg[0], nu_full, nu_free, tx0, ty0, z0, nzc, &s_nsrc, s_src_x, s_src_y, s_src_z, s_src_f);
     else if (w < 2 * C::NW)
-        ai_consumer<1>(p, rg[1], nu_full, nu_free, tx0, ty0, z0, nzc, &s_nsrc, s_src_x, s_src_y, s_src_z, s_src_f);
+        ai_consumer<TY, 1>(p, rg[1], nu_full, nu_free, tx0, ty0, z0, nzc, &s_nsrc, s_src_x, s_src_y, s_src_z, s_src_f);
     else if (w == 2 * C::NW && (threadIdx.x & 31) == 0)
-        ai_producer<0>(&m.nu2, &m.nu3, &m.vel, rg[0], p.g.halo, tx0, ty0, z0, nzc, &s_bnext);
+        ai_producer<TY, 0>(&m.nu2, &m.nu3, &m.vel, rg[0], p.g.halo, tx0, ty0, z0, nzc, &s_bnext);
     else if (w == 2 * C::NW + 1 && (threadIdx.x & 31) == 0)
-        ai_producer<1>(&m.um, &m.g, &m.vel, rg[1], p.g.halo, tx0, ty0, z0, nzc, &s_bnext);
+        ai_producer<TY, 1>(&m.um, &m.g, &m.vel, rg[1], p.g.halo, tx0, ty0, z0, nzc, &s_bnext);
 }
 
 // Receivers beyond the fused ones: nu^{m+1} += (v dt)^2 a, and the imaging
@@ -600,6 +606,7 @@ __global__ void k_inject_image(Grid gc, Grid g, float *nu, float *gp, const floa
     atomicAdd(gp + at, lap * d * w);
 }
 
+template <int TY>
 cudaError_t prepare_ai()
 {
     static bool done[64] = {};
@@ -609,7 +616,7 @@ cudaError_t prepare_ai()
         return e;
     if (dev >= 0 && dev < 64 && done[dev])
         return cudaSuccess;
-    e = cudaFuncSetAttribute(k_adjimg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AiCfg::SMEM);
+    e = cudaFuncSetAttribute(k_adjimg<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AiCfg<TY>::SMEM);
     if (e == cudaSuccess && dev >= 0 && dev < 64)
         done[dev] = true;
     return e;
@@ -617,36 +624,54 @@ cudaError_t prepare_ai()
 
 }  // namespace
 
-cudaError_t adjimg_prepare() { return prepare_ai(); }
+cudaError_t adjimg_prepare()
+{
+    cudaError_t e = prepare_ai<16>();
+    return e == cudaSuccess ? prepare_ai<28>() : e;
+}
 
-// z-chunks: the least (waves of one CTA per SM) x (planes + 2R halo planes).
-int adjimg_zchunk(const Grid &g)
+// Shape: one CTA per SM, so a launch lasts about (waves) x (tile rows + R) x
+// (chunk planes + 2R) x (a CTA's cost per row-plane); among tile heights 16
+// and 28 and chunk counts, take the least, preferring one wave (a chunk
+// shorter than 48 planes spends too much of itself filling the rings).
+void adjimg_shape(const Grid &g, int *tile_y, int *zchunk)
 {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t tiles = ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY);
     double best = 1e300;
-    int64_t bestc = 1;
-    for (int64_t c = 1; c <= g.nz && c <= 64; ++c) {
-        const int64_t zc = (g.nz + c - 1) / c;
-        const int64_t n = (g.nz + zc - 1) / zc;
-        const double waves = std::ceil((double)(tiles * n) / (double)sms);
-        const double cost = waves * (double)(zc + 2 * kR);
-        if (cost < best * 0.999) {
-            best = cost;
-            bestc = zc;
+    *tile_y = 16;
+    *zchunk = (int)g.nz;
+    for (int ty : {28, 16}) {
+        const int64_t tiles = ((g.nx + kTX - 1) / kTX) * ((g.ny + ty - 1) / ty);
+        for (int64_t c = 1; c <= g.nz && c <= 64; ++c) {
+            const int64_t zc = (g.nz + c - 1) / c;
+            if (c > 1 && zc < 48)
+                break;
+            const int64_t n = (g.nz + zc - 1) / zc;
+            const double waves = std::ceil((double)(tiles * n) / (double)sms);
+            const double cost = waves * (double)(zc + 2 * kR) * (double)(ty + kR);
+            if (cost < best * 0.999) {
+                best = cost;
+                *tile_y = ty;
+                *zchunk = (int)zc;
+            }
         }
     }
-    return (int)bestc;
 }
 
 cudaError_t launch_adjimg(const Grid &g, const CUtensorMap &nu2, const CUtensorMap &nu3, const CUtensorMap &vel,
                           const CUtensorMap &um, const CUtensorMap &gmap, float *nu_out, float *gp, float dt, float h,
-                          const Coeffs &cf, const gbs_src *rec_src, const Grid &gc, int64_t m, int zchunk,
-                          cudaStream_t st)
+                          const Coeffs &cf, const gbs_src *rec_src, const Grid &gc, int64_t m, int tile_y,
+                          int zchunk, cudaStream_t st)
 {
-    cudaError_t e = prepare_ai();
+    int ty = 16, zc = 0;
+    adjimg_shape(g, &ty, &zc);
+    if (tile_y == 16 || tile_y == 28)
+        ty = tile_y;
+    if (zchunk > 0)
+        zc = zchunk;
+    cudaError_t e = ty == 28 ? prepare_ai<28>() : prepare_ai<16>();
     if (e != cudaSuccess)
         return e;
     AiMaps mp;
@@ -667,8 +692,8 @@ cudaError_t launch_adjimg(const Grid &g, const CUtensorMap &nu2, const CUtensorM
     p.dt = dt;
     p.two_over_h2 = (float)(2.0 / ((double)h * (double)h));
     p.tiles_x = (int)((g.nx + kTX - 1) / kTX);
-    p.tiles_y = (int)((g.ny + kTY - 1) / kTY);
-    p.zchunk = zchunk > 0 ? zchunk : adjimg_zchunk(g);
+    p.tiles_y = (int)((g.ny + ty - 1) / ty);
+    p.zchunk = zc;
     const int64_t nchunks = (g.nz + p.zchunk - 1) / p.zchunk;
     const bool fused_src = rec_src && rec_src->n > 0 && rec_src->n <= kMaxFusedSrc;
     if (fused_src) {
@@ -683,7 +708,10 @@ cudaError_t launch_adjimg(const Grid &g, const CUtensorMap &nu2, const CUtensorM
     const int64_t ctas = (int64_t)p.tiles_x * p.tiles_y * nchunks;
     if (ctas <= 0 || ctas > 0x7fffffff)
         return cudaErrorInvalidConfiguration;
-    k_adjimg<<<(unsigned)ctas, AiCfg::NTHREADS, AiCfg::SMEM, st>>>(mp, p);
+    if (ty == 28)
+        k_adjimg<28><<<(unsigned)ctas, AiCfg<28>::NTHREADS, AiCfg<28>::SMEM, st>>>(mp, p);
+    else
+        k_adjimg<16><<<(unsigned)ctas, AiCfg<16>::NTHREADS, AiCfg<16>::SMEM, st>>>(mp, p);
     return cudaGetLastError();
 }
 
