@@ -683,12 +683,10 @@ def adjoint_form(args, stream, hbm, n=256, nsteps=1000, nshots=8):
         for si in srcs:
             gbs.wave_propagate(torch.zeros_like(vel), torch.zeros_like(vel), vel, dt, h, halo, nsteps, src_idx=si,
                                src_amp=amp, rec_idx=rec, rec_trace=tr)
-    gradient(fused=False)
-    ms_two, _, _ = time_calls(lambda: gradient(fused=False), 1, stream)
-    other_ty = {}
-    for ty in (16, 28):
-        gradient(tile_y=ty)
-        other_ty[str(ty)], _, _ = time_calls(lambda: gradient(tile_y=ty), 1, stream)
+    fused_ms = {}
+    for ty in (0, 16, 28):
+        gradient(fused=True, tile_y=ty)
+        fused_ms[str(ty) if ty else "auto"], _, _ = time_calls(lambda: gradient(fused=True, tile_y=ty), 1, stream)
     gradient()
     ms_g, kms, kl = time_calls(gradient, 1, stream)
     gbs.device_status()
@@ -697,10 +695,9 @@ def adjoint_form(args, stream, hbm, n=256, nsteps=1000, nshots=8):
     k = int(np.ceil(np.sqrt(nsteps)))
     pts = n ** 3
     # algorithmic bytes per point per step: forward 16, recomputation 16 (K-1)/K,
-    # the fused backward step 28 (nu^{m+2}, nu^{m+3}, vel, u^m, g read; nu^{m+1},
-    # g written) and the FP64 fold every 32 steps (FP32 read + write, FP64
-    # read + write: 24/32)
-    bpp = 16 + 16 * (k - 1) / k + 28 + 24 / 32
+    # adjoint step 16, imaging 20 (u^m, nu, w, FP32 partial read + write) and
+    # the FP64 fold every 32 steps (FP32 read + write, FP64 read + write: 24/32)
+    bpp = 16 + 16 * (k - 1) / k + 16 + 20 + 24 / 32
     alg = pts * nshots * nsteps * bpp
     kernel_ms = kms * kl            # summed duration of the step and imaging launches
     ach = alg / (kernel_ms * 1e-3) / 1e9
@@ -709,10 +706,9 @@ def adjoint_form(args, stream, hbm, n=256, nsteps=1000, nshots=8):
                        f"{k} steps, FP64 gradient",
            "value": pts * nsteps * nshots / (ms_g * 1e-3) / 1e9, "unit": "gradient point-steps/s (x1e9)",
            "ms_per_gradient": ms_g, "shots": nshots, "forward_only_ms": ms_f, "gradient_over_forward": ms_g / ms_f,
-           "two_kernel_backward": {"ms_per_gradient": ms_two, "gradient_over_forward": ms_two / ms_f,
-                                   "note": "each backward step as the adjoint-step kernel then the imaging kernel "
-                                           "(36 B per point-step instead of 28)"},
-           "fused_ms_per_gradient_by_tile_y": other_ty,
+           "fused_backward": {"ms_per_gradient_by_tile_y": fused_ms,
+                              "note": "each backward step as one launch of the adjoint step and the imaging "
+                                      "condition (k_adjimg; 28 B per point-step instead of 36)"},
            "misfit": float(misfit.cpu()[0]),
            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                         "bytes_per_point_step": bpp, "kernel_ms": kernel_ms,

@@ -508,13 +508,15 @@ void gbs_batch_plan_destroy(gbs_batch_plan *plan);
  *   writes trace and resid = trace - d_obs (DEVICE [nsteps][nrec], distinct
  *   buffers), ADDS J to *misfit (DEVICE FP64) and dJ/dv to grad.
  * Sources: as gbs_wave_propagate (more than 16 take a separate kernel).
- * A backward step is one launch that runs the adjoint step and the imaging
- * condition together (reading u^m and nu^{m+2} boxes once: 28 bytes per
- * point instead of 36 for the two kernels one after the other); up to 16
- * receivers are injected inside it, more by a separate kernel that also adds
- * their imaging term.  opts->kernel = 1 selects the two-kernel form instead
- * (same gradient to FP32 rounding); other opts fields as gbs_wave_propagate
- * (tile_y, zchunk of the forward and two-kernel steps; no absorbing layer).
+ * A backward step is the adjoint step kernel, then the imaging kernel.
+ * opts->kernel = 3 runs both in one launch instead (reading u^m and
+ * nu^{m+2} boxes once: 28 bytes per point instead of 36; up to 16 receivers
+ * injected inside it, more by a separate kernel that also adds their imaging
+ * term; the same gradient to FP32 rounding; slower at 256^3, where both of
+ * its pipelines stream DRAM on one CTA per SM); its tile height is 16 or 28
+ * (opts->tile_y, else chosen by size).  Other opts fields as
+ * gbs_wave_propagate (tile_y, zchunk of the forward and two-kernel steps; no
+ * absorbing layer).
  * Nothing is allocated; calls enqueue on `stream`.
  * Errors: GBS_EINVAL (sizes, halo < 4, nsteps <= 0, null or unaligned
  * workspace, too small a workspace), GBS_ECUDA.

@@ -776,12 +776,13 @@ def adjoint_forward(vel: torch.Tensor, dt: float, h: float, halo: int, nsteps: i
 
 def adjoint_backward(vel: torch.Tensor, dt: float, h: float, halo: int, nsteps: int, adj_src: torch.Tensor,
                      work: torch.Tensor, *, src_idx=None, src_amp=None, rec_idx=None, ckpt_every: int = 0,
-                     grad: Optional[torch.Tensor] = None, tile_y: int = 0, zchunk: int = 0, fused: bool = True,
+                     grad: Optional[torch.Tensor] = None, tile_y: int = 0, zchunk: int = 0, fused: bool = False,
                      stream=None):
     """Adds dJ/dv to ``grad`` (float64, shaped like vel) for the trace
     cotangent ``adj_src`` (nsteps, nrec); needs the workspace of the
-    matching :func:`adjoint_forward`.  ``fused=False`` runs each backward
-    step as two kernels (the step, then the imaging condition)."""
+    matching :func:`adjoint_forward`.  ``fused=True`` runs each backward
+    step as one launch (the step and the imaging condition together) instead
+    of two kernels."""
     pv = _field(vel, "vel")
     nx, ny, nz = _dims(vel, halo)
     if grad is None:
@@ -794,7 +795,7 @@ def adjoint_backward(vel: torch.Tensor, dt: float, h: float, halo: int, nsteps: 
         raise TypeError("adj_src must be a float32 CUDA tensor of shape (nsteps, nrec)")
     src = _make_src(src_idx, src_amp)
     wp, wn = _aligned(work)
-    opts = _opts(0 if fused else 1, tile_y, zchunk, False)
+    opts = _opts(3 if fused else 0, tile_y, zchunk, False)
     _check(load().gbs_adjoint_backward(pv, float(dt), float(h), nx, ny, nz, halo, int(nsteps), _ptr(src),
                                        rec_idx.data_ptr(), rec_idx.numel(), a.data_ptr(), int(ckpt_every), wp, wn,
                                        grad.data_ptr(), ctypes.byref(opts), _stream(stream)))
@@ -804,11 +805,12 @@ def adjoint_backward(vel: torch.Tensor, dt: float, h: float, halo: int, nsteps: 
 def fwi_gradient(vel: torch.Tensor, dt: float, h: float, halo: int, nsteps: int, d_obs: torch.Tensor, *,
                  src_idx=None, src_amp=None, rec_idx=None, ckpt_every: int = 0, work: Optional[torch.Tensor] = None,
                  grad: Optional[torch.Tensor] = None, misfit: Optional[torch.Tensor] = None, tile_y: int = 0,
-                 zchunk: int = 0, fused: bool = True, stream=None):
+                 zchunk: int = 0, fused: bool = False, stream=None):
     """L2 trace misfit and its velocity gradient (both passes).  Returns
     (misfit, grad, trace, resid); misfit (float64, 1 value) and grad are
-    accumulated into when given.  ``fused=False`` runs each backward step as
-    two kernels (the step, then the imaging condition)."""
+    accumulated into when given.  ``fused=True`` runs each backward step as
+    one launch (the step and the imaging condition together) instead of two
+    kernels."""
     pv = _field(vel, "vel")
     nx, ny, nz = _dims(vel, halo)
     _idx(rec_idx, "rec_idx")
@@ -826,7 +828,7 @@ def fwi_gradient(vel: torch.Tensor, dt: float, h: float, halo: int, nsteps: int,
     resid = torch.empty_like(trace)
     src = _make_src(src_idx, src_amp)
     wp, wn = _aligned(work)
-    opts = _opts(0 if fused else 1, tile_y, zchunk, False)
+    opts = _opts(3 if fused else 0, tile_y, zchunk, False)
     _check(load().gbs_fwi_gradient(pv, float(dt), float(h), nx, ny, nz, halo, int(nsteps), _ptr(src),
                                    rec_idx.data_ptr(), nrec, d.data_ptr(), trace.data_ptr(), resid.data_ptr(),
                                    int(ckpt_every), wp, wn, grad.data_ptr(), misfit.data_ptr(), ctypes.byref(opts),

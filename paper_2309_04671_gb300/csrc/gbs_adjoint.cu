@@ -14,13 +14,13 @@
 // With K = 1 every state is kept once instead (N+1 fields: 74 GB for 1000
 // steps at 256^3, which HBM holds) and nothing is recomputed.
 //
-// A backward step is one launch of the fused adjoint-imaging kernel
-// (k_adjimg.cu: the adjoint step, and the stencil of u^m times nu^{m+1}
+// A backward step is the forward wave-step kernel (the adjoint step), then
+// the same TMA kernel in its kImage mode (the stencil of u^m times nu^{m+1},
 // summed in FP32 over at most 32 steps, then folded into the FP64
-// gradient); receivers beyond the fused ones and the source cells get their
-// terms from small kernels.  opts->kernel = 1 selects the two-kernel form
-// instead (the forward wave-step kernel, then the same TMA kernel in its
-// kImage mode), kept for comparison.  The forward pass stores (u^{sK-1}, u^{sK}) every K steps;
+// gradient); the source cells get their term from a small kernel.
+// opts->kernel = 3 runs both in one launch instead (k_adjimg.cu: fewer DRAM
+// bytes, slower at the sizes measured: both of its pipelines stream DRAM on
+// one CTA per SM).  The forward pass stores (u^{sK-1}, u^{sK}) every K steps;
 // the backward pass walks the segments last to first, recomputes the K
 // states of a segment from its checkpoint into a segment buffer, and runs
 // the adjoint steps of the segment against them.  All fields live in the
@@ -264,9 +264,10 @@ Ctx make_ctx(const AdjLayout &L, int64_t nx, int64_t ny, int64_t nz, int halo, v
     c.wt = c.fld(L.off_w);
     c.gp = c.fld(L.off_gp);
     c.tile_y = (opts && opts->tile_y == 32) ? 32 : 16;
-    // kernel = 1 keeps the two-kernel form (the step, then the imaging
-    // kernel) for comparison; otherwise one fused launch per backward step
-    c.fused_image = !(opts && opts->kernel == 1);
+    // kernel = 3 runs each backward step as one fused launch; otherwise two
+    // kernels (the step, then the imaging kernel), the faster form at the
+    // sizes measured
+    c.fused_image = opts && opts->kernel == 3;
     // tile_y 16 or 28 also chooses the fused kernel's tile height (28 leaves the forward kernels at 16)
     adjimg_shape(c.gi, &c.ai_ty, &c.ai_zc);
     if (opts && (opts->tile_y == 16 || opts->tile_y == 28) && opts->tile_y != c.ai_ty) {

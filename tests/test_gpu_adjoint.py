@@ -190,12 +190,12 @@ def test_gpu_gradient_matches_gpu_finite_differences_32():
 
 @pytest.mark.parametrize("shape,nsteps,nrec", [((37, 29, 24), 40, 40), ((64, 48, 36), 33, 7)])
 def test_fused_backward_step_matches_two_kernel_form(shape, nsteps, nrec):
-    """One launch per backward step (the adjoint step and the imaging
+    """One launch per backward step (opt-in: the adjoint step and the imaging
     condition together; receivers injected inside it when there are at most
     16, else by the separate kernel that also adds their imaging term)
-    against the two-kernel form: the same gradient to FP32 rounding, and
-    both against the oracle; the fused form is bit-identical for two
-    checkpoint intervals."""
+    against the default two-kernel form: the same gradient to FP32 rounding,
+    both against the oracle, and both tile heights of the fused kernel; the
+    fused form is bit-identical for two checkpoint intervals."""
     need_gpu()
     p = _problem(*shape, nsteps, nrec, seed=sum(shape) + 3 * nsteps)
     args = (to_dev(p["vel"]), p["dt"], H, HALO, p["nsteps"], to_dev(p["d_obs"]))
@@ -203,11 +203,13 @@ def test_fused_backward_step_matches_two_kernel_form(shape, nsteps, nrec):
     J1, g1, _, _ = gbs.fwi_gradient(*args, **kw, fused=True)
     J2, g2, _, _ = gbs.fwi_gradient(*args, **kw, fused=False)
     _, g3, _, _ = gbs.fwi_gradient(*args, **kw, fused=True, ckpt_every=5)
+    _, g4, _, _ = gbs.fwi_gradient(*args, **kw, fused=True, tile_y=28)
     gbs.device_status()
     assert torch.equal(J1, J2)                       # the forward pass is the same
     assert torch.equal(g1, g3)
-    e = oracle.err_norms(g1.cpu().numpy(), g2.cpu().numpy())
-    assert e["norm_max_rel"] <= grad_tol(nsteps), e
+    for got in (g1, g4):
+        e = oracle.err_norms(got.cpu().numpy(), g2.cpu().numpy())
+        assert e["norm_max_rel"] <= grad_tol(nsteps), e
     _, g = oracle.fwi_gradient(p["vel"], p["dt"], H, HALO, nsteps, p["d_obs"], src_idx=p["src"], src_amp=p["amp"],
                                rec_idx=p["rec"])
     for got in (g1, g2):
