@@ -472,6 +472,14 @@ gbs_status gbs_batch_run(gbs_batch_plan *plan, int64_t nsteps, int64_t t0, int u
 /* The tiling the plan uses, its number of work items and interior points. */
 gbs_status gbs_batch_plan_info(const gbs_batch_plan *plan, int *tile_y, int *zchunk, int64_t *items,
                                int64_t *points);
+/* The rest of the tuner's choice (Table 2's tuning knobs; the paper's
+ * auto-tuning is future work, Sec. 15.2): the queue depth, as the number of
+ * u-box stages in the kernel's landing ring (the tuner times the
+ * single-field kernel's rings and an alternative: shallower FP32 rings for
+ * three CTAs per SM, deeper 16-bit rings at two), and the steps fused per
+ * launch (1: a batch's work list outnumbers the SMs, so steps are not
+ * fused).  Either pointer may be NULL.  Errors: GBS_EINVAL (null plan). */
+gbs_status gbs_batch_plan_tuning(const gbs_batch_plan *plan, int *ring_stages, int *time_block);
 void gbs_batch_plan_destroy(gbs_batch_plan *plan);
 
 /*

@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4
 EXPORTS = ("gbs_stencil_apply", "gbs_wave_step", "gbs_wave_propagate", "gbs_lp_workspace_bytes",
            "gbs_wave_propagate_lp", "gbs_tb_workspace_bytes", "gbs_wave_propagate_tb", "gbs_tb_supported",
            "gbs_tbn_workspace_bytes", "gbs_wave_propagate_tbn", "gbs_tbn_supported",
-           "gbs_pml_state_bytes", "gbs_wave_propagate_pml",
+           "gbs_pml_state_bytes", "gbs_wave_propagate_pml", "gbs_batch_plan_tuning",
            "gbs_selftest_tb_timeout", "gbs_host_workspace_bytes", "gbs_wave_propagate_host", "gbs_check_cfl",
            "gbs_pipeline_create", "gbs_pipeline_submit", "gbs_pipeline_wait", "gbs_pipeline_workspace_bytes",
            "gbs_pipeline_destroy",
@@ -165,6 +165,8 @@ def load() -> ctypes.CDLL:
         lib.gbs_batch_plan_info.argtypes = [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                             ctypes.POINTER(i64), ctypes.POINTER(i64)]
         lib.gbs_batch_plan_info.restype = c_int
+        lib.gbs_batch_plan_tuning.argtypes = [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+        lib.gbs_batch_plan_tuning.restype = c_int
         lib.gbs_batch_plan_destroy.argtypes = [vp]
         lib.gbs_batch_plan_destroy.restype = None
         lib.gbs_adjoint_workspace_bytes.argtypes = [i64, i64, i64, i64, i64]
@@ -720,7 +722,10 @@ class BatchPlan:
         ty, zc, items, pts = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
         _check(load().gbs_batch_plan_info(self._plan, ctypes.byref(ty), ctypes.byref(zc), ctypes.byref(items),
                                           ctypes.byref(pts)))
-        return {"tile_y": ty.value, "zchunk": zc.value, "items": items.value, "points": pts.value}
+        ring, tblk = ctypes.c_int(), ctypes.c_int()
+        _check(load().gbs_batch_plan_tuning(self._plan, ctypes.byref(ring), ctypes.byref(tblk)))
+        return {"tile_y": ty.value, "zchunk": zc.value, "items": items.value, "points": pts.value,
+                "ring_stages": ring.value, "time_block": tblk.value}
 
     def close(self) -> None:
         if getattr(self, "_plan", None):

@@ -24,6 +24,7 @@ struct gbs_batch_plan {
     gbs_dtype storage = GBS_F32;
     int tile_y = 16;
     int zchunk = 0;
+    int ring = 0;                         // ring-depth variant of the batch kernel (tuned)
     std::vector<gbs_shot> shots;          // caller's descriptors (pointers stay valid for the plan's life)
     std::vector<gbs::Grid> gc, gi;        // caller and internal layouts per shot
     std::vector<size_t> off_a, off_b, off_vel, off_meta;
@@ -93,8 +94,9 @@ gbs_status build_maps(gbs_batch_plan &P, int tile_y, std::vector<CUtensorMap> &m
     return GBS_OK;
 }
 
-// Upload descriptors and the work list for (tile_y, zchunk).
-gbs_status configure(gbs_batch_plan &P, int tile_y, int zchunk, cudaStream_t st)
+// Upload descriptors and the work list for (tile_y, zchunk); ring picks the
+// kernel's ring-depth variant.
+gbs_status configure(gbs_batch_plan &P, int tile_y, int zchunk, int ring, cudaStream_t st)
 {
     std::vector<CUtensorMap> maps;
     gbs_status s = build_maps(P, tile_y, maps);
@@ -117,6 +119,7 @@ gbs_status configure(gbs_batch_plan &P, int tile_y, int zchunk, cudaStream_t st)
         return set_cuda_error(e, "batch plan upload");
     P.tile_y = tile_y;
     P.zchunk = zchunk;
+    P.ring = ring;
     P.nitems = (int)items.size();
     if (P.graph) {
         cudaGraphExecDestroy(P.graph);
@@ -129,7 +132,7 @@ gbs_status enqueue_steps(gbs_batch_plan &P, int64_t nsteps, int64_t t0, cudaStre
 {
     for (int64_t q = 0; q < nsteps; ++q) {
         cudaEvent_t e0 = profile_begin(st);
-        cudaError_t e = launch_tma_batch(P.tile_y, P.storage, P.d_items, P.nitems, P.d_params, P.d_maps,
+        cudaError_t e = launch_tma_batch(P.tile_y, P.storage, P.ring, P.d_items, P.nitems, P.d_params, P.d_maps,
                                          (int)(q & 1), t0 + q, st);
         profile_end(e0, st);
         if (e != cudaSuccess)
@@ -209,13 +212,14 @@ gbs_status tune(gbs_batch_plan &P, cudaStream_t st)
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return set_cuda_error(cudaGetLastError(), "tuner events");
     float best = 1e30f;
-    int by = 16, bz = 0;
+    int by = 16, bz = 0, bring = 0;
     gbs_status r = GBS_OK;
+    for (int ring : {0, 1})
     for (int ty : ycands) {
         for (int zc : zcands) {
             if (zc > 0 && zc >= maxnz)
                 continue;
-            if ((r = configure(P, ty, zc, st)) != GBS_OK)
+            if ((r = configure(P, ty, zc, ring, st)) != GBS_OK)
                 break;
             if ((r = enqueue_steps(P, 2, 0, st)) != GBS_OK)   // warm-up
                 break;
@@ -232,6 +236,7 @@ gbs_status tune(gbs_batch_plan &P, cudaStream_t st)
                 best = ms;
                 by = ty;
                 bz = zc;
+                bring = ring;
             }
         }
         if (r != GBS_OK)
@@ -241,7 +246,7 @@ gbs_status tune(gbs_batch_plan &P, cudaStream_t st)
     cudaEventDestroy(e1);
     if (r != GBS_OK)
         return r;
-    return configure(P, by, bz, st);
+    return configure(P, by, bz, bring, st);
 }
 
 void release(gbs_batch_plan *P)
@@ -349,9 +354,13 @@ extern "C" gbs_status gbs_batch_plan_create(gbs_batch_plan **plan, const gbs_sho
     const int zc = opts ? opts->zchunk : 0;
     const bool autotune = !opts || (opts->tile_y == 0 && opts->zchunk == 0);
     gbs_status r = GBS_OK;
-    if ((e = tma_prepare_batch(storage, 16)) != cudaSuccess || (e = tma_prepare_batch(storage, 32)) != cudaSuccess)
+    for (int ring : {0, 1})
+        if (e == cudaSuccess && ((e = tma_prepare_batch(storage, 16, ring)) != cudaSuccess ||
+                                 (e = tma_prepare_batch(storage, 32, ring)) != cudaSuccess))
+            break;
+    if (e != cudaSuccess)
         return release(P), set_cuda_error(e, "kernel attributes");
-    r = autotune ? tune(*P, st) : configure(*P, ty, zc, st);
+    r = autotune ? tune(*P, st) : configure(*P, ty, zc, 0, st);
     if (r != GBS_OK)
         return release(P), r;
     *plan = P;
@@ -416,6 +425,18 @@ extern "C" gbs_status gbs_batch_plan_info(const gbs_batch_plan *plan, int *tile_
         *items = plan->nitems;
     if (points)
         *points = plan->points;
+    return GBS_OK;
+}
+
+extern "C" gbs_status gbs_batch_plan_tuning(const gbs_batch_plan *plan, int *ring_stages, int *time_block)
+{
+    clear_error();
+    if (!plan)
+        return set_error(GBS_EINVAL, "null plan");
+    if (ring_stages)
+        *ring_stages = tma_batch_ring_stages(plan->storage, plan->tile_y, plan->ring);
+    if (time_block)
+        *time_block = 1;   // one launch per step: the work list of a batch outnumbers the SMs
     return GBS_OK;
 }
 

@@ -145,11 +145,15 @@ struct TmaPlan {
 cudaError_t launch_tma(int radius, Mode mode, int tile_y, gbs_dtype storage, const TmaPlan &plan,
                        const StepParams &p, int64_t t, cudaStream_t st);
 // Batched wave steps: one CTA per item; shots[i] and maps[(i*2 + parity)*3 + {0,1,2}]
-// (u, u_prev, vel descriptors) live in device memory.
-cudaError_t launch_tma_batch(int tile_y, gbs_dtype storage, const BatchItem *items, int nitems,
+// (u, u_prev, vel descriptors) live in device memory.  ring 0: the
+// single-field kernel's ring depths; 1: the alternative (FP32 shallower, three
+// CTAs per SM; 16-bit deeper, two).
+cudaError_t launch_tma_batch(int tile_y, gbs_dtype storage, int ring, const BatchItem *items, int nitems,
                              const StepParams *shots, const CUtensorMap *maps, int parity, int64_t t,
                              cudaStream_t st);
-cudaError_t tma_prepare_batch(gbs_dtype storage, int tile_y);
+cudaError_t tma_prepare_batch(gbs_dtype storage, int tile_y, int ring);
+// u-box ring stages of a batch kernel (the queue depth the tuner chose)
+int tma_batch_ring_stages(gbs_dtype storage, int tile_y, int ring);
 int tma_default_zchunk(int radius, Mode mode, int tile_y, gbs_dtype storage, const Grid &g);
 // Sets the wave kernel's shared-memory attribute (call before stream capture).
 cudaError_t tma_prepare_wave_absorb(int tile_y);

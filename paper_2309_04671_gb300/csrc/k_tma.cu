@@ -56,7 +56,9 @@ struct Storage {
     static constexpr bool kLow = !std::is_same<T, float>::value;
 };
 
-template <int R, int MODE, int TY, typename T>
+// RING = 1: the batch plan's alternative ring depths (FP32: shallower rings
+// for three CTAs per SM; 16-bit: deeper rings at two CTAs per SM).
+template <int R, int MODE, int TY, typename T, int RING = 0>
 struct Cfg {
     static constexpr bool LOW = Storage<T>::kLow;
     static constexpr int ES = (int)sizeof(T);
@@ -72,7 +74,7 @@ struct Cfg {
     // planes k..k+R resident + 4 ahead.  16-bit: converted on arrival, 2 ahead
     // (small rings keep three CTAs per SM).
     // Each stage completes on its own mbarrier (expect_tx).
-    static constexpr int SL = LOW ? 3 : R + 5;
+    static constexpr int SL = LOW ? (RING ? 5 : 3) : (RING ? R + 3 : R + 5);
     static constexpr int L_BYTES = BW * BH * ES;
     static constexpr int L_STRIDE = (L_BYTES + 127) / 128 * 128;
     // 16-bit: FP32 copies of the last R+2 stencil-centre planes (one more than
@@ -92,14 +94,14 @@ struct Cfg {
     static constexpr int PV_STRIDE = PVU_BYTES + PVV_BYTES + PVG_BYTES;
     // stages of (u_prev|nu, vel|w[, g]); imaging stages are 1.5x as large,
     // so fewer keep two CTAs per SM
-    static constexpr int SP = LOW ? 3 : (MODE == kImage ? 4 : 5);
+    static constexpr int SP = LOW ? (RING ? 5 : 3) : (MODE == kImage ? 4 : (RING ? 3 : 5));
     static constexpr size_t SMEM_L = (size_t)SL * L_STRIDE;
     static constexpr size_t SMEM_F = (size_t)SF * F_STRIDE;
     static constexpr bool WAVE = MODE == kWave || MODE == kWaveAbsorb;
     static constexpr bool PV = WAVE || MODE == kImage;   // second ring (u_prev|nu, vel|w[, g])
     static constexpr size_t SMEM_PV = PV ? (size_t)SP * PV_STRIDE : 0;
     static constexpr size_t SMEM = SMEM_L + SMEM_F + SMEM_PV + (SL + SP) * 8;
-    static constexpr int MIN_BLOCKS = NT > 128 ? 1 : (LOW ? 3 : 2);
+    static constexpr int MIN_BLOCKS = NT > 128 ? 1 : (LOW ? (RING ? 2 : 3) : (RING ? 3 : 2));
     // halo groups of 4 elements converted by all threads (16-bit): 2 side
     // groups per row and 16 groups per top/bottom halo row
     static constexpr int HALO_GROUPS = 2 * BH + 16 * 2 * R;
@@ -262,14 +264,14 @@ __device__ __forceinline__ f2 xpair(const float4 &lf, const float4 &cen, const f
 
 // One CTA's work: the output planes [z0, z1) of the 64 x TY tile at (tx0, ty0)
 // of the field described by p; t = time level of u, parity selects p.out.
-template <int R, int MODE, int TY, typename T>
+template <int R, int MODE, int TY, typename T, int RING = 0>
 __device__ __forceinline__ void tma_body(const CUtensorMap *__restrict__ pm_u, const CUtensorMap *__restrict__ pm_prev,
                                          const CUtensorMap *__restrict__ pm_vel, const CUtensorMap *__restrict__ pm_g,
                                          const StepParams &p,
                                          const int64_t tx0, const int64_t ty0, const int z0, const int z1,
                                          const int64_t t, const int parity)
 {
-    using C = Cfg<R, MODE, TY, T>;
+    using C = Cfg<R, MODE, TY, T, RING>;
     constexpr bool kLow = C::LOW;
     constexpr int Q = 2 * R + 1;               // z-queue length
     constexpr int U = kUnroll;
@@ -777,14 +779,15 @@ __global__ void __launch_bounds__(Cfg<R, MODE, TY, T>::NT, Cfg<R, MODE, TY, T>::
 
 // Many fields (shots) in one launch: CTA i does items[i].  Per-shot
 // parameters and TMA descriptors are read from device memory.
-template <int TY, typename T>
-__global__ void __launch_bounds__(Cfg<4, kWave, TY, T>::NT, Cfg<4, kWave, TY, T>::MIN_BLOCKS)
+template <int TY, typename T, int RING>
+__global__ void __launch_bounds__(Cfg<4, kWave, TY, T, RING>::NT, Cfg<4, kWave, TY, T, RING>::MIN_BLOCKS)
     k_tma_batch(const BatchItem *__restrict__ items, const StepParams *__restrict__ shots,
                 const CUtensorMap *__restrict__ maps, const int parity, const int64_t t)
 {
     const BatchItem it = items[blockIdx.x];
     const CUtensorMap *m = maps + ((int64_t)it.shot * 2 + parity) * 3;
-    tma_body<4, kWave, TY, T>(m, m + 1, m + 2, nullptr, shots[it.shot], it.tx0, it.ty0, it.z0, it.z1, t, parity);
+    tma_body<4, kWave, TY, T, RING>(m, m + 1, m + 2, nullptr, shots[it.shot], it.tx0, it.ty0, it.z0, it.z1, t,
+                                    parity);
 }
 
 // The dynamic shared-memory opt-in, set once per instantiation and device
@@ -806,7 +809,7 @@ cudaError_t prepare_cfg()
     return e;
 }
 
-template <int TY, typename T>
+template <int TY, typename T, int RING>
 cudaError_t prepare_batch_cfg()
 {
     static bool done[64] = {};
@@ -816,25 +819,39 @@ cudaError_t prepare_batch_cfg()
         return e;
     if (dev >= 0 && dev < 64 && done[dev])
         return cudaSuccess;
-    e = cudaFuncSetAttribute(k_tma_batch<TY, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Cfg<4, kWave, TY, T>::SMEM);
+    e = cudaFuncSetAttribute(k_tma_batch<TY, T, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Cfg<4, kWave, TY, T, RING>::SMEM);
     if (e == cudaSuccess && dev >= 0 && dev < 64)
         done[dev] = true;
     return e;
 }
 
-template <int TY, typename T>
+template <int TY, typename T, int RING>
 cudaError_t launch_batch_cfg(const BatchItem *items, int nitems, const StepParams *shots, const CUtensorMap *maps,
                              int parity, int64_t t, cudaStream_t st)
 {
-    cudaError_t e = prepare_batch_cfg<TY, T>();
+    cudaError_t e = prepare_batch_cfg<TY, T, RING>();
     if (e != cudaSuccess)
         return e;
     if (nitems <= 0)
         return cudaSuccess;
-    using C = Cfg<4, kWave, TY, T>;
-    k_tma_batch<TY, T><<<(unsigned)nitems, C::NT, C::SMEM, st>>>(items, shots, maps, parity, t);
+    using C = Cfg<4, kWave, TY, T, RING>;
+    k_tma_batch<TY, T, RING><<<(unsigned)nitems, C::NT, C::SMEM, st>>>(items, shots, maps, parity, t);
     return cudaGetLastError();
+}
+
+template <int TY, typename T>
+cudaError_t launch_batch_ring(int ring, const BatchItem *items, int nitems, const StepParams *shots,
+                              const CUtensorMap *maps, int parity, int64_t t, cudaStream_t st)
+{
+    return ring ? launch_batch_cfg<TY, T, 1>(items, nitems, shots, maps, parity, t, st)
+                : launch_batch_cfg<TY, T, 0>(items, nitems, shots, maps, parity, t, st);
+}
+
+template <int TY, typename T>
+cudaError_t prepare_batch_ring(int ring)
+{
+    return ring ? prepare_batch_cfg<TY, T, 1>() : prepare_batch_cfg<TY, T, 0>();
 }
 
 template <int R, int MODE, int TY, typename T>
@@ -916,34 +933,43 @@ cudaError_t launch_tma(int radius, Mode mode, int tile_y, gbs_dtype storage, con
                         : launch_stencil_r<kStencil, 16>(radius, plan, p, st);
 }
 
-cudaError_t launch_tma_batch(int tile_y, gbs_dtype storage, const BatchItem *items, int nitems,
+cudaError_t launch_tma_batch(int tile_y, gbs_dtype storage, int ring, const BatchItem *items, int nitems,
                              const StepParams *shots, const CUtensorMap *maps, int parity, int64_t t,
                              cudaStream_t st)
 {
     const bool t32 = tile_y == 32;
     switch (storage) {
     case GBS_F32:
-        return t32 ? launch_batch_cfg<32, float>(items, nitems, shots, maps, parity, t, st)
-                   : launch_batch_cfg<16, float>(items, nitems, shots, maps, parity, t, st);
+        return t32 ? launch_batch_ring<32, float>(ring, items, nitems, shots, maps, parity, t, st)
+                   : launch_batch_ring<16, float>(ring, items, nitems, shots, maps, parity, t, st);
     case GBS_BF16:
-        return t32 ? launch_batch_cfg<32, __nv_bfloat16>(items, nitems, shots, maps, parity, t, st)
-                   : launch_batch_cfg<16, __nv_bfloat16>(items, nitems, shots, maps, parity, t, st);
+        return t32 ? launch_batch_ring<32, __nv_bfloat16>(ring, items, nitems, shots, maps, parity, t, st)
+                   : launch_batch_ring<16, __nv_bfloat16>(ring, items, nitems, shots, maps, parity, t, st);
     case GBS_F16:
-        return t32 ? launch_batch_cfg<32, __half>(items, nitems, shots, maps, parity, t, st)
-                   : launch_batch_cfg<16, __half>(items, nitems, shots, maps, parity, t, st);
+        return t32 ? launch_batch_ring<32, __half>(ring, items, nitems, shots, maps, parity, t, st)
+                   : launch_batch_ring<16, __half>(ring, items, nitems, shots, maps, parity, t, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t tma_prepare_batch(gbs_dtype storage, int tile_y)
+cudaError_t tma_prepare_batch(gbs_dtype storage, int tile_y, int ring)
 {
     const bool t32 = tile_y == 32;
     switch (storage) {
-    case GBS_F32: return t32 ? prepare_batch_cfg<32, float>() : prepare_batch_cfg<16, float>();
-    case GBS_BF16: return t32 ? prepare_batch_cfg<32, __nv_bfloat16>() : prepare_batch_cfg<16, __nv_bfloat16>();
-    case GBS_F16: return t32 ? prepare_batch_cfg<32, __half>() : prepare_batch_cfg<16, __half>();
+    case GBS_F32: return t32 ? prepare_batch_ring<32, float>(ring) : prepare_batch_ring<16, float>(ring);
+    case GBS_BF16:
+        return t32 ? prepare_batch_ring<32, __nv_bfloat16>(ring) : prepare_batch_ring<16, __nv_bfloat16>(ring);
+    case GBS_F16: return t32 ? prepare_batch_ring<32, __half>(ring) : prepare_batch_ring<16, __half>(ring);
     default: return cudaErrorInvalidValue;
     }
+}
+
+int tma_batch_ring_stages(gbs_dtype storage, int tile_y, int ring)
+{
+    (void)tile_y;
+    if (storage == GBS_F32)
+        return ring ? Cfg<4, kWave, 16, float, 1>::SL : Cfg<4, kWave, 16, float, 0>::SL;
+    return ring ? Cfg<4, kWave, 16, __half, 1>::SL : Cfg<4, kWave, 16, __half, 0>::SL;
 }
 
 cudaError_t tma_prepare_wave_absorb(int tile_y)

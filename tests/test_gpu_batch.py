@@ -74,6 +74,9 @@ def test_fp32_batch_against_oracle(tiling):
     info = plan.info()
     assert info["tile_y"] in (16, 32) and info["items"] > 0
     assert info["points"] == sum(s["nx"] * s["ny"] * s["nz"] for s in specs)
+    # the queue depth: the single-field kernel's 9 u stages (FP32), or the
+    # shallower 7 the tuner may pick instead; steps are not fused in batches
+    assert info["ring_stages"] in ((9,) if tiling[0] else (9, 7)) and info["time_block"] == 1
     plan.run(nsteps)
     gbs.device_status()
     for k, (s, sh) in enumerate(zip(specs, shots)):
