@@ -22,13 +22,14 @@
 //
 // Storage: phi (3 components) and psi live only on the slabs, in a compact
 // layout of six boxes (z-low, z-high, y-low, y-high, x-low, x-high; each x
-// fastest), twice (the step reads one copy and writes the other).  A CTA
-// streams a 32 x 8 column of one box along z with u staged in shared memory.
+// fastest), twice (the step reads one copy and writes the other).  A
+// thread updates one slab point; the thread index is its compact index.
 #include "gbs_internal.cuh"
 
 namespace gbs {
 namespace {
 
+constexpr int kThreadsPml = 256;
 
 // Region bases and box sizes of the compact layout (32-bit: the host
 // rejects layers of 2^31 points or more).
@@ -86,8 +87,6 @@ __device__ __forceinline__ float masked(const float *__restrict__ f, int c)
     return c >= 0 ? v : 0.f;
 }
 
-constexpr int kR_PML = 4;
-
 struct PmlParams {
     Grid g;
     Slabs s;
@@ -109,126 +108,83 @@ __device__ __forceinline__ float zeta_of(const PmlParams &p, int d)
     return d < w1 ? p.zmax * r * r : 0.f;
 }
 
-// Bricks.  A CTA of kBX x kBY threads owns a kBX x kBY column of one slab
-// box over a z-chunk of up to kZC planes and streams it along z: each plane
-// of u around the brick ((kBX+8) x (kBY+8), loaded with coalesced reads) goes
-// into a ring of kQ planes in shared memory, so the 25-point stencil and the
-// central differences of u read shared memory.  The auxiliary fields are read
-// at the point and its six neighbours from the compact layout.
-constexpr int kBX = 32, kBY = 8, kZC = 64, kQ = 2 * kR_PML + 2;
-constexpr int kTW = kBX + 2 * kR_PML, kTH = kBY + 2 * kR_PML;
-
-struct BrickPlan {
-    int base[7];               // region r covers CTAs [base[r], base[r+1])
-    int nbx[6], nby[6], nzc[6];  // bricks in x, y and z-chunks per region
-};
-
-__global__ void __launch_bounds__(kBX * kBY) k_pml(const float *__restrict__ u_prev, const float *__restrict__ u,
-                                                  float *__restrict__ u_next, const float *__restrict__ vel,
-                                                  const __grid_constant__ PmlParams p,
-                                                  const __grid_constant__ BrickPlan bp)
+// One thread per slab point; the thread index is the point's compact index
+// (x fastest within each of the six boxes).
+__global__ void __launch_bounds__(kThreadsPml) k_pml(const float *__restrict__ u_prev, const float *__restrict__ u,
+                                                    float *__restrict__ u_next, const float *__restrict__ vel,
+                                                    const __grid_constant__ PmlParams p)
 {
-    __shared__ float ring[kQ][kTH][kTW];
     const Slabs &s = p.s;
-    const int cta = (int)blockIdx.x;
+    const int c = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= s.base[6])
+        return;
     int r = 0;
 #pragma unroll
     for (int q = 1; q < 6; ++q)
-        r += cta >= bp.base[q] ? 1 : 0;
+        r += c >= s.base[q] ? 1 : 0;
     int x0, y0, z0, bx, by, bz;
     region_box(s, r, x0, y0, z0, bx, by, bz);
-    const int l = cta - bp.base[r];
-    const int bxi = l % bp.nbx[r], t = l / bp.nbx[r];
-    const int byi = t % bp.nby[r], zci = t / bp.nby[r];
-    const int lx = (int)(threadIdx.x % kBX), ly = (int)(threadIdx.x / kBX);
-    const int li = bxi * kBX + lx, lj = byi * kBY + ly;       // point within the region box
-    const int i = x0 + li, j = y0 + lj;
-    const bool own = li < bx && lj < by;
-    const int kz0 = zci * kZC, kz1 = min(bz, kz0 + kZC);      // planes of the box, local
-    const int tx0 = x0 + bxi * kBX - kR_PML, ty0 = y0 + byi * kBY - kR_PML;   // tile origin (interior coordinates)
+    const int l = c - s.base[r];
+    const int li = l % bx, t = l / bx;
+    const int i = x0 + li, j = y0 + t % by, k = z0 + t / by;
 
     const Grid &g = p.g;
-    const int64_t plane = g.px * g.py;
-    // load plane k (interior z) of u around the brick into ring slot; cells
-    // past the padded array's last column or row (bricks overhanging the box)
-    // are no point's neighbours and are not read
-    const int xmax = (int)g.nx + g.halo - 1 - tx0, ymax = (int)g.ny + g.halo - 1 - ty0;
-    auto load_plane = [&](int k, int slot) {
-        const float *src = u + (g.halo + tx0) + g.px * (int64_t)(g.halo + ty0) + plane * (int64_t)(g.halo + k);
-        for (int e = (int)threadIdx.x; e < kTW * kTH; e += kBX * kBY) {
-            const int ex = e % kTW, ey = e / kTW;
-            if (ex <= xmax && ey <= ymax)
-                ring[slot][ey][ex] = __ldg(src + ex + g.px * (int64_t)ey);
-        }
-    };
-    const int zfirst = z0 + kz0;
-    for (int q = 0; q < 2 * kR_PML; ++q)
-        load_plane(zfirst - kR_PML + q, q);
-
-    const int dx = min(i, s.nx - 1 - i), dy = min(j, s.ny - 1 - j);
-    const float zx = zeta_of(p, dx), zy = zeta_of(p, dy);
-    const float dt = p.dt, inv2h = 0.5f / p.h;
-    const float c0 = p.c[0] + p.c[0] + p.c[0];
+    const int64_t sy = g.px, sz = g.px * g.py;
+    const int64_t at = (g.halo + i) + g.px * ((g.halo + j) + g.py * (int64_t)(g.halo + k));
+    // neighbours of the auxiliary fields (central differences)
+    const int cxm = nb_index(s, i - 1, j, k), cxp = nb_index(s, i + 1, j, k);
+    const int cym = nb_index(s, i, j - 1, k), cyp = nb_index(s, i, j + 1, k);
+    const int czm = nb_index(s, i, j, k - 1), czp = nb_index(s, i, j, k + 1);
     const float *__restrict__ phx = p.phi_in[0];
     const float *__restrict__ phy = p.phi_in[1];
     const float *__restrict__ phz = p.phi_in[2];
     const float *__restrict__ psin = p.psi_in;
-    const int sx = lx + kR_PML, sy = ly + kR_PML;
-    for (int kk = kz0; kk < kz1; ++kk) {
-        const int k = z0 + kk;
-        const int q0 = (kk - kz0) % kQ;                 // slot of plane k - R
-        load_plane(k + kR_PML, (q0 + 2 * kR_PML) % kQ);
-        __syncthreads();
-        if (own) {
-            const int qc = (q0 + kR_PML) % kQ;
-            const float uc = ring[qc][sy][sx];
-            float lap = c0 * uc;
+    const float div_h2 = 0.5f * p.h *
+                         ((masked(phx, cxp) - masked(phx, cxm)) + (masked(phy, cyp) - masked(phy, cym)) +
+                          (masked(phz, czp) - masked(phz, czm)));
+    const float uc = __ldg(u + at);
+    // the 25-point operator with unit-spacing weights: centre, then
+    // distance 1..4 (x, y, z pairs)
+    float lap = (p.c[0] + p.c[0] + p.c[0]) * uc;
+    float du[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-            for (int m = 1; m <= kR_PML; ++m) {
-                const float zs = ring[(q0 + kR_PML + m) % kQ][sy][sx] + ring[(q0 + kR_PML - m) % kQ][sy][sx];
-                lap += p.c[m] * ((ring[qc][sy][sx + m] + ring[qc][sy][sx - m]) +
-                                 (ring[qc][sy + m][sx] + ring[qc][sy - m][sx]) + zs);
-            }
-            const float du[3] = {ring[qc][sy][sx + 1] - ring[qc][sy][sx - 1], ring[qc][sy + 1][sx] - ring[qc][sy - 1][sx],
-                                 ring[(q0 + kR_PML + 1) % kQ][sy][sx] - ring[(q0 + kR_PML - 1) % kQ][sy][sx]};
-            const int c = s.base[r] + li + bx * (lj + by * kk);
-            // neighbours in the compact layout: inside the box at fixed offsets, else looked up
-            const int cxm = li > 0 ? c - 1 : nb_index(s, i - 1, j, k);
-            const int cxp = li + 1 < bx ? c + 1 : nb_index(s, i + 1, j, k);
-            const int cym = lj > 0 ? c - bx : nb_index(s, i, j - 1, k);
-            const int cyp = lj + 1 < by ? c + bx : nb_index(s, i, j + 1, k);
-            const int czm = kk > 0 ? c - bx * by : nb_index(s, i, j, k - 1);
-            const int czp = kk + 1 < bz ? c + bx * by : nb_index(s, i, j, k + 1);
-            const float div_h2 = 0.5f * p.h *
-                                 ((masked(phx, cxp) - masked(phx, cxm)) + (masked(phy, cyp) - masked(phy, cym)) +
-                                  (masked(phz, czp) - masked(phz, czm)));
-            const int dz = p.free_top ? s.nz - 1 - k : min(k, s.nz - 1 - k);
-            const float zz = zeta_of(p, dz);
-            const float S1 = zx + zy + zz;
-            const float S2 = zx * zy + zy * zz + zz * zx;
-            const float S3 = zx * zy * zz;
-            const int64_t at = (g.halo + i) + g.px * ((g.halo + j) + g.py * (int64_t)(g.halo + k));
-            const float psi = __ldg(psin + c);
-            const float vs = __ldg(vel + at) * p.sdt;
-            const float A = 1.f / (1.f + 0.5f * dt * S1), B = 1.f - 0.5f * dt * S1;
-            const float un =
-                A * (2.f * uc - B * __ldg(u_prev + at) + vs * vs * (lap + div_h2) - dt * dt * (S2 * uc + S3 * psi));
-            u_next[at] = un;
-            p.psi_out[c] = psi + dt * un;
-            const float zeta[3] = {zx, zy, zz};
-            const float aj[3] = {zy + zz - zx, zz + zx - zy, zx + zy - zz};
-            const float bj[3] = {zy * zz, zz * zx, zx * zy};
-            const int cm[3] = {cxm, cym, czm}, cp[3] = {cxp, cyp, czp};
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                // psi's central difference matters only where b_q != 0 (edges and corners of the layer)
-                const float dpsi = bj[q] != 0.f ? (masked(psin, cp[q]) - masked(psin, cm[q])) * inv2h : 0.f;
-                const float ph = __ldg(p.phi_in[q] + c);
-                p.phi_out[q][c] = ((1.f - 0.5f * dt * zeta[q]) * ph + dt * (aj[q] * du[q] * inv2h + bj[q] * dpsi)) /
-                                  (1.f + 0.5f * dt * zeta[q]);
-            }
+    for (int m = 1; m <= 4; ++m) {
+        const float xm = __ldg(u + at - m), xp = __ldg(u + at + m);
+        const float ym = __ldg(u + at - m * sy), yp = __ldg(u + at + m * sy);
+        const float zm = __ldg(u + at - m * sz), zp = __ldg(u + at + m * sz);
+        if (m == 1) {
+            du[0] = xp - xm;
+            du[1] = yp - ym;
+            du[2] = zp - zm;
         }
-        __syncthreads();   // the slot of plane k - R is refilled next
+        lap += p.c[m] * ((xp + xm) + (yp + ym) + (zp + zm));
+    }
+    const int dx = min(i, s.nx - 1 - i), dy = min(j, s.ny - 1 - j);
+    const int dz = p.free_top ? s.nz - 1 - k : min(k, s.nz - 1 - k);
+    const float zx = zeta_of(p, dx), zy = zeta_of(p, dy), zz = zeta_of(p, dz);
+    const float S1 = zx + zy + zz;
+    const float S2 = zx * zy + zy * zz + zz * zx;
+    const float S3 = zx * zy * zz;
+    const float dt = p.dt, inv2h = 0.5f / p.h;
+    const float psi = __ldg(psin + c);
+    const float vs = __ldg(vel + at) * p.sdt;
+    const float A = 1.f / (1.f + 0.5f * dt * S1), B = 1.f - 0.5f * dt * S1;
+    const float un =
+        A * (2.f * uc - B * __ldg(u_prev + at) + vs * vs * (lap + div_h2) - dt * dt * (S2 * uc + S3 * psi));
+    u_next[at] = un;
+    p.psi_out[c] = psi + dt * un;
+    // phi^{n+1/2}
+    const float zeta[3] = {zx, zy, zz};
+    const float aj[3] = {zy + zz - zx, zz + zx - zy, zx + zy - zz};
+    const float bj[3] = {zy * zz, zz * zx, zx * zy};
+    const int cm[3] = {cxm, cym, czm}, cp[3] = {cxp, cyp, czp};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        // psi's central difference matters only where b_q != 0 (edges and corners of the layer)
+        const float dpsi = bj[q] != 0.f ? (masked(psin, cp[q]) - masked(psin, cm[q])) * inv2h : 0.f;
+        const float ph = __ldg(p.phi_in[q] + c);
+        p.phi_out[q][c] = ((1.f - 0.5f * dt * zeta[q]) * ph + dt * (aj[q] * du[q] * inv2h + bj[q] * dpsi)) /
+                          (1.f + 0.5f * dt * zeta[q]);
     }
 }
 
@@ -278,31 +234,10 @@ cudaError_t launch_pml(const Grid &g, const float *u_prev, const float *u, float
     }
     p.psi_in = state_in + 3 * n;
     p.psi_out = state_out + 3 * n;
-    BrickPlan bp;
-    bp.base[0] = 0;
-    for (int r = 0; r < 6; ++r) {
-        int x0, y0, z0, bx, by, bz;
-        // region boxes as the kernel computes them
-        const int w_ = s.w, nm_ = s.nz - s.w - s.zl;
-        if (r < 2) {
-            bx = s.nx; by = s.ny; bz = r == 0 ? s.zl : w_;
-        } else if (r < 4) {
-            bx = s.nx; by = w_; bz = nm_;
-        } else {
-            bx = w_; by = s.ny - 2 * w_; bz = nm_;
-        }
-        (void)x0; (void)y0; (void)z0;
-        bp.nbx[r] = (bx + kBX - 1) / kBX;
-        bp.nby[r] = (by + kBY - 1) / kBY;
-        bp.nzc[r] = (bz + kZC - 1) / kZC;
-        const int64_t n = bz > 0 ? (int64_t)bp.nbx[r] * bp.nby[r] * bp.nzc[r] : 0;
-        if ((int64_t)bp.base[r] + n > 0x7fffffff)
-            return cudaErrorInvalidValue;
-        bp.base[r + 1] = bp.base[r] + (int)n;
-    }
-    if (bp.base[6] <= 0)
+    const int64_t blocks = ((int64_t)s.base[6] + kThreadsPml - 1) / kThreadsPml;
+    if (blocks <= 0)
         return cudaSuccess;
-    k_pml<<<(unsigned)bp.base[6], kBX * kBY, 0, st>>>(u_prev, u, u_next, vel, p, bp);
+    k_pml<<<(unsigned)blocks, kThreadsPml, 0, st>>>(u_prev, u, u_next, vel, p);
     return cudaGetLastError();
 }
 

@@ -133,3 +133,25 @@ def test_time_block_two_is_the_pair_path_and_bad_blocks_are_rejected():
         gbs.wave_propagate_tbn(to_dev(up), to_dev(u), d_vel, dt, h, halo, 10, 4)
     assert gbs.tbn_workspace_bytes(64, 64, 64, 4, 3) > gbs.tbn_workspace_bytes(64, 64, 64, 4, 2) > 0
     assert gbs.tbn_workspace_bytes(64, 64, 64, 4, 1) == 0
+
+
+def test_three_steps_with_the_absorbing_layer():
+    """The damping layer on three steps per launch against single steps
+    with the same layer (both against the multi-step bound, on a layered
+    model with the layer over a quarter of each axis)."""
+    need_gpu()
+    n, nsteps, width = 96, 12, 12
+    up, u, vel, dt, h, halo, src, amp, _ = _case((n, n, n), nsteps, 95)
+    assert gbs.tbn_supported(n, n, n, halo, 3)[0]
+    eta_max = 3 * float(W.interior(vel, halo).max()) * np.log(1e3) / (2 * width * h)
+    d_vel, si, sa = to_dev(vel), to_dev(src), to_dev(amp)
+    p1, c1 = gbs.wave_propagate(to_dev(up), to_dev(u), d_vel, dt, h, halo, nsteps, src_idx=si, src_amp=sa,
+                                absorb=(width, eta_max))
+    p3, c3 = gbs.wave_propagate_tbn(to_dev(up), to_dev(u), d_vel, dt, h, halo, nsteps, 3, src_idx=si, src_amp=sa,
+                                    absorb=(width, eta_max))
+    gbs.device_status()
+    eta = oracle.absorbing_eta(n, n, n, halo, width, eta_max)
+    rp, ru = oracle.wave_propagate_damped(up, u, vel, eta, dt, h, halo, nsteps, src_idx=src, src_amp=amp)
+    for got, ref in ((c3, ru), (p3, rp), (c1, ru)):
+        e = oracle.err_norms(got.cpu().numpy(), ref)
+        assert e["finite"] and e["norm_max_rel"] <= tol_steps(nsteps), e
