@@ -23,13 +23,27 @@
 // Storage: phi (3 components) and psi live only on the slabs, in a compact
 // layout of six boxes (z-low, z-high, y-low, y-high, x-low, x-high; each x
 // fastest), twice (the step reads one copy and writes the other).  A
-// thread updates one slab point; the thread index is its compact index.
+// block covers a TX x TY tile of one box over kZB consecutive planes (TX x
+// TY = 256, TX chosen per box so that the tiles waste the fewest lanes); a
+// thread updates one (x, y) column of the tile plane by plane.  Inside a box
+// the neighbours of the auxiliary fields are at fixed compact offsets
+// (1, bx, bx by); only threads on a box face take the general index.
 #include "gbs_internal.cuh"
 
 namespace gbs {
 namespace {
 
 constexpr int kThreadsPml = 256;
+constexpr int kZB = 8;        // planes per block (a column's planes share their z neighbours in L1)
+
+// Block tiling of the six boxes: box r has nbx x nby tiles of 2^ltx x
+// 2^(8-ltx) points per plane and nbz groups of kZB planes; its blocks are
+// [bstart[r], bstart[r+1]).
+struct BoxTiles {
+    int ltx[6];
+    int nbx[6], nby[6];
+    int bstart[7];
+};
 
 // Region bases and box sizes of the compact layout (32-bit: the host
 // rejects layers of 2^31 points or more).
@@ -99,6 +113,7 @@ struct PmlParams {
     const float *psi_in;
     float *phi_out[3];
     float *psi_out;
+    BoxTiles bt;
 };
 
 __device__ __forceinline__ float zeta_of(const PmlParams &p, int d)
@@ -108,83 +123,107 @@ __device__ __forceinline__ float zeta_of(const PmlParams &p, int d)
     return d < w1 ? p.zmax * r * r : 0.f;
 }
 
-// One thread per slab point; the thread index is the point's compact index
-// (x fastest within each of the six boxes).
-__global__ void __launch_bounds__(kThreadsPml) k_pml(const float *__restrict__ u_prev, const float *__restrict__ u,
+// Neighbour of compact index c in box r at (li, lj, lk) of a box of
+// bx x by x bz points, one step along an axis: a fixed offset inside the
+// box, the general index on a face.
+__device__ __forceinline__ int nb_step(const Slabs &s, int c, int off, bool inside, int i, int j, int k)
+{
+    return inside ? c + off : nb_index(s, i, j, k);
+}
+
+// Block b: box r, tile (bxi, byi), planes [kZB bzi, kZB bzi + kZB) of the box.
+// Five blocks per SM (48 registers): the loads of a point are independent,
+// and more warps in flight beat more registers per thread here.
+__global__ void __launch_bounds__(kThreadsPml, 5) k_pml(const float *__restrict__ u_prev, const float *__restrict__ u,
                                                     float *__restrict__ u_next, const float *__restrict__ vel,
                                                     const __grid_constant__ PmlParams p)
 {
     const Slabs &s = p.s;
-    const int c = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (c >= s.base[6])
-        return;
+    const BoxTiles &bt = p.bt;
+    const int b = (int)blockIdx.x;
     int r = 0;
 #pragma unroll
     for (int q = 1; q < 6; ++q)
-        r += c >= s.base[q] ? 1 : 0;
+        r += b >= bt.bstart[q] ? 1 : 0;
     int x0, y0, z0, bx, by, bz;
     region_box(s, r, x0, y0, z0, bx, by, bz);
-    const int l = c - s.base[r];
-    const int li = l % bx, t = l / bx;
-    const int i = x0 + li, j = y0 + t % by, k = z0 + t / by;
+    const int ltx = bt.ltx[r];
+    int q = b - bt.bstart[r];
+    const int bxi = q % bt.nbx[r];
+    q /= bt.nbx[r];
+    const int byi = q % bt.nby[r];
+    const int bzi = q / bt.nby[r];
+    const int li = (bxi << ltx) + (int)(threadIdx.x & ((1u << ltx) - 1u));
+    const int lj = (byi << (8 - ltx)) + (int)(threadIdx.x >> ltx);
+    if (li >= bx || lj >= by)
+        return;
+    const int i = x0 + li, j = y0 + lj;
+    const int sxy = bx * by;
 
     const Grid &g = p.g;
     const int64_t sy = g.px, sz = g.px * g.py;
-    const int64_t at = (g.halo + i) + g.px * ((g.halo + j) + g.py * (int64_t)(g.halo + k));
-    // neighbours of the auxiliary fields (central differences)
-    const int cxm = nb_index(s, i - 1, j, k), cxp = nb_index(s, i + 1, j, k);
-    const int cym = nb_index(s, i, j - 1, k), cyp = nb_index(s, i, j + 1, k);
-    const int czm = nb_index(s, i, j, k - 1), czp = nb_index(s, i, j, k + 1);
     const float *__restrict__ phx = p.phi_in[0];
     const float *__restrict__ phy = p.phi_in[1];
     const float *__restrict__ phz = p.phi_in[2];
     const float *__restrict__ psin = p.psi_in;
-    const float div_h2 = 0.5f * p.h *
-                         ((masked(phx, cxp) - masked(phx, cxm)) + (masked(phy, cyp) - masked(phy, cym)) +
-                          (masked(phz, czp) - masked(phz, czm)));
-    const float uc = __ldg(u + at);
-    // the 25-point operator with unit-spacing weights: centre, then
-    // distance 1..4 (x, y, z pairs)
-    float lap = (p.c[0] + p.c[0] + p.c[0]) * uc;
-    float du[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int m = 1; m <= 4; ++m) {
-        const float xm = __ldg(u + at - m), xp = __ldg(u + at + m);
-        const float ym = __ldg(u + at - m * sy), yp = __ldg(u + at + m * sy);
-        const float zm = __ldg(u + at - m * sz), zp = __ldg(u + at + m * sz);
-        if (m == 1) {
-            du[0] = xp - xm;
-            du[1] = yp - ym;
-            du[2] = zp - zm;
-        }
-        lap += p.c[m] * ((xp + xm) + (yp + ym) + (zp + zm));
-    }
     const int dx = min(i, s.nx - 1 - i), dy = min(j, s.ny - 1 - j);
-    const int dz = p.free_top ? s.nz - 1 - k : min(k, s.nz - 1 - k);
-    const float zx = zeta_of(p, dx), zy = zeta_of(p, dy), zz = zeta_of(p, dz);
-    const float S1 = zx + zy + zz;
-    const float S2 = zx * zy + zy * zz + zz * zx;
-    const float S3 = zx * zy * zz;
+    const float zx = zeta_of(p, dx), zy = zeta_of(p, dy);
     const float dt = p.dt, inv2h = 0.5f / p.h;
-    const float psi = __ldg(psin + c);
-    const float vs = __ldg(vel + at) * p.sdt;
-    const float A = 1.f / (1.f + 0.5f * dt * S1), B = 1.f - 0.5f * dt * S1;
-    const float un =
-        A * (2.f * uc - B * __ldg(u_prev + at) + vs * vs * (lap + div_h2) - dt * dt * (S2 * uc + S3 * psi));
-    u_next[at] = un;
-    p.psi_out[c] = psi + dt * un;
-    // phi^{n+1/2}
-    const float zeta[3] = {zx, zy, zz};
-    const float aj[3] = {zy + zz - zx, zz + zx - zy, zx + zy - zz};
-    const float bj[3] = {zy * zz, zz * zx, zx * zy};
-    const int cm[3] = {cxm, cym, czm}, cp[3] = {cxp, cyp, czp};
+    const bool xm_in = li > 0, xp_in = li < bx - 1, ym_in = lj > 0, yp_in = lj < by - 1;
+#pragma unroll 1
+    for (int lk = bzi * kZB; lk < min(bz, bzi * kZB + kZB); ++lk) {
+        const int k = z0 + lk;
+        const int c = s.base[r] + li + bx * (lj + by * lk);
+        const int64_t at = (g.halo + i) + g.px * ((g.halo + j) + g.py * (int64_t)(g.halo + k));
+        // neighbours of the auxiliary fields (central differences)
+        const int cxm = nb_step(s, c, -1, xm_in, i - 1, j, k), cxp = nb_step(s, c, 1, xp_in, i + 1, j, k);
+        const int cym = nb_step(s, c, -bx, ym_in, i, j - 1, k), cyp = nb_step(s, c, bx, yp_in, i, j + 1, k);
+        const int czm = nb_step(s, c, -sxy, lk > 0, i, j, k - 1), czp = nb_step(s, c, sxy, lk < bz - 1, i, j, k + 1);
+        const float div_h2 = 0.5f * p.h *
+                             ((masked(phx, cxp) - masked(phx, cxm)) + (masked(phy, cyp) - masked(phy, cym)) +
+                              (masked(phz, czp) - masked(phz, czm)));
+        const float uc = __ldg(u + at);
+        // the 25-point operator with unit-spacing weights: centre, then
+        // distance 1..4 (x, y, z pairs)
+        float lap = (p.c[0] + p.c[0] + p.c[0]) * uc;
+        float du[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        // psi's central difference matters only where b_q != 0 (edges and corners of the layer)
-        const float dpsi = bj[q] != 0.f ? (masked(psin, cp[q]) - masked(psin, cm[q])) * inv2h : 0.f;
-        const float ph = __ldg(p.phi_in[q] + c);
-        p.phi_out[q][c] = ((1.f - 0.5f * dt * zeta[q]) * ph + dt * (aj[q] * du[q] * inv2h + bj[q] * dpsi)) /
-                          (1.f + 0.5f * dt * zeta[q]);
+        for (int m = 1; m <= 4; ++m) {
+            const float xm = __ldg(u + at - m), xp = __ldg(u + at + m);
+            const float ym = __ldg(u + at - m * sy), yp = __ldg(u + at + m * sy);
+            const float zm = __ldg(u + at - m * sz), zp = __ldg(u + at + m * sz);
+            if (m == 1) {
+                du[0] = xp - xm;
+                du[1] = yp - ym;
+                du[2] = zp - zm;
+            }
+            lap += p.c[m] * ((xp + xm) + (yp + ym) + (zp + zm));
+        }
+        const int dz = p.free_top ? s.nz - 1 - k : min(k, s.nz - 1 - k);
+        const float zz = zeta_of(p, dz);
+        const float S1 = zx + zy + zz;
+        const float S2 = zx * zy + zy * zz + zz * zx;
+        const float S3 = zx * zy * zz;
+        const float psi = __ldg(psin + c);
+        const float vs = __ldg(vel + at) * p.sdt;
+        const float A = 1.f / (1.f + 0.5f * dt * S1), B = 1.f - 0.5f * dt * S1;
+        const float un =
+            A * (2.f * uc - B * __ldg(u_prev + at) + vs * vs * (lap + div_h2) - dt * dt * (S2 * uc + S3 * psi));
+        u_next[at] = un;
+        p.psi_out[c] = psi + dt * un;
+        // phi^{n+1/2}
+        const float zeta[3] = {zx, zy, zz};
+        const float aj[3] = {zy + zz - zx, zz + zx - zy, zx + zy - zz};
+        const float bj[3] = {zy * zz, zz * zx, zx * zy};
+        const int cm[3] = {cxm, cym, czm}, cp[3] = {cxp, cyp, czp};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            // psi's central difference matters only where b_a != 0 (edges and corners of the layer)
+            const float dpsi = bj[a] != 0.f ? (masked(psin, cp[a]) - masked(psin, cm[a])) * inv2h : 0.f;
+            const float ph = __ldg(p.phi_in[a] + c);
+            p.phi_out[a][c] = ((1.f - 0.5f * dt * zeta[a]) * ph + dt * (aj[a] * du[a] * inv2h + bj[a] * dpsi)) /
+                              (1.f + 0.5f * dt * zeta[a]);
+        }
     }
 }
 
@@ -234,9 +273,34 @@ cudaError_t launch_pml(const Grid &g, const float *u_prev, const float *u, float
     }
     p.psi_in = state_in + 3 * n;
     p.psi_out = state_out + 3 * n;
-    const int64_t blocks = ((int64_t)s.base[6] + kThreadsPml - 1) / kThreadsPml;
+    // tile shape per box: the fewest padded points, then the preferred width
+    // (32 x 8 keeps the y neighbours of a block close)
+    BoxTiles &bt = p.bt;
+    int64_t blocks = 0;
+    for (int r = 0; r < 6; ++r) {
+        const int bxr = r < 4 ? s.nx : w, byr = r < 2 ? s.ny : (r < 4 ? w : s.ny - 2 * w);
+        static const int pref[6] = {5, 6, 4, 7, 3, 8};
+        int best = -1;
+        int64_t best_area = 0;
+        for (int e : pref) {
+            const int tx = 1 << e, ty = kThreadsPml / tx;
+            const int64_t area = (int64_t)((bxr + tx - 1) / tx) * tx * ((byr + ty - 1) / ty) * ty;
+            if (best < 0 || area < best_area) {
+                best = e;
+                best_area = area;
+            }
+        }
+        bt.ltx[r] = best;
+        bt.nbx[r] = (bxr + (1 << best) - 1) >> best;
+        bt.nby[r] = (byr + (kThreadsPml >> best) - 1) / (kThreadsPml >> best);
+        bt.bstart[r] = (int)blocks;
+        blocks += (int64_t)bt.nbx[r] * bt.nby[r] * ((zb[r] + kZB - 1) / kZB);
+    }
+    bt.bstart[6] = (int)blocks;
     if (blocks <= 0)
         return cudaSuccess;
+    if (blocks >= ((int64_t)1 << 31))
+        return cudaErrorInvalidValue;
     k_pml<<<(unsigned)blocks, kThreadsPml, 0, st>>>(u_prev, u, u_next, vel, p);
     return cudaGetLastError();
 }
