@@ -123,18 +123,12 @@ __device__ __forceinline__ float zeta_of(const PmlParams &p, int d)
     return d < w1 ? p.zmax * r * r : 0.f;
 }
 
-// Neighbour of compact index c in box r at (li, lj, lk) of a box of
-// bx x by x bz points, one step along an axis: a fixed offset inside the
-// box, the general index on a face.
-__device__ __forceinline__ int nb_step(const Slabs &s, int c, int off, bool inside, int i, int j, int k)
-{
-    return inside ? c + off : nb_index(s, i, j, k);
-}
-
 // Block b: box r, tile (bxi, byi), planes [kZB bzi, kZB bzi + kZB) of the box.
-// Five blocks per SM (48 registers): the loads of a point are independent,
-// and more warps in flight beat more registers per thread here.
-__global__ void __launch_bounds__(kThreadsPml, 5) k_pml(const float *__restrict__ u_prev, const float *__restrict__ u,
+// Four blocks per SM (64 registers): the loads of a point are independent,
+// and warps in flight beat registers per thread here (two blocks per SM at
+// 106 registers ran at half the rate).  The divisors of the phi update are
+// reciprocals taken once per column (x, y) or plane (z).
+__global__ void __launch_bounds__(kThreadsPml, 4) k_pml(const float *__restrict__ u_prev, const float *__restrict__ u,
                                                     float *__restrict__ u_next, const float *__restrict__ vel,
                                                     const __grid_constant__ PmlParams p)
 {
@@ -161,7 +155,7 @@ __global__ void __launch_bounds__(kThreadsPml, 5) k_pml(const float *__restrict_
     const int sxy = bx * by;
 
     const Grid &g = p.g;
-    const int64_t sy = g.px, sz = g.px * g.py;
+    const int sy = (int)g.px, sz = (int)(g.px * g.py);
     const float *__restrict__ phx = p.phi_in[0];
     const float *__restrict__ phy = p.phi_in[1];
     const float *__restrict__ phz = p.phi_in[2];
@@ -169,29 +163,41 @@ __global__ void __launch_bounds__(kThreadsPml, 5) k_pml(const float *__restrict_
     const int dx = min(i, s.nx - 1 - i), dy = min(j, s.ny - 1 - j);
     const float zx = zeta_of(p, dx), zy = zeta_of(p, dy);
     const float dt = p.dt, inv2h = 0.5f / p.h;
+    const float rx = 1.f / (1.f + 0.5f * dt * zx), ry = 1.f / (1.f + 0.5f * dt * zy);
     const bool xm_in = li > 0, xp_in = li < bx - 1, ym_in = lj > 0, yp_in = lj < by - 1;
 #pragma unroll 1
     for (int lk = bzi * kZB; lk < min(bz, bzi * kZB + kZB); ++lk) {
         const int k = z0 + lk;
         const int c = s.base[r] + li + bx * (lj + by * lk);
         const int64_t at = (g.halo + i) + g.px * ((g.halo + j) + g.py * (int64_t)(g.halo + k));
-        // neighbours of the auxiliary fields (central differences)
-        const int cxm = nb_step(s, c, -1, xm_in, i - 1, j, k), cxp = nb_step(s, c, 1, xp_in, i + 1, j, k);
-        const int cym = nb_step(s, c, -bx, ym_in, i, j - 1, k), cyp = nb_step(s, c, bx, yp_in, i, j + 1, k);
-        const int czm = nb_step(s, c, -sxy, lk > 0, i, j, k - 1), czp = nb_step(s, c, sxy, lk < bz - 1, i, j, k + 1);
+        const float *__restrict__ up = u + at;
+        // neighbours of the auxiliary fields (central differences): fixed
+        // offsets inside the box; warps with a lane on a box face fix theirs
+        // up with the general index (a warp-uniform branch)
+        int cxm = c - 1, cxp = c + 1, cym = c - bx, cyp = c + bx, czm = c - sxy, czp = c + sxy;
+        const bool zm_in = lk > 0, zp_in = lk < bz - 1;
+        const bool face = !(xm_in && xp_in && ym_in && yp_in && zm_in && zp_in);
+        if (__any_sync(__activemask(), face)) {
+            if (!xm_in) cxm = nb_index(s, i - 1, j, k);
+            if (!xp_in) cxp = nb_index(s, i + 1, j, k);
+            if (!ym_in) cym = nb_index(s, i, j - 1, k);
+            if (!yp_in) cyp = nb_index(s, i, j + 1, k);
+            if (!zm_in) czm = nb_index(s, i, j, k - 1);
+            if (!zp_in) czp = nb_index(s, i, j, k + 1);
+        }
         const float div_h2 = 0.5f * p.h *
                              ((masked(phx, cxp) - masked(phx, cxm)) + (masked(phy, cyp) - masked(phy, cym)) +
                               (masked(phz, czp) - masked(phz, czm)));
-        const float uc = __ldg(u + at);
+        const float uc = __ldg(up);
         // the 25-point operator with unit-spacing weights: centre, then
         // distance 1..4 (x, y, z pairs)
         float lap = (p.c[0] + p.c[0] + p.c[0]) * uc;
         float du[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int m = 1; m <= 4; ++m) {
-            const float xm = __ldg(u + at - m), xp = __ldg(u + at + m);
-            const float ym = __ldg(u + at - m * sy), yp = __ldg(u + at + m * sy);
-            const float zm = __ldg(u + at - m * sz), zp = __ldg(u + at + m * sz);
+            const float xm = __ldg(up - m), xp = __ldg(up + m);
+            const float ym = __ldg(up - m * sy), yp = __ldg(up + m * sy);
+            const float zm = __ldg(up - m * sz), zp = __ldg(up + m * sz);
             if (m == 1) {
                 du[0] = xp - xm;
                 du[1] = yp - ym;
@@ -213,6 +219,7 @@ __global__ void __launch_bounds__(kThreadsPml, 5) k_pml(const float *__restrict_
         p.psi_out[c] = psi + dt * un;
         // phi^{n+1/2}
         const float zeta[3] = {zx, zy, zz};
+        const float rq[3] = {rx, ry, 1.f / (1.f + 0.5f * dt * zz)};
         const float aj[3] = {zy + zz - zx, zz + zx - zy, zx + zy - zz};
         const float bj[3] = {zy * zz, zz * zx, zx * zy};
         const int cm[3] = {cxm, cym, czm}, cp[3] = {cxp, cyp, czp};
@@ -221,8 +228,7 @@ __global__ void __launch_bounds__(kThreadsPml, 5) k_pml(const float *__restrict_
             // psi's central difference matters only where b_a != 0 (edges and corners of the layer)
             const float dpsi = bj[a] != 0.f ? (masked(psin, cp[a]) - masked(psin, cm[a])) * inv2h : 0.f;
             const float ph = __ldg(p.phi_in[a] + c);
-            p.phi_out[a][c] = ((1.f - 0.5f * dt * zeta[a]) * ph + dt * (aj[a] * du[a] * inv2h + bj[a] * dpsi)) /
-                              (1.f + 0.5f * dt * zeta[a]);
+            p.phi_out[a][c] = ((1.f - 0.5f * dt * zeta[a]) * ph + dt * (aj[a] * du[a] * inv2h + bj[a] * dpsi)) * rq[a];
         }
     }
 }
