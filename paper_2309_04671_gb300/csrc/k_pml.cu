@@ -165,21 +165,23 @@ __global__ void __launch_bounds__(kThreadsPml, 4) k_pml(const float *__restrict_
     const float dt = p.dt, inv2h = 0.5f / p.h;
     const float rx = 1.f / (1.f + 0.5f * dt * zx), ry = 1.f / (1.f + 0.5f * dt * zy);
     const bool xm_in = li > 0, xp_in = li < bx - 1, ym_in = lj > 0, yp_in = lj < by - 1;
+    const int lk0 = bzi * kZB;
+    int c = s.base[r] + li + bx * (lj + by * lk0);
+    int64_t at = (g.halo + i) + g.px * ((g.halo + j) + g.py * (int64_t)(g.halo + z0 + lk0));
 #pragma unroll 1
-    for (int lk = bzi * kZB; lk < min(bz, bzi * kZB + kZB); ++lk) {
+    for (int lk = lk0; lk < min(bz, lk0 + kZB); ++lk, c += sxy, at += sz) {
         const int k = z0 + lk;
-        const int c = s.base[r] + li + bx * (lj + by * lk);
-        const int64_t at = (g.halo + i) + g.px * ((g.halo + j) + g.py * (int64_t)(g.halo + k));
         const float *__restrict__ up = u + at;
         // neighbours of the auxiliary fields (central differences): fixed
         // offsets inside the box; warps with a lane on a box face fix theirs
         // up with the general index (a warp-uniform branch)
-        int cxm = c - 1, cxp = c + 1, cym = c - bx, cyp = c + bx, czm = c - sxy, czp = c + sxy;
+        // An x face of any box borders the halo or the inner box (no slab
+        // shares an x face), so its neighbour has no auxiliary value.
+        const int cxm = xm_in ? c - 1 : -1, cxp = xp_in ? c + 1 : -1;
+        int cym = c - bx, cyp = c + bx, czm = c - sxy, czp = c + sxy;
         const bool zm_in = lk > 0, zp_in = lk < bz - 1;
-        const bool face = !(xm_in && xp_in && ym_in && yp_in && zm_in && zp_in);
+        const bool face = !(ym_in && yp_in && zm_in && zp_in);
         if (__any_sync(__activemask(), face)) {
-            if (!xm_in) cxm = nb_index(s, i - 1, j, k);
-            if (!xp_in) cxp = nb_index(s, i + 1, j, k);
             if (!ym_in) cym = nb_index(s, i, j - 1, k);
             if (!yp_in) cyp = nb_index(s, i, j + 1, k);
             if (!zm_in) czm = nb_index(s, i, j, k - 1);
