@@ -34,7 +34,7 @@ namespace gbs {
 namespace {
 
 constexpr int kThreadsPml = 256;
-constexpr int kZB = 8;        // planes per block (a column's planes share their z neighbours in L1)
+constexpr int kZB = 16;        // planes per block (a column's planes share their z neighbours in L1)
 
 // Block tiling of the six boxes: box r has nbx x nby tiles of 2^ltx x
 // 2^(8-ltx) points per plane and nbz groups of kZB planes; its blocks are
@@ -124,11 +124,11 @@ __device__ __forceinline__ float zeta_of(const PmlParams &p, int d)
 }
 
 // Block b: box r, tile (bxi, byi), planes [kZB bzi, kZB bzi + kZB) of the box.
-// Four blocks per SM (64 registers): the loads of a point are independent,
+// Five blocks per SM (48 registers): the loads of a point are independent,
 // and warps in flight beat registers per thread here (two blocks per SM at
 // 106 registers ran at half the rate).  The divisors of the phi update are
 // reciprocals taken once per column (x, y) or plane (z).
-__global__ void __launch_bounds__(kThreadsPml, 4) k_pml(const float *__restrict__ u_prev, const float *__restrict__ u,
+__global__ void __launch_bounds__(kThreadsPml, 5) k_pml(const float *__restrict__ u_prev, const float *__restrict__ u,
                                                     float *__restrict__ u_next, const float *__restrict__ vel,
                                                     const __grid_constant__ PmlParams p)
 {
