@@ -93,7 +93,8 @@ typedef struct {
 
 /* Tuning choices; a zero field means "library default". */
 typedef struct {
-    int kernel;     /* 0 auto, 1 TMA-staged (fails with GBS_EALIGN if not possible), 2 plain-load */
+    int kernel;     /* 0 auto, 1 TMA-staged (fails with GBS_EALIGN if not possible), 2 plain-load;
+                     * gbs_wave_propagate_tb only: 4 = pairs on overlapped tiles (below) */
     int tile_y;     /* rows per CTA tile of the TMA kernel: 16 or 32 (x is always 64) */
     int zchunk;     /* planes streamed per CTA (>= 1) */
     int use_graph;  /* wave_propagate: 1 = capture the step loop in a CUDA graph and replay it */
@@ -213,8 +214,19 @@ gbs_status gbs_wave_propagate_lp(float *u_prev, float *u, const float *vel, floa
  * workspace fields; after an odd number of pairs the two newest fields are
  * copied back (two device-to-device copies).  A remaining odd step (all
  * steps, when pairs cannot run fused) runs as gbs_wave_propagate.
+ * opts->kernel = 4 runs every pair on overlapped tiles instead: a tile's
+ * first step also recomputes the 4-cell frame of its neighbours that its
+ * second step reads, so no tile waits for another, the launch is an ordinary
+ * one and any number of tiles runs (grids beyond gbs_tb_supported too).  The
+ * fields are bit-identical to the cooperative pairs.  It computes 2.5 stencil
+ * points per two updates instead of 2 and measures slower than both the
+ * cooperative pairs and single steps on every grid tried (512^3: 350 against
+ * 487 and 398 Gpoint-updates/s; 1024^3: 398 against 411 for single steps),
+ * so it is never chosen by default.  It needs the TMA layout (halo % 4 == 0,
+ * nx % 4 == 0, 16-byte aligned fields), at most 16 sources and no absorbing
+ * layer (else GBS_EUNSUPPORTED).
  * Errors: GBS_EINVAL (as gbs_wave_propagate, a small, misaligned or
- * overlapping workspace), GBS_EALIGN, GBS_ECUDA.
+ * overlapping workspace), GBS_EALIGN, GBS_EUNSUPPORTED, GBS_ECUDA.
  */
 size_t gbs_tb_workspace_bytes(int64_t nx, int64_t ny, int64_t nz, int halo);
 gbs_status gbs_wave_propagate_tb(float *u_prev, float *u, const float *vel, float dt, float h,

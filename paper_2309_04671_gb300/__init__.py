@@ -517,7 +517,9 @@ def wave_propagate_tb(u_prev: torch.Tensor, u: torch.Tensor, vel: torch.Tensor, 
     of steps fused into one launch.
 
     Returns (prev, cur) as wave_propagate.  ``work`` is device scratch of at
-    least tb_workspace_bytes(...) bytes (allocated per call if None).  With
+    least tb_workspace_bytes(...) bytes (allocated per call if None).
+    ``kernel=4`` runs the pairs on overlapped tiles (no tile waits for
+    another; any number of tiles; bit-identical, measured slower).  With
     CPU tensors (ideally pinned) the call copies the inputs to the device,
     runs, copies both fields (and the trace) back, and returns CPU tensors.
     """

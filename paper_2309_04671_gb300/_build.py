@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgbstencil.so")
 
-SOURCES = ["gbs_api.cu", "k_tma.cu", "k_generic.cu", "k_misc.cu", "k_lp.cu", "k_norms.cu", "gbs_batch.cu", "gbs_adjoint.cu", "k_adjoint.cu", "gbs_suite.cu", "k_suite.cu", "k_wf.cu", "k_pml.cu", "k_adjimg.cu"]
+SOURCES = ["gbs_api.cu", "k_tma.cu", "k_generic.cu", "k_misc.cu", "k_lp.cu", "k_norms.cu", "gbs_batch.cu", "gbs_adjoint.cu", "k_adjoint.cu", "gbs_suite.cu", "k_suite.cu", "k_wf.cu", "k_pml.cu", "k_adjimg.cu", "k_ov.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
               "-Xptxas", "-v"]

@@ -12,6 +12,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "gbs_internal.cuh"
+#include "gbs_ov.cuh"
 #include "gbs_wf.cuh"
 
 namespace gbs {
@@ -648,6 +649,105 @@ TbLayout tb_layout(const Grid &g, int steps)
 
 bool tb_steps_ok(int time_block) { return time_block == 2 || time_block == 3; }
 
+// Pairs of steps on overlapped tiles (k_ov.cu): ordinary launches, any
+// number of tiles.  Same buffers and slot rotation as the cooperative pairs
+// (the workspace's counter words are unused); an odd last step runs alone.
+gbs_status propagate_ov(float *u_prev, float *u, const float *vel, float dt, float h, const Grid &g, int64_t nsteps,
+                        int64_t t0, const gbs_src *src, const gbs_rec *rec, void *work, const gbs_opts *opts,
+                        cudaStream_t st)
+{
+    if (!tma_shape_ok(g) || !aligned16(u_prev) || !aligned16(u) || !aligned16(vel) ||
+        (src && src->n > kMaxFusedSrc) || (opts && opts->absorb_width != 0))
+        return fail(GBS_EUNSUPPORTED, "overlapped-tile pairs need the TMA layout, at most %d sources and no "
+                                      "absorbing layer", kMaxFusedSrc);
+    OvShape sh{};
+    if (!ov_shape(g, &sh))
+        return fail(GBS_ECUDA, "overlapped-tile kernel attributes");
+    const TbLayout L = tb_layout(g, 2);
+    const int64_t nl = nsteps / 2;
+    if (nl > 0) {
+        const int nslots = 4;
+        float *slot[4] = {u_prev, u, reinterpret_cast<float *>(static_cast<char *>(work) + L.off_w1),
+                          reinterpret_cast<float *>(static_cast<char *>(work) + L.off_w1 + L.field_stride)};
+        OvMaps maps[4];
+        gbs_status s = GBS_OK;
+        for (int a = 0; a < nslots; ++a) {
+            float *pr = slot[a], *cu = slot[(a + 1) % nslots];
+            OvMaps &m = maps[a];
+            if ((s = make_map(&m.ua, cu, g, kOvBoxA, kOvBoxAH)) != GBS_OK ||
+                (s = make_map(&m.pa, pr, g, kOvFrameW, kOvFrameH)) != GBS_OK ||
+                (s = make_map(&m.va, vel, g, kOvFrameW, kOvFrameH)) != GBS_OK ||
+                (s = make_map(&m.pb, cu, g, 64, kOvTileY)) != GBS_OK ||
+                (s = make_map(&m.vb, vel, g, 64, kOvTileY)) != GBS_OK)
+                return s;
+        }
+        OvParams p;
+        memset(&p, 0, sizeof(p));
+        p.g = g;
+        p.cf = wave_coeffs();
+        p.s = (float)((double)dt / (double)h);
+        p.dt = dt;
+        if (src && src->n > 0) {
+            p.src_idx = src->idx;
+            p.src_amp = src->amp;
+            p.src_nt = src->nt;
+            p.nsrc = (int)src->n;
+        }
+        p.inx = g.nx;
+        p.iny = g.ny;
+        p.tiles_x = sh.tiles_x;
+        p.tiles_y = sh.tiles_y;
+        p.zchunk = sh.zchunk;
+        p.nchunks = sh.nchunks;
+        auto enqueue = [&]() -> gbs_status {
+            cudaError_t r = launch_zero_shell(slot[2], (int64_t)(L.field_stride / 4), 2, g, st);
+            if (r != cudaSuccess)
+                return cuda_fail(r, "workspace halo");
+            for (int64_t i = 0; i < nl; ++i) {
+                const int a = (int)((i * 2) % nslots);
+                OvParams pi = p;
+                pi.out[0] = slot[(a + 2) % nslots];
+                pi.out[1] = slot[(a + 3) % nslots];
+                pi.t = t0 + 2 * i;
+                cudaEvent_t e0 = prof_begin(st);
+                r = launch_ov(sh, maps[a], pi, st);
+                prof_end(e0, st);
+                if (r != cudaSuccess)
+                    return cuda_fail(r, "overlapped-tile launch");
+                for (int k = 0; k < 2; ++k)
+                    if ((r = launch_record(g, pi.out[k], rec, pi.t + k, st)) != cudaSuccess)
+                        return cuda_fail(r, "receiver launch");
+            }
+            const int a = (int)((nl * 2) % nslots);
+            if (a != 0) {
+                const size_t fbytes = (size_t)field_elems(g) * 4;
+                const int older = a, newer = (a + 1) % nslots;
+                if (newer == 0) {
+                    if ((r = cudaMemcpyAsync(u, slot[newer], fbytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+                        (r = cudaMemcpyAsync(u_prev, slot[older], fbytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+                        return cuda_fail(r, "copy of the newest fields");
+                } else {
+                    if ((r = cudaMemcpyAsync(u_prev, slot[older], fbytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+                        (r = cudaMemcpyAsync(u, slot[newer], fbytes, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+                        return cuda_fail(r, "copy of the newest fields");
+                }
+            }
+            return GBS_OK;
+        };
+        const bool graph = opts && opts->use_graph && st != nullptr;
+        if ((s = graph ? run_captured(st, enqueue) : enqueue()) != GBS_OK)
+            return s;
+    }
+    const int64_t rest = nsteps - 2 * nl;
+    if (rest == 0)
+        return GBS_OK;
+    gbs_opts o1 = {};
+    if (opts)
+        o1 = *opts;
+    o1.kernel = 0;
+    return gbs_wave_propagate(u_prev, u, vel, dt, h, g.nx, g.ny, g.nz, g.halo, rest, t0 + 2 * nl, src, rec, &o1, st);
+}
+
 // gbs_wave_propagate_tbn after argument checks: `steps` steps per launch
 // while at least `steps` remain, then a pair (three-step launches) or a
 // single step for the rest.
@@ -655,6 +755,8 @@ gbs_status propagate_tb(int steps, float *u_prev, float *u, const float *vel, fl
                         int64_t nsteps, int64_t t0, const gbs_src *src, const gbs_rec *rec, void *work,
                         const gbs_opts *opts, cudaStream_t st)
 {
+    if (steps == 2 && opts && opts->kernel == 4)
+        return propagate_ov(u_prev, u, vel, dt, h, g, nsteps, t0, src, rec, work, opts, st);
     const TbLayout L = tb_layout(g, steps);
     WfShape sh{};
     const bool fused = tma_shape_ok(g) && aligned16(u_prev) && aligned16(u) && aligned16(vel) &&
@@ -1702,7 +1804,8 @@ extern "C" gbs_status gbs_device_status(void *stream)
     const unsigned c = suite_status_take(st);
     const unsigned d = wf_status_take(st);
     const unsigned e = adjimg_status_take(st);
-    const unsigned v = a ? a : (b ? b : (c ? c : (d ? d : e)));
+    const unsigned f = ov_status_take(st);
+    const unsigned v = a ? a : (b ? b : (c ? c : (d ? d : (e ? e : f))));
     if (v != 0)
         return fail((gbs_status)v, "device status %u", v);
     return GBS_OK;

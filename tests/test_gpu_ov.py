@@ -1,0 +1,122 @@
+"""GPU parity of fused pairs of leapfrog steps on overlapped tiles
+(`gbs_wave_propagate_tb` with opts->kernel = 4): Algorithm 1, two steps per
+launch (the paper's temporal blocking, Sec. 3), where each tile's first stage
+also recomputes the 4-cell frame its second stage reads, so that no tile waits
+for another and any number of tiles runs.
+
+Covers: agreement with the FP64 oracle within the multi-step bound; bit
+identity with the cooperative pair kernel wherever that one runs (both stages
+use the same arithmetic in the same order, the recomputed frame included);
+ragged x/y/z extents (a frame that leaves the interior is the zero halo); an
+odd step count (the last step alone); grids with more tiles than SMs and with
+many z-chunks; sixteen sources on tile seams and chunk seams, with receivers;
+run-to-run bit identity.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2309_04671_gb300 as gbs
+import workloads as W
+from gpu_util import dev, halo_mask, need_gpu, to_dev, tol_steps, torch
+
+pytestmark = pytest.mark.gpu
+
+OVERLAPPED = 4   # opts->kernel: pairs on overlapped tiles
+
+
+def _case(shape, nsteps, seed, src=None, nsrc=3):
+    nx, ny, nz = shape
+    halo, h = 4, 10.0
+    up = W.uniform_field(nx, ny, nz, halo, seed, halo_random=False)
+    u = W.uniform_field(nx, ny, nz, halo, seed + 1, halo_random=False)
+    vel = W.layered_velocity(nx, ny, nz, halo, seed + 2)
+    dt = W.dt_for_cfl(0.4, h, float(W.interior(vel, halo).max()))
+    rng = np.random.default_rng(seed)
+    npts = nx * ny * nz
+    if src is None:
+        src = rng.integers(0, npts, nsrc).astype(np.int64)
+    amp = rng.standard_normal((nsteps, src.size)).astype(np.float32)
+    rec = rng.integers(0, npts, 40).astype(np.int64)
+    return up, u, vel, dt, h, halo, src, amp, rec
+
+
+def _run(case, nsteps, kernel):
+    up, u, vel, dt, h, halo, src, amp, rec = case
+    trace = torch.zeros((nsteps, rec.size), device=dev())
+    p, c = gbs.wave_propagate_tb(to_dev(up), to_dev(u), to_dev(vel), dt, h, halo, nsteps, src_idx=to_dev(src),
+                                 src_amp=to_dev(amp), rec_idx=to_dev(rec), rec_trace=trace, kernel=kernel)
+    gbs.device_status()
+    return p.cpu().numpy(), c.cpu().numpy(), trace.cpu().numpy()
+
+
+def _check_oracle(case, nsteps, got):
+    up, u, vel, dt, h, halo, src, amp, rec = case
+    rp, ru, rtr = oracle.wave_propagate(up, u, vel, dt, h, halo, nsteps, src_idx=src, src_amp=amp, rec_idx=rec)
+    tol = tol_steps(nsteps)
+    for g, ref in zip(got, (rp, ru, rtr)):
+        e = oracle.err_norms(g, ref)
+        assert e["finite"] and e["norm_max_rel"] <= tol, e
+    assert np.all(got[1][halo_mask(got[1].shape, halo)] == 0)
+    assert np.all(got[0][halo_mask(got[0].shape, halo)] == 0)
+
+
+# (shape, steps): whole tiles; ragged y and z with an odd step count; a
+# single ragged tile row; ragged y over several rows
+@pytest.mark.parametrize("shape,nsteps", [((64, 48, 40), 8), ((128, 56, 37), 9), ((132, 20, 9), 6),
+                                          ((68, 45, 37), 10)])
+def test_overlapped_pairs_vs_oracle_and_cooperative_pairs(shape, nsteps):
+    need_gpu()
+    case = _case(shape, nsteps, 300 + nsteps)
+    got = _run(case, nsteps, OVERLAPPED)
+    _check_oracle(case, nsteps, got)
+    ok, _, _ = gbs.tb_supported(*shape, 4)
+    assert ok
+    coop = _run(case, nsteps, 0)
+    for a, b in zip(got, coop):
+        assert np.array_equal(a, b)
+
+
+def _seam_sources(nx, ny, nz, n=16, seed=5, zseam=None):
+    """Sources on the seams of 64 x 24 tiles (x 63/64, y 23/24) and, given
+    zseam, on the planes either side of a z-chunk seam; pairs share a cell."""
+    rng = np.random.default_rng(seed)
+    pts = []
+    for k in range(n // 2):
+        i = 64 * int(rng.integers(1, max(2, nx // 64))) - int(rng.integers(0, 2))
+        j = 24 * int(rng.integers(1, max(2, ny // 24))) - int(rng.integers(0, 2))
+        z = int(rng.integers(0, nz)) if zseam is None else zseam - int(rng.integers(0, 2))
+        lin = min(i, nx - 1) + nx * (min(j, ny - 1) + ny * z)
+        pts += [lin, lin]
+    return np.array(pts, dtype=np.int64)
+
+
+def test_more_tiles_than_sms_with_seam_sources_and_repeat():
+    """640 x 600 x 16 has 250 tiles of 64 x 24 (two waves of CTAs; the
+    cooperative kernel cannot hold it); 16 sources on tile seams, in pairs
+    sharing a cell."""
+    need_gpu()
+    shape, nsteps = (640, 600, 16), 6
+    ok, _, _ = gbs.tb_supported(*shape, 4)
+    assert not ok
+    case = _case(shape, nsteps, 410, src=_seam_sources(*shape))
+    got = _run(case, nsteps, OVERLAPPED)
+    _check_oracle(case, nsteps, got)
+    again = _run(case, nsteps, OVERLAPPED)
+    for a, b in zip(got, again):
+        assert np.array_equal(a, b)
+
+
+def test_many_z_chunks_with_sources_on_chunk_seams():
+    """A tall grid splits into z-chunks (600 planes: 8 chunks of 75 on two
+    tiles); stage A of each chunk recomputes the 4 planes either side, which
+    must equal what the neighbouring chunk computes, sources on the planes
+    74 and 75 (either side of the first seam) included."""
+    need_gpu()
+    shape, nsteps = (64, 48, 600), 7
+    case = _case(shape, nsteps, 520, src=_seam_sources(*shape, zseam=75))
+    got = _run(case, nsteps, OVERLAPPED)
+    _check_oracle(case, nsteps, got)
+    coop = _run(case, nsteps, 0)
+    for a, b in zip(got, coop):
+        assert np.array_equal(a, b)
