@@ -13,11 +13,12 @@
 // order), so it equals the neighbour's own stored values bit for bit.
 // Points of the frame outside the interior are the Dirichlet halo: zero.
 //
-// Against the cooperative pair kernel (k_wf.cu) this costs 33 % more
-// stage-A points, and buys independence: any number of tiles (an ordinary
-// launch, several waves), no block counters, and stage B right behind stage
-// A (its u^{t+1} never leaves the SM; its u^t and vel re-reads come from L2
-// a few planes after stage A read them).  DRAM moves 20 B per two updates.
+// Against the cooperative pair kernel (k_wf.cu) this costs 50 % more
+// stage-A points (2.5 stencil points per two updates instead of 2), and buys
+// independence: any number of tiles (an ordinary launch, several waves), no
+// block counters, and stage B right behind stage A (its u^{t+1} never leaves
+// the SM; its u^t and vel re-reads come from L2 a few planes after stage A
+// read them).  DRAM moves 20 B per two updates.
 //
 // Both stages sweep z in the semi-stencil order (Sec. 9.3 `semi`): each
 // plane is used once, when it lands.  Warps: 9 for stage A, 6 for stage B,
