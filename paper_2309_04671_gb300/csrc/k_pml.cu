@@ -23,22 +23,24 @@
 // Storage: phi (3 components) and psi live only on the slabs, in a compact
 // layout of six boxes (z-low, z-high, y-low, y-high, x-low, x-high; each x
 // fastest), twice (the step reads one copy and writes the other).  A
-// block covers a TX x TY tile of one box over kZB consecutive planes (TX x
-// TY = 256, TX chosen per box so that the tiles waste the fewest lanes); a
-// thread updates one (x, y) column of the tile plane by plane.  Inside a box
-// the neighbours of the auxiliary fields are at fixed compact offsets
-// (1, bx, bx by); only threads on a box face take the general index.
+// block covers a tile of one box over kZB consecutive planes: 2^e x 2^(8-e)
+// threads, each updating two x-adjacent points (e chosen per box so that
+// the tiles waste the fewest lanes), column by column, plane by plane.
+// Inside a box the neighbours of the auxiliary fields are at fixed compact
+// offsets (1, bx, bx by); only warps with a lane on a y or z face of a box
+// take the general index (an x face always borders the halo or the inner
+// box).
 #include "gbs_internal.cuh"
 
 namespace gbs {
 namespace {
 
 constexpr int kThreadsPml = 256;
-constexpr int kZB = 16;        // planes per block (a column's planes share their z neighbours in L1)
+constexpr int kZB = 8;        // planes per block (a column's planes share their z neighbours in L1)
 
-// Block tiling of the six boxes: box r has nbx x nby tiles of 2^ltx x
-// 2^(8-ltx) points per plane and nbz groups of kZB planes; its blocks are
-// [bstart[r], bstart[r+1]).
+// Block tiling of the six boxes: box r has nbx x nby tiles of 2^(ltx+1) x
+// 2^(8-ltx) points per plane (2^ltx x 2^(8-ltx) threads of two points) and
+// nbz groups of kZB planes; its blocks are [bstart[r], bstart[r+1]).
 struct BoxTiles {
     int ltx[6];
     int nbx[6], nby[6];
@@ -123,12 +125,40 @@ __device__ __forceinline__ float zeta_of(const PmlParams &p, int d)
     return d < w1 ? p.zmax * r * r : 0.f;
 }
 
+__device__ __forceinline__ float2 ld2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+
+// The update of one point from its loaded values (the same arithmetic as a
+// point on its own): writes u_next, psi and phi.
+__device__ __forceinline__ void pml_point(const PmlParams &p, float *__restrict__ u_next, int64_t at, int c, float uc,
+                                          float lap, const float *du, float div_h2, float psi, float vs, float upv,
+                                          float zx, float zy, float zz, float rx, float ry, float rz, const float *ph,
+                                          const int *cm, const int *cp)
+{
+    const float dt = p.dt, inv2h = 0.5f / p.h;
+    const float S1 = zx + zy + zz;
+    const float S2 = zx * zy + zy * zz + zz * zx;
+    const float S3 = zx * zy * zz;
+    const float A = 1.f / (1.f + 0.5f * dt * S1), B = 1.f - 0.5f * dt * S1;
+    const float un = A * (2.f * uc - B * upv + vs * vs * (lap + div_h2) - dt * dt * (S2 * uc + S3 * psi));
+    u_next[at] = un;
+    p.psi_out[c] = psi + dt * un;
+    const float zeta[3] = {zx, zy, zz};
+    const float rq[3] = {rx, ry, rz};
+    const float aj[3] = {zy + zz - zx, zz + zx - zy, zx + zy - zz};
+    const float bj[3] = {zy * zz, zz * zx, zx * zy};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float dpsi = bj[a] != 0.f ? (masked(p.psi_in, cp[a]) - masked(p.psi_in, cm[a])) * inv2h : 0.f;
+        p.phi_out[a][c] = ((1.f - 0.5f * dt * zeta[a]) * ph[a] + dt * (aj[a] * du[a] * inv2h + bj[a] * dpsi)) * rq[a];
+    }
+}
+
 // Block b: box r, tile (bxi, byi), planes [kZB bzi, kZB bzi + kZB) of the box.
-// Five blocks per SM (48 registers): the loads of a point are independent,
-// and warps in flight beat registers per thread here (two blocks per SM at
-// 106 registers ran at half the rate).  The divisors of the phi update are
-// reciprocals taken once per column (x, y) or plane (z).
-__global__ void __launch_bounds__(kThreadsPml, 5) k_pml(const float *__restrict__ u_prev, const float *__restrict__ u,
+// A thread updates two x-adjacent points (li even: box widths, origins and
+// compact bases are even), so its loads of u, u_prev, vel and its own
+// auxiliary values are 8-byte pairs: 21 loads of u for two points where
+// one point needs 25.  Four blocks per SM (64 registers).
+__global__ void __launch_bounds__(kThreadsPml, 4) k_pml(const float *__restrict__ u_prev, const float *__restrict__ u,
                                                     float *__restrict__ u_next, const float *__restrict__ vel,
                                                     const __grid_constant__ PmlParams p)
 {
@@ -147,7 +177,7 @@ __global__ void __launch_bounds__(kThreadsPml, 5) k_pml(const float *__restrict_
     q /= bt.nbx[r];
     const int byi = q % bt.nby[r];
     const int bzi = q / bt.nby[r];
-    const int li = (bxi << ltx) + (int)(threadIdx.x & ((1u << ltx) - 1u));
+    const int li = 2 * ((bxi << ltx) + (int)(threadIdx.x & ((1u << ltx) - 1u)));
     const int lj = (byi << (8 - ltx)) + (int)(threadIdx.x >> ltx);
     if (li >= bx || lj >= by)
         return;
@@ -159,12 +189,15 @@ __global__ void __launch_bounds__(kThreadsPml, 5) k_pml(const float *__restrict_
     const float *__restrict__ phx = p.phi_in[0];
     const float *__restrict__ phy = p.phi_in[1];
     const float *__restrict__ phz = p.phi_in[2];
-    const float *__restrict__ psin = p.psi_in;
-    const int dx = min(i, s.nx - 1 - i), dy = min(j, s.ny - 1 - j);
-    const float zx = zeta_of(p, dx), zy = zeta_of(p, dy);
-    const float dt = p.dt, inv2h = 0.5f / p.h;
-    const float rx = 1.f / (1.f + 0.5f * dt * zx), ry = 1.f / (1.f + 0.5f * dt * zy);
-    const bool xm_in = li > 0, xp_in = li < bx - 1, ym_in = lj > 0, yp_in = lj < by - 1;
+    const int dx0 = min(i, s.nx - 1 - i), dx1 = min(i + 1, s.nx - 2 - i), dy = min(j, s.ny - 1 - j);
+    const float zx0 = zeta_of(p, dx0), zx1 = zeta_of(p, dx1), zy = zeta_of(p, dy);
+    const float dt = p.dt;
+    const float rx0 = 1.f / (1.f + 0.5f * dt * zx0), rx1 = 1.f / (1.f + 0.5f * dt * zx1);
+    const float ry = 1.f / (1.f + 0.5f * dt * zy);
+    // An x face of any box borders the halo or the inner box (no slab shares
+    // an x face), so its neighbour has no auxiliary value.
+    const bool xm_in = li > 0, xp_in = li + 1 < bx - 1, ym_in = lj > 0, yp_in = lj < by - 1;
+    const float c0 = p.c[0] + p.c[0] + p.c[0];
     const int lk0 = bzi * kZB;
     int c = s.base[r] + li + bx * (lj + by * lk0);
     int64_t at = (g.halo + i) + g.px * ((g.halo + j) + g.py * (int64_t)(g.halo + z0 + lk0));
@@ -172,66 +205,67 @@ __global__ void __launch_bounds__(kThreadsPml, 5) k_pml(const float *__restrict_
     for (int lk = lk0; lk < min(bz, lk0 + kZB); ++lk, c += sxy, at += sz) {
         const int k = z0 + lk;
         const float *__restrict__ up = u + at;
-        // neighbours of the auxiliary fields (central differences): fixed
-        // offsets inside the box; warps with a lane on a box face fix theirs
-        // up with the general index (a warp-uniform branch)
-        // An x face of any box borders the halo or the inner box (no slab
-        // shares an x face), so its neighbour has no auxiliary value.
-        const int cxm = xm_in ? c - 1 : -1, cxp = xp_in ? c + 1 : -1;
-        int cym = c - bx, cyp = c + bx, czm = c - sxy, czp = c + sxy;
-        const bool zm_in = lk > 0, zp_in = lk < bz - 1;
-        const bool face = !(ym_in && yp_in && zm_in && zp_in);
-        if (__any_sync(__activemask(), face)) {
-            if (!ym_in) cym = nb_index(s, i, j - 1, k);
-            if (!yp_in) cyp = nb_index(s, i, j + 1, k);
-            if (!zm_in) czm = nb_index(s, i, j, k - 1);
-            if (!zp_in) czp = nb_index(s, i, j, k + 1);
+        // u at x - 4 .. x + 5 of the row: the two points are w[4], w[5]
+        float w[10];
+#pragma unroll
+        for (int e = 0; e < 5; ++e) {
+            const float2 v = ld2(up - 4 + 2 * e);
+            w[2 * e] = v.x;
+            w[2 * e + 1] = v.y;
         }
-        const float div_h2 = 0.5f * p.h *
-                             ((masked(phx, cxp) - masked(phx, cxm)) + (masked(phy, cyp) - masked(phy, cym)) +
-                              (masked(phz, czp) - masked(phz, czm)));
-        const float uc = __ldg(up);
-        // the 25-point operator with unit-spacing weights: centre, then
-        // distance 1..4 (x, y, z pairs)
-        float lap = (p.c[0] + p.c[0] + p.c[0]) * uc;
-        float du[3] = {0.f, 0.f, 0.f};
+        float lap0 = c0 * w[4], lap1 = c0 * w[5];
+        float du0[3] = {0.f, 0.f, 0.f}, du1[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int m = 1; m <= 4; ++m) {
-            const float xm = __ldg(up - m), xp = __ldg(up + m);
-            const float ym = __ldg(up - m * sy), yp = __ldg(up + m * sy);
-            const float zm = __ldg(up - m * sz), zp = __ldg(up + m * sz);
+            const float2 ym = ld2(up - m * sy), yp = ld2(up + m * sy);
+            const float2 zm = ld2(up - m * sz), zp = ld2(up + m * sz);
             if (m == 1) {
-                du[0] = xp - xm;
-                du[1] = yp - ym;
-                du[2] = zp - zm;
+                du0[0] = w[5] - w[3];
+                du0[1] = yp.x - ym.x;
+                du0[2] = zp.x - zm.x;
+                du1[0] = w[6] - w[4];
+                du1[1] = yp.y - ym.y;
+                du1[2] = zp.y - zm.y;
             }
-            lap += p.c[m] * ((xp + xm) + (yp + ym) + (zp + zm));
+            lap0 += p.c[m] * ((w[4 + m] + w[4 - m]) + (yp.x + ym.x) + (zp.x + zm.x));
+            lap1 += p.c[m] * ((w[5 + m] + w[5 - m]) + (yp.y + ym.y) + (zp.y + zm.y));
+        }
+        // neighbours of the auxiliary fields: fixed offsets inside the box;
+        // warps with a lane on a y or z face of the box fix theirs up with the
+        // general index (a warp-uniform branch)
+        const bool zm_in = lk > 0, zp_in = lk < bz - 1;
+        const bool face = !(ym_in && yp_in && zm_in && zp_in);
+        int cm0[3] = {xm_in ? c - 1 : -1, c - bx, c - sxy}, cp0[3] = {c + 1, c + bx, c + sxy};
+        int cm1[3] = {c, c + 1 - bx, c + 1 - sxy}, cp1[3] = {xp_in ? c + 2 : -1, c + 1 + bx, c + 1 + sxy};
+        float div0, div1;
+        const float hh = 0.5f * p.h;
+        const float2 fx = ld2(phx + c), fy = ld2(phy + c), fz = ld2(phz + c);
+        if (__any_sync(__activemask(), face)) {
+            if (!ym_in) { cm0[1] = nb_index(s, i, j - 1, k); cm1[1] = nb_index(s, i + 1, j - 1, k); }
+            if (!yp_in) { cp0[1] = nb_index(s, i, j + 1, k); cp1[1] = nb_index(s, i + 1, j + 1, k); }
+            if (!zm_in) { cm0[2] = nb_index(s, i, j, k - 1); cm1[2] = nb_index(s, i + 1, j, k - 1); }
+            if (!zp_in) { cp0[2] = nb_index(s, i, j, k + 1); cp1[2] = nb_index(s, i + 1, j, k + 1); }
+            div0 = hh * ((fx.y - masked(phx, cm0[0])) + (masked(phy, cp0[1]) - masked(phy, cm0[1])) +
+                         (masked(phz, cp0[2]) - masked(phz, cm0[2])));
+            div1 = hh * ((masked(phx, cp1[0]) - fx.x) + (masked(phy, cp1[1]) - masked(phy, cm1[1])) +
+                         (masked(phz, cp1[2]) - masked(phz, cm1[2])));
+        } else {
+            const float2 ym = ld2(phy + c - bx), yp = ld2(phy + c + bx);
+            const float2 zm = ld2(phz + c - sxy), zp = ld2(phz + c + sxy);
+            div0 = hh * ((fx.y - masked(phx, cm0[0])) + (yp.x - ym.x) + (zp.x - zm.x));
+            div1 = hh * ((masked(phx, cp1[0]) - fx.x) + (yp.y - ym.y) + (zp.y - zm.y));
         }
         const int dz = p.free_top ? s.nz - 1 - k : min(k, s.nz - 1 - k);
         const float zz = zeta_of(p, dz);
-        const float S1 = zx + zy + zz;
-        const float S2 = zx * zy + zy * zz + zz * zx;
-        const float S3 = zx * zy * zz;
-        const float psi = __ldg(psin + c);
-        const float vs = __ldg(vel + at) * p.sdt;
-        const float A = 1.f / (1.f + 0.5f * dt * S1), B = 1.f - 0.5f * dt * S1;
-        const float un =
-            A * (2.f * uc - B * __ldg(u_prev + at) + vs * vs * (lap + div_h2) - dt * dt * (S2 * uc + S3 * psi));
-        u_next[at] = un;
-        p.psi_out[c] = psi + dt * un;
-        // phi^{n+1/2}
-        const float zeta[3] = {zx, zy, zz};
-        const float rq[3] = {rx, ry, 1.f / (1.f + 0.5f * dt * zz)};
-        const float aj[3] = {zy + zz - zx, zz + zx - zy, zx + zy - zz};
-        const float bj[3] = {zy * zz, zz * zx, zx * zy};
-        const int cm[3] = {cxm, cym, czm}, cp[3] = {cxp, cyp, czp};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            // psi's central difference matters only where b_a != 0 (edges and corners of the layer)
-            const float dpsi = bj[a] != 0.f ? (masked(psin, cp[a]) - masked(psin, cm[a])) * inv2h : 0.f;
-            const float ph = __ldg(p.phi_in[a] + c);
-            p.phi_out[a][c] = ((1.f - 0.5f * dt * zeta[a]) * ph + dt * (aj[a] * du[a] * inv2h + bj[a] * dpsi)) * rq[a];
-        }
+        const float rz = 1.f / (1.f + 0.5f * dt * zz);
+        const float2 ps = ld2(p.psi_in + c);
+        const float2 vv = ld2(vel + at);
+        const float2 pv = ld2(u_prev + at);
+        const float ph0[3] = {fx.x, fy.x, fz.x}, ph1[3] = {fx.y, fy.y, fz.y};
+        pml_point(p, u_next, at, c, w[4], lap0, du0, div0, ps.x, vv.x * p.sdt, pv.x, zx0, zy, zz, rx0, ry, rz, ph0,
+                  cm0, cp0);
+        pml_point(p, u_next, at + 1, c + 1, w[5], lap1, du1, div1, ps.y, vv.y * p.sdt, pv.y, zx1, zy, zz, rx1, ry, rz,
+                  ph1, cm1, cp1);
     }
 }
 
@@ -282,16 +316,16 @@ cudaError_t launch_pml(const Grid &g, const float *u_prev, const float *u, float
     p.psi_in = state_in + 3 * n;
     p.psi_out = state_out + 3 * n;
     // tile shape per box: the fewest padded points, then the preferred width
-    // (32 x 8 keeps the y neighbours of a block close)
+    // (32 x 16 points keeps the y neighbours of a block close)
     BoxTiles &bt = p.bt;
     int64_t blocks = 0;
     for (int r = 0; r < 6; ++r) {
         const int bxr = r < 4 ? s.nx : w, byr = r < 2 ? s.ny : (r < 4 ? w : s.ny - 2 * w);
-        static const int pref[6] = {5, 6, 4, 7, 3, 8};
+        static const int pref[6] = {4, 5, 3, 6, 2, 7};
         int best = -1;
         int64_t best_area = 0;
         for (int e : pref) {
-            const int tx = 1 << e, ty = kThreadsPml / tx;
+            const int tx = 2 << e, ty = kThreadsPml >> e;   // two x points per thread
             const int64_t area = (int64_t)((bxr + tx - 1) / tx) * tx * ((byr + ty - 1) / ty) * ty;
             if (best < 0 || area < best_area) {
                 best = e;
@@ -299,7 +333,7 @@ cudaError_t launch_pml(const Grid &g, const float *u_prev, const float *u, float
             }
         }
         bt.ltx[r] = best;
-        bt.nbx[r] = (bxr + (1 << best) - 1) >> best;
+        bt.nbx[r] = (bxr + (2 << best) - 1) / (2 << best);
         bt.nby[r] = (byr + (kThreadsPml >> best) - 1) / (kThreadsPml >> best);
         bt.bstart[r] = (int)blocks;
         blocks += (int64_t)bt.nbx[r] * bt.nby[r] * ((zb[r] + kZB - 1) / kZB);
