@@ -23,6 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgbstencil.so")
 
 GBS_OK, GBS_EINVAL, GBS_EALIGN, GBS_ECUDA, GBS_ETIMEOUT, GBS_EUNSTABLE = 0, 1, 2, 3, 4, 5
+GBS_ENOMEM, GBS_ENAN, GBS_EUNSUPPORTED = 6, 7, 8
 STATUS_NAMES = {0: "GBS_OK", 1: "GBS_EINVAL", 2: "GBS_EALIGN", 3: "GBS_ECUDA", 4: "GBS_ETIMEOUT",
                 5: "GBS_EUNSTABLE", 6: "GBS_ENOMEM", 7: "GBS_ENAN", 8: "GBS_EUNSUPPORTED"}
 

@@ -256,6 +256,14 @@ def test_tb_workspace_and_validation(lib, no_device):
     assert call(*args(fake[0], fake[1], work, big, opts=absorb)) == gbs.GBS_EINVAL
     assert call(*args(fake[0], fake[1], work, big, nsteps=0)) == gbs.GBS_OK
     assert call(*args(fake[0], fake[1], work, big, nsteps=-1)) == gbs.GBS_EINVAL
+    # pairs on overlapped tiles (kernel 4): no absorbing layer, at most 16 sources;
+    # both are refused before any CUDA call
+    ov_absorb = ctypes.byref(gbs._Opts(4, 0, 0, 0, 4, 10.0, 0))
+    assert call(*args(fake[0], fake[1], work, big, opts=ov_absorb)) == gbs.GBS_EUNSUPPORTED
+    many = gbs._Src(17, ctypes.c_void_p(5 << 20), ctypes.c_void_p(6 << 20), 4)
+    ov = ctypes.byref(gbs._Opts(4, 0, 0, 0, 0, 0.0, 0))
+    assert call(fake[0], fake[1], fake[2], ctypes.c_float(1e-3), ctypes.c_float(10.0), 8, 8, 8, 4, 4, 0,
+                ctypes.byref(many), None, work, big, ov, None) == gbs.GBS_EUNSUPPORTED
 
 
 def test_host_entry_workspace_and_validation(lib, no_device):
