@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--adj-n", type=int, default=256, help="adjoint form: interior side")
     ap.add_argument("--adj-steps", type=int, default=1000, help="adjoint form: time steps")
     ap.add_argument("--adj-shots", type=int, default=8, help="adjoint form: shots")
+    ap.add_argument("--adj-no-fused", action="store_true",
+                    help="adjoint form: skip timing the one-launch backward step (for profiling runs)")
     ap.add_argument("--batch-shots", type=int, default=64, help="batched form: shots")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--ref-leapfrog", type=int, default=16, help="oracle leapfrog steps per reference step")
@@ -671,7 +673,7 @@ def adjoint_form(args, stream, hbm, n=256, nsteps=1000, nshots=8):
     grad = torch.zeros(vel.shape, dtype=torch.float64, device=dev)
     misfit = torch.zeros(1, dtype=torch.float64, device=dev)
 
-    def gradient(fused=True, tile_y=0):
+    def gradient(fused=False, tile_y=0):
         grad.zero_()
         misfit.zero_()
         for si, d in zip(srcs, d_obs):
@@ -684,7 +686,7 @@ def adjoint_form(args, stream, hbm, n=256, nsteps=1000, nshots=8):
             gbs.wave_propagate(torch.zeros_like(vel), torch.zeros_like(vel), vel, dt, h, halo, nsteps, src_idx=si,
                                src_amp=amp, rec_idx=rec, rec_trace=tr)
     fused_ms = {}
-    for ty in (0, 16, 28):
+    for ty in (() if args.adj_no_fused else (0, 16, 28)):
         gradient(fused=True, tile_y=ty)
         fused_ms[str(ty) if ty else "auto"], _, _ = time_calls(lambda: gradient(fused=True, tile_y=ty), 1, stream)
     gradient()
