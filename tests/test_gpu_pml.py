@@ -125,3 +125,36 @@ def test_bad_widths_and_sizes_are_rejected():
             gbs.wave_propagate_pml(z, z.clone(), z.clone() + 1500.0, 1e-3, h, H, 2, width, 10.0)
     assert gbs.pml_state_bytes(16, 44, 40, 8) == 0           # nx - 2W < 4
     assert gbs.pml_state_bytes(48, 44, 40, 8) > gbs.pml_state_bytes(48, 44, 40, 8, free_top=True) > 0
+
+
+def test_full_size_layer_zero_damping_and_restart():
+    """At the benchmark's size and layer (512^3, 20 cells, the launch shapes
+    the bench times): with zeta_max = 0 the PML path is Eq. 2 (the plain
+    loop, within the multi-step bound), and with damping a 2 + 3 step split
+    with the carried state equals one 5-step call bit for bit."""
+    need_gpu()
+    n, width, nsteps = 512, 20, 5
+    vel = W.layered_velocity(n, n, n, H, 700)
+    vmax = float(W.interior(vel, H).max())
+    dt = W.dt_for_cfl(0.4, h, vmax)
+    up = W.uniform_field(n, n, n, H, 701, halo_random=False)
+    u = W.uniform_field(n, n, n, H, 702, halo_random=False)
+    d_vel = to_dev(vel)
+    p0, c0 = gbs.wave_propagate_pml(to_dev(up), to_dev(u), d_vel, dt, h, H, nsteps, width, 0.0)
+    p1, c1 = gbs.wave_propagate(to_dev(up), to_dev(u), d_vel, dt, h, H, nsteps)
+    gbs.device_status()
+    for x, y in ((c0, c1), (p0, p1)):
+        e = oracle.err_norms(x.cpu().numpy(), y.cpu().numpy())
+        assert e["finite"] and e["norm_max_rel"] <= tol_steps(nsteps), e
+    del p0, c0, p1, c1
+    zmax = _zmax(vmax, width)
+    st_a = gbs.pml_state(d_vel, H, width)
+    pa, ca = gbs.wave_propagate_pml(to_dev(up), to_dev(u), d_vel, dt, h, H, nsteps, width, zmax, state=st_a,
+                                    state_init=True)
+    st_b = gbs.pml_state(d_vel, H, width)
+    pb, cb = gbs.wave_propagate_pml(to_dev(up), to_dev(u), d_vel, dt, h, H, 2, width, zmax, state=st_b,
+                                    state_init=True)
+    pb, cb = gbs.wave_propagate_pml(pb, cb, d_vel, dt, h, H, 3, width, zmax, t0=2, state=st_b, state_init=False)
+    gbs.device_status()
+    assert torch.equal(pa, pb) and torch.equal(ca, cb)
+    assert torch.isfinite(ca).all()
