@@ -138,3 +138,35 @@ def test_graph_replay_and_host_buffers_are_bit_identical():
         got = _run(case, nsteps, OVERLAPPED, **kw)
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), kw
+
+
+def test_full_size_1024_against_single_steps():
+    """1024^3 (688 tiles of 64 x 24, several waves; the cooperative pairs
+    cannot hold it, so the plain path takes single steps): overlapped pairs
+    against single steps over 5 steps (two pairs and a single step), within
+    the multi-step bound, with a source on a tile seam.  Fields are drawn on
+    the device from a seeded generator."""
+    need_gpu()
+    n, halo, h, nsteps = 1024, 4, 10.0, 5
+    ok, _, _ = gbs.tb_supported(n, n, n, halo)
+    assert not ok
+    gen = torch.Generator(device=dev()).manual_seed(880)
+    shape = (n + 2 * halo,) * 3
+    inner = (slice(halo, -halo),) * 3
+    up = torch.zeros(shape, device=dev())
+    u = torch.zeros(shape, device=dev())
+    up[inner] = torch.rand((n, n, n), generator=gen, device=dev()) * 2 - 1
+    u[inner] = torch.rand((n, n, n), generator=gen, device=dev()) * 2 - 1
+    z = torch.arange(n + 2 * halo, device=dev()).clamp(halo, n + halo - 1) - halo
+    vel = (1500.0 + (z // (n // 8)).float() * (3000.0 / 7)).view(-1, 1, 1).expand(shape).contiguous()
+    dt = W.dt_for_cfl(0.4, h, 4500.0)
+    src = torch.tensor([64 * 7 - 1 + n * (24 * 9 + n * 512)], dtype=torch.int64, device=dev())
+    amp = torch.ones((nsteps, 1), device=dev())
+    p1, c1 = gbs.wave_propagate(up.clone(), u.clone(), vel, dt, h, halo, nsteps, src_idx=src, src_amp=amp)
+    p4, c4 = gbs.wave_propagate_tb(up, u, vel, dt, h, halo, nsteps, src_idx=src, src_amp=amp, kernel=OVERLAPPED)
+    gbs.device_status()
+    # normwise max relative difference, in FP64 on the device (two 4.4 GB fields)
+    for got, ref in ((c4, c1), (p4, p1)):
+        assert bool(torch.isfinite(got).all())
+        diff = float((got.double() - ref.double()).abs().max() / ref.double().abs().max())
+        assert diff <= tol_steps(nsteps), diff
